@@ -1,0 +1,368 @@
+"""Benchmark: FP64 TRSM by selective diagonal-block inversion on one GB300.
+
+One step = the whole method on one batch of the FP64 k/n sweep workload:
+for each shape (n, k) in {(16384, 256), (8192, 8192), (2048, 131072)} at its
+block size n0, trsm_plan (invert the diagonal blocks) + trsm_solve (blocked
+solve), inputs resident in HBM.  value = sum(n^2 k) / step time (TFLOP/s).
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the CPU oracle
+(forward substitution, the plain definition of X = L^-1 B) on the host cores
+instead, on a bounded column sample of the same workload.  `--sweep` prints
+one extra line per (shape, n0) of the block-size sweep.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TRSM TFLOP/s (n²k) and roofline fraction at stated error; served solves/s, p50/p99"
+SHAPES = [(16384, 256), (8192, 8192), (2048, 131072)]
+# Block sizes chosen by the n0 sweep on GB300 (see the tuning table in the
+# package); the paper's a-priori rule for p = 1 is n0 ~ min(sqrt(n k), n).
+DEFAULT_N0 = {(16384, 256): 256, (8192, 8192): 512, (2048, 131072): 2048}
+SWEEP_N0 = [64, 128, 256, 512, 1024, None]  # None = n (full inversion)
+NOMINAL_SM_MHZ = 2070.0
+SMS = 152
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_inputs(shapes, seed=0):
+    from paper_1612_01855_gb300 import inputs
+    return [inputs.well_conditioned(n, k, seed=seed + i) for i, (n, k) in enumerate(shapes)]
+
+
+def to_dev(a, torch):
+    return torch.from_numpy(np.ascontiguousarray(a.T)).cuda().t()
+
+
+def cpu_oracle_rate(data, shapes, budget_s, max_cols=None):
+    """Times the CPU oracle (forward substitution) on a column sample of each
+    shape; returns (TFLOP/s counting n^2 k_sample, sample description, cores)."""
+    import oracle
+    flops, secs, desc = 0.0, 0.0, []
+    per_shape = budget_s / len(shapes)
+    cores = oracle.max_threads()
+    for (L, B), (n, k) in zip(data, shapes):
+        cols = max(cores, 1)
+        if max_cols:
+            cols = min(cols, max_cols)
+        t_used, c_used = 0.0, 0
+        while t_used < per_shape and c_used < k:
+            c = min(cols, k - c_used)
+            t0 = time.perf_counter()
+            oracle.forward_subst(L, B[:, c_used:c_used + c])
+            dt = time.perf_counter() - t0
+            t_used += dt
+            c_used += c
+            cols = min(cols * 2, k)
+        flops += float(n) * n * c_used
+        secs += t_used
+        desc.append(f"n={n}: {c_used} of {k} columns")
+    return flops / secs / 1e12, "; ".join(desc), cores
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the CPU oracle on the host cores, bounded samples."""
+    if rank != 0:
+        return
+    shapes = SHAPES
+    data = make_inputs(shapes)
+    # each step: a bounded column sample of every shape
+    import oracle
+    cores = oracle.max_threads()
+    cols = [max(cores, 1)] * len(shapes)
+    for _ in range(args.warmup):
+        for (L, B), c in zip(data, cols):
+            oracle.forward_subst(L, B[:, :c])
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        for (L, B), c in zip(data, cols):
+            oracle.forward_subst(L, B[:, :c])
+        times.append(time.perf_counter() - t0)
+    fl = sum(float(n) * n * c for (n, k), c in zip(shapes, cols))
+    t = sum(times) / len(times)
+    value = fl / t / 1e12
+    sample = "; ".join(f"n={n}: {c} of {k} columns" for (n, k), c in zip(shapes, cols))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded PCG64)",
+        "config": {"workload": "fp64 k/n sweep shapes (16384,256),(8192,8192),(2048,131072); "
+                               "CPU oracle forward substitution on a column sample per step"},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    import paper_1612_01855_gb300 as g
+    from paper_1612_01855_gb300 import build as pkg_build
+
+    torch.cuda.set_device(local)
+    if rank == 0 or not os.path.exists(pkg_build.LIB):
+        pkg_build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    g.load_library()
+    shapes = SHAPES
+    n0s = [DEFAULT_N0[s] for s in shapes]
+    data = make_inputs(shapes)
+    dev_in = [(to_dev(L, torch), to_dev(B, torch)) for L, B in data]
+    outs = [torch.empty((k, n), dtype=torch.float64, device="cuda").t() for n, k in shapes]
+    stream = torch.cuda.current_stream()
+
+    def step(timers=None):
+        for si, ((Ld, Bd), X, n0) in enumerate(zip(dev_in, outs, n0s)):
+            if timers is not None:
+                timers[si][0].record(stream)
+            p = g.trsm_plan(Ld, n0)
+            if timers is not None:
+                timers[si][1].record(stream)
+            g.trsm_solve(p, Bd, X=X)
+            if timers is not None:
+                timers[si][2].record(stream)
+            g.trsm_sync_status(p)
+            p.destroy()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    fp64_peak = g.fp64_peak(8192)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    g.launch_count(reset=True)
+    ev = [[[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in shapes]
+          for _ in range(args.steps)]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s in range(args.steps):
+        step(ev[s])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = g.launch_count()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    total_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    flops_step = sum(float(n) * n * k for n, k in shapes)
+    value = flops_step * world / (ms_per_step * 1e-3) / 1e12
+
+    per_shape = []
+    solve_ms_tot, solve_flops_tot = 0.0, 0.0
+    for si, ((n, k), n0) in enumerate(zip(shapes, n0s)):
+        plan_ms = statistics.median(ev[s][si][0].elapsed_time(ev[s][si][1]) for s in range(args.steps))
+        solve_ms = statistics.median(ev[s][si][1].elapsed_time(ev[s][si][2]) for s in range(args.steps))
+        solve_ms_tot += solve_ms
+        solve_flops_tot += float(n) * n * k
+        per_shape.append({"n": n, "k": k, "n0": n0, "plan_ms": round(plan_ms, 3),
+                          "solve_ms": round(solve_ms, 3),
+                          "tflops": round(float(n) * n * k / ((plan_ms + solve_ms) * 1e-3) / 1e12, 4)})
+    solve_achieved = solve_flops_tot / (solve_ms_tot * 1e-3) / 1e12
+
+    # parity check of this run's results on a few sampled columns (oracle)
+    err = None
+    if rank == 0 and not args.no_check:
+        import oracle
+        errs = []
+        for (L, B), X in zip(data, outs):
+            cols = np.array([0, B.shape[1] // 2, B.shape[1] - 1])
+            want = oracle.forward_subst_columns(L, B, cols)
+            got = X[:, torch.from_numpy(cols).cuda()].cpu().numpy()
+            errs.append(float(np.max(np.abs(got - want)) / np.max(np.abs(want))))
+        err = max(errs)
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    e2e = None
+    if not args.no_e2e:
+        pinned = []
+        for (L, B), (n, k) in zip(data, shapes):
+            Lh = torch.from_numpy(np.ascontiguousarray(L.T)).pin_memory()
+            Bh = torch.from_numpy(np.ascontiguousarray(B.T)).pin_memory()
+            Xh = torch.empty((k, n), dtype=torch.float64).pin_memory()
+            pinned.append((Lh, Bh, Xh))
+        sptr = stream.cuda_stream
+
+        def e2e_step():
+            for (Lh, Bh, Xh), (n, k), n0 in zip(pinned, shapes, n0s):
+                g.trsm_host_ptr(Lh.data_ptr(), n, n, n0, Bh.data_ptr(), k, n, Xh.data_ptr(), n, sptr)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(max(1, args.steps)):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / max(1, args.steps)
+        h2d = sum(8 * (n * n + n * k) for n, k in shapes)
+        d2h = sum(8 * n * k for n, k in shapes)
+        e2e = {"value": flops_step * world / e2e_s / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": e2e_s * 1e3}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, sample, cores = cpu_oracle_rate(data, shapes, args.cpu_budget)
+        cpu = {"value": rate, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+               "sample": sample + " (forward substitution, FP64, OpenMP over columns)"}
+
+    if args.sweep and rank == 0:
+        for (L, B), (n, k), (Ld, Bd), X in zip(data, shapes, dev_in, outs):
+            for n0 in SWEEP_N0:
+                n0v = n if n0 is None else n0
+                for _ in range(2):
+                    p = g.trsm_plan(Ld, n0v)
+                    g.trsm_solve(p, Bd, X=X)
+                    g.trsm_sync_status(p)
+                    p.destroy()
+                a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                a.record(stream)
+                p = g.trsm_plan(Ld, n0v)
+                b.record(stream)
+                g.trsm_solve(p, Bd, X=X)
+                c.record(stream)
+                g.trsm_sync_status(p)
+                p.destroy()
+                pm, sm_ = a.elapsed_time(b), b.elapsed_time(c)
+                print(json.dumps({"sweep": True, "n": n, "k": k, "n0": n0v, "plan_ms": pm,
+                                  "solve_ms": sm_, "tflops": n * n * k / ((pm + sm_) * 1e-3) / 1e12,
+                                  "solve_tflops": n * n * k / (sm_ * 1e-3) / 1e12}), flush=True)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded PCG64; diag U[2,3], tril U[-1,1]/n, B U[-1,1])",
+            "config": {"workload": "fp64 k/n sweep (n,k) = (16384,256),(8192,8192),(2048,131072); "
+                                   "step = trsm_plan + trsm_solve per shape",
+                       "n0": {f"{n}x{k}": n0 for (n, k), n0 in zip(shapes, n0s)},
+                       "flops_per_step": flops_step, "l2": "inputs larger than L2 (no flush)",
+                       "parallelism": f"replicas{world}" if world > 1 else "single GPU",
+                       "shapes": per_shape},
+            "roofline": {"bound": "alu", "kernel": "it_inv_solve_kernel",
+                         "achieved": solve_achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                         "frac": solve_achieved / fp64_peak,
+                         "peak_source": "measured DFMA throughput (trsm_fp64_peak) in this run; "
+                                        f"nominal {SMS} SMs x 2 DFMA/clk x 2 flop x {NOMINAL_SM_MHZ:.0f} MHz"
+                                        f" = {SMS * 4 * NOMINAL_SM_MHZ / 1e6:.3f}",
+                         "traffic": None},
+            "parity_max_rel_err": err,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--sweep", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if args.impl == "ours":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

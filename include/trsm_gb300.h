@@ -1,0 +1,139 @@
+/*
+ * trsm_gb300.h — C ABI of a single-GPU (GB300, sm_103a) triangular solver
+ * with many right-hand sides by selective diagonal-block inversion, after
+ * Wicky, Solomonik & Hoefler, "Communication-Avoiding Parallel Algorithms for
+ * Solving Triangular Systems of Linear Equations", arXiv:1612.01855.
+ *
+ * Problem (Section 1): L X = B with L n x n lower-triangular, B and X n x k
+ * dense.  Left side, lower, not transposed, non-unit diagonal: the only case
+ * the paper treats.
+ *
+ * Conventions shared by every call:
+ *   - FP64 matrices are column-major: element (i, j) of M with leading
+ *     dimension ld is M[j*ld + i]; ld >= max(1, rows).  Only the lower
+ *     triangle of L (diagonal included) is read; its strict upper triangle
+ *     is never touched.
+ *   - Pointers named *_dev are device pointers of the current CUDA device;
+ *     *_host are host pointers (pinned or pageable).  The library never
+ *     retains a caller pointer beyond the call unless stated.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device work is enqueued on it; calls marked "synchronous"
+ *     wait for their own work before returning.
+ *   - Return value: TRSM_SUCCESS (0) or a negative TRSM_E* code.  A failing
+ *     call leaves outputs unspecified and frees what it allocated.
+ */
+#ifndef TRSM_GB300_H
+#define TRSM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define TRSM_SUCCESS 0
+#define TRSM_EINVAL (-1)     /* bad size, leading dimension, pointer or option   */
+#define TRSM_ESINGULAR (-2)  /* a diagonal entry of L is zero, Inf or NaN        */
+#define TRSM_ENOMEM (-3)     /* device or host allocation failed                 */
+#define TRSM_ECUDA (-4)      /* a CUDA runtime call failed (see trsm_last_cuda)  */
+#define TRSM_ETIMEOUT (-5)   /* a device-side dependency wait hit its time limit */
+
+/* Opaque plan: the paper's L~ (Algorithm Diagonal-Inverter, Section 6.1) —
+ * a device copy of L whose n0 x n0 diagonal blocks are replaced by their
+ * inverses — plus sizes.  It owns its device memory. */
+typedef struct trsm_plan_s* trsm_handle_t;
+
+/* trsm_plan — Algorithm Diagonal-Inverter (Section 6.1) with Algorithm
+ * RecTriInv (Section 5.1) for every diagonal block.
+ *   L_dev  : device, n x n column-major, leading dimension ldl >= n.  Read
+ *            only; the caller may free it once trsm_plan has returned.
+ *   n      : order of L, n >= 1.
+ *   n0     : diagonal block size, 1 <= n0 (n0 >= n means one block, the full
+ *            inversion; a last block shorter than n0 is allowed).
+ *   out    : receives the handle (NULL on failure).
+ * Synchronous: waits for the inversion so that a singular L is reported as
+ * TRSM_ESINGULAR (trsm_singular_index gives the row).  Errors: TRSM_EINVAL,
+ * TRSM_ESINGULAR, TRSM_ENOMEM, TRSM_ECUDA. */
+int trsm_plan(const double* L_dev, int64_t n, int64_t ldl, int64_t n0, void* stream,
+              trsm_handle_t* out);
+
+/* trsm_solve — Algorithm It-Inv-TRSM (Section 6.2) with the plan's L~:
+ * for every block row i, X_i = L~_ii (B_i - L_{i,<i} X_{<i}).
+ *   B_dev : device, n x k, leading dimension ldb >= n; read only.
+ *   X_dev : device, n x k, leading dimension ldx >= n; written.  X_dev may
+ *           equal B_dev with ldx == ldb (in place); other overlaps are
+ *           undefined.
+ *   k     : number of right-hand sides, k >= 0 (k == 0 is a no-op).
+ * Asynchronous on `stream`; it allocates its workspace (n x k doubles plus
+ * dependency counters) stream-ordered and frees it stream-ordered.  A
+ * device-side wait that times out is reported by trsm_sync_status.
+ * Errors (immediate): TRSM_EINVAL, TRSM_ENOMEM, TRSM_ECUDA. */
+int trsm_solve(trsm_handle_t h, const double* B_dev, int64_t k, int64_t ldb, double* X_dev,
+               int64_t ldx, void* stream);
+
+/* Workspace-explicit form of trsm_solve: the caller passes device memory
+ * `ws_dev` of at least trsm_solve_workspace_size(h, k) bytes (256-byte
+ * aligned); nothing is allocated.  Concurrent calls must not share ws_dev. */
+int trsm_solve_workspace_size(trsm_handle_t h, int64_t k, size_t* bytes);
+int trsm_solve_ws(trsm_handle_t h, const double* B_dev, int64_t k, int64_t ldb, double* X_dev,
+                  int64_t ldx, void* ws_dev, size_t ws_bytes, void* stream);
+
+/* trsm_host — the whole method (trsm_plan + trsm_solve) on HOST buffers:
+ * copies L and B to the device, plans, solves, copies X back and waits.
+ *   L_host (n x n, ldl), B_host (n x k, ldb), X_host (n x k, ldx), all
+ *   column-major host memory; pinned memory makes the copies asynchronous.
+ * Synchronous.  Errors as trsm_plan and trsm_solve. */
+int trsm_host(const double* L_host, int64_t n, int64_t ldl, int64_t n0, const double* B_host,
+              int64_t k, int64_t ldb, double* X_host, int64_t ldx, void* stream);
+
+/* trtri_blocks — Algorithm Diagonal-Inverter's output in packed form: the
+ * inverses of the N = ceil(n/n0) diagonal blocks L(S_b, S_b),
+ * S_b = [b*n0, min((b+1)*n0, n)), each by RecTriInv (Section 5.1).
+ *   Linv_dev : device, N*n0*n0 doubles, caller-owned; block b is the n0 x n0
+ *              column-major matrix at Linv_dev + b*n0*n0 (leading dimension
+ *              n0).  Its strict upper triangle is written as zero; a short
+ *              last block occupies its leading m x m corner, the rest zero.
+ * Synchronous.  Errors: TRSM_EINVAL, TRSM_ESINGULAR, TRSM_ENOMEM, TRSM_ECUDA. */
+int trtri_blocks(const double* L_dev, int64_t n, int64_t ldl, int64_t n0, double* Linv_dev,
+                 void* stream);
+
+/* Releases the plan's device memory (after the work queued on it). */
+void trsm_destroy(trsm_handle_t h);
+
+/* Plan accessors.  trsm_plan_lt returns the device pointer of L~ (n x n,
+ * leading dimension *ldt), owned by the plan: its diagonal blocks hold the
+ * inverses, below them L itself, above the diagonal zeros. */
+int trsm_plan_sizes(trsm_handle_t h, int64_t* n, int64_t* n0, int64_t* nblocks);
+const double* trsm_plan_lt(trsm_handle_t h, int64_t* ldt);
+
+/* Waits for `stream` and returns the device status of the last solve
+ * enqueued with this plan: TRSM_SUCCESS or TRSM_ETIMEOUT. */
+int trsm_sync_status(trsm_handle_t h, void* stream);
+
+/* Row of the first zero or non-finite diagonal entry met by the last plan
+ * or trtri_blocks on this thread, or -1. */
+int64_t trsm_singular_index(void);
+
+/* Last CUDA runtime error code seen by the library on this thread (0 if none). */
+int trsm_last_cuda(void);
+
+/* Human-readable text of a TRSM_* code (static storage). */
+const char* trsm_error_string(int code);
+
+/* Number of kernel launches the library enqueued on this thread since the
+ * counter was last reset (for launch accounting around a timed region). */
+int64_t trsm_launch_count(int reset);
+
+/* Measures the device's FP64 fused-multiply-add throughput (no counterpart
+ * in the paper: a roofline denominator).  Runs a DFMA-only kernel for about
+ * `iters` x 8 x 2 flops per thread on every SM and writes TFLOP/s to
+ * *tflops.  Synchronous. */
+int trsm_fp64_peak(int iters, double* tflops, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TRSM_GB300_H */

@@ -1,0 +1,303 @@
+// C ABI of the library (declarations and documentation in
+// include/trsm_gb300.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+#include "trsm_gb300.h"
+
+struct trsm_plan_s {
+  int64_t n = 0, n0 = 0, N = 0, ldt = 0;
+  double* Lt = nullptr;  // L~: n x n, leading dimension ldt
+  int* status = nullptr; // sticky device status of solves
+  int device = 0;
+};
+
+namespace {
+
+thread_local int64_t t_singular = -1;
+thread_local int t_last_cuda = 0;
+thread_local int64_t t_launches = 0;
+
+int from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return TRSM_SUCCESS;
+  t_last_cuda = (int)e;
+  cudaGetLastError();  // clear a sticky-free error so later calls are not poisoned
+  return (e == cudaErrorMemoryAllocation) ? TRSM_ENOMEM : TRSM_ECUDA;
+}
+
+inline int64_t align4(int64_t x) { return (x + 3) / 4 * 4; }
+
+std::vector<trsm::DiagBlock> diag_blocks(int64_t n, int64_t n0, int64_t ld, bool packed) {
+  std::vector<trsm::DiagBlock> v;
+  for (int64_t s0 = 0, b = 0; s0 < n; s0 += n0, ++b) {
+    trsm::DiagBlock d;
+    d.m = std::min(n0, n - s0);
+    d.row0 = s0;
+    d.off = packed ? b * n0 * n0 : s0 * ld + s0;
+    v.push_back(d);
+  }
+  return v;
+}
+
+// Inverts the listed blocks and reports a singular pivot.  Synchronous.
+int invert_and_check(double* A, int64_t ld, const std::vector<trsm::DiagBlock>& blocks,
+                     cudaStream_t s) {
+  unsigned long long* sing = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&sing, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return from_cuda(e);
+  unsigned long long h_sing = ULLONG_MAX;
+  e = cudaMemsetAsync(sing, 0xFF, sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = trsm::invert_diag_blocks(A, ld, blocks, sing, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&h_sing, sing, sizeof(h_sing), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(sing, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return from_cuda(e);
+  if (h_sing != ULLONG_MAX) {
+    t_singular = (int64_t)h_sing;
+    return TRSM_ESINGULAR;
+  }
+  return TRSM_SUCCESS;
+}
+
+__global__ void dfma_peak_kernel(double* out, int iters, double a, double b) {
+  double acc[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) acc[c] = threadIdx.x * 1e-3 + c;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] = fma(acc[c], a, b);
+  }
+  double s = 0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) s += acc[c];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+}  // namespace
+
+namespace trsm {
+
+void count_launch(int64_t n) { t_launches += n; }
+
+int device_sm_count() {
+  static int cache[128] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 128) dev = 0;
+  if (cache[dev] == 0) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cache[dev] = v > 0 ? v : 1;
+  }
+  return cache[dev];
+}
+
+}  // namespace trsm
+
+extern "C" {
+
+int trsm_plan(const double* L_dev, int64_t n, int64_t ldl, int64_t n0, void* stream,
+              trsm_handle_t* out) {
+  if (out) *out = nullptr;
+  if (!L_dev || !out || n < 1 || n0 < 1 || ldl < n) return TRSM_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n0 > n) n0 = n;
+  t_singular = -1;
+  trsm_plan_s* h = new (std::nothrow) trsm_plan_s;
+  if (!h) return TRSM_ENOMEM;
+  h->n = n;
+  h->n0 = n0;
+  h->N = (n + n0 - 1) / n0;
+  h->ldt = align4(n);
+  cudaGetDevice(&h->device);
+  cudaError_t e = cudaMalloc((void**)&h->Lt, sizeof(double) * (size_t)h->ldt * (size_t)n);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = trsm::copy_lower(L_dev, ldl, h->Lt, h->ldt, n, s);
+  int rc = from_cuda(e);
+  if (rc == TRSM_SUCCESS) rc = invert_and_check(h->Lt, h->ldt, diag_blocks(n, n0, h->ldt, false), s);
+  if (rc != TRSM_SUCCESS) {
+    trsm_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return TRSM_SUCCESS;
+}
+
+int trsm_solve_workspace_size(trsm_handle_t h, int64_t k, size_t* bytes) {
+  if (!h || k < 0 || !bytes) return TRSM_EINVAL;
+  *bytes = (k == 0) ? 0 : trsm::solve_workspace_bytes(h->n, h->n0, k);
+  return TRSM_SUCCESS;
+}
+
+static int check_solve_args(trsm_handle_t h, const double* B, int64_t k, int64_t ldb,
+                            const double* X, int64_t ldx) {
+  if (!h || k < 0) return TRSM_EINVAL;
+  if (k == 0) return TRSM_SUCCESS;
+  if (!B || !X || ldb < h->n || ldx < h->n) return TRSM_EINVAL;
+  if (B == X && ldb != ldx) return TRSM_EINVAL;
+  return TRSM_SUCCESS;
+}
+
+int trsm_solve_ws(trsm_handle_t h, const double* B_dev, int64_t k, int64_t ldb, double* X_dev,
+                  int64_t ldx, void* ws_dev, size_t ws_bytes, void* stream) {
+  int rc = check_solve_args(h, B_dev, k, ldb, X_dev, ldx);
+  if (rc != TRSM_SUCCESS || k == 0) return rc;
+  const size_t need = trsm::solve_workspace_bytes(h->n, h->n0, k);
+  if (!ws_dev || ws_bytes < need || ((uintptr_t)ws_dev % 256) != 0) return TRSM_EINVAL;
+  return from_cuda(trsm::solve_enqueue(h->Lt, h->ldt, h->n, h->n0, B_dev, k, ldb, X_dev, ldx,
+                                       ws_dev, h->status, (cudaStream_t)stream));
+}
+
+int trsm_solve(trsm_handle_t h, const double* B_dev, int64_t k, int64_t ldb, double* X_dev,
+               int64_t ldx, void* stream) {
+  int rc = check_solve_args(h, B_dev, k, ldb, X_dev, ldx);
+  if (rc != TRSM_SUCCESS || k == 0) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t need = trsm::solve_workspace_bytes(h->n, h->n0, k);
+  void* ws = nullptr;
+  cudaError_t e = cudaMallocAsync(&ws, need, s);
+  if (e != cudaSuccess) return from_cuda(e);
+  e = trsm::solve_enqueue(h->Lt, h->ldt, h->n, h->n0, B_dev, k, ldb, X_dev, ldx, ws, h->status, s);
+  cudaError_t e2 = cudaFreeAsync(ws, s);
+  return from_cuda(e != cudaSuccess ? e : e2);
+}
+
+int trsm_host(const double* L_host, int64_t n, int64_t ldl, int64_t n0, const double* B_host,
+              int64_t k, int64_t ldb, double* X_host, int64_t ldx, void* stream) {
+  if (!L_host || n < 1 || ldl < n || n0 < 1 || k < 0) return TRSM_EINVAL;
+  if (k > 0 && (!B_host || !X_host || ldb < n || ldx < n)) return TRSM_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  double *dL = nullptr, *dB = nullptr;
+  const int64_t ld = align4(n);
+  cudaError_t e = cudaMallocAsync((void**)&dL, sizeof(double) * (size_t)ld * (size_t)n, s);
+  if (e == cudaSuccess && k > 0)
+    e = cudaMallocAsync((void**)&dB, sizeof(double) * (size_t)ld * (size_t)k, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(dL, sizeof(double) * ld, L_host, sizeof(double) * ldl,
+                          sizeof(double) * n, (size_t)n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && k > 0)
+    e = cudaMemcpy2DAsync(dB, sizeof(double) * ld, B_host, sizeof(double) * ldb,
+                          sizeof(double) * n, (size_t)k, cudaMemcpyHostToDevice, s);
+  int rc = from_cuda(e);
+  trsm_handle_t h = nullptr;
+  if (rc == TRSM_SUCCESS) rc = trsm_plan(dL, n, ld, n0, stream, &h);
+  if (rc == TRSM_SUCCESS && k > 0) rc = trsm_solve(h, dB, k, ld, dB, ld, stream);
+  if (rc == TRSM_SUCCESS && k > 0)
+    rc = from_cuda(cudaMemcpy2DAsync(X_host, sizeof(double) * ldx, dB, sizeof(double) * ld,
+                                     sizeof(double) * n, (size_t)k, cudaMemcpyDeviceToHost, s));
+  if (rc == TRSM_SUCCESS) rc = trsm_sync_status(h, stream);
+  if (h) trsm_destroy(h);
+  if (dB) cudaFreeAsync(dB, s);
+  if (dL) cudaFreeAsync(dL, s);
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  if (rc == TRSM_SUCCESS) rc = from_cuda(e2);
+  return rc;
+}
+
+int trtri_blocks(const double* L_dev, int64_t n, int64_t ldl, int64_t n0, double* Linv_dev,
+                 void* stream) {
+  if (!L_dev || !Linv_dev || n < 1 || n0 < 1 || ldl < n) return TRSM_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  t_singular = -1;
+  int rc = from_cuda(trsm::pack_diag_blocks(L_dev, ldl, Linv_dev, n, n0, s));
+  if (rc == TRSM_SUCCESS) rc = invert_and_check(Linv_dev, n0, diag_blocks(n, n0, n0, true), s);
+  return rc;
+}
+
+void trsm_destroy(trsm_handle_t h) {
+  if (!h) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != h->device) cudaSetDevice(h->device);
+  // cudaFree waits for the device work that may still use the memory.
+  if (h->Lt) cudaFree(h->Lt);
+  if (h->status) cudaFree(h->status);
+  if (cur != h->device) cudaSetDevice(cur);
+  delete h;
+}
+
+int trsm_plan_sizes(trsm_handle_t h, int64_t* n, int64_t* n0, int64_t* nblocks) {
+  if (!h) return TRSM_EINVAL;
+  if (n) *n = h->n;
+  if (n0) *n0 = h->n0;
+  if (nblocks) *nblocks = h->N;
+  return TRSM_SUCCESS;
+}
+
+const double* trsm_plan_lt(trsm_handle_t h, int64_t* ldt) {
+  if (!h) return nullptr;
+  if (ldt) *ldt = h->ldt;
+  return h->Lt;
+}
+
+int trsm_sync_status(trsm_handle_t h, void* stream) {
+  if (!h) return TRSM_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  int st = 0;
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemcpy(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && st != 0) e = cudaMemset(h->status, 0, sizeof(int));
+  if (e != cudaSuccess) return from_cuda(e);
+  return st ? TRSM_ETIMEOUT : TRSM_SUCCESS;
+}
+
+int64_t trsm_singular_index(void) { return t_singular; }
+
+int trsm_last_cuda(void) { return t_last_cuda; }
+
+const char* trsm_error_string(int code) {
+  switch (code) {
+    case TRSM_SUCCESS: return "success";
+    case TRSM_EINVAL: return "invalid argument";
+    case TRSM_ESINGULAR: return "zero or non-finite diagonal entry in L";
+    case TRSM_ENOMEM: return "out of memory";
+    case TRSM_ECUDA: return "CUDA runtime error";
+    case TRSM_ETIMEOUT: return "device-side dependency wait timed out";
+    default: return "unknown status";
+  }
+}
+
+int64_t trsm_launch_count(int reset) {
+  const int64_t v = t_launches;
+  if (reset) t_launches = 0;
+  return v;
+}
+
+int trsm_fp64_peak(int iters, double* tflops, void* stream) {
+  if (iters < 1 || !tflops) return TRSM_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int sms = trsm::device_sm_count();
+  const int blocks = sms * 2, threads = 256;
+  double* out = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&out, sizeof(double) * blocks * threads, s);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) {
+    dfma_peak_kernel<<<blocks, threads, 0, s>>>(out, 64, 1.0000001, 1e-9);  // warm-up
+    cudaEventRecord(e0, s);
+    dfma_peak_kernel<<<blocks, threads, 0, s>>>(out, iters, 1.0000001, 1e-9);
+    cudaEventRecord(e1, s);
+    trsm::count_launch(2);
+    e = cudaEventSynchronize(e1);
+  }
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (out) cudaFreeAsync(out, s);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) return from_cuda(e);
+  const double flops = 2.0 * 8.0 * (double)iters * blocks * threads;
+  *tflops = flops / ((double)ms * 1e-3) / 1e12;
+  return TRSM_SUCCESS;
+}
+
+}  // extern "C"

@@ -1,0 +1,52 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+namespace trsm {
+
+// A diagonal block to invert in place: top-left element at A + off, order m;
+// row0 is its first row in the caller's numbering (for singular reports).
+struct DiagBlock {
+  int64_t off;
+  int64_t m;
+  int64_t row0;
+};
+
+// Inverts every listed diagonal block of A (leading dimension ld) in place
+// by recursive triangular inversion; the strict upper triangle of each block
+// must hold zeros on entry.  The smallest row index with a zero or non-finite
+// pivot is folded (atomic min) into *sing_dev.  Asynchronous on `s`;
+// allocates its scratch stream-ordered.  Returns a cudaError_t.
+cudaError_t invert_diag_blocks(double* A, int64_t ld, const std::vector<DiagBlock>& blocks,
+                               unsigned long long* sing_dev, cudaStream_t s);
+
+// Lt(i, j) = (i >= j) ? L(i, j) : 0 for an n x n matrix.
+cudaError_t copy_lower(const double* L, int64_t ldl, double* Lt, int64_t ldt, int64_t n,
+                       cudaStream_t s);
+
+// Packs the diagonal blocks of L into P (N blocks of n0 x n0, ld n0),
+// lower triangle only, zero elsewhere.
+cudaError_t pack_diag_blocks(const double* L, int64_t ldl, double* P, int64_t n, int64_t n0,
+                             cudaStream_t s);
+
+// W (n x k, ldw) = B (n x k, ldb).
+cudaError_t copy_panel(const double* B, int64_t ldb, double* W, int64_t ldw, int64_t n,
+                       int64_t k, cudaStream_t s);
+
+// Solve with a planned L~: see solve.cu.
+size_t solve_workspace_bytes(int64_t n, int64_t n0, int64_t k);
+cudaError_t solve_enqueue(const double* Lt, int64_t ldt, int64_t n, int64_t n0, const double* B,
+                          int64_t k, int64_t ldb, double* X, int64_t ldx, void* ws,
+                          int* status_dev, cudaStream_t s);
+
+// Launch accounting (every kernel launch of the library goes through here).
+void count_launch(int64_t n = 1);
+
+// Number of SMs and CTAs per SM of the persistent solve kernel on the
+// current device (cached per device).
+int device_sm_count();
+
+}  // namespace trsm

@@ -1,0 +1,232 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerance: the FP64 path must match the oracle to a relative error of
+1e-12 (max-norm of the difference over max-norm of the oracle's X, or per
+inverted block).  Both sides are backward stable; on the well-conditioned
+workloads the difference is a few hundred ulps at most, and a real mistake
+(a missing update, a wrong block, a stale tile) is off by O(1).
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from conftest import EPS, load_golden
+from paper_1612_01855_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+def _t():
+    import torch
+    return torch
+
+
+def dev(a):
+    """numpy (any order) -> column-major float64 CUDA tensor."""
+    torch = _t()
+    a = np.asarray(a, dtype=np.float64)
+    if a.ndim == 1:
+        a = a[:, None]
+    return torch.from_numpy(np.ascontiguousarray(a.T)).cuda().t()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def rel_err(A, B):
+    return float(np.max(np.abs(A - B)) / max(np.max(np.abs(B)), 1e-300))
+
+
+def test_golden_worked_example(cuda_lib):
+    import paper_1612_01855_gb300 as g
+    fx = load_golden("worked_example_4x4.txt")
+    L, B = dev(fx["L"]), dev(fx["B"])
+    p = g.trsm_plan(L, 2)
+    Lt = host(p.lt())
+    assert np.array_equal(np.tril(Lt), fx["Ltilde_n0_2"])
+    assert np.array_equal(np.triu(Lt, 1), np.zeros((4, 4)))
+    X = host(g.trsm_solve(p, B))
+    _t().cuda.synchronize()
+    assert np.array_equal(X, fx["X"])
+    inv = host(g.trtri_blocks(L, 4))
+    assert np.array_equal(inv[0], fx["Linv"])
+    g.trsm_sync_status(p)
+
+
+@pytest.mark.parametrize("n,n0", [(512, 64), (1000, 64), (300, 128), (200, 200), (77, 32),
+                                  (33, 1), (130, 48), (1024, 512), (70, 100)])
+def test_trtri_blocks_parity(cuda_lib, n, n0):
+    import paper_1612_01855_gb300 as g
+    L = inputs.well_conditioned_L(n, seed=n + n0)
+    got = host(g.trtri_blocks(dev(L), n0))
+    want = oracle.diag_block_inverses(L, n0, base=16)  # n0 > n: one block in an n0 x n0 slot
+    assert got.shape == want.shape
+    for b in range(got.shape[0]):
+        assert rel_err(got[b], want[b]) < TOL, b
+    # strict upper triangles are zero, short last block zero-padded
+    assert np.all(np.triu(got, 1) == 0.0)
+
+
+@pytest.mark.parametrize("n,n0", [(512, 64), (1000, 64), (257, 32), (96, 96)])
+def test_plan_matches_diagonal_inverter(cuda_lib, n, n0):
+    import paper_1612_01855_gb300 as g
+    L = inputs.well_conditioned_L(n, seed=7)
+    p = g.trsm_plan(dev(L), n0)
+    assert (p.n, p.n0, p.nblocks) == (n, n0, (n + n0 - 1) // n0)
+    Lt = host(p.lt())
+    want = oracle.diagonal_inverter(L, n0, base=16)
+    assert rel_err(np.tril(Lt), want) < TOL
+    assert np.all(np.triu(Lt, 1) == 0.0)
+    # off the block diagonal L~ is L itself, bit for bit
+    mask = np.ones((n, n), dtype=bool)
+    for s in range(0, n, n0):
+        mask[s:s + n0, s:s + n0] = False
+    assert np.array_equal(np.tril(Lt)[mask], np.tril(L)[mask])
+
+
+SOLVE_CASES = [
+    (512, 512, 64),    # the oracle-sized workload
+    (1000, 37, 64),    # ragged last block and ragged column tile
+    (257, 1, 32),      # single right-hand side
+    (130, 65, 16),
+    (64, 64, 64),      # one block: full inversion
+    (300, 100, 300),   # n0 = n
+    (300, 100, 1000),  # n0 > n
+    (97, 33, 1),       # n0 = 1: plain substitution
+    (1, 5, 1),
+    (31, 31, 7),
+    (2048, 96, 256),
+    (1536, 40, 100),   # n0 not a multiple of the tile
+]
+
+
+@pytest.mark.parametrize("n,k,n0", SOLVE_CASES)
+def test_solve_parity(cuda_lib, n, k, n0):
+    import paper_1612_01855_gb300 as g
+    L, B = inputs.well_conditioned(n, k, seed=n * 31 + k)
+    p = g.trsm_plan(dev(L), n0)
+    Xd = g.trsm_solve(p, dev(B))
+    g.trsm_sync_status(p)
+    X = host(Xd)
+    want = oracle.forward_subst(L, B)
+    assert rel_err(X, want) < TOL
+    back = np.linalg.norm(L @ X - B, np.inf) / (np.linalg.norm(L, np.inf) * np.linalg.norm(X, np.inf))
+    assert back <= 10 * n * EPS
+
+
+def test_n0_sweep_same_result(cuda_lib):
+    """Every block size reaches the same X (substitution ... full inversion)."""
+    import paper_1612_01855_gb300 as g
+    n, k = 1024, 96
+    L, B = inputs.well_conditioned(n, k, seed=1)
+    want = oracle.forward_subst(L, B)
+    Ld, Bd = dev(L), dev(B)
+    for n0 in (1, 16, 32, 64, 100, 128, 256, 512, 1024):
+        p = g.trsm_plan(Ld, n0)
+        X = host(g.trsm_solve(p, Bd))
+        g.trsm_sync_status(p)
+        assert rel_err(X, want) < TOL, n0
+
+
+def test_in_place_and_leading_dimensions(cuda_lib):
+    import paper_1612_01855_gb300 as g
+    torch = _t()
+    n, k, n0 = 333, 21, 64
+    L, B = inputs.well_conditioned(n, k, seed=2)
+    want = oracle.forward_subst(L, B)
+    # L, B embedded in larger column-major buffers (ld > n)
+    bigL = torch.zeros((n + 5, n + 3), dtype=torch.float64, device="cuda")
+    bigL = bigL.t().contiguous().t()
+    bigL[:n, :n] = torch.from_numpy(L).cuda()
+    Lv = bigL[:n, :n]
+    assert Lv.stride(0) == 1 and Lv.stride(1) == n + 5
+    bigB = torch.zeros((k + 2, n + 7), dtype=torch.float64, device="cuda").t()
+    bigB[:n, :k] = torch.from_numpy(B).cuda()
+    Bv = bigB[:n, :k]
+    p = g.trsm_plan(Lv, n0)
+    out = g.trsm_solve(p, Bv, X=Bv)  # in place
+    g.trsm_sync_status(p)
+    assert out.data_ptr() == Bv.data_ptr()
+    assert rel_err(host(Bv), want) < TOL
+    assert torch.all(bigB[n:, :] == 0) and torch.all(bigB[:, k:] == 0)
+
+
+def test_workspace_variant_and_determinism(cuda_lib):
+    import paper_1612_01855_gb300 as g
+    torch = _t()
+    n, k, n0 = 1200, 70, 128
+    L, B = inputs.well_conditioned(n, k, seed=3)
+    p = g.trsm_plan(dev(L), n0)
+    Bd = dev(B)
+    X1 = host(g.trsm_solve(p, Bd))
+    ws = torch.empty(g.trsm_solve_workspace_size(p, k), dtype=torch.uint8, device="cuda")
+    X2 = torch.empty((k, n), dtype=torch.float64, device="cuda").t()
+    g.trsm_solve_ws(p, Bd, X2, ws)
+    X3 = host(g.trsm_solve(p, Bd))
+    g.trsm_sync_status(p)
+    # updates of each tile are applied in a fixed order: bitwise reproducible
+    assert np.array_equal(X1, host(X2))
+    assert np.array_equal(X1, X3)
+
+
+def test_k_zero_is_noop(cuda_lib):
+    import paper_1612_01855_gb300 as g
+    torch = _t()
+    L = inputs.well_conditioned_L(40, seed=0)
+    p = g.trsm_plan(dev(L), 16)
+    lib = cuda_lib
+    assert lib.trsm_solve(p.handle, None, 0, 40, None, 40, None) == 0
+    ws = ctypes.c_size_t(123)
+    assert lib.trsm_solve_workspace_size(p.handle, 0, ctypes.byref(ws)) == 0 and ws.value == 0
+    g.trsm_sync_status(p)
+    torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("bad", [0.0, float("nan"), float("inf")])
+def test_singular_diagonal_reported(cuda_lib, bad):
+    import paper_1612_01855_gb300 as g
+    L = inputs.well_conditioned_L(100, seed=9)
+    L[57, 57] = bad
+    with pytest.raises(g.TrsmError) as ei:
+        g.trsm_plan(dev(L), 32)
+    assert ei.value.code == -2 and "row 57" in str(ei.value)
+    with pytest.raises(g.TrsmError) as ei:
+        g.trtri_blocks(dev(L), 64)
+    assert ei.value.code == -2
+
+
+def test_host_buffers_through_c_abi(cuda_lib):
+    import paper_1612_01855_gb300 as g
+    n, k, n0 = 700, 45, 64
+    L, B = inputs.well_conditioned(n, k, seed=4)
+    X = g.trsm_host(L, B, n0)
+    assert rel_err(X, oracle.forward_subst(L, B)) < TOL
+
+
+FULL_SIZES = [(16384, 256, 256), (8192, 8192, 512), (2048, 131072, 2048)]
+
+
+@pytest.mark.parametrize("n,k,n0", FULL_SIZES)
+def test_full_size_sampled_columns(cuda_lib, n, k, n0):
+    """At the measured sizes and launch configuration: the oracle computes a
+    seeded sample of columns one by one (columns of X are independent)."""
+    import paper_1612_01855_gb300 as g
+    torch = _t()
+    L, B = inputs.well_conditioned(n, k, seed=0)
+    cols = np.sort(np.random.default_rng(5).choice(k, size=min(6, k), replace=False))
+    want = oracle.forward_subst_columns(L, B, cols)
+    Ld = dev(L)
+    del L
+    p = g.trsm_plan(Ld, n0)
+    del Ld
+    Bd = dev(B)
+    Xd = g.trsm_solve(p, Bd, X=Bd)
+    g.trsm_sync_status(p)
+    got = Xd[:, torch.from_numpy(cols).cuda()].cpu().numpy()
+    assert rel_err(got, want) < TOL
+    assert torch.isfinite(Xd).all().item()
