@@ -174,8 +174,10 @@ def run_ours(args, rank, world, local):
     if world > 1:
         torch.distributed.barrier()
     g.load_library()
-    shapes = SHAPES
-    n0s = [DEFAULT_N0[s] for s in shapes]
+    shapes, n0s = SHAPES, [DEFAULT_N0[s] for s in SHAPES]
+    if args.shapes:  # override (profiling of small cases): "n:k:n0,n:k:n0"
+        trip = [tuple(int(v) for v in item.split(":")) for item in args.shapes.split(",")]
+        shapes, n0s = [(a, b) for a, b, _ in trip], [c for _, _, c in trip]
     data = make_inputs(shapes)
     dev_in = [(to_dev(L, torch), to_dev(B, torch)) for L, B in data]
     outs = [torch.empty((k, n), dtype=torch.float64, device="cuda").t() for n, k in shapes]
@@ -345,6 +347,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--shapes", default="", help="override workload, e.g. 6144:1024:256 (not a bench line)")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if world > 1:
