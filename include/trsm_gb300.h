@@ -39,6 +39,7 @@ extern "C" {
 #define TRSM_ENOMEM (-3)     /* device or host allocation failed                 */
 #define TRSM_ECUDA (-4)      /* a CUDA runtime call failed (see trsm_last_cuda)  */
 #define TRSM_ETIMEOUT (-5)   /* a device-side dependency wait hit its time limit */
+#define TRSM_ENOSCRATCH (-6) /* trsm_solve_noalloc: workspace exceeds its fixed scratch */
 
 /* Opaque plan: the paper's L~ (Algorithm Diagonal-Inverter, Section 6.1) —
  * a device copy of L whose n0 x n0 diagonal blocks are replaced by their
@@ -79,6 +80,28 @@ int trsm_solve(trsm_handle_t h, const double* B_dev, int64_t k, int64_t ldb, dou
 int trsm_solve_workspace_size(trsm_handle_t h, int64_t k, size_t* bytes);
 int trsm_solve_ws(trsm_handle_t h, const double* B_dev, int64_t k, int64_t ldb, double* X_dev,
                   int64_t ldx, void* ws_dev, size_t ws_bytes, void* stream);
+
+/* trsm_solve_noalloc — trsm_solve that allocates nothing.  The paper has no
+ * counterpart: this exists for callers that may not allocate device memory
+ * while solving (an application or server that owns all GPU memory through
+ * its own arena, or a latency-critical loop that cannot afford an
+ * allocation's device synchronisation or pool growth).
+ *   Same arguments, result and layout rules as trsm_solve; the current device
+ *   must be the plan's device (else TRSM_EINVAL).
+ *   Workspace: a fixed 64 MiB device array compiled into the library (held on
+ *   every GPU that loads it until the process exits).  If
+ *   trsm_solve_workspace_size(h, k) exceeds 64 MiB the call returns
+ *   TRSM_ENOSCRATCH before any device work.
+ *   All calls on a device share that array and find the previous call's data
+ *   there; each call resets what must start at zero.  Calls whose device work
+ *   overlaps (other streams, other host threads) race: serialise them.
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress, with that device current) and caches it; make it
+ *   before any stream capture begins.
+ * Asynchronous on `stream`.  Errors: TRSM_EINVAL, TRSM_ENOSCRATCH,
+ * TRSM_ECUDA. */
+int trsm_solve_noalloc(trsm_handle_t h, const double* B_dev, int64_t k, int64_t ldb,
+                       double* X_dev, int64_t ldx, void* stream);
 
 /* trsm_host — the whole method (trsm_plan + trsm_solve) on HOST buffers:
  * copies L and B to the device, plans, solves, copies X back and waits.

@@ -23,6 +23,7 @@ TRSM_ESINGULAR = -2
 TRSM_ENOMEM = -3
 TRSM_ECUDA = -4
 TRSM_ETIMEOUT = -5
+TRSM_ENOSCRATCH = -6
 
 # Every symbol the header declares, with (restype, argtypes).
 _i64, _vp, _dp, _int = ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int
@@ -32,6 +33,7 @@ SIGNATURES = {
     "trsm_solve": (_int, [_vp, _dp, _i64, _i64, _dp, _i64, _vp]),
     "trsm_solve_workspace_size": (_int, [_vp, _i64, ctypes.POINTER(ctypes.c_size_t)]),
     "trsm_solve_ws": (_int, [_vp, _dp, _i64, _i64, _dp, _i64, _vp, ctypes.c_size_t, _vp]),
+    "trsm_solve_noalloc": (_int, [_vp, _dp, _i64, _i64, _dp, _i64, _vp]),
     "trsm_host": (_int, [_dp, _i64, _i64, _i64, _dp, _i64, _i64, _dp, _i64, _vp]),
     "trtri_blocks": (_int, [_dp, _i64, _i64, _i64, _dp, _vp]),
     "trsm_destroy": (None, [_vp]),
@@ -188,6 +190,22 @@ def trsm_solve(plan, B, X=None):
     _check(load_library().trsm_solve(plan.handle, ctypes.c_void_p(B.data_ptr()), k, _ld(B),
                                      ctypes.c_void_p(X.data_ptr()), _ld(X), _stream(B)),
            "trsm_solve")
+    return X
+
+
+def trsm_solve_noalloc(plan, B, X):
+    """trsm_solve without device allocation: the workspace is the library's
+    fixed 64 MiB scratch array (for callers that may not allocate while
+    solving).  Overlapping calls on one device race; larger problems raise
+    TrsmError(TRSM_ENOSCRATCH)."""
+    B = _dev_matrix(B, "B")
+    X = _dev_matrix(X, "X")
+    n, k = B.shape
+    if n != plan.n or X.shape != B.shape:
+        raise ValueError("B and X must be n x k")
+    _check(load_library().trsm_solve_noalloc(plan.handle, ctypes.c_void_p(B.data_ptr()), k, _ld(B),
+                                             ctypes.c_void_p(X.data_ptr()), _ld(X), _stream(B)),
+           "trsm_solve_noalloc")
     return X
 
 

@@ -86,6 +86,10 @@ namespace trsm {
 
 void count_launch(int64_t n) { t_launches += n; }
 
+int* plan_status_word(trsm_handle_t h) { return h ? h->status : nullptr; }
+
+int plan_device(trsm_handle_t h) { return h ? h->device : -1; }
+
 int device_sm_count() {
   static int cache[128] = {0};
   int dev = 0;
@@ -261,6 +265,7 @@ const char* trsm_error_string(int code) {
     case TRSM_ENOMEM: return "out of memory";
     case TRSM_ECUDA: return "CUDA runtime error";
     case TRSM_ETIMEOUT: return "device-side dependency wait timed out";
+    case TRSM_ENOSCRATCH: return "workspace larger than the fixed no-allocation scratch (64 MiB)";
     default: return "unknown status";
   }
 }

@@ -5,6 +5,8 @@
 
 #include <vector>
 
+#include "trsm_gb300.h"
+
 namespace trsm {
 
 // A diagonal block to invert in place: top-left element at A + off, order m;
@@ -41,6 +43,11 @@ size_t solve_workspace_bytes(int64_t n, int64_t n0, int64_t k);
 cudaError_t solve_enqueue(const double* Lt, int64_t ldt, int64_t n, int64_t n0, const double* B,
                           int64_t k, int64_t ldb, double* X, int64_t ldx, void* ws,
                           int* status_dev, cudaStream_t s);
+
+// Device status word and device ordinal of a plan (for entry points that
+// live outside api.cu).
+int* plan_status_word(trsm_handle_t h);
+int plan_device(trsm_handle_t h);
 
 // Launch accounting (every kernel launch of the library goes through here).
 void count_launch(int64_t n = 1);
