@@ -40,6 +40,14 @@ extern "C" {
 #define TRSM_ECUDA (-4)      /* a CUDA runtime call failed (see trsm_last_cuda)  */
 #define TRSM_ETIMEOUT (-5)   /* a device-side dependency wait hit its time limit */
 #define TRSM_ENOSCRATCH (-6) /* trsm_solve_noalloc: workspace exceeds its fixed scratch */
+#define TRSM_ENOCONV (-7)    /* trsm_solve_mixed: refinement did not converge        */
+
+/* Low-precision formats of the mixed-precision solve (tensor-core updates). */
+#define TRSM_INNER_BF16 1
+#define TRSM_INNER_TF32 2
+/* Residual of the mixed-precision solve. */
+#define TRSM_RESIDUAL_SLICED 0 /* FP64-class, bf16 tensor cores, integer digit slices */
+#define TRSM_RESIDUAL_FP64 1   /* FP64 fused multiply-add                              */
 
 /* Opaque plan: the paper's L~ (Algorithm Diagonal-Inverter, Section 6.1) —
  * a device copy of L whose n0 x n0 diagonal blocks are replaced by their
@@ -102,6 +110,40 @@ int trsm_solve_ws(trsm_handle_t h, const double* B_dev, int64_t k, int64_t ldb, 
  * TRSM_ECUDA. */
 int trsm_solve_noalloc(trsm_handle_t h, const double* B_dev, int64_t k, int64_t ldb,
                        double* X_dev, int64_t ldx, void* stream);
+
+/* trsm_plan_mixed — adds the data of the mixed-precision solve to a plan
+ * (no counterpart in the paper, which works in exact arithmetic; the block
+ * structure is its Algorithm It-Inv-TRSM):
+ *   - the off-diagonal block columns L(T_{i+1}, S_i) in `inner` precision
+ *     (TRSM_INNER_BF16 or TRSM_INNER_TF32), for the tensor-core updates;
+ *   - the original diagonal blocks and diagonal of L in FP64;
+ *   - seven 6-bit integer digit planes of the strictly lower L, for the
+ *     FP64-class residual.
+ *   L_dev : the same matrix the plan was made from (n x n, ldl >= n).
+ * Synchronous.  Errors: TRSM_EINVAL, TRSM_ENOMEM, TRSM_ECUDA. */
+int trsm_plan_mixed(trsm_handle_t h, const double* L_dev, int64_t ldl, int inner, void* stream);
+
+/* trsm_solve_mixed — X = L^-1 B by iterative refinement around a
+ * low-precision solve: X = 0, R = B; repeat D = inner_solve(R), X += D,
+ * R = B - L X, until max|D| <= tol * max|X| or the updates stagnate (an
+ * update larger than half the previous one: the residual's accuracy floor
+ * is reached; accepted when max|D|/max|X| <= 1e-10).  inner_solve follows
+ * It-Inv-TRSM (Section 6.2) in its right-looking order: per block row,
+ * D_i = L~_ii W_i with the FP64 inverse (FP64 arithmetic), then the trailing
+ * update W(T_{i+1}) -= L(T_{i+1}, S_i) D_i as one tcgen05 GEMM in the plan's
+ * inner precision with FP32 accumulation (W is the FP32 copy of R).
+ *   residual : TRSM_RESIDUAL_SLICED or TRSM_RESIDUAL_FP64 (the latter needs
+ *              n0 a multiple of 32 when there is more than one block).
+ *   max_iter : >= 1 inner solves at most; tol >= 0.
+ *   iters, last_update (may be NULL): inner solves done, and the last
+ *              max|D| / max|X|.
+ *   B_dev must not alias X_dev.  Requires trsm_plan_mixed.  Synchronous.
+ * Errors: TRSM_EINVAL, TRSM_ENOMEM, TRSM_ECUDA, TRSM_ETIMEOUT, and
+ * TRSM_ENOCONV when the updates stop shrinking, turn non-finite or the
+ * iteration limit is reached (X then holds the last iterate). */
+int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k, int64_t ldb, double* X_dev,
+                     int64_t ldx, int residual, int max_iter, double tol, int* iters,
+                     double* last_update, void* stream);
 
 /* trsm_host — the whole method (trsm_plan + trsm_solve) on HOST buffers:
  * copies L and B to the device, plans, solves, copies X back and waits.

@@ -24,6 +24,11 @@ TRSM_ENOMEM = -3
 TRSM_ECUDA = -4
 TRSM_ETIMEOUT = -5
 TRSM_ENOSCRATCH = -6
+TRSM_ENOCONV = -7
+TRSM_INNER_BF16 = 1
+TRSM_INNER_TF32 = 2
+TRSM_RESIDUAL_SLICED = 0
+TRSM_RESIDUAL_FP64 = 1
 
 # Every symbol the header declares, with (restype, argtypes).
 _i64, _vp, _dp, _int = ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int
@@ -34,6 +39,9 @@ SIGNATURES = {
     "trsm_solve_workspace_size": (_int, [_vp, _i64, ctypes.POINTER(ctypes.c_size_t)]),
     "trsm_solve_ws": (_int, [_vp, _dp, _i64, _i64, _dp, _i64, _vp, ctypes.c_size_t, _vp]),
     "trsm_solve_noalloc": (_int, [_vp, _dp, _i64, _i64, _dp, _i64, _vp]),
+    "trsm_plan_mixed": (_int, [_vp, _dp, _i64, _int, _vp]),
+    "trsm_solve_mixed": (_int, [_vp, _dp, _i64, _i64, _dp, _i64, _int, _int, ctypes.c_double,
+                                ctypes.POINTER(_int), ctypes.POINTER(ctypes.c_double), _vp]),
     "trsm_host": (_int, [_dp, _i64, _i64, _i64, _dp, _i64, _i64, _dp, _i64, _vp]),
     "trtri_blocks": (_int, [_dp, _i64, _i64, _i64, _dp, _vp]),
     "trsm_destroy": (None, [_vp]),
@@ -45,6 +53,8 @@ SIGNATURES = {
     "trsm_error_string": (ctypes.c_char_p, [_int]),
     "trsm_launch_count": (_i64, [_int]),
     "trsm_fp64_peak": (_int, [_int, ctypes.POINTER(ctypes.c_double), _vp]),
+    "trsm_tc_gemm_selftest": (_int, [_int, _vp, _vp, _vp, _i64, _i64, _i64, _vp, _vp]),
+    "trsm_residual_sliced": (_int, [_dp, _i64, _i64, _dp, _i64, _i64, _dp, _i64, _dp, _i64, _vp, _vp]),
 }
 
 _lib = None
@@ -207,6 +217,38 @@ def trsm_solve_noalloc(plan, B, X):
                                              ctypes.c_void_p(X.data_ptr()), _ld(X), _stream(B)),
            "trsm_solve_noalloc")
     return X
+
+
+def trsm_plan_mixed(plan, L, inner="tf32"):
+    """Adds the mixed-precision data (inner = "bf16" or "tf32") to a plan made from L."""
+    L = _dev_matrix(L, "L")
+    code = {"bf16": TRSM_INNER_BF16, "tf32": TRSM_INNER_TF32}[inner]
+    _check(load_library().trsm_plan_mixed(plan.handle, ctypes.c_void_p(L.data_ptr()), _ld(L), code,
+                                          _stream(L)), "trsm_plan_mixed")
+    plan.inner = inner
+    return plan
+
+
+def trsm_solve_mixed(plan, B, X=None, residual="sliced", max_iter=30, tol=1e-14, raise_on_noconv=True):
+    """Iterative refinement around the low-precision solve.  Returns
+    (X, iterations, last max|D|/max|X|)."""
+    torch = _torch()
+    B = _dev_matrix(B, "B")
+    n, k = B.shape
+    if X is None:
+        X = torch.empty((k, n), dtype=torch.float64, device=B.device).t()
+    else:
+        X = _dev_matrix(X, "X")
+    it = ctypes.c_int()
+    upd = ctypes.c_double()
+    code = {"sliced": TRSM_RESIDUAL_SLICED, "fp64": TRSM_RESIDUAL_FP64}[residual]
+    rc = load_library().trsm_solve_mixed(plan.handle, ctypes.c_void_p(B.data_ptr()), k, _ld(B),
+                                         ctypes.c_void_p(X.data_ptr()), _ld(X), code, int(max_iter),
+                                         float(tol), ctypes.byref(it), ctypes.byref(upd), _stream(B))
+    if rc == TRSM_ENOCONV and not raise_on_noconv:
+        return X, it.value, upd.value
+    _check(rc, "trsm_solve_mixed")
+    return X, it.value, upd.value
 
 
 def trsm_solve_workspace_size(plan, k):

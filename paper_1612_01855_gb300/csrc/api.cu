@@ -11,12 +11,6 @@
 #include "internal.h"
 #include "trsm_gb300.h"
 
-struct trsm_plan_s {
-  int64_t n = 0, n0 = 0, N = 0, ldt = 0;
-  double* Lt = nullptr;  // L~: n x n, leading dimension ldt
-  int* status = nullptr; // sticky device status of solves
-  int device = 0;
-};
 
 namespace {
 
@@ -224,6 +218,7 @@ void trsm_destroy(trsm_handle_t h) {
   // cudaFree waits for the device work that may still use the memory.
   if (h->Lt) cudaFree(h->Lt);
   if (h->status) cudaFree(h->status);
+  trsm::mixed_release(h);
   if (cur != h->device) cudaSetDevice(cur);
   delete h;
 }
@@ -266,6 +261,7 @@ const char* trsm_error_string(int code) {
     case TRSM_ECUDA: return "CUDA runtime error";
     case TRSM_ETIMEOUT: return "device-side dependency wait timed out";
     case TRSM_ENOSCRATCH: return "workspace larger than the fixed no-allocation scratch (64 MiB)";
+    case TRSM_ENOCONV: return "iterative refinement did not converge";
     default: return "unknown status";
   }
 }

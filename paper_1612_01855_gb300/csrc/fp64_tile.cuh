@@ -33,15 +33,20 @@ __device__ __forceinline__ double ld_elem(const double* p) {
   if constexpr (kMutable) return __ldcg(p);
   else return __ldg(p);
 }
+template <bool kMutable>
+__device__ __forceinline__ double ld_elem(const float* p) {
+  if constexpr (kMutable) return static_cast<double>(__ldcg(p));
+  else return static_cast<double>(__ldg(p));
+}
 
 // acc(TM x TN) += A(rows [0,m), K [kbeg,kend)) * B(K [kbeg,kend), cols [0,nc))
 // A(r, t) = A[t*lda + r]; B(t, c) = B[c*ldb + t] (column-major).  Rows,
 // columns and K indices outside the given ranges contribute zero.
 // Thread (ty = tid/16, tx = tid%16) owns rows ty*TM.. and cols tx*TN.. of
 // the tile.  Every thread of the CTA must call this (it synchronises).
-template <bool kAMutable, bool kBMutable>
+template <bool kAMutable, bool kBMutable, class TB = double>
 __device__ __forceinline__ void tile_mma_fp64(const double* __restrict__ A, int64_t lda,
-                                              const double* __restrict__ B, int64_t ldb, int m,
+                                              const TB* __restrict__ B, int64_t ldb, int m,
                                               int nc, int64_t kbeg, int64_t kend, TileSmem& sm,
                                               double (&acc)[TM][TN]) {
   const int tid = threadIdx.x;

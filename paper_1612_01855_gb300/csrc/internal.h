@@ -8,6 +8,22 @@
 #include "trsm_gb300.h"
 
 namespace trsm {
+struct MixedPlan;
+}
+
+// The plan behind trsm_handle_t.
+struct trsm_plan_s {
+  int64_t n = 0, n0 = 0, N = 0, ldt = 0;
+  double* Lt = nullptr;   // L~: n x n, leading dimension ldt
+  int* status = nullptr;  // sticky device status of solves
+  int device = 0;
+  trsm::MixedPlan* mixed = nullptr;  // low-precision data (trsm_plan_mixed), or null
+};
+
+namespace trsm {
+
+// Frees the mixed-precision part of a plan (no-op when absent).
+void mixed_release(trsm_plan_s* h);
 
 // A diagonal block to invert in place: top-left element at A + off, order m;
 // row0 is its first row in the caller's numbering (for singular reports).

@@ -1,0 +1,421 @@
+// Mixed-precision solve with iterative refinement.
+//
+// The paper's method is exact-arithmetic TRSM; this path keeps its structure
+// (inverted FP64 diagonal blocks, matrix-multiply updates) but runs the bulk
+// of the updates on the tensor cores in low precision and wins the accuracy
+// back by classical iterative refinement:
+//
+//   X = 0, R = B
+//   repeat:  D = inner_solve(R)        low precision (see below)
+//            X += D                    FP64
+//            stop if max|D| <= tol max|X|
+//            R = B - L X               FP64-class residual
+//
+// inner_solve is the right-looking form of Algorithm It-Inv-TRSM: for every
+// block row i, D_i = L~_ii W_i with the FP64 inverse of the diagonal block
+// (DFMA tile kernel), then W(T_{i+1}) -= L(T_{i+1}, S_i) D_i as one
+// tcgen05 GEMM with bf16 or tf32 operands and FP32 accumulation; W is the
+// FP32 working copy of R.
+//
+// The residual is either the digit-sliced tensor-core product of sliced.cu
+// (about 2^-40 relative to |L||X|) or a plain FP64 DFMA product.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "fp64_tile.cuh"
+#include "internal.h"
+#include "sliced.h"
+#include "tc_host.h"
+#include "trsm_gb300.h"
+
+namespace trsm {
+
+struct MixedPlan {
+  int inner = 0;            // TRSM_INNER_BF16 or TRSM_INNER_TF32
+  int64_t n0p = 0;          // n0 rounded up to 8 (TMA row granule)
+  void* panels = nullptr;   // low-precision L(T_{i+1}, S_i), i = 0..N-2, row-major [rows][n0p]
+  double* diag = nullptr;   // diag(L)
+  double* dblk = nullptr;   // the original diagonal blocks of L, N x n0 x n0 (FP64 residual)
+  void* lsl = nullptr;      // digit planes of the strictly lower L
+  SlicedOperand Ls;
+};
+
+void mixed_release(trsm_plan_s* h) {
+  if (!h || !h->mixed) return;
+  MixedPlan* mp = h->mixed;
+  if (mp->panels) cudaFree(mp->panels);
+  if (mp->diag) cudaFree(mp->diag);
+  if (mp->dblk) cudaFree(mp->dblk);
+  if (mp->lsl) cudaFree(mp->lsl);
+  delete mp;
+  h->mixed = nullptr;
+}
+
+namespace {
+
+__host__ __device__ inline int64_t panel_off(int64_t i, int64_t n, int64_t n0, int64_t n0p) {
+  // sum over j < i of (n - (j + 1) n0) rows of n0p elements
+  return n0p * (i * n - n0 * (i * (i + 1) / 2));
+}
+
+template <bool kTf32>
+struct LowP;
+template <>
+struct LowP<false> {
+  using T = __nv_bfloat16;
+  __device__ static T from(double v) { return __double2bfloat16(v); }
+};
+template <>
+struct LowP<true> {
+  using T = float;  // tf32 kept in fp32 storage, rounded to tf32 (round-to-nearest-away)
+  __device__ static T from(double v) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(static_cast<float>(v)));
+    return __uint_as_float(r);
+  }
+};
+
+template <bool kTf32>
+__global__ void pack_panels_kernel(const double* __restrict__ L, int64_t ldl, int64_t n, int64_t n0,
+                                   int64_t n0p, typename LowP<kTf32>::T* __restrict__ out) {
+  const int64_t i = blockIdx.y;  // block column, 0 .. N-2
+  const int64_t rows = n - (i + 1) * n0;
+  if (rows <= 0) return;
+  typename LowP<kTf32>::T* P = out + panel_off(i, n, n0, n0p);
+  const int64_t total = rows * n0p;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = e / n0p, c = e % n0p;
+    const double v = (c < n0) ? L[(i * n0 + c) * ldl + (i + 1) * n0 + r] : 0.0;
+    P[e] = LowP<kTf32>::from(v);
+  }
+}
+
+__global__ void extract_diag_kernel(const double* __restrict__ L, int64_t ldl, int64_t n, int64_t n0,
+                                    double* __restrict__ diag, double* __restrict__ dblk) {
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < n * n0;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    // dblk: block b = e / (n0*n0), column c, row r (column-major n0 x n0)
+    const int64_t b = e / (n0 * n0), w = e % (n0 * n0), c = w / n0, r = w % n0;
+    const int64_t gr = b * n0 + r, gc = b * n0 + c;
+    dblk[e] = (gr < n && gc < n && r >= c) ? L[gc * ldl + gr] : 0.0;
+    if (e < n) diag[e] = L[e * ldl + e];
+  }
+}
+
+__global__ void to_float_kernel(const double* __restrict__ R, int64_t ldr, float* __restrict__ W,
+                                int64_t ldw, int64_t n, int64_t k) {
+  for (int64_t j = blockIdx.y; j < k; j += gridDim.y)
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+      W[j * ldw + i] = static_cast<float>(R[j * ldr + i]);
+}
+
+// D_i = L~_ii W_i for one 32 x 32 tile (FP64 DFMA), written to D (FP64) and,
+// transposed and rounded, to Dt (the B operand of the next update GEMM).
+template <bool kTf32>
+__global__ void __launch_bounds__(NTHREADS) s_step_kernel(const double* __restrict__ Lt, int64_t ldt,
+                                                          const float* __restrict__ W, int64_t ldw,
+                                                          double* __restrict__ D, int64_t ldd,
+                                                          typename LowP<kTf32>::T* __restrict__ Dt,
+                                                          int64_t n0p, int64_t s0, int m, int64_t k) {
+  __shared__ TileSmem sm;
+  const int r = blockIdx.x, j = blockIdx.y;
+  const int mr = min(TILE, m - r * TILE);
+  const int nc = static_cast<int>(imin64(TILE, k - static_cast<int64_t>(j) * TILE));
+  double acc[TM][TN];
+  zero_acc(acc);
+  tile_mma_fp64<false, false, float>(Lt + s0 * ldt + s0 + r * TILE, ldt,
+                                     W + static_cast<int64_t>(j) * TILE * ldw + s0, ldw, mr, nc, 0,
+                                     min((r + 1) * TILE, m), sm, acc);
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+#pragma unroll
+  for (int a = 0; a < TM; ++a) {
+    const int rr = ty * TM + a;
+    if (rr >= mr) continue;
+#pragma unroll
+    for (int b = 0; b < TN; ++b) {
+      const int cc = tx * TN + b;
+      if (cc >= nc) continue;
+      const int64_t col = static_cast<int64_t>(j) * TILE + cc;
+      const int64_t row = static_cast<int64_t>(r) * TILE + rr;
+      D[col * ldd + s0 + row] = acc[a][b];
+      Dt[col * n0p + row] = LowP<kTf32>::from(acc[a][b]);
+    }
+  }
+}
+
+// max that keeps a NaN once it has been seen (fmax would drop it)
+__device__ __forceinline__ double nanmax(double m, double v) { return (v > m || isnan(v)) ? v : m; }
+
+// X += D; folds max|D| and max|X| (as ordered bit patterns) into norms[0..1].
+__global__ void correct_kernel(double* __restrict__ X, int64_t ldx, const double* __restrict__ D,
+                               int64_t ldd, int64_t n, int64_t k,
+                               unsigned long long* __restrict__ norms) {
+  double dm = 0.0, xm = 0.0;
+  for (int64_t j = blockIdx.y; j < k; j += gridDim.y)
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+      const double d = D[j * ldd + i];
+      const double x = X[j * ldx + i] + d;
+      X[j * ldx + i] = x;
+      dm = nanmax(dm, fabs(d));
+      xm = nanmax(xm, fabs(x));
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    dm = nanmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+    xm = nanmax(xm, __shfl_xor_sync(0xffffffffu, xm, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    // NaN propagates as the largest pattern so that divergence is visible
+    const unsigned long long bd = isnan(dm) ? ~0ull : __double_as_longlong(dm);
+    const unsigned long long bx = isnan(xm) ? ~0ull : __double_as_longlong(xm);
+    atomicMax(norms, bd);
+    atomicMax(norms + 1, bx);
+  }
+}
+
+// R = B - L X in FP64: off the block diagonal L comes from L~, on it from
+// the saved original blocks.  One 32 x 32 tile of R per CTA.
+__global__ void __launch_bounds__(NTHREADS) residual_fp64_kernel(
+    const double* __restrict__ Lt, int64_t ldt, const double* __restrict__ dblk, int64_t n0,
+    const double* __restrict__ X, int64_t ldx, const double* __restrict__ B, int64_t ldb,
+    double* __restrict__ R, int64_t ldr, int64_t n, int64_t k) {
+  __shared__ TileSmem sm;
+  const int64_t r0 = static_cast<int64_t>(blockIdx.x) * TILE;
+  const int64_t j0 = static_cast<int64_t>(blockIdx.y) * TILE;
+  const int mr = static_cast<int>(imin64(TILE, n - r0));
+  const int nc = static_cast<int>(imin64(TILE, k - j0));
+  const int64_t b = r0 / n0, s0 = b * n0;  // the tile lies inside block row b (n0 % 32 == 0)
+  double acc[TM][TN];
+  zero_acc(acc);
+  if (s0 > 0)
+    tile_mma_fp64<false, false>(Lt + r0, ldt, X + j0 * ldx, ldx, mr, nc, 0, s0, sm, acc);
+  tile_mma_fp64<false, false>(dblk + b * n0 * n0 + (r0 - s0) - s0 * n0, n0, X + j0 * ldx, ldx, mr, nc,
+                              s0, r0 + mr, sm, acc);
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+#pragma unroll
+  for (int a = 0; a < TM; ++a) {
+    const int rr = ty * TM + a;
+    if (rr >= mr) continue;
+#pragma unroll
+    for (int c = 0; c < TN; ++c) {
+      const int cc = tx * TN + c;
+      if (cc >= nc) continue;
+      const int64_t row = r0 + rr, col = j0 + cc;
+      R[col * ldr + row] = B[col * ldb + row] - acc[a][c];
+    }
+  }
+}
+
+inline int64_t align4(int64_t x) { return (x + 3) / 4 * 4; }
+inline size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+dim3 grid_nk(int64_t n, int64_t k) {
+  return dim3(static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 64))),
+              static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(k, 65535))));
+}
+
+}  // namespace
+
+}  // namespace trsm
+
+using trsm::MixedPlan;
+
+extern "C" int trsm_plan_mixed(trsm_handle_t h, const double* L_dev, int64_t ldl, int inner, void* stream) {
+  if (!h || !L_dev || ldl < h->n || (inner != TRSM_INNER_BF16 && inner != TRSM_INNER_TF32))
+    return TRSM_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  trsm::mixed_release(h);
+  MixedPlan* mp = new (std::nothrow) MixedPlan;
+  if (!mp) return TRSM_ENOMEM;
+  h->mixed = mp;
+  const int64_t n = h->n, n0 = h->n0, N = h->N;
+  const bool tf32 = inner == TRSM_INNER_TF32;
+  mp->inner = inner;
+  mp->n0p = (n0 + 7) / 8 * 8;
+  const size_t esz = tf32 ? 4 : 2;
+  const size_t panel_elems = static_cast<size_t>(trsm::panel_off(N - 1, n, n0, mp->n0p));
+  cudaError_t e = cudaSuccess;
+  if (panel_elems > 0) e = cudaMalloc(&mp->panels, esz * panel_elems);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&mp->diag), sizeof(double) * n);
+  if (e == cudaSuccess)
+    e = cudaMalloc(reinterpret_cast<void**>(&mp->dblk), sizeof(double) * static_cast<size_t>(N * n0 * n0));
+  const size_t lbytes = trsm::sliced_operand_bytes(n, n);
+  if (e == cudaSuccess) e = cudaMalloc(&mp->lsl, lbytes);
+  double* tmp = nullptr;
+  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&tmp), sizeof(double) * n * n, s);
+  if (e == cudaSuccess && panel_elems > 0) {
+    dim3 grid(static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((n * mp->n0p + 255) / 256, 1024))),
+              static_cast<unsigned>(N - 1));
+    if (tf32)
+      trsm::pack_panels_kernel<true><<<grid, 256, 0, s>>>(L_dev, ldl, n, n0, mp->n0p,
+                                                          static_cast<float*>(mp->panels));
+    else
+      trsm::pack_panels_kernel<false><<<grid, 256, 0, s>>>(L_dev, ldl, n, n0, mp->n0p,
+                                                           static_cast<__nv_bfloat16*>(mp->panels));
+    trsm::count_launch();
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    trsm::extract_diag_kernel<<<1024, 256, 0, s>>>(L_dev, ldl, n, n0, mp->diag, mp->dblk);
+    trsm::count_launch();
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    mp->Ls = trsm::sliced_operand_view(mp->lsl, n, n);
+    e = trsm::slice_lower_rows(L_dev, ldl, n, mp->Ls, tmp, s);
+  }
+  if (tmp) cudaFreeAsync(tmp, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    trsm::mixed_release(h);
+    return e == cudaErrorMemoryAllocation ? TRSM_ENOMEM : TRSM_ECUDA;
+  }
+  return TRSM_SUCCESS;
+}
+
+extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k, int64_t ldb, double* X_dev,
+                                int64_t ldx, int residual, int max_iter, double tol, int* iters,
+                                double* last_update, void* stream) {
+  if (iters) *iters = 0;
+  if (last_update) *last_update = 0.0;
+  if (!h || !h->mixed || k < 0 || max_iter < 1 || !(tol >= 0.0)) return TRSM_EINVAL;
+  if (residual != TRSM_RESIDUAL_SLICED && residual != TRSM_RESIDUAL_FP64) return TRSM_EINVAL;
+  if (k == 0) return TRSM_SUCCESS;
+  if (!B_dev || !X_dev || ldb < h->n || ldx < h->n || B_dev == X_dev) return TRSM_EINVAL;
+  if (residual == TRSM_RESIDUAL_FP64 && h->n0 % trsm::TILE != 0 && h->N > 1) return TRSM_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  MixedPlan* mp = h->mixed;
+  const bool tf32 = mp->inner == TRSM_INNER_TF32;
+  const int64_t n = h->n, n0 = h->n0, N = h->N, n0p = mp->n0p;
+  const int64_t ld = trsm::align4(n);
+  const size_t esz = tf32 ? 4 : 2;
+
+  // workspace: R, D (FP64), W (FP32), Dt (low precision), X digit planes, norms, error word
+  size_t off = 0;
+  const size_t oR = off;
+  off = trsm::align256(off + sizeof(double) * ld * k);
+  const size_t oD = off;
+  off = trsm::align256(off + sizeof(double) * ld * k);
+  const size_t oW = off;
+  off = trsm::align256(off + sizeof(float) * ld * k);
+  const size_t oDt = off;
+  off = trsm::align256(off + esz * n0p * k);
+  const size_t oXs = off;
+  off = trsm::align256(off + trsm::sliced_operand_bytes(k, n));
+  const size_t oPart = off;
+  off = trsm::align256(off + trsm::sliced_partial_bytes(n, k));
+  const size_t oNorm = off;
+  off = trsm::align256(off + 2 * sizeof(unsigned long long) + sizeof(int));
+  unsigned char* ws = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), off, s);
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? TRSM_ENOMEM : TRSM_ECUDA;
+  double* R = reinterpret_cast<double*>(ws + oR);
+  double* D = reinterpret_cast<double*>(ws + oD);
+  float* W = reinterpret_cast<float*>(ws + oW);
+  void* Dt = ws + oDt;
+  trsm::SlicedOperand Xs = trsm::sliced_operand_view(ws + oXs, k, n);
+  unsigned long long* norms = reinterpret_cast<unsigned long long*>(ws + oNorm);
+  int* err = reinterpret_cast<int*>(ws + oNorm + 2 * sizeof(unsigned long long));
+
+  int rc = TRSM_SUCCESS;
+  e = cudaMemsetAsync(err, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(Dt, 0, esz * n0p * k, s);  // padding columns stay zero
+  if (e == cudaSuccess) e = cudaMemset2DAsync(X_dev, sizeof(double) * ldx, 0, sizeof(double) * n, k, s);
+  if (e == cudaSuccess) e = trsm::copy_panel(B_dev, ldb, R, ld, n, k, s);
+  double best = HUGE_VAL, prev = HUGE_VAL;
+  int it = 0;
+  for (it = 1; it <= max_iter && e == cudaSuccess; ++it) {
+    // ---- D = inner_solve(R) ----
+    trsm::to_float_kernel<<<trsm::grid_nk(n, k), 256, 0, s>>>(R, ld, W, ld, n, k);
+    trsm::count_launch();
+    for (int64_t i = 0; i < N && e == cudaSuccess; ++i) {
+      const int64_t s0 = i * n0;
+      const int m = static_cast<int>(std::min(n0, n - s0));
+      dim3 g(static_cast<unsigned>((m + trsm::TILE - 1) / trsm::TILE),
+             static_cast<unsigned>((k + trsm::TILE - 1) / trsm::TILE));
+      if (tf32)
+        trsm::s_step_kernel<true><<<g, trsm::NTHREADS, 0, s>>>(h->Lt, h->ldt, W, ld, D, ld,
+                                                                static_cast<float*>(Dt), n0p, s0, m, k);
+      else
+        trsm::s_step_kernel<false><<<g, trsm::NTHREADS, 0, s>>>(h->Lt, h->ldt, W, ld, D, ld,
+                                                                 static_cast<__nv_bfloat16*>(Dt), n0p, s0, m, k);
+      trsm::count_launch();
+      e = cudaGetLastError();
+      if (e == cudaSuccess && i < N - 1) {
+        const int64_t rows = n - (i + 1) * n0;
+        const unsigned char* P =
+            static_cast<const unsigned char*>(mp->panels) + esz * trsm::panel_off(i, n, n0, n0p);
+        e = trsm::tc::gemm_lowp(tf32, P, n0p, Dt, n0p, W + (i + 1) * n0, ld, rows, k, n0p, -1.f, 1.f, err, s);
+      }
+    }
+    // ---- X += D ----
+    if (e == cudaSuccess) e = cudaMemsetAsync(norms, 0, 2 * sizeof(unsigned long long), s);
+    if (e == cudaSuccess) {
+      trsm::correct_kernel<<<trsm::grid_nk(n, k), 256, 0, s>>>(X_dev, ldx, D, ld, n, k, norms);
+      trsm::count_launch();
+      e = cudaGetLastError();
+    }
+    unsigned long long hn[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hn, norms, sizeof(hn), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) break;
+    double dmax, xmax;
+    memcpy(&dmax, &hn[0], 8);
+    memcpy(&xmax, &hn[1], 8);
+    const double ratio = (hn[0] == ~0ull || hn[1] == ~0ull) ? NAN : (xmax > 0.0 ? dmax / xmax : 0.0);
+    if (last_update) *last_update = ratio;
+    if (iters) *iters = it;
+    if (ratio <= tol) break;
+    if (!(ratio < 1e3 * best) || !std::isfinite(ratio)) {
+      rc = TRSM_ENOCONV;  // diverging or non-finite
+      break;
+    }
+    // Stagnation: once an update fails to halve the previous one, the
+    // refinement has reached the accuracy the residual allows (its error
+    // floor) and further sweeps cannot improve X.  Accept the iterate when
+    // that floor is small, otherwise report non-convergence.
+    if (it >= 2 && ratio > 0.5 * prev) {
+      if (ratio > 1e-10) rc = TRSM_ENOCONV;
+      break;
+    }
+    prev = ratio;
+    best = std::min(best, ratio);
+    if (it == max_iter) {
+      rc = TRSM_ENOCONV;
+      break;
+    }
+    // ---- R = B - L X ----
+    if (residual == TRSM_RESIDUAL_SLICED) {
+      e = trsm::slice_rows(X_dev, ldx, Xs, s);
+      if (e == cudaSuccess)
+        e = trsm::sliced_residual(mp->Ls, mp->diag, 0, Xs, X_dev, ldx, B_dev, ldb, R, ld, ws + oPart, true,
+                                  err, s);
+    } else {
+      dim3 g(static_cast<unsigned>((n + trsm::TILE - 1) / trsm::TILE),
+             static_cast<unsigned>((k + trsm::TILE - 1) / trsm::TILE));
+      trsm::residual_fp64_kernel<<<g, trsm::NTHREADS, 0, s>>>(h->Lt, h->ldt, mp->dblk, n0, X_dev, ldx, B_dev,
+                                                              ldb, R, ld, n, k);
+      trsm::count_launch();
+      e = cudaGetLastError();
+    }
+  }
+  int herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(ws, s);
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? TRSM_ENOMEM : TRSM_ECUDA;
+  }
+  if (herr) return TRSM_ETIMEOUT;
+  return rc;
+}

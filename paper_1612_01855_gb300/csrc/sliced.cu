@@ -1,0 +1,353 @@
+// FP64-class residual R = B - L X on the BF16 tensor cores (tcgen05), by
+// splitting both factors into integer slices (the error-free splitting of
+// Ozaki, Ogita, Oishi and Rump, "Error-free transformations of matrix
+// multiplication by using fast routines of matrix multiplication and its
+// applications", Numer. Algorithms 59, 2012), restated for this hardware:
+//
+//   * every row of the strictly lower L (and every column of X) is cut along
+//     K into chunks of KC = 1024 elements; each (row, chunk) gets a
+//     power-of-two exponent e with max|a| < 2^e, and a / 2^e, rounded to
+//     42 fraction bits, is written as seven balanced base-64 digits
+//     d_0..d_6 (|d_0| <= 64, |d_s| <= 32 for s >= 1); plane s stores
+//     d_s 2^(-6s), exact in bf16, so that a = 2^(e-6) sum_s plane_s(a);
+//   * the tensor core multiplies plane pairs (s, u) with s + u <= 6 (28
+//     pairs, A plane fixed for consecutive MMAs) into five FP32 groups:
+//     d = s + u = 0, 1, 2, 3 each alone, and d >= 4 together.  Within one
+//     K chunk the sums of groups 0..3 are integer multiples of 2^(-6d)
+//     below 2^24 units (group 0: 1024 * 64^2 = 2^22; d = 1..3: at most
+//     1024 * 2^10 * (d + 3) <= 6.3e6), so they are exact; group 4 is
+//     2^-24 of the total, and the FP32 rounding of its 1024-term running sum
+//     stays near 2^-42 of the total;
+//   * after each chunk the epilogue adds the four groups in float-float
+//     arithmetic (about 48 bits), scales by 2^(eL + eX - 12) and
+//     accumulates (in a float-float partial buffer when a tile has more than
+//     one chunk); finally R = B - diag(L) X - (hi + lo) in FP64.
+// The diagonal of L stays out of the digit planes (it would set the row
+// exponents and push the off-diagonal entries into the low digits).  Each
+// digit expansion is exact to 2^(e-43), dropped pairs (s + u > 6) are below
+// 2^(eL+eX-41) per product, so entries much smaller than their (row, chunk)
+// maximum carry fewer significant bits; on the workloads here the residual
+// is accurate to about 2^-40 relative to |L| |X|.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "internal.h"
+#include "sliced.h"
+#include "tc_gemm.cuh"
+#include "tc_host.h"
+#include "trsm_gb300_engine.h"
+
+namespace trsm {
+namespace sliced {
+
+using tc::TileCfg;
+
+constexpr int BN = 96;
+constexpr int NG = 5;  // groups d = 0, 1, 2, 3 and d >= 4
+// bf16, 128-byte rows (64 elements of K per stage), one 196 KB stage of
+// 7 + 7 planes: the 28 pairs of one stage keep the tensor core busy long
+// enough that a deeper ring buys little, and two stages do not fit.  Five
+// groups of 96 FP32 columns fill 480 of the 512 TMEM columns.
+using Cfg = TileCfg<false, BN, kSlices, kSlices, NG, 1, 128>;
+static_assert(kChunk % Cfg::KB == 0, "chunk must be a whole number of stages");
+
+// Digit pairs (s, u), s + u <= kSlices - 1, in s-major order (the A plane
+// stays the same for consecutive MMAs, which the tensor core streams
+// faster), group min(s + u, 4).
+struct DigitPairs {
+  static constexpr int N = kSlices * (kSlices + 1) / 2;
+  __device__ static constexpr int s_of(int p) {
+    int s = 0, cnt = kSlices;
+    while (p >= cnt) {
+      p -= cnt;
+      ++s;
+      cnt = kSlices - s;
+    }
+    return s;
+  }
+  __device__ static constexpr int u_of(int p) {
+    int s = 0, cnt = kSlices;
+    while (p >= cnt) {
+      p -= cnt;
+      ++s;
+      cnt = kSlices - s;
+    }
+    return p;
+  }
+  __device__ static constexpr int a(int p) { return s_of(p); }
+  __device__ static constexpr int b(int p) { return u_of(p); }
+  __device__ static constexpr int g(int p) { return s_of(p) + u_of(p) < 4 ? s_of(p) + u_of(p) : 4; }
+};
+
+// ---------------------------------------------------------------- slicing
+// One warp per (row, chunk): rows hold K contiguous FP64 values (stride ld
+// between rows).  Writes kSlices bf16 digit planes (plane stride plane_elems,
+// row stride kp) and the chunk exponent.
+__global__ void slice_rows_kernel(const double* __restrict__ src, int64_t ld, int64_t rows, int64_t K,
+                                  int64_t nch, __nv_bfloat16* __restrict__ dst, int64_t kp,
+                                  int64_t plane_elems, int16_t* __restrict__ ex) {
+  const int64_t wid = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= rows * nch) return;
+  const int64_t r = wid / nch, c = wid % nch;
+  const double* p = src + r * ld;
+  const int64_t k0 = c * kChunk, k1 = (K < k0 + kChunk) ? K : k0 + kChunk;
+  double m = 0.0;
+  for (int64_t k = k0 + lane; k < k1; k += 32) m = fmax(m, fabs(p[k]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  int e = 0;
+  if (m > 0.0) frexp(m, &e);  // m = f 2^e, f in [0.5, 1): max|a| < 2^e
+  if (lane == 0) ex[r * nch + c] = static_cast<int16_t>(e);
+  // padding columns of the last chunk (up to kp) are written as zeros
+  const int64_t kw1 = (c == nch - 1) ? kp : k1;
+  for (int64_t k = k0 + lane; k < kw1; k += 32) {
+    // v = round(a 2^(42 - e)), |v| < 2^42; balanced base-64 digits from
+    // the least significant end with integer arithmetic
+    long long v = (k < K) ? __double2ll_rn(ldexp(p[k], 6 * kSlices - e)) : 0ll;
+    float dig[kSlices];
+#pragma unroll
+    for (int s = kSlices - 1; s >= 1; --s) {
+      long long rem = v & 63;
+      if (rem >= 32) rem -= 64;
+      v = (v - rem) >> kDigitBits;
+      dig[s] = static_cast<float>(rem);
+    }
+    dig[0] = static_cast<float>(v);  // |d_0| <= 64
+#pragma unroll
+    for (int s = 0; s < kSlices; ++s)
+      dst[s * plane_elems + r * kp + k] =
+          __float2bfloat16_rn(dig[s] * __int_as_float((127 - kDigitBits * s) << 23));
+  }
+}
+
+// Row-major copy of the strictly lower triangle of a column-major n x n
+// matrix (zeros on and above the diagonal).  The diagonal is kept out of the
+// digit planes: it usually dominates its row, and fixed-point digits
+// relative to the row maximum would cost the off-diagonal entries their low
+// bits; the epilogue applies it in FP64 instead.
+__global__ void transpose_lower_kernel(const double* __restrict__ L, int64_t ldl, double* __restrict__ T,
+                                       int64_t n) {
+  __shared__ double tile[32][33];
+  const int64_t bi = blockIdx.y * 32, bj = blockIdx.x * 32;  // source rows bi.., cols bj..
+  const int tx = threadIdx.x, ty = threadIdx.y;               // 32 x 8
+  for (int yy = ty; yy < 32; yy += 8) {
+    const int64_t i = bi + tx, j = bj + yy;
+    double v = 0.0;
+    if (i < n && j < n && i > j) v = L[j * ldl + i];
+    tile[yy][tx] = v;  // tile[col][row]
+  }
+  __syncthreads();
+  for (int yy = ty; yy < 32; yy += 8) {
+    const int64_t i = bi + yy, j = bj + tx;  // write row i, column j of T (row-major)
+    if (i < n && j < n) T[i * n + j] = tile[tx][yy];
+  }
+}
+
+// ---------------------------------------------------------------- epilogue
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// (h, l) += (bh, bl) in float-float arithmetic.
+__device__ __forceinline__ void ff_add(float& h, float& l, float bh, float bl) {
+  float s, e;
+  two_sum(h, bh, s, e);
+  e += l + bl;
+  h = s + e;
+  l = e - (h - s);
+}
+
+struct ResidualEpi {
+  const double* B;
+  int64_t ldb;
+  const double* Ld;  // L (diagonal read at Ld[i*ldl + i]; ldl = 0: a vector of the diagonal)
+  int64_t ldl;
+  const double* X;
+  int64_t ldx;
+  double* R;
+  int64_t ldr;
+  float2* part;  // float-float partial sums (column-major, ld = M), for tiles of several chunks
+  const int16_t* eA;  // [M][nch]
+  const int16_t* eB;  // [N][nch]
+  int64_t nch;
+  int M, N, K;  // R is M x N, L is M x K
+  int lower;
+  struct State {
+    float ph[16], pl[16];
+  };
+  __device__ void k_range(int tm, int, int& kb0, int& kb1, int& chunk) const {
+    const int kend = lower ? min(K, (tm + 1) * 128) : K;
+    kb0 = 0;
+    kb1 = (kend + Cfg::KB - 1) / Cfg::KB;
+    chunk = kChunk / Cfg::KB;
+  }
+  __device__ void init(State&) const {}
+  __device__ void group(State& st, int, int, int, int, int, int g, const float (&v)[16]) const {
+    if (g == 0) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        st.ph[j] = v[j];
+        st.pl[j] = 0.f;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) ff_add(st.ph[j], st.pl[j], v[j], 0.f);
+    }
+  }
+  __device__ void slab_done(State& st, int tm, int tn, int c, int row, int sl) const {
+    const int grow = tm * 128 + row;
+    if (grow >= M) return;
+    const int ea = eA[static_cast<int64_t>(grow) * nch + c];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int col = tn * BN + sl * 16 + j;
+      if (col >= N) continue;
+      const int sc = ea + __ldg(eB + static_cast<int64_t>(col) * nch + c) - 2 * kDigitBits;
+      float h = ldexpf(st.ph[j], sc), l = ldexpf(st.pl[j], sc);
+      float2* pp = part + static_cast<int64_t>(col) * M + grow;
+      if (c > 0) {
+        const float2 o = *pp;
+        ff_add(h, l, o.x, o.y);
+      }
+      *pp = make_float2(h, l);
+    }
+  }
+  __device__ void finish(State&, int tm, int tn, int nchunks, int row) const {
+    const int grow = tm * 128 + row;
+    if (grow >= M) return;
+    for (int col0 = 0; col0 < BN; ++col0) {
+      const int col = tn * BN + col0;
+      if (col >= N) break;
+      double lx = 0.0;
+      if (nchunks > 0) {
+        const float2 o = part[static_cast<int64_t>(col) * M + grow];
+        lx = static_cast<double>(o.x) + static_cast<double>(o.y);
+      }
+      const double t = fma(-Ld[static_cast<int64_t>(grow) * ldl + grow],
+                           X[static_cast<int64_t>(col) * ldx + grow],
+                           B[static_cast<int64_t>(col) * ldb + grow]);
+      R[static_cast<int64_t>(col) * ldr + grow] = t - lx;
+    }
+  }
+};
+
+}  // namespace sliced
+
+// ---------------------------------------------------------------- host
+size_t sliced_operand_bytes(int64_t rows, int64_t K) {
+  const int64_t kp = (K + 7) / 8 * 8;
+  const int64_t nch = (K + kChunk - 1) / kChunk;
+  size_t b = sizeof(__nv_bfloat16) * static_cast<size_t>(kSlices) * rows * kp;
+  b = (b + 255) / 256 * 256;
+  b += sizeof(int16_t) * static_cast<size_t>(rows) * nch;
+  return (b + 255) / 256 * 256;
+}
+
+SlicedOperand sliced_operand_view(void* base, int64_t rows, int64_t K) {
+  SlicedOperand o;
+  o.rows = rows;
+  o.K = K;
+  o.kp = (K + 7) / 8 * 8;
+  o.nch = (K + kChunk - 1) / kChunk;
+  o.digits = static_cast<__nv_bfloat16*>(base);
+  size_t b = sizeof(__nv_bfloat16) * static_cast<size_t>(kSlices) * rows * o.kp;
+  b = (b + 255) / 256 * 256;
+  o.ex = reinterpret_cast<int16_t*>(static_cast<unsigned char*>(base) + b);
+  return o;
+}
+
+cudaError_t slice_rows(const double* src, int64_t ld, const SlicedOperand& o, cudaStream_t s) {
+  const int64_t warps = o.rows * o.nch;
+  const int64_t threads = warps * 32;
+  const unsigned blocks = static_cast<unsigned>((threads + 255) / 256);
+  sliced::slice_rows_kernel<<<blocks, 256, 0, s>>>(src, ld, o.rows, o.K, o.nch, o.digits, o.kp,
+                                                   o.rows * o.kp, o.ex);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t slice_lower_rows(const double* L, int64_t ldl, int64_t n, const SlicedOperand& o,
+                             double* tmp_rowmajor, cudaStream_t s) {
+  dim3 grid(static_cast<unsigned>((n + 31) / 32), static_cast<unsigned>((n + 31) / 32));
+  sliced::transpose_lower_kernel<<<grid, dim3(32, 8), 0, s>>>(L, ldl, tmp_rowmajor, n);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return slice_rows(tmp_rowmajor, n, o, s);
+}
+
+size_t sliced_partial_bytes(int64_t n, int64_t k) { return sizeof(float2) * static_cast<size_t>(n) * k; }
+
+cudaError_t sliced_residual(const SlicedOperand& Ls, const double* L, int64_t ldl, const SlicedOperand& Xs,
+                            const double* X, int64_t ldx, const double* B, int64_t ldb, double* R,
+                            int64_t ldr, void* partial, bool lower, int* err, cudaStream_t s) {
+  using sliced::Cfg;
+  CUtensorMap ma, mb;
+  if (!tc::make_kmajor_map(&ma, Ls.digits, false, Ls.kp, Ls.rows, Ls.kp, kSlices, Ls.rows * Ls.kp, 128,
+                           kSlices, 128))
+    return cudaErrorInvalidValue;
+  if (!tc::make_kmajor_map(&mb, Xs.digits, false, Xs.kp, Xs.rows, Xs.kp, kSlices, Xs.rows * Xs.kp,
+                           sliced::BN, kSlices, 128))
+    return cudaErrorInvalidValue;
+  sliced::ResidualEpi epi;
+  epi.B = B;
+  epi.ldb = ldb;
+  epi.Ld = L;
+  epi.ldl = ldl;
+  epi.X = X;
+  epi.ldx = ldx;
+  epi.R = R;
+  epi.ldr = ldr;
+  epi.part = static_cast<float2*>(partial);
+  epi.eA = Ls.ex;
+  epi.eB = Xs.ex;
+  epi.nch = Ls.nch;
+  epi.M = static_cast<int>(Ls.rows);
+  epi.N = static_cast<int>(Xs.rows);
+  epi.K = static_cast<int>(Ls.K);
+  epi.lower = lower ? 1 : 0;
+  auto kern = tc::tc_tile_kernel<Cfg, sliced::DigitPairs, sliced::ResidualEpi>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(Cfg::SMEM_BYTES));
+  if (e != cudaSuccess) return e;
+  dim3 grid(static_cast<unsigned>((Ls.rows + 127) / 128),
+            static_cast<unsigned>((Xs.rows + sliced::BN - 1) / sliced::BN));
+  kern<<<grid, 192, Cfg::SMEM_BYTES, s>>>(ma, mb, epi, err);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace trsm
+
+extern "C" int trsm_residual_sliced(const double* L_dev, int64_t n, int64_t ldl, const double* X_dev,
+                                    int64_t k, int64_t ldx, const double* B_dev, int64_t ldb,
+                                    double* R_dev, int64_t ldr, int* err_dev, void* stream) {
+  if (!L_dev || !X_dev || !B_dev || !R_dev || !err_dev || n < 1 || k < 1 || ldl < n || ldx < n ||
+      ldb < n || ldr < n)
+    return -1;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t lb = trsm::sliced_operand_bytes(n, n);
+  const size_t xb = trsm::sliced_operand_bytes(k, n);
+  const size_t tb = sizeof(double) * static_cast<size_t>(n) * n;
+  const size_t pb = (trsm::sliced_partial_bytes(n, k) + 255) / 256 * 256;
+  unsigned char* buf = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&buf), lb + xb + tb + pb, s);
+  if (e != cudaSuccess) return -3;
+  trsm::SlicedOperand Ls = trsm::sliced_operand_view(buf, n, n);
+  trsm::SlicedOperand Xs = trsm::sliced_operand_view(buf + lb, k, n);
+  e = trsm::slice_lower_rows(L_dev, ldl, n, Ls, reinterpret_cast<double*>(buf + lb + xb), s);
+  if (e == cudaSuccess) e = trsm::slice_rows(X_dev, ldx, Xs, s);
+  if (e == cudaSuccess)
+    e = trsm::sliced_residual(Ls, L_dev, ldl, Xs, X_dev, ldx, B_dev, ldb, R_dev, ldr, buf + lb + xb + tb,
+                              true, err_dev, s);
+  cudaFreeAsync(buf, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return -4;
+  }
+  return 0;
+}

@@ -154,15 +154,18 @@ __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (SBO); LBO unused for this layout; descriptor version 1.
-__device__ __forceinline__ uint64_t desc_kmajor_sw128(uint32_t saddr) {
+// Shared-memory matrix descriptor, K-major, swizzled: rows of ROWB bytes
+// (128 -> 128-byte swizzle, 64 -> 64-byte swizzle), 8-row groups 8*ROWB
+// bytes apart (SBO); LBO unused for these layouts; descriptor version 1.
+template <int ROWB>
+__device__ __forceinline__ uint64_t desc_kmajor(uint32_t saddr) {
+  static_assert(ROWB == 128 || ROWB == 64, "unsupported row width");
   uint64_t d = 0;
   d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
   d |= static_cast<uint64_t>(1) << 16;
-  d |= static_cast<uint64_t>(1024 >> 4) << 32;
+  d |= static_cast<uint64_t>((8 * ROWB) >> 4) << 32;
   d |= static_cast<uint64_t>(1) << 46;
-  d |= static_cast<uint64_t>(2) << 61;
+  d |= static_cast<uint64_t>(ROWB == 128 ? 2 : 4) << 61;
   return d;
 }
 

@@ -34,7 +34,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 bool make_kmajor_map(CUtensorMap* map, const void* base, bool tf32, int64_t K, int64_t rows,
                      int64_t ld_elems, int64_t slices, int64_t slice_stride_elems, int box_rows,
-                     int box_slices) {
+                     int box_slices, int row_bytes) {
   auto fn = encode_fn();
   if (!fn) return false;
   const int esz = tf32 ? 4 : 2;
@@ -42,12 +42,13 @@ bool make_kmajor_map(CUtensorMap* map, const void* base, bool tf32, int64_t K, i
                         static_cast<cuuint64_t>(slices)};
   cuuint64_t strides[2] = {static_cast<cuuint64_t>(ld_elems * esz),
                            static_cast<cuuint64_t>(slice_stride_elems * esz)};
-  cuuint32_t box[3] = {static_cast<cuuint32_t>(128 / esz), static_cast<cuuint32_t>(box_rows),
+  cuuint32_t box[3] = {static_cast<cuuint32_t>(row_bytes / esz), static_cast<cuuint32_t>(box_rows),
                        static_cast<cuuint32_t>(box_slices)};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = fn(map, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
                   const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  row_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -61,34 +62,37 @@ struct StoreF32Epi {
   int64_t ldc;
   int M, N, nkb;
   float alpha, beta;
+  struct State {};
   __device__ void k_range(int, int, int& kb0, int& kb1, int& chunk) const {
     kb0 = 0;
     kb1 = nkb;
     chunk = nkb > 0 ? nkb : 1;
   }
-  template <int NG>
-  __device__ void slab(int tm, int tn, int, int, int row, int col0, const float (&v)[NG][16]) const {
+  __device__ void init(State&) const {}
+  __device__ void group(State&, int tm, int tn, int, int row, int sl, int, const float (&v)[16]) const {
     const int r = tm * 128 + row;
     if (r >= M) return;
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
-      const int col = tn * BN + col0 + j;
+      const int col = tn * BN + sl * 16 + j;
       if (col < N) {
         float* p = C + static_cast<int64_t>(col) * ldc + r;
-        *p = (beta == 0.f) ? alpha * v[0][j] : alpha * v[0][j] + beta * *p;
+        *p = (beta == 0.f) ? alpha * v[j] : alpha * v[j] + beta * *p;
       }
     }
   }
-  __device__ void finish(int, int, int, int) const {}
+  __device__ void slab_done(State&, int, int, int, int, int) const {}
+  __device__ void finish(State&, int, int, int, int) const {}
 };
 
 template <bool kTf32, int BN>
-cudaError_t plain_gemm(const void* A, const void* B, float* C, int64_t M, int64_t N, int64_t K,
-                       int64_t ldc, float alpha, float beta, int* err, cudaStream_t s) {
+cudaError_t plain_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t M,
+                       int64_t N, int64_t K, int64_t ldc, float alpha, float beta, int* err,
+                       cudaStream_t s) {
   using Cfg = TileCfg<kTf32, BN, 1, 1, 1, 4>;
   CUtensorMap ma, mb;
-  if (!make_kmajor_map(&ma, A, kTf32, K, M, K, 1, M * K, 128, 1)) return cudaErrorInvalidValue;
-  if (!make_kmajor_map(&mb, B, kTf32, K, N, K, 1, N * K, BN, 1)) return cudaErrorInvalidValue;
+  if (!make_kmajor_map(&ma, A, kTf32, K, M, lda, 1, M * lda, 128, 1, 128)) return cudaErrorInvalidValue;
+  if (!make_kmajor_map(&mb, B, kTf32, K, N, ldb, 1, N * ldb, BN, 1, 128)) return cudaErrorInvalidValue;
   StoreF32Epi<BN> epi{C, ldc, static_cast<int>(M), static_cast<int>(N),
                       static_cast<int>((K + Cfg::KB - 1) / Cfg::KB), alpha, beta};
   auto kern = tc_tile_kernel<Cfg, OnePair, StoreF32Epi<BN>>;
@@ -103,6 +107,14 @@ cudaError_t plain_gemm(const void* A, const void* B, float* C, int64_t M, int64_
 
 }  // namespace
 
+cudaError_t gemm_lowp(bool tf32, const void* A, int64_t lda, const void* B, int64_t ldb, float* C,
+                      int64_t ldc, int64_t M, int64_t N, int64_t K, float alpha, float beta, int* err,
+                      cudaStream_t s) {
+  if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+  return tf32 ? plain_gemm<true, 128>(A, lda, B, ldb, C, M, N, K, ldc, alpha, beta, err, s)
+              : plain_gemm<false, 128>(A, lda, B, ldb, C, M, N, K, ldc, alpha, beta, err, s);
+}
+
 }  // namespace tc
 }  // namespace trsm
 
@@ -112,10 +124,8 @@ extern "C" int trsm_tc_gemm_selftest(int tf32, const void* A_dev, const void* B_
   if ((tf32 && K % 4) || (!tf32 && K % 8)) return -1;  // TMA: 16-byte row strides
   if (((uintptr_t)A_dev | (uintptr_t)B_dev) & 15) return -1;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaError_t e = tf32 ? trsm::tc::plain_gemm<true, 128>(A_dev, B_dev, C_dev, M, N, K, M, 1.f, 0.f,
-                                                          err_dev, s)
-                       : trsm::tc::plain_gemm<false, 128>(A_dev, B_dev, C_dev, M, N, K, M, 1.f, 0.f,
-                                                           err_dev, s);
+  cudaError_t e = trsm::tc::gemm_lowp(tf32 != 0, A_dev, K, B_dev, K, C_dev, M, M, N, K, 1.f, 0.f,
+                                      err_dev, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return -4;

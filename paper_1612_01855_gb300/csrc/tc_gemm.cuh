@@ -20,7 +20,7 @@
 namespace trsm {
 namespace tc {
 
-template <bool kTf32_, int BN_, int NSA_, int NSB_, int NG_, int STAGES_>
+template <bool kTf32_, int BN_, int NSA_, int NSB_, int NG_, int STAGES_, int ROWB_ = 128>
 struct TileCfg {
   static constexpr bool kTf32 = kTf32_;
   static constexpr int BN = BN_;
@@ -28,10 +28,12 @@ struct TileCfg {
   static constexpr int NSB = NSB_;
   static constexpr int NG = NG_;
   static constexpr int STAGES = STAGES_;
-  static constexpr int KB = kTf32 ? 32 : 64;  // K elements per stage
+  static constexpr int ROWB = ROWB_;                // bytes of K per shared-memory row
   static constexpr int ESIZE = kTf32 ? 4 : 2;
-  static constexpr uint32_t A_SLICE = 128u * 128u;
-  static constexpr uint32_t B_SLICE = static_cast<uint32_t>(BN) * 128u;
+  static constexpr int KB = ROWB / ESIZE;           // K elements per stage
+  static constexpr int MMAS = ROWB / 32;            // MMAs per stage (32 bytes of K each)
+  static constexpr uint32_t A_SLICE = 128u * ROWB;
+  static constexpr uint32_t B_SLICE = static_cast<uint32_t>(BN) * ROWB;
   static constexpr uint32_t STAGE_BYTES = NSA * A_SLICE + NSB * B_SLICE;
   static constexpr uint32_t TMEM_COLS_USED = NG * BN;
   static constexpr uint32_t TMEM_COLS = TMEM_COLS_USED <= 32    ? 32
@@ -120,10 +122,10 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
           for (int p = 0; p < Pairs::N; ++p) {
             const int g = Pairs::g(p);
-            const uint64_t ad = desc_kmajor_sw128(sa + Pairs::a(p) * Cfg::A_SLICE);
-            const uint64_t bd = desc_kmajor_sw128(sb + Pairs::b(p) * Cfg::B_SLICE);
+            const uint64_t ad = desc_kmajor<Cfg::ROWB>(sa + Pairs::a(p) * Cfg::A_SLICE);
+            const uint64_t bd = desc_kmajor<Cfg::ROWB>(sb + Pairs::b(p) * Cfg::B_SLICE);
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
+            for (int kk = 0; kk < Cfg::MMAS; ++kk) {
               // +32 bytes along K per MMA (16 bf16 or 8 tf32): start address field += 2
               mma<Cfg::kTf32>(tbase + static_cast<uint32_t>(g * BN), ad + 2u * kk, bd + 2u * kk, IDESC,
                               ((started >> g) & 1u) | (kk > 0 ? 1u : 0u));
@@ -139,27 +141,32 @@ __global__ void __launch_bounds__(192, 1)
     // epilogue warps 2..5: TMEM lane quarter q = warp % 4
     const int q = warp & 3;
     const int row = q * 32 + lane;
+    typename Epi::State st;
+    epi.init(st);
     for (int c = 0; c < nchunks; ++c) {
       if (!mbar_wait(&tfull_bar, c & 1, abort_flag)) break;
       tc_fence_after();
-#pragma unroll 1
-      for (int col0 = 0; col0 < BN; col0 += 16) {
-        float v[NG][16];
+#pragma unroll
+      for (int sl = 0; sl < BN / 16; ++sl) {
+        // the epilogue consumes the NG groups of a 16-column slab one group
+        // at a time (keeps the register footprint at 16 values per group)
 #pragma unroll
         for (int g = 0; g < NG; ++g) {
           uint32_t r[16];
-          tmem_ld16(tbase + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(g * BN + col0), r);
+          tmem_ld16(tbase + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(g * BN + sl * 16), r);
           tmem_wait_ld();
+          float v[16];
 #pragma unroll
-          for (int j = 0; j < 16; ++j) v[g][j] = __uint_as_float(r[j]);
+          for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+          epi.group(st, tm, tn, c, row, sl, g, v);
         }
-        epi.slab(tm, tn, c, kb0 + c * kb_chunk, row, col0, v);
+        epi.slab_done(st, tm, tn, c, row, sl);
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty_bar);
     }
-    epi.finish(tm, tn, nchunks, row);
+    epi.finish(st, tm, tn, nchunks, row);
   }
   __syncthreads();
   if (warp == 1) {

@@ -1,6 +1,7 @@
 // Host helpers for the tcgen05 kernels.
 #pragma once
 #include <cuda.h>
+#include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace trsm {
@@ -9,11 +10,20 @@ namespace tc {
 // Tensor map of a K-major operand: `slices` matrices of `rows` rows, each
 // row holding K elements (bf16, or fp32 read as tf32) at a row stride of
 // ld_elems, consecutive slices slice_stride_elems apart.  The box is one
-// 128-byte row of K by box_rows rows by box_slices slices, 128-byte swizzle,
-// zero fill outside the matrix.  Requires 16-byte aligned base and strides.
+// row_bytes-wide (128 or 64) row of K by box_rows rows by box_slices
+// slices, swizzled by row_bytes, zero fill outside the matrix.  Requires
+// 16-byte aligned base and strides.
 bool make_kmajor_map(CUtensorMap* map, const void* base, bool tf32, int64_t K, int64_t rows,
                      int64_t ld_elems, int64_t slices, int64_t slice_stride_elems, int box_rows,
-                     int box_slices);
+                     int box_slices, int row_bytes);
+
+// C (fp32, column-major, ldc) = alpha * A B^T + beta * C on the tensor cores:
+// A is M x K and B is N x K, both K-major (row strides lda, ldb elements,
+// multiples of 8 for bf16 / 4 for tf32, 16-byte aligned bases); tf32 reads
+// fp32 storage.  128 x 128 tiles, 4-stage TMA ring.
+cudaError_t gemm_lowp(bool tf32, const void* A, int64_t lda, const void* B, int64_t ldb, float* C,
+                      int64_t ldc, int64_t M, int64_t N, int64_t K, float alpha, float beta, int* err,
+                      cudaStream_t s);
 
 }  // namespace tc
 }  // namespace trsm
