@@ -126,6 +126,64 @@ def cpu_oracle_rate(data, shapes, budget_s, max_cols=None):
     return flops / secs / 1e12, "; ".join(desc), cores
 
 
+def precision_study(g, torch, n, k, n0, cs, inners, s_modes, dd_cols=2, stream=None, quick=False):
+    """Mixed-precision refinement on the graded-diagonal workload (diagonal
+    geomspace(1, 10^-c), permuted): time, iterations and forward error
+    against the double-double oracle on sampled columns, beside the FP64
+    solve of the same system."""
+    import oracle
+    from paper_1612_01855_gb300 import inputs
+    out = []
+    for c in cs:
+        L, B = inputs.graded_diagonal(n, k, c, seed=0)
+        cols = np.linspace(0, k - 1, dd_cols).astype(int)
+        hi, lo = oracle.forward_subst_dd(L, B[:, cols])
+        ref = hi + lo
+        ref_ok = bool(np.all(np.isfinite(ref)))
+        Ld, Bd = to_dev(L, torch), to_dev(B, torch)
+        del L
+
+        def ferr(X):
+            got = X[:, torch.from_numpy(cols).cuda()].cpu().numpy()
+            if not ref_ok or not np.all(np.isfinite(got)):
+                return None
+            return float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+
+        plan = g.trsm_plan(Ld, n0)
+        X64 = g.trsm_solve(plan, Bd)
+        g.trsm_sync_status(plan)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        X64 = g.trsm_solve(plan, Bd, X=X64)
+        e1.record()
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1)
+        rec = {"c": c, "n": n, "k": k, "n0": n0, "fp64_solve_ms": round(t64, 2),
+               "fp64_fwd_err": ferr(X64), "dd_reference_finite": ref_ok, "mixed": []}
+        for inner in inners:
+            g.trsm_plan_mixed(plan, Ld, inner)
+            for s32 in s_modes:
+                X, it, upd = g.trsm_solve_mixed(plan, Bd, residual="sliced", max_iter=30, tol=1e-12,
+                                                raise_on_noconv=False, s_fp32=s32)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                X, it, upd = g.trsm_solve_mixed(plan, Bd, X=X, residual="sliced", max_iter=30, tol=1e-12,
+                                                raise_on_noconv=False, s_fp32=s32)
+                torch.cuda.synchronize()
+                tm = (time.perf_counter() - t0) * 1e3
+                fe = ferr(X)
+                rec["mixed"].append({"inner": inner, "s_step": "fp32" if s32 else "fp64",
+                                     "residual": "sliced-bf16", "ms": round(tm, 2),
+                                     "tflops_equiv": round(float(n) * n * k / (tm * 1e-3) / 1e12, 3),
+                                     "iterations": it, "last_update": upd, "fwd_err": fe,
+                                     "converged": bool(fe is not None and fe <= 1e-10),
+                                     "speedup_vs_fp64": round(t64 / tm, 3)})
+        plan.destroy()
+        del Ld, Bd, X64
+        out.append(rec)
+    return out
+
+
 def run_reference(args, rank, world):
     """--impl reference: the CPU oracle on the host cores, bounded samples."""
     if rank != 0:
@@ -286,6 +344,14 @@ def run_ours(args, rank, world, local):
         cpu = {"value": rate, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
                "sample": sample + " (forward substitution, FP64, OpenMP over columns)"}
 
+    mixed = None
+    if rank == 0 and not args.no_mixed and not args.shapes:
+        mixed = precision_study(g, torch, 16384, 4096, 256, [2], ["tf32"], [False, True], dd_cols=2)
+
+    if args.precision and rank == 0:
+        for rec in precision_study(g, torch, 16384, 4096, 256, [2, 4, 6], ["tf32", "bf16"], [False, True]):
+            print(json.dumps({"precision_study": True, **rec}), flush=True)
+
     if args.sweep and rank == 0:
         for (L, B), (n, k), (Ld, Bd), X in zip(data, shapes, dev_in, outs):
             for n0 in SWEEP_N0:
@@ -328,6 +394,7 @@ def run_ours(args, rank, world, local):
                                         f" = {SMS * 4 * NOMINAL_SM_MHZ / 1e6:.3f}",
                          "traffic": None},
             "parity_max_rel_err": err,
+            "mixed_precision": mixed,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "gpu_launches": launches,
@@ -347,6 +414,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision refinement figure")
+    ap.add_argument("--precision", action="store_true", help="print the full c x inner x s-step study")
     ap.add_argument("--shapes", default="", help="override workload, e.g. 6144:1024:256 (not a bench line)")
     args = ap.parse_args()
     rank, world, local = dist_env()

@@ -48,6 +48,9 @@ extern "C" {
 /* Residual of the mixed-precision solve. */
 #define TRSM_RESIDUAL_SLICED 0 /* FP64-class, bf16 tensor cores, integer digit slices */
 #define TRSM_RESIDUAL_FP64 1   /* FP64 fused multiply-add                              */
+/* Flag or-ed into `residual`: apply the FP64 inverses of the diagonal blocks
+ * in FP32 arithmetic inside the inner solve (default: FP64 arithmetic). */
+#define TRSM_SOLVE_S_FP32 0x100
 
 /* Opaque plan: the paper's L~ (Algorithm Diagonal-Inverter, Section 6.1) —
  * a device copy of L whose n0 x n0 diagonal blocks are replaced by their
@@ -133,7 +136,8 @@ int trsm_plan_mixed(trsm_handle_t h, const double* L_dev, int64_t ldl, int inner
  * update W(T_{i+1}) -= L(T_{i+1}, S_i) D_i as one tcgen05 GEMM in the plan's
  * inner precision with FP32 accumulation (W is the FP32 copy of R).
  *   residual : TRSM_RESIDUAL_SLICED or TRSM_RESIDUAL_FP64 (the latter needs
- *              n0 a multiple of 32 when there is more than one block).
+ *              n0 a multiple of 32 when there is more than one block),
+ *              optionally or-ed with TRSM_SOLVE_S_FP32.
  *   max_iter : >= 1 inner solves at most; tol >= 0.
  *   iters, last_update (may be NULL): inner solves done, and the last
  *              max|D| / max|X|.

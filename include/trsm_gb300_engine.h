@@ -23,12 +23,14 @@ extern "C" {
 int trsm_tc_gemm_selftest(int tf32, const void* A_dev, const void* B_dev, float* C_dev, int64_t M,
                           int64_t N, int64_t K, int* err_dev, void* stream);
 
-/* FP64-class residual R = B - tril(L) X on the BF16 tensor cores: L and X
- * are split into seven 6-bit integer digit planes per (row, 1024-wide chunk
- * of K) with a power-of-two exponent each; all digit-pair products with
- * s + u <= 6 are accumulated exactly in FP32 per chunk and combined in
- * float-float arithmetic (error-free splitting after Ozaki, Ogita, Oishi &
- * Rump 2012).  Relative error about 2^-42 of (|L| |X|).
+/* FP64-class residual R = B - tril(L) X on the BF16 tensor cores: the
+ * strictly lower L and X are split into seven 6-bit integer digit planes
+ * per (row, 2048-wide chunk of K) with a power-of-two exponent each; the
+ * digit-pair products with s + u <= 6 are accumulated in FP32 per chunk
+ * (exactly for s + u <= 3) and combined in float-float arithmetic
+ * (error-free splitting after Ozaki, Ogita, Oishi & Rump 2012); the
+ * diagonal of L is applied in FP64.  Relative error about 2^-40 of
+ * (|L| |X|).
  *   L_dev n x n column-major (lower triangle read), X_dev, B_dev, R_dev
  *   n x k column-major.  Allocates its slice buffers stream-ordered.
  *   Asynchronous; err_dev as for the self-test. */

@@ -29,6 +29,7 @@ TRSM_INNER_BF16 = 1
 TRSM_INNER_TF32 = 2
 TRSM_RESIDUAL_SLICED = 0
 TRSM_RESIDUAL_FP64 = 1
+TRSM_SOLVE_S_FP32 = 0x100
 
 # Every symbol the header declares, with (restype, argtypes).
 _i64, _vp, _dp, _int = ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int
@@ -229,7 +230,8 @@ def trsm_plan_mixed(plan, L, inner="tf32"):
     return plan
 
 
-def trsm_solve_mixed(plan, B, X=None, residual="sliced", max_iter=30, tol=1e-14, raise_on_noconv=True):
+def trsm_solve_mixed(plan, B, X=None, residual="sliced", max_iter=30, tol=1e-14, raise_on_noconv=True,
+                     s_fp32=False):
     """Iterative refinement around the low-precision solve.  Returns
     (X, iterations, last max|D|/max|X|)."""
     torch = _torch()
@@ -242,6 +244,8 @@ def trsm_solve_mixed(plan, B, X=None, residual="sliced", max_iter=30, tol=1e-14,
     it = ctypes.c_int()
     upd = ctypes.c_double()
     code = {"sliced": TRSM_RESIDUAL_SLICED, "fp64": TRSM_RESIDUAL_FP64}[residual]
+    if s_fp32:
+        code |= TRSM_SOLVE_S_FP32
     rc = load_library().trsm_solve_mixed(plan.handle, ctypes.c_void_p(B.data_ptr()), k, _ld(B),
                                          ctypes.c_void_p(X.data_ptr()), _ld(X), code, int(max_iter),
                                          float(tol), ctypes.byref(it), ctypes.byref(upd), _stream(B))

@@ -20,35 +20,33 @@ constexpr int NTHREADS = 128; // threads per CTA
 constexpr int TM = 4;         // rows per thread
 constexpr int TN = 2;         // columns per thread
 
-struct TileSmem {
-  double a[KCH][TILE + 1];  // a[kk][row]: A(row, k0 + kk)
-  double b[KCH][TILE + 1];  // b[kk][col]: B(k0 + kk, col)
+template <class T>
+struct TileSmemT {
+  T a[KCH][TILE + 1];  // a[kk][row]: A(row, k0 + kk)
+  T b[KCH][TILE + 1];  // b[kk][col]: B(k0 + kk, col)
 };
+using TileSmem = TileSmemT<double>;
 
 // Loads that may see data written by other CTAs during the same kernel go
 // to L2 (.cg): L1 is not coherent across SMs.  Read-only data may use the
 // read-only path.
-template <bool kMutable>
-__device__ __forceinline__ double ld_elem(const double* p) {
+template <bool kMutable, class T>
+__device__ __forceinline__ T ld_raw(const T* p) {
   if constexpr (kMutable) return __ldcg(p);
   else return __ldg(p);
-}
-template <bool kMutable>
-__device__ __forceinline__ double ld_elem(const float* p) {
-  if constexpr (kMutable) return static_cast<double>(__ldcg(p));
-  else return static_cast<double>(__ldg(p));
 }
 
 // acc(TM x TN) += A(rows [0,m), K [kbeg,kend)) * B(K [kbeg,kend), cols [0,nc))
 // A(r, t) = A[t*lda + r]; B(t, c) = B[c*ldb + t] (column-major).  Rows,
-// columns and K indices outside the given ranges contribute zero.
+// columns and K indices outside the given ranges contribute zero.  TC is
+// the arithmetic type (double: DFMA, float: FFMA); A and B are converted
+// to it as they are staged.
 // Thread (ty = tid/16, tx = tid%16) owns rows ty*TM.. and cols tx*TN.. of
 // the tile.  Every thread of the CTA must call this (it synchronises).
-template <bool kAMutable, bool kBMutable, class TB = double>
-__device__ __forceinline__ void tile_mma_fp64(const double* __restrict__ A, int64_t lda,
-                                              const TB* __restrict__ B, int64_t ldb, int m,
-                                              int nc, int64_t kbeg, int64_t kend, TileSmem& sm,
-                                              double (&acc)[TM][TN]) {
+template <class TC, bool kAMutable, bool kBMutable, class TA, class TB>
+__device__ __forceinline__ void tile_mma(const TA* __restrict__ A, int64_t lda, const TB* __restrict__ B,
+                                         int64_t ldb, int m, int nc, int64_t kbeg, int64_t kend,
+                                         TileSmemT<TC>& sm, TC (&acc)[TM][TN]) {
   const int tid = threadIdx.x;
   const int ty = tid >> 4, tx = tid & 15;
   for (int64_t k0 = kbeg; k0 < kend; k0 += KCH) {
@@ -57,8 +55,8 @@ __device__ __forceinline__ void tile_mma_fp64(const double* __restrict__ A, int6
       const int r = tid & 31;
       const int kk = (tid >> 5) + 4 * it;
       const int64_t t = k0 + kk;
-      double v = 0.0;
-      if (r < m && t < kend) v = ld_elem<kAMutable>(A + t * lda + r);
+      TC v = TC(0);
+      if (r < m && t < kend) v = static_cast<TC>(ld_raw<kAMutable>(A + t * lda + r));
       sm.a[kk][r] = v;
     }
 #pragma unroll
@@ -66,14 +64,14 @@ __device__ __forceinline__ void tile_mma_fp64(const double* __restrict__ A, int6
       const int kk = tid & 31;
       const int c = (tid >> 5) + 4 * it;
       const int64_t t = k0 + kk;
-      double v = 0.0;
-      if (c < nc && t < kend) v = ld_elem<kBMutable>(B + (int64_t)c * ldb + t);
+      TC v = TC(0);
+      if (c < nc && t < kend) v = static_cast<TC>(ld_raw<kBMutable>(B + static_cast<int64_t>(c) * ldb + t));
       sm.b[kk][c] = v;
     }
     __syncthreads();
 #pragma unroll 8
     for (int kk = 0; kk < KCH; ++kk) {
-      double a[TM], b[TN];
+      TC a[TM], b[TN];
 #pragma unroll
       for (int i = 0; i < TM; ++i) a[i] = sm.a[kk][ty * TM + i];
 #pragma unroll
@@ -87,13 +85,23 @@ __device__ __forceinline__ void tile_mma_fp64(const double* __restrict__ A, int6
   }
 }
 
+// FP64 form used by the solve and inversion kernels.
+template <bool kAMutable, bool kBMutable, class TB = double>
+__device__ __forceinline__ void tile_mma_fp64(const double* __restrict__ A, int64_t lda,
+                                              const TB* __restrict__ B, int64_t ldb, int m, int nc,
+                                              int64_t kbeg, int64_t kend, TileSmem& sm,
+                                              double (&acc)[TM][TN]) {
+  tile_mma<double, kAMutable, kBMutable>(A, lda, B, ldb, m, nc, kbeg, kend, sm, acc);
+}
+
 __host__ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
 
-__device__ __forceinline__ void zero_acc(double (&acc)[TM][TN]) {
+template <class T>
+__device__ __forceinline__ void zero_acc(T (&acc)[TM][TN]) {
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
 }
 
 }  // namespace trsm

@@ -115,23 +115,21 @@ __global__ void to_float_kernel(const double* __restrict__ R, int64_t ldr, float
       W[j * ldw + i] = static_cast<float>(R[j * ldr + i]);
 }
 
-// D_i = L~_ii W_i for one 32 x 32 tile (FP64 DFMA), written to D (FP64) and,
-// transposed and rounded, to Dt (the B operand of the next update GEMM).
-template <bool kTf32>
-__global__ void __launch_bounds__(NTHREADS) s_step_kernel(const double* __restrict__ Lt, int64_t ldt,
-                                                          const float* __restrict__ W, int64_t ldw,
-                                                          double* __restrict__ D, int64_t ldd,
-                                                          typename LowP<kTf32>::T* __restrict__ Dt,
-                                                          int64_t n0p, int64_t s0, int m, int64_t k) {
-  __shared__ TileSmem sm;
-  const int r = blockIdx.x, j = blockIdx.y;
+// D_i = L~_ii W_i (FP64 DFMA), written to D (FP64) and, transposed and
+// rounded, to Dt (the B operand of the next update GEMM).  L~_ii is lower
+// triangular, so row tile r costs (r + 1) K chunks: each CTA takes the
+// pair of row tiles (p, R - 1 - p), which all cost the same.
+template <bool kTf32, class TC>
+__device__ __forceinline__ void s_tile(const double* __restrict__ Lt, int64_t ldt, const float* __restrict__ W,
+                                       int64_t ldw, double* __restrict__ D, int64_t ldd,
+                                       typename LowP<kTf32>::T* __restrict__ Dt, int64_t n0p, int64_t s0, int m,
+                                       int64_t k, int r, int j, TileSmemT<TC>& sm) {
   const int mr = min(TILE, m - r * TILE);
   const int nc = static_cast<int>(imin64(TILE, k - static_cast<int64_t>(j) * TILE));
-  double acc[TM][TN];
+  TC acc[TM][TN];
   zero_acc(acc);
-  tile_mma_fp64<false, false, float>(Lt + s0 * ldt + s0 + r * TILE, ldt,
-                                     W + static_cast<int64_t>(j) * TILE * ldw + s0, ldw, mr, nc, 0,
-                                     min((r + 1) * TILE, m), sm, acc);
+  tile_mma<TC, false, false>(Lt + s0 * ldt + s0 + r * TILE, ldt, W + static_cast<int64_t>(j) * TILE * ldw + s0,
+                             ldw, mr, nc, 0, min((r + 1) * TILE, m), sm, acc);
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
 #pragma unroll
   for (int a = 0; a < TM; ++a) {
@@ -143,10 +141,26 @@ __global__ void __launch_bounds__(NTHREADS) s_step_kernel(const double* __restri
       if (cc >= nc) continue;
       const int64_t col = static_cast<int64_t>(j) * TILE + cc;
       const int64_t row = static_cast<int64_t>(r) * TILE + rr;
-      D[col * ldd + s0 + row] = acc[a][b];
-      Dt[col * n0p + row] = LowP<kTf32>::from(acc[a][b]);
+      const double v = static_cast<double>(acc[a][b]);
+      D[col * ldd + s0 + row] = v;
+      Dt[col * n0p + row] = LowP<kTf32>::from(v);
     }
   }
+}
+
+// TC = double: FP64 DFMA with the FP64 inverses (the default); TC = float:
+// FFMA with the inverses rounded to FP32 (TRSM_SOLVE_S_FP32).
+template <bool kTf32, class TC>
+__global__ void __launch_bounds__(NTHREADS) s_step_kernel(const double* __restrict__ Lt, int64_t ldt,
+                                                          const float* __restrict__ W, int64_t ldw,
+                                                          double* __restrict__ D, int64_t ldd,
+                                                          typename LowP<kTf32>::T* __restrict__ Dt,
+                                                          int64_t n0p, int64_t s0, int m, int64_t k) {
+  __shared__ TileSmemT<TC> sm;
+  const int R = (m + TILE - 1) / TILE;
+  const int p = blockIdx.x, j = blockIdx.y;
+  s_tile<kTf32, TC>(Lt, ldt, W, ldw, D, ldd, Dt, n0p, s0, m, k, p, j, sm);
+  if (R - 1 - p != p) s_tile<kTf32, TC>(Lt, ldt, W, ldw, D, ldd, Dt, n0p, s0, m, k, R - 1 - p, j, sm);
 }
 
 // max that keeps a NaN once it has been seen (fmax would drop it)
@@ -171,7 +185,18 @@ __global__ void correct_kernel(double* __restrict__ X, int64_t ldx, const double
     dm = nanmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
     xm = nanmax(xm, __shfl_xor_sync(0xffffffffu, xm, o));
   }
+  __shared__ double sd[32], sx[32];
+  const int w = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0) {
+    sd[w] = dm;
+    sx[w] = xm;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < static_cast<int>(blockDim.x >> 5); ++i) {
+      dm = nanmax(dm, sd[i]);
+      xm = nanmax(xm, sx[i]);
+    }
     // NaN propagates as the largest pattern so that divergence is visible
     const unsigned long long bd = isnan(dm) ? ~0ull : __double_as_longlong(dm);
     const unsigned long long bx = isnan(xm) ? ~0ull : __double_as_longlong(xm);
@@ -287,6 +312,8 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
   if (iters) *iters = 0;
   if (last_update) *last_update = 0.0;
   if (!h || !h->mixed || k < 0 || max_iter < 1 || !(tol >= 0.0)) return TRSM_EINVAL;
+  const bool s32 = (residual & TRSM_SOLVE_S_FP32) != 0;
+  residual &= ~TRSM_SOLVE_S_FP32;
   if (residual != TRSM_RESIDUAL_SLICED && residual != TRSM_RESIDUAL_FP64) return TRSM_EINVAL;
   if (k == 0) return TRSM_SUCCESS;
   if (!B_dev || !X_dev || ldb < h->n || ldx < h->n || B_dev == X_dev) return TRSM_EINVAL;
@@ -339,14 +366,20 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
     for (int64_t i = 0; i < N && e == cudaSuccess; ++i) {
       const int64_t s0 = i * n0;
       const int m = static_cast<int>(std::min(n0, n - s0));
-      dim3 g(static_cast<unsigned>((m + trsm::TILE - 1) / trsm::TILE),
-             static_cast<unsigned>((k + trsm::TILE - 1) / trsm::TILE));
-      if (tf32)
-        trsm::s_step_kernel<true><<<g, trsm::NTHREADS, 0, s>>>(h->Lt, h->ldt, W, ld, D, ld,
-                                                                static_cast<float*>(Dt), n0p, s0, m, k);
+      const int R = (m + trsm::TILE - 1) / trsm::TILE;
+      dim3 g(static_cast<unsigned>((R + 1) / 2), static_cast<unsigned>((k + trsm::TILE - 1) / trsm::TILE));
+      if (tf32 && !s32)
+        trsm::s_step_kernel<true, double><<<g, trsm::NTHREADS, 0, s>>>(h->Lt, h->ldt, W, ld, D, ld,
+                                                                        static_cast<float*>(Dt), n0p, s0, m, k);
+      else if (tf32)
+        trsm::s_step_kernel<true, float><<<g, trsm::NTHREADS, 0, s>>>(h->Lt, h->ldt, W, ld, D, ld,
+                                                                       static_cast<float*>(Dt), n0p, s0, m, k);
+      else if (!s32)
+        trsm::s_step_kernel<false, double><<<g, trsm::NTHREADS, 0, s>>>(
+            h->Lt, h->ldt, W, ld, D, ld, static_cast<__nv_bfloat16*>(Dt), n0p, s0, m, k);
       else
-        trsm::s_step_kernel<false><<<g, trsm::NTHREADS, 0, s>>>(h->Lt, h->ldt, W, ld, D, ld,
-                                                                 static_cast<__nv_bfloat16*>(Dt), n0p, s0, m, k);
+        trsm::s_step_kernel<false, float><<<g, trsm::NTHREADS, 0, s>>>(
+            h->Lt, h->ldt, W, ld, D, ld, static_cast<__nv_bfloat16*>(Dt), n0p, s0, m, k);
       trsm::count_launch();
       e = cudaGetLastError();
       if (e == cudaSuccess && i < N - 1) {
@@ -359,7 +392,9 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
     // ---- X += D ----
     if (e == cudaSuccess) e = cudaMemsetAsync(norms, 0, 2 * sizeof(unsigned long long), s);
     if (e == cudaSuccess) {
-      trsm::correct_kernel<<<trsm::grid_nk(n, k), 256, 0, s>>>(X_dev, ldx, D, ld, n, k, norms);
+      dim3 gc(static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 64))),
+              static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(k, 256))));
+      trsm::correct_kernel<<<gc, 256, 0, s>>>(X_dev, ldx, D, ld, n, k, norms);
       trsm::count_launch();
       e = cudaGetLastError();
     }

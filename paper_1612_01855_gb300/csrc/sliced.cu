@@ -5,7 +5,7 @@
 // applications", Numer. Algorithms 59, 2012), restated for this hardware:
 //
 //   * every row of the strictly lower L (and every column of X) is cut along
-//     K into chunks of KC = 1024 elements; each (row, chunk) gets a
+//     K into chunks of KC = 2048 elements; each (row, chunk) gets a
 //     power-of-two exponent e with max|a| < 2^e, and a / 2^e, rounded to
 //     42 fraction bits, is written as seven balanced base-64 digits
 //     d_0..d_6 (|d_0| <= 64, |d_s| <= 32 for s >= 1); plane s stores
@@ -14,10 +14,10 @@
 //     pairs, A plane fixed for consecutive MMAs) into five FP32 groups:
 //     d = s + u = 0, 1, 2, 3 each alone, and d >= 4 together.  Within one
 //     K chunk the sums of groups 0..3 are integer multiples of 2^(-6d)
-//     below 2^24 units (group 0: 1024 * 64^2 = 2^22; d = 1..3: at most
-//     1024 * 2^10 * (d + 3) <= 6.3e6), so they are exact; group 4 is
-//     2^-24 of the total, and the FP32 rounding of its 1024-term running sum
-//     stays near 2^-42 of the total;
+//     below 2^24 units (group 0: 2048 * 64^2 = 2^23; d = 1..3: at most
+//     2048 * 2^10 * (d + 3) <= 1.26e7 < 2^24 = 1.68e7), so they are exact;
+//     group 4 is 2^-24 of the total, and the FP32 rounding of its running
+//     sum stays near 2^-42 of the total;
 //   * after each chunk the epilogue adds the four groups in float-float
 //     arithmetic (about 48 bits), scales by 2^(eL + eX - 12) and
 //     accumulates (in a float-float partial buffer when a tile has more than
@@ -83,7 +83,32 @@ struct DigitPairs {
 // ---------------------------------------------------------------- slicing
 // One warp per (row, chunk): rows hold K contiguous FP64 values (stride ld
 // between rows).  Writes kSlices bf16 digit planes (plane stride plane_elems,
-// row stride kp) and the chunk exponent.
+// row stride kp) and the chunk exponent.  Each lane converts four
+// consecutive elements and stores four digits per plane at once.
+// Balanced base-64 digits of round(a 2^(42 - e)) (|.| < 2^42 because
+// |a| < 2^e), computed from the bit fields of `a` with integer operations
+// only (GB300's FP64 pipe is narrow): a = +-m 2^(E - 1075) with m the
+// 53-bit significand, so the rounded value is m shifted right by
+// (1075 - E) - (42 - e) bits, rounded to nearest.
+__device__ __forceinline__ void digits_of(double a, int e, float (&dig)[kSlices]) {
+  const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(a));
+  const int E = static_cast<int>((bits >> 52) & 0x7FF);
+  unsigned long long m = bits & ((1ull << 52) - 1);
+  if (E != 0) m |= 1ull << 52;
+  const int rsh = (1075 - (E != 0 ? E : 1)) - (6 * kSlices - e);  // >= 11 when |a| < 2^e
+  long long v = 0;
+  if (rsh < 64) v = static_cast<long long>((m + (1ull << (rsh - 1))) >> rsh);
+  if (bits >> 63) v = -v;
+#pragma unroll
+  for (int s = kSlices - 1; s >= 1; --s) {
+    long long rem = v & 63;
+    if (rem >= 32) rem -= 64;
+    v = (v - rem) >> kDigitBits;
+    dig[s] = static_cast<float>(rem);
+  }
+  dig[0] = static_cast<float>(v);  // |d_0| <= 64
+}
+
 __global__ void slice_rows_kernel(const double* __restrict__ src, int64_t ld, int64_t rows, int64_t K,
                                   int64_t nch, __nv_bfloat16* __restrict__ dst, int64_t kp,
                                   int64_t plane_elems, int16_t* __restrict__ ex) {
@@ -93,32 +118,42 @@ __global__ void slice_rows_kernel(const double* __restrict__ src, int64_t ld, in
   const int64_t r = wid / nch, c = wid % nch;
   const double* p = src + r * ld;
   const int64_t k0 = c * kChunk, k1 = (K < k0 + kChunk) ? K : k0 + kChunk;
-  double m = 0.0;
-  for (int64_t k = k0 + lane; k < k1; k += 32) m = fmax(m, fabs(p[k]));
+  // max |a| over the chunk, compared as the bit patterns of |a| (ordered
+  // like the values for non-negative doubles)
+  unsigned long long mb = 0;
+  for (int64_t k = k0 + lane; k < k1; k += 32) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(p[k])) & ~(1ull << 63);
+    mb = b > mb ? b : mb;
+  }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long b = __shfl_xor_sync(0xffffffffu, mb, o);
+    mb = b > mb ? b : mb;
+  }
+  // e with max|a| < 2^e: a normal max = 1.f 2^(E - 1023) < 2^(E - 1022)
   int e = 0;
-  if (m > 0.0) frexp(m, &e);  // m = f 2^e, f in [0.5, 1): max|a| < 2^e
+  if (mb != 0) {
+    const int E = static_cast<int>(mb >> 52);
+    e = (E != 0) ? E - 1022 : -1022;
+  }
   if (lane == 0) ex[r * nch + c] = static_cast<int16_t>(e);
-  // padding columns of the last chunk (up to kp) are written as zeros
+  // padding columns of the last chunk (up to kp, a multiple of 8) are zeros
   const int64_t kw1 = (c == nch - 1) ? kp : k1;
-  for (int64_t k = k0 + lane; k < kw1; k += 32) {
-    // v = round(a 2^(42 - e)), |v| < 2^42; balanced base-64 digits from
-    // the least significant end with integer arithmetic
-    long long v = (k < K) ? __double2ll_rn(ldexp(p[k], 6 * kSlices - e)) : 0ll;
-    float dig[kSlices];
+  __nv_bfloat16* drow = dst + r * kp;
+  for (int64_t k = k0 + 4 * lane; k < kw1; k += 128) {
+    float dig[4][kSlices];
 #pragma unroll
-    for (int s = kSlices - 1; s >= 1; --s) {
-      long long rem = v & 63;
-      if (rem >= 32) rem -= 64;
-      v = (v - rem) >> kDigitBits;
-      dig[s] = static_cast<float>(rem);
+    for (int q = 0; q < 4; ++q) digits_of((k + q < K) ? p[k + q] : 0.0, e, dig[q]);
+#pragma unroll
+    for (int s = 0; s < kSlices; ++s) {
+      const float w = __int_as_float((127 - kDigitBits * s) << 23);
+      __nv_bfloat162 lo2 = __floats2bfloat162_rn(dig[0][s] * w, dig[1][s] * w);
+      __nv_bfloat162 hi2 = __floats2bfloat162_rn(dig[2][s] * w, dig[3][s] * w);
+      uint2 pk;
+      pk.x = *reinterpret_cast<uint32_t*>(&lo2);
+      pk.y = *reinterpret_cast<uint32_t*>(&hi2);
+      *reinterpret_cast<uint2*>(drow + s * plane_elems + k) = pk;  // 8-byte aligned: k, kp multiples of 4
     }
-    dig[0] = static_cast<float>(v);  // |d_0| <= 64
-#pragma unroll
-    for (int s = 0; s < kSlices; ++s)
-      dst[s * plane_elems + r * kp + k] =
-          __float2bfloat16_rn(dig[s] * __int_as_float((127 - kDigitBits * s) << 23));
   }
 }
 
@@ -179,6 +214,11 @@ struct ResidualEpi {
   struct State {
     float ph[16], pl[16];
   };
+  // With a triangular L the last row tiles carry the longest K ranges: run
+  // them first so that they do not form the tail of the launch.
+  __device__ void tile(int& tm, int&) const {
+    if (lower) tm = static_cast<int>(gridDim.x) - 1 - tm;
+  }
   __device__ void k_range(int tm, int, int& kb0, int& kb1, int& chunk) const {
     const int kend = lower ? min(K, (tm + 1) * 128) : K;
     kb0 = 0;
@@ -202,35 +242,48 @@ struct ResidualEpi {
     const int grow = tm * 128 + row;
     if (grow >= M) return;
     const int ea = eA[static_cast<int64_t>(grow) * nch + c];
+    const int col0 = tn * BN + sl * 16;
+    const int ncol = min(16, N - col0);
+    float2* base = part + static_cast<int64_t>(col0) * M + grow;
+    // issue every load of the slab before using any (overlapped latencies)
+    int eb[16];
+    float2 o[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
-      const int col = tn * BN + sl * 16 + j;
-      if (col >= N) continue;
-      const int sc = ea + __ldg(eB + static_cast<int64_t>(col) * nch + c) - 2 * kDigitBits;
+      eb[j] = (j < ncol) ? __ldg(eB + static_cast<int64_t>(col0 + j) * nch + c) : 0;
+      o[j] = (c > 0 && j < ncol) ? base[static_cast<int64_t>(j) * M] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (j >= ncol) continue;
+      const int sc = ea + eb[j] - 2 * kDigitBits;
       float h = ldexpf(st.ph[j], sc), l = ldexpf(st.pl[j], sc);
-      float2* pp = part + static_cast<int64_t>(col) * M + grow;
-      if (c > 0) {
-        const float2 o = *pp;
-        ff_add(h, l, o.x, o.y);
-      }
-      *pp = make_float2(h, l);
+      ff_add(h, l, o[j].x, o[j].y);
+      base[static_cast<int64_t>(j) * M] = make_float2(h, l);
     }
   }
   __device__ void finish(State&, int tm, int tn, int nchunks, int row) const {
     const int grow = tm * 128 + row;
     if (grow >= M) return;
-    for (int col0 = 0; col0 < BN; ++col0) {
-      const int col = tn * BN + col0;
-      if (col >= N) break;
-      double lx = 0.0;
-      if (nchunks > 0) {
-        const float2 o = part[static_cast<int64_t>(col) * M + grow];
-        lx = static_cast<double>(o.x) + static_cast<double>(o.y);
+    const double dg = Ld[static_cast<int64_t>(grow) * ldl + grow];
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      const int col0 = tn * BN + c0;
+      const int ncol = min(16, N - col0);
+      if (ncol <= 0) break;
+      float2 o[16];
+      double xv[16], bv[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int64_t col = col0 + j;
+        o[j] = (nchunks > 0 && j < ncol) ? part[col * M + grow] : make_float2(0.f, 0.f);
+        xv[j] = (j < ncol) ? X[col * ldx + grow] : 0.0;
+        bv[j] = (j < ncol) ? B[col * ldb + grow] : 0.0;
       }
-      const double t = fma(-Ld[static_cast<int64_t>(grow) * ldl + grow],
-                           X[static_cast<int64_t>(col) * ldx + grow],
-                           B[static_cast<int64_t>(col) * ldb + grow]);
-      R[static_cast<int64_t>(col) * ldr + grow] = t - lx;
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (j < ncol)
+          R[static_cast<int64_t>(col0 + j) * ldr + grow] =
+              fma(-dg, xv[j], bv[j]) - (static_cast<double>(o[j].x) + static_cast<double>(o[j].y));
     }
   }
 };

@@ -8,7 +8,7 @@ namespace trsm {
 
 constexpr int kSlices = 7;     // base-64 digits per value
 constexpr int kDigitBits = 6;  // bits per digit
-constexpr int kChunk = 1024;   // K elements per exactly-summed chunk
+constexpr int kChunk = 2048;   // K elements per exactly-summed chunk
 
 // kSlices digit planes of a rows x K operand (K-major: each row's K digits
 // contiguous, row stride kp = K rounded up to 8), plus one int16 exponent

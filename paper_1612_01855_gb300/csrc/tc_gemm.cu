@@ -63,6 +63,7 @@ struct StoreF32Epi {
   int M, N, nkb;
   float alpha, beta;
   struct State {};
+  __device__ void tile(int&, int&) const {}
   __device__ void k_range(int, int, int& kb0, int& kb1, int& chunk) const {
     kb0 = 0;
     kb1 = nkb;
@@ -72,24 +73,25 @@ struct StoreF32Epi {
   __device__ void group(State&, int tm, int tn, int, int row, int sl, int, const float (&v)[16]) const {
     const int r = tm * 128 + row;
     if (r >= M) return;
+    float* base = C + static_cast<int64_t>(tn * BN + sl * 16) * ldc + r;
+    const int ncol = min(16, N - (tn * BN + sl * 16));
+    // all loads of the slab first, so that their latencies overlap
+    float old[16];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const int col = tn * BN + sl * 16 + j;
-      if (col < N) {
-        float* p = C + static_cast<int64_t>(col) * ldc + r;
-        *p = (beta == 0.f) ? alpha * v[j] : alpha * v[j] + beta * *p;
-      }
-    }
+    for (int j = 0; j < 16; ++j) old[j] = (beta != 0.f && j < ncol) ? base[static_cast<int64_t>(j) * ldc] : 0.f;
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if (j < ncol) base[static_cast<int64_t>(j) * ldc] = alpha * v[j] + beta * old[j];
   }
   __device__ void slab_done(State&, int, int, int, int, int) const {}
   __device__ void finish(State&, int, int, int, int) const {}
 };
 
-template <bool kTf32, int BN>
+template <bool kTf32, int BN, int STAGES>
 cudaError_t plain_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t M,
                        int64_t N, int64_t K, int64_t ldc, float alpha, float beta, int* err,
                        cudaStream_t s) {
-  using Cfg = TileCfg<kTf32, BN, 1, 1, 1, 4>;
+  using Cfg = TileCfg<kTf32, BN, 1, 1, 1, STAGES>;
   CUtensorMap ma, mb;
   if (!make_kmajor_map(&ma, A, kTf32, K, M, lda, 1, M * lda, 128, 1, 128)) return cudaErrorInvalidValue;
   if (!make_kmajor_map(&mb, B, kTf32, K, N, ldb, 1, N * ldb, BN, 1, 128)) return cudaErrorInvalidValue;
@@ -111,8 +113,15 @@ cudaError_t gemm_lowp(bool tf32, const void* A, int64_t lda, const void* B, int6
                       int64_t ldc, int64_t M, int64_t N, int64_t K, float alpha, float beta, int* err,
                       cudaStream_t s) {
   if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
-  return tf32 ? plain_gemm<true, 128>(A, lda, B, ldb, C, M, N, K, ldc, alpha, beta, err, s)
-              : plain_gemm<false, 128>(A, lda, B, ldb, C, M, N, K, ldc, alpha, beta, err, s);
+  // Short K (a few stages, as in the blocked solve's updates): a 2-stage
+  // ring leaves room for three CTAs per SM, which hides the epilogue's
+  // read-modify-write of C behind the other CTAs' MMAs.
+  const int kb = static_cast<int>((K * (tf32 ? 4 : 2) + 127) / 128);
+  if (kb <= 8)
+    return tf32 ? plain_gemm<true, 128, 2>(A, lda, B, ldb, C, M, N, K, ldc, alpha, beta, err, s)
+                : plain_gemm<false, 128, 2>(A, lda, B, ldb, C, M, N, K, ldc, alpha, beta, err, s);
+  return tf32 ? plain_gemm<true, 128, 4>(A, lda, B, ldb, C, M, N, K, ldc, alpha, beta, err, s)
+              : plain_gemm<false, 128, 4>(A, lda, B, ldb, C, M, N, K, ldc, alpha, beta, err, s);
 }
 
 }  // namespace tc

@@ -49,7 +49,7 @@ struct TileCfg {
 // The pair table of a configuration: MMA i multiplies A slice pa(i) by
 // B slice pb(i) into group pg(i).
 template <class Cfg, class Pairs, class Epi>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(192)
     tc_tile_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    const Epi epi, int* err) {
   constexpr int STAGES = Cfg::STAGES;
@@ -64,7 +64,8 @@ __global__ void __launch_bounds__(192, 1)
   __shared__ int abort_sh;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tm = blockIdx.x, tn = blockIdx.y;
+  int tm = blockIdx.x, tn = blockIdx.y;
+  epi.tile(tm, tn);  // the epilogue may reorder tiles (e.g. longest first)
   int kb0 = 0, kb1 = 0, kb_chunk = 1;
   epi.k_range(tm, tn, kb0, kb1, kb_chunk);
   const int nkb = kb1 > kb0 ? kb1 - kb0 : 0;

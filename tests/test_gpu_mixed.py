@@ -19,16 +19,16 @@ def _rel(a, b):
 
 
 @pytest.mark.parametrize("inner", ["tf32", "bf16"])
-@pytest.mark.parametrize("residual", ["sliced", "fp64"])
+@pytest.mark.parametrize("residual,s32", [("sliced", False), ("fp64", False), ("sliced", True)])
 @pytest.mark.parametrize("n,k,n0", [(1024, 64, 128), (1000, 37, 64), (300, 5, 300)])
-def test_mixed_well_conditioned(cuda_lib, inner, residual, n, k, n0):
+def test_mixed_well_conditioned(cuda_lib, inner, residual, s32, n, k, n0):
     import paper_1612_01855_gb300 as g
     L, B = inputs.well_conditioned(n, k, seed=n + k)
     Ld = _dev(L)
     plan = g.trsm_plan(Ld, n0)
     g.trsm_plan_mixed(plan, Ld, inner)
     X, iters, upd = g.trsm_solve_mixed(plan, _dev(B), residual=residual, max_iter=40, tol=1e-15,
-                                       raise_on_noconv=False)
+                                       raise_on_noconv=False, s_fp32=s32)
     got = X.cpu().numpy()
     want = oracle.forward_subst(L, B)
     err = _rel(got, want)
