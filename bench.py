@@ -184,6 +184,60 @@ def precision_study(g, torch, n, k, n0, cs, inners, s_modes, dd_cols=2, stream=N
     return out
 
 
+def run_case(args):
+    """Single kernels for profiling (no JSON bench line):
+    sliced:N:K       the tensor-core residual R = B - L X, twice;
+    mixed:N:K:N0     one mixed-precision refined solve (graded diagonal, c = 2);
+    engine:M:N:K     the bf16 tensor-core GEMM self-test, twice."""
+    import ctypes
+    import torch
+    import paper_1612_01855_gb300 as g
+    from paper_1612_01855_gb300 import build as pkg_build
+    pkg_build.build()
+    lib = g.load_library()
+    kind, *dims = args.case.split(":")
+    dims = [int(v) for v in dims]
+    torch.manual_seed(0)
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    if kind in ("sliced", "mixed"):
+        n, k = dims[0], dims[1]
+        L = torch.tril(torch.rand(n, n, dtype=torch.float64, device="cuda") * 2 - 1) / n
+        if kind == "mixed":
+            d = torch.from_numpy(np.geomspace(1.0, 1e-2, n)).cuda()[torch.randperm(n, device="cuda")]
+        else:
+            d = 2 + torch.rand(n, dtype=torch.float64, device="cuda")
+        L.diagonal().copy_(d)
+        L = L.t().contiguous().t()
+        B = (torch.rand(k, n, dtype=torch.float64, device="cuda") * 2 - 1).t()
+        if kind == "sliced":
+            X = (torch.rand(k, n, dtype=torch.float64, device="cuda") * 2 - 1).t()
+            R = torch.empty(k, n, dtype=torch.float64, device="cuda").t()
+            for _ in range(2):
+                rc = lib.trsm_residual_sliced(ctypes.c_void_p(L.data_ptr()), n, n, ctypes.c_void_p(X.data_ptr()), k,
+                                              n, ctypes.c_void_p(B.data_ptr()), n, ctypes.c_void_p(R.data_ptr()),
+                                              n, ctypes.c_void_p(err.data_ptr()), s)
+                assert rc == 0
+        else:
+            plan = g.trsm_plan(L, dims[2])
+            g.trsm_plan_mixed(plan, L, "tf32")
+            g.trsm_solve_mixed(plan, B, max_iter=30, tol=1e-12, raise_on_noconv=False)
+    elif kind == "engine":
+        M, N, K = dims
+        A = torch.randn(M, K, device="cuda").to(torch.bfloat16)
+        Bm = torch.randn(N, K, device="cuda").to(torch.bfloat16)
+        C = torch.empty(N, M, device="cuda", dtype=torch.float32)
+        for _ in range(2):
+            assert lib.trsm_tc_gemm_selftest(0, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(Bm.data_ptr()),
+                                             ctypes.c_void_p(C.data_ptr()), M, N, K,
+                                             ctypes.c_void_p(err.data_ptr()), s) == 0
+    else:
+        raise SystemExit(f"unknown case {kind}")
+    torch.cuda.synchronize()
+    assert err.item() == 0
+    print(f"case {args.case} done")
+
+
 def run_reference(args, rank, world):
     """--impl reference: the CPU oracle on the host cores, bounded samples."""
     if rank != 0:
@@ -416,6 +470,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision refinement figure")
     ap.add_argument("--precision", action="store_true", help="print the full c x inner x s-step study")
+    ap.add_argument("--case", default="", help="profiling case: sliced:N:K, mixed:N:K:N0, engine:M:N:K")
     ap.add_argument("--shapes", default="", help="override workload, e.g. 6144:1024:256 (not a bench line)")
     args = ap.parse_args()
     rank, world, local = dist_env()
@@ -426,7 +481,9 @@ def main():
         if args.impl == "ours":
             torch.cuda.set_device(local)
         dist.init_process_group(backend=backend)
-    if args.impl == "reference":
+    if args.case:
+        run_case(args)
+    elif args.impl == "reference":
         run_reference(args, rank, world)
     else:
         run_ours(args, rank, world, local)
