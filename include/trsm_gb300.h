@@ -149,6 +149,58 @@ int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k, int64_t ld
                      int64_t ldx, int residual, int max_iter, double tol, int* iters,
                      double* last_update, void* stream);
 
+/* ---- Many independent systems in one persistent launch ----
+ * Each item is Algorithm It-Inv-TRSM (Section 6.2) on its own system; the
+ * systems may differ in n, k and block size.  An item either carries a
+ * resident plan (its inverted blocks are reused: no inversion work) or its
+ * own L, whose n0 x n0 diagonal blocks (n0 = 32 or 64) are inverted inside
+ * the same launch by Algorithm RecTriInv (Section 5.1, one level).  One
+ * run is one memset and one kernel, so it can be captured in a CUDA graph;
+ * the results do not depend on which other items share the launch (every
+ * tile's updates are applied in a fixed order). */
+#define TRSM_F64 0
+#define TRSM_F32 1
+
+typedef struct trsm_batch_item {
+  const void* L;        /* device, n x n column-major (ignored when plan != NULL) */
+  int64_t ldl;
+  trsm_handle_t plan;   /* resident plan for this L (FP64 batches only), or NULL */
+  const void* B;        /* device, n x k, read only; must not alias X          */
+  int64_t ldb;
+  void* X;              /* device, n x k, written                              */
+  int64_t ldx;
+  int64_t n, k;
+  int64_t n0;           /* 32 or 64 when plan == NULL (ignored otherwise)      */
+} trsm_batch_item;
+
+typedef struct trsm_batch_s* trsm_batch_t;
+
+/* Validates the items, lays out the workspace (working copies of B, the
+ * inverted blocks of plan-less items, dependency counters) and uploads the
+ * task table.  Pointers in the items are retained by the batch: they must
+ * stay valid while it is run.  dtype: TRSM_F64 (double data) or TRSM_F32
+ * (float data; plan-less items only).  Errors: TRSM_EINVAL, TRSM_ENOMEM,
+ * TRSM_ECUDA. */
+int trsm_batch_create(const trsm_batch_item* items, int count, int dtype, trsm_batch_t* out);
+
+/* Enqueues one solve of every item (asynchronous). */
+int trsm_batch_run(trsm_batch_t b, void* stream);
+
+/* Records trsm_batch_run into a CUDA graph held by the batch (on a private
+ * stream; `stream` is unused and may be NULL); trsm_batch_launch_graph
+ * replays it on `stream`. */
+int trsm_batch_capture(trsm_batch_t b, void* stream);
+int trsm_batch_launch_graph(trsm_batch_t b, void* stream);
+
+/* Waits for `stream`; returns TRSM_SUCCESS, TRSM_ETIMEOUT (a device wait ran
+ * out) or TRSM_ESINGULAR with the first failing item and its row. */
+int trsm_batch_status(trsm_batch_t b, void* stream, int* first_bad_item, int64_t* singular_row);
+
+void trsm_batch_destroy(trsm_batch_t b);
+
+/* Device bytes the batch holds. */
+size_t trsm_batch_workspace_bytes(trsm_batch_t b);
+
 /* trsm_host — the whole method (trsm_plan + trsm_solve) on HOST buffers:
  * copies L and B to the device, plans, solves, copies X back and waits.
  *   L_host (n x n, ldl), B_host (n x k, ldb), X_host (n x k, ldx), all

@@ -31,6 +31,18 @@ TRSM_RESIDUAL_SLICED = 0
 TRSM_RESIDUAL_FP64 = 1
 TRSM_SOLVE_S_FP32 = 0x100
 
+TRSM_F64 = 0
+TRSM_F32 = 1
+
+
+class BatchItem(ctypes.Structure):
+    """Mirror of trsm_batch_item (include/trsm_gb300.h)."""
+    _fields_ = [("L", ctypes.c_void_p), ("ldl", ctypes.c_int64), ("plan", ctypes.c_void_p),
+                ("B", ctypes.c_void_p), ("ldb", ctypes.c_int64), ("X", ctypes.c_void_p),
+                ("ldx", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int64),
+                ("n0", ctypes.c_int64)]
+
+
 # Every symbol the header declares, with (restype, argtypes).
 _i64, _vp, _dp, _int = ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int
 _pi64 = ctypes.POINTER(ctypes.c_int64)
@@ -43,6 +55,13 @@ SIGNATURES = {
     "trsm_plan_mixed": (_int, [_vp, _dp, _i64, _int, _vp]),
     "trsm_solve_mixed": (_int, [_vp, _dp, _i64, _i64, _dp, _i64, _int, _int, ctypes.c_double,
                                 ctypes.POINTER(_int), ctypes.POINTER(ctypes.c_double), _vp]),
+    "trsm_batch_create": (_int, [ctypes.POINTER(BatchItem), _int, _int, ctypes.POINTER(_vp)]),
+    "trsm_batch_run": (_int, [_vp, _vp]),
+    "trsm_batch_capture": (_int, [_vp, _vp]),
+    "trsm_batch_launch_graph": (_int, [_vp, _vp]),
+    "trsm_batch_status": (_int, [_vp, _vp, ctypes.POINTER(_int), ctypes.POINTER(ctypes.c_int64)]),
+    "trsm_batch_destroy": (None, [_vp]),
+    "trsm_batch_workspace_bytes": (ctypes.c_size_t, [_vp]),
     "trsm_host": (_int, [_dp, _i64, _i64, _i64, _dp, _i64, _i64, _dp, _i64, _vp]),
     "trtri_blocks": (_int, [_dp, _i64, _i64, _i64, _dp, _vp]),
     "trsm_destroy": (None, [_vp]),
@@ -334,3 +353,69 @@ def fp64_peak(iters=4096, device=None):
 
 def launch_count(reset=False):
     return int(load_library().trsm_launch_count(1 if reset else 0))
+
+
+class Batch:
+    """Many independent systems solved by one persistent launch
+    (trsm_batch_*).  `systems` is a list of dicts with keys L (or plan), B,
+    X (CUDA tensors, column-major) and n0 (32 or 64, plan-less items)."""
+
+    def __init__(self, systems, dtype="f64"):
+        torch = _torch()
+        items = (BatchItem * len(systems))()
+        self._keep = []
+        want = torch.float64 if dtype == "f64" else torch.float32
+        for i, sy in enumerate(systems):
+            B, X = colmajor(sy["B"]), colmajor(sy["X"])
+            for t in (B, X):
+                if not t.is_cuda or t.dtype != want:
+                    raise TypeError("batch tensors must be CUDA tensors of the batch dtype")
+            n, k = B.shape
+            it = items[i]
+            if sy.get("plan") is not None:
+                it.plan = sy["plan"].handle.value
+                it.L, it.ldl, it.n0 = None, 0, 0
+            else:
+                L = colmajor(sy["L"])
+                if L.dtype != want:
+                    raise TypeError("L must have the batch dtype")
+                it.L, it.ldl, it.n0 = L.data_ptr(), _ld(L), int(sy.get("n0", 32))
+                self._keep.append(L)
+            it.B, it.ldb, it.X, it.ldx, it.n, it.k = B.data_ptr(), _ld(B), X.data_ptr(), _ld(X), n, k
+            self._keep += [B, X]
+        h = ctypes.c_void_p()
+        _check(load_library().trsm_batch_create(items, len(systems), TRSM_F64 if dtype == "f64" else TRSM_F32,
+                                                ctypes.byref(h)), "trsm_batch_create")
+        self._h = h
+
+    def _s(self):
+        torch = _torch()
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def run(self):
+        _check(load_library().trsm_batch_run(self._h, self._s()), "trsm_batch_run")
+
+    def capture(self):
+        _check(load_library().trsm_batch_capture(self._h, self._s()), "trsm_batch_capture")
+
+    def launch_graph(self):
+        _check(load_library().trsm_batch_launch_graph(self._h, self._s()), "trsm_batch_launch_graph")
+
+    def status(self):
+        item, row = ctypes.c_int(), ctypes.c_int64()
+        rc = load_library().trsm_batch_status(self._h, self._s(), ctypes.byref(item), ctypes.byref(row))
+        return rc, item.value, row.value
+
+    def workspace_bytes(self):
+        return int(load_library().trsm_batch_workspace_bytes(self._h))
+
+    def destroy(self):
+        if self._h is not None and self._h.value:
+            load_library().trsm_batch_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

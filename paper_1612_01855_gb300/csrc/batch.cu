@@ -1,0 +1,553 @@
+// Many independent triangular systems in one persistent launch.
+//
+// Every system is Algorithm It-Inv-TRSM (Section 6.2) on its own L, B, X;
+// the systems differ in n, k and block size.  One kernel serves all of
+// them: each CTA repeatedly takes the next ticket of a global counter, and
+// tickets enumerate the systems one after another, each as
+//   INV(b)          invert diagonal block b (only when the system has no plan:
+//                   Algorithm RecTriInv with one level, n0 <= 64)
+//   wave l:  S(l, r, j)        X_l[r, j]  = L~_ll[r, :] W_l[:, j]
+//            U(i, r, j, l)     W_i[r, j] -= L_il[r, :] X_l[:, j]      (i > l)
+// with the same dependency counters as the single-system kernel: a task's
+// dependencies always hold smaller tickets (same system, earlier position),
+// so the scheme cannot deadlock whatever the residency.  The first update
+// of a tile reads B instead of the working copy W, so no copy launch is
+// needed and a whole batch is one memset plus one kernel (and so one CUDA
+// graph).  The arithmetic type T is double or float.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <new>
+#include <vector>
+
+#include "fp64_tile.cuh"
+#include "internal.h"
+#include "trsm_gb300.h"
+
+namespace trsm {
+namespace {
+
+constexpr long long kWaitNs = 4000000000LL;
+constexpr long long kWaitIters = 1LL << 26;
+
+template <class T>
+struct BatchSys {
+  const T* Linv;        // inverted diagonal blocks: block l starts at Linv + l * inv_bstride
+  int64_t ldinv, inv_bstride;
+  const T* Loff;        // L off the block diagonal (the user's L, or a plan's L~)
+  int64_t ldoff;
+  const T* L;           // the user's L for INV tasks (null when the system has a plan)
+  int64_t ldl;
+  T* Tsc;               // INV scratch: 32 x 32 per block (n0 = 64 only)
+  const T* B;
+  int64_t ldb;
+  T* W;                 // working copy of B, ldw = align4(n)
+  int64_t ldw;
+  T* X;
+  int64_t ldx;
+  int64_t n, k, n0;
+  int N, R, Rlast, C;
+  int64_t total_rt;
+  int64_t task0;        // first ticket of the system
+  int64_t inv_tasks;    // N when the system inverts its own blocks, else 0
+  int* wdone;           // [total_rt * C]
+  int* xdone;           // [N * C]
+  int* invdone;         // [N]
+  int* status;          // per-system status word: 0, or INT_MAX - first singular row
+};
+
+__device__ __forceinline__ int ld_acquire_b(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ long long gtime() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ bool wait_geq_b(const int* p, int target, int* err) {
+  if (ld_acquire_b(p) >= target) return true;
+  const long long t0 = gtime();
+  unsigned ns = 64;
+  for (long long it = 0; it < kWaitIters; ++it) {
+    __nanosleep(ns);
+    if (ns < 2048) ns <<= 1;
+    if (ld_acquire_b(p) >= target) return true;
+    if (*(volatile int*)err != 0) return false;
+    if (gtime() - t0 > kWaitNs) break;
+  }
+  atomicCAS(err, 0, 1);
+  return false;
+}
+
+__host__ __device__ __forceinline__ int64_t wave_first(int64_t l, int64_t R, int64_t total_rt, int64_t C) {
+  return C * (l * total_rt - R * (l * (l - 1) / 2));
+}
+
+template <class T>
+__device__ void leaf_invert_warp(const T* __restrict__ A, int64_t lda, int m, T* __restrict__ out,
+                                 int64_t ldo, T (*ls)[33], int* status, int64_t row0) {
+  const int lane = threadIdx.x & 31;
+  for (int c = 0; c < 32; ++c) {
+    T v = T(0);
+    if (lane < m && c < m && lane >= c) v = A[static_cast<int64_t>(c) * lda + lane];
+    ls[lane][c] = v;
+  }
+  __syncwarp();
+  if (lane < m) {
+    const T dl = ls[lane][lane];
+    // status 0 = fine; otherwise INT_MAX - (smallest singular row)
+    if (dl == T(0) || !isfinite(static_cast<double>(dl))) atomicMax(status, INT_MAX - static_cast<int>(row0 + lane));
+  }
+  T y[32];
+#pragma unroll
+  for (int r = 0; r < 32; ++r) y[r] = (r == lane) ? T(1) : T(0);
+#pragma unroll
+  for (int l = 0; l < 32; ++l) {
+    if (l < m) {
+      y[l] = y[l] / ls[l][l];
+#pragma unroll
+      for (int r = l + 1; r < 32; ++r) y[r] = fma(-ls[r][l], y[l], y[r]);
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < 32; ++r) ls[r][lane] = y[r];
+  __syncwarp();
+  // the m x m leaf only: the output block may be narrower than 32 (n < 32)
+  if (lane < m)
+    for (int c = 0; c < m; ++c) out[static_cast<int64_t>(c) * ldo + lane] = ls[lane][c];
+}
+
+template <class T>
+__global__ void __launch_bounds__(NTHREADS) batch_kernel(const BatchSys<T>* __restrict__ sys, int nsys,
+                                                        int64_t total, unsigned long long* ticket, int* err) {
+  __shared__ TileSmemT<T> sm;
+  __shared__ T ls[2][32][33];
+  __shared__ long long s_ticket;
+  __shared__ int s_ok;
+  const int tid = threadIdx.x;
+  const int ty = tid >> 4, tx = tid & 15;
+  for (;;) {
+    if (tid == 0) s_ticket = static_cast<long long>(atomicAdd(ticket, 1ULL));
+    __syncthreads();
+    const int64_t t = s_ticket;
+    if (t >= total) break;
+    int lo = 0, hi = nsys - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (sys[mid].task0 <= t) lo = mid;
+      else hi = mid - 1;
+    }
+    const BatchSys<T>& a = sys[lo];
+    int64_t o = t - a.task0;
+    if (o < a.inv_tasks) {
+      // ---- INV(b): diagonal block b of order m <= 64 ----
+      const int b = static_cast<int>(o);
+      const int64_t s0 = static_cast<int64_t>(b) * a.n0;
+      const int m = static_cast<int>(imin64(a.n0, a.n - s0));
+      T* inv = const_cast<T*>(a.Linv) + b * a.inv_bstride;
+      const T* Lb = a.L + s0 * a.ldl + s0;
+      const int warp = tid >> 5;
+      const int h = (m > 32) ? 32 : m, r2 = m - h;
+      if (warp == 0) leaf_invert_warp<T>(Lb, a.ldl, h, inv, a.ldinv, ls[0], a.status, s0);
+      if (warp == 1 && r2 > 0)
+        leaf_invert_warp<T>(Lb + 32 * a.ldl + 32, a.ldl, r2, inv + 32 * a.ldinv + 32, a.ldinv, ls[1], a.status,
+                            s0 + 32);
+      __threadfence_block();
+      __syncthreads();
+      if (r2 > 0) {
+        // upper-right 32 x 32 of the block inverse is zero
+        for (int e = tid; e < 32 * 32; e += NTHREADS) inv[(32 + e / 32) * a.ldinv + (e % 32)] = T(0);
+        // T = -(L22^-1 L21): r2 x 32, then L21^-1 = T L11^-1 (RecTriInv, one level)
+        T acc[TM][TN];
+        zero_acc(acc);
+        tile_mma<T, true, false>(inv + 32 * a.ldinv + 32, a.ldinv, Lb + 32, a.ldl, r2, 32, 0, r2, sm, acc);
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) {
+            const int rr = ty * TM + i, cc = tx * TN + j;
+            if (rr < r2) a.Tsc[b * 1024 + cc * 32 + rr] = -acc[i][j];
+          }
+        __threadfence_block();
+        __syncthreads();
+        zero_acc(acc);
+        tile_mma<T, true, true>(a.Tsc + b * 1024, 32, inv, a.ldinv, r2, 32, 0, 32, sm, acc);
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) {
+            const int rr = ty * TM + i, cc = tx * TN + j;
+            if (rr < r2) inv[cc * a.ldinv + 32 + rr] = acc[i][j];
+          }
+      }
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) atomicAdd(a.invdone + b, 1);
+      continue;
+    }
+    o -= a.inv_tasks;
+    int l = 0;
+    {
+      int l0 = 0, l1 = a.N - 1;
+      while (l0 < l1) {
+        const int mid = (l0 + l1 + 1) >> 1;
+        if (wave_first(mid, a.R, a.total_rt, a.C) <= o) l0 = mid;
+        else l1 = mid - 1;
+      }
+      l = l0;
+    }
+    o -= wave_first(l, a.R, a.total_rt, a.C);
+    const int Rl = (l == a.N - 1) ? a.Rlast : a.R;
+    const int64_t s0 = static_cast<int64_t>(l) * a.n0;
+    const int64_t ml = imin64(a.n0, a.n - s0);
+    T acc[TM][TN];
+    zero_acc(acc);
+    if (o < static_cast<int64_t>(Rl) * a.C) {
+      // ---- S(l, r, j) ----
+      const int r = Rl - 1 - static_cast<int>(o / a.C);
+      const int j = static_cast<int>(o % a.C);
+      if (tid == 0) {
+        bool ok = true;
+        if (a.inv_tasks > 0) ok = wait_geq_b(a.invdone + l, 1, err);
+        if (l > 0) {
+          const int64_t q0 = static_cast<int64_t>(l) * a.R;
+          for (int rr = 0; rr <= r && ok; ++rr) ok = wait_geq_b(a.wdone + (q0 + rr) * a.C + j, l, err);
+        }
+        s_ok = ok;
+      }
+      __syncthreads();
+      if (!s_ok) break;
+      const int m = static_cast<int>(imin64(TILE, ml - static_cast<int64_t>(r) * TILE));
+      const int nc = static_cast<int>(imin64(TILE, a.k - static_cast<int64_t>(j) * TILE));
+      const int64_t kend = imin64(static_cast<int64_t>(r + 1) * TILE, ml);
+      const T* Ainv = a.Linv + l * a.inv_bstride + r * TILE;
+      if (l == 0)
+        tile_mma<T, true, false>(Ainv, a.ldinv, a.B + static_cast<int64_t>(j) * TILE * a.ldb, a.ldb, m, nc, 0,
+                                 kend, sm, acc);
+      else
+        tile_mma<T, true, true>(Ainv, a.ldinv, a.W + static_cast<int64_t>(j) * TILE * a.ldw + s0, a.ldw, m, nc, 0,
+                                kend, sm, acc);
+      const int64_t row0 = s0 + static_cast<int64_t>(r) * TILE;
+#pragma unroll
+      for (int i = 0; i < TM; ++i) {
+        const int rr = ty * TM + i;
+        if (rr >= m) continue;
+#pragma unroll
+        for (int jj = 0; jj < TN; ++jj) {
+          const int cc = tx * TN + jj;
+          if (cc >= nc) continue;
+          __stcg(a.X + (static_cast<int64_t>(j) * TILE + cc) * a.ldx + row0 + rr, acc[i][jj]);
+        }
+      }
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) atomicAdd(a.xdone + static_cast<int64_t>(l) * a.C + j, 1);
+    } else {
+      // ---- U(i, r, j, l) ----
+      const int64_t o2 = o - static_cast<int64_t>(Rl) * a.C;
+      const int64_t q = static_cast<int64_t>(l + 1) * a.R + o2 / a.C;
+      const int j = static_cast<int>(o2 % a.C);
+      const int i = static_cast<int>(imin64(q / a.R, a.N - 1));
+      const int r = static_cast<int>(q - static_cast<int64_t>(i) * a.R);
+      if (tid == 0) {
+        bool ok = wait_geq_b(a.xdone + static_cast<int64_t>(l) * a.C + j, Rl, err);
+        if (ok && l > 0) ok = wait_geq_b(a.wdone + q * a.C + j, l, err);
+        s_ok = ok;
+      }
+      __syncthreads();
+      if (!s_ok) break;
+      const int64_t si = static_cast<int64_t>(i) * a.n0;
+      const int64_t mi = imin64(a.n0, a.n - si);
+      const int64_t row0 = si + static_cast<int64_t>(r) * TILE;
+      const int m = static_cast<int>(imin64(TILE, mi - static_cast<int64_t>(r) * TILE));
+      const int nc = static_cast<int>(imin64(TILE, a.k - static_cast<int64_t>(j) * TILE));
+      tile_mma<T, false, true>(a.Loff + s0 * a.ldoff + row0, a.ldoff,
+                               a.X + static_cast<int64_t>(j) * TILE * a.ldx + s0, a.ldx, m, nc, 0, ml, sm, acc);
+#pragma unroll
+      for (int ii = 0; ii < TM; ++ii) {
+        const int rr = ty * TM + ii;
+        if (rr >= m) continue;
+#pragma unroll
+        for (int jj = 0; jj < TN; ++jj) {
+          const int cc = tx * TN + jj;
+          if (cc >= nc) continue;
+          const int64_t col = static_cast<int64_t>(j) * TILE + cc;
+          // the first update of a tile starts from B, the others from W
+          const T base = (l == 0) ? a.B[col * a.ldb + row0 + rr] : __ldcg(a.W + col * a.ldw + row0 + rr);
+          __stcg(a.W + col * a.ldw + row0 + rr, base - acc[ii][jj]);
+        }
+      }
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) atomicAdd(a.wdone + q * a.C + j, 1);
+    }
+    __syncthreads();
+  }
+}
+
+inline int64_t align4b(int64_t x) { return (x + 3) / 4 * 4; }
+inline size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+
+}  // namespace
+}  // namespace trsm
+
+struct trsm_batch_s {
+  int dtype = TRSM_F64;
+  int count = 0;
+  int device = 0;
+  void* sys_dev = nullptr;   // BatchSys<T>[count]
+  void* ws = nullptr;        // W, inverses, scratch, counters
+  size_t ws_bytes = 0;
+  size_t counters_off = 0;   // counters, statuses, ticket, error: zeroed by every run
+  int* status_dev = nullptr; // [count]
+  unsigned long long* ticket = nullptr;
+  int* err = nullptr;
+  int64_t total = 0;
+  int grid = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaStream_t capture_stream = nullptr;
+};
+
+namespace {
+
+template <class T>
+int build_batch(const trsm_batch_item* items, int count, trsm_batch_s* b) {
+  using trsm::BatchSys;
+  std::vector<BatchSys<T>> sys(count);
+  // pass 1: sizes and workspace layout
+  size_t off = 0;
+  struct Off {
+    size_t W, inv, tsc;
+  };
+  std::vector<Off> offs(count);
+  int64_t task = 0;
+  for (int s = 0; s < count; ++s) {
+    const trsm_batch_item& it = items[s];
+    BatchSys<T>& a = sys[s];
+    a.n = it.n;
+    a.k = it.k;
+    const bool planned = it.plan != nullptr;
+    int64_t n0 = planned ? 0 : it.n0;
+    if (planned) {
+      int64_t pn = 0, pn0 = 0, pnb = 0;
+      trsm_plan_sizes(it.plan, &pn, &pn0, &pnb);
+      n0 = pn0;
+    }
+    a.n0 = std::min<int64_t>(n0, it.n);
+    a.N = static_cast<int>((a.n + a.n0 - 1) / a.n0);
+    a.R = static_cast<int>((a.n0 + trsm::TILE - 1) / trsm::TILE);
+    const int64_t mlast = a.n - static_cast<int64_t>(a.N - 1) * a.n0;
+    a.Rlast = static_cast<int>((mlast + trsm::TILE - 1) / trsm::TILE);
+    a.C = static_cast<int>((a.k + trsm::TILE - 1) / trsm::TILE);
+    a.total_rt = static_cast<int64_t>(a.N - 1) * a.R + a.Rlast;
+    a.inv_tasks = planned ? 0 : a.N;
+    a.task0 = task;
+    task += a.inv_tasks + trsm::wave_first(a.N - 1, a.R, a.total_rt, a.C) + static_cast<int64_t>(a.Rlast) * a.C;
+    a.ldw = trsm::align4b(a.n);
+    offs[s].W = off;
+    off = trsm::al256(off + sizeof(T) * a.ldw * a.k);
+    offs[s].inv = off;
+    if (!planned) off = trsm::al256(off + sizeof(T) * a.N * a.n0 * a.n0);
+    offs[s].tsc = off;
+    if (!planned && a.n0 > 32) off = trsm::al256(off + sizeof(T) * a.N * 1024);
+  }
+  b->counters_off = off;
+  size_t cnt = 0;
+  std::vector<size_t> coff(count);
+  for (int s = 0; s < count; ++s) {
+    coff[s] = cnt;
+    cnt += static_cast<size_t>(sys[s].total_rt * sys[s].C + static_cast<int64_t>(sys[s].N) * sys[s].C + sys[s].N);
+  }
+  off = trsm::al256(off + sizeof(int) * cnt);
+  const size_t status_off = off;
+  off = trsm::al256(off + sizeof(int) * count);
+  const size_t ticket_off = off;
+  off = trsm::al256(off + sizeof(unsigned long long) + sizeof(int));
+  b->ws_bytes = off;
+  cudaError_t e = cudaMalloc(&b->ws, b->ws_bytes);
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? TRSM_ENOMEM : TRSM_ECUDA;
+  unsigned char* ws = static_cast<unsigned char*>(b->ws);
+  int* cbase = reinterpret_cast<int*>(ws + b->counters_off);
+  b->status_dev = reinterpret_cast<int*>(ws + status_off);
+  b->ticket = reinterpret_cast<unsigned long long*>(ws + ticket_off);
+  b->err = reinterpret_cast<int*>(ws + ticket_off + sizeof(unsigned long long));
+  // pass 2: pointers
+  for (int s = 0; s < count; ++s) {
+    const trsm_batch_item& it = items[s];
+    BatchSys<T>& a = sys[s];
+    a.B = static_cast<const T*>(it.B);
+    a.ldb = it.ldb;
+    a.X = static_cast<T*>(it.X);
+    a.ldx = it.ldx;
+    a.W = reinterpret_cast<T*>(ws + offs[s].W);
+    if (it.plan) {
+      int64_t ldt = 0;
+      const double* Lt = trsm_plan_lt(it.plan, &ldt);
+      a.Linv = reinterpret_cast<const T*>(Lt);
+      a.ldinv = ldt;
+      a.inv_bstride = ldt * a.n0 + a.n0;
+      a.Loff = reinterpret_cast<const T*>(Lt);
+      a.ldoff = ldt;
+      a.L = nullptr;
+      a.ldl = 0;
+      a.Tsc = nullptr;
+    } else {
+      a.Linv = reinterpret_cast<const T*>(ws + offs[s].inv);
+      a.ldinv = a.n0;
+      a.inv_bstride = a.n0 * a.n0;
+      a.Loff = static_cast<const T*>(it.L);
+      a.ldoff = it.ldl;
+      a.L = static_cast<const T*>(it.L);
+      a.ldl = it.ldl;
+      a.Tsc = reinterpret_cast<T*>(ws + offs[s].tsc);
+    }
+    int* c = cbase + coff[s];
+    a.wdone = c;
+    a.xdone = c + a.total_rt * a.C;
+    a.invdone = a.xdone + static_cast<int64_t>(a.N) * a.C;
+    a.status = b->status_dev + s;
+  }
+  b->total = task;
+  e = cudaMalloc(&b->sys_dev, sizeof(BatchSys<T>) * count);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->sys_dev, sys.data(), sizeof(BatchSys<T>) * count, cudaMemcpyHostToDevice);
+  int per_sm = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trsm::batch_kernel<T>, trsm::NTHREADS, 0);
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? TRSM_ENOMEM : TRSM_ECUDA;
+  per_sm = std::max(1, std::min(per_sm, 8));
+  b->grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(static_cast<int64_t>(trsm::device_sm_count()) * per_sm,
+                                                                    b->total)));
+  return TRSM_SUCCESS;
+}
+
+int enqueue(trsm_batch_s* b, cudaStream_t s) {
+  if (b->total == 0) return TRSM_SUCCESS;
+  // counters, per-system statuses (0 = fine), ticket and error word start at zero
+  cudaError_t e = cudaMemsetAsync(static_cast<unsigned char*>(b->ws) + b->counters_off, 0,
+                                  b->ws_bytes - b->counters_off, s);
+  if (e != cudaSuccess) return TRSM_ECUDA;
+  if (b->dtype == TRSM_F64)
+    trsm::batch_kernel<double><<<b->grid, trsm::NTHREADS, 0, s>>>(
+        static_cast<const trsm::BatchSys<double>*>(b->sys_dev), b->count, b->total, b->ticket, b->err);
+  else
+    trsm::batch_kernel<float><<<b->grid, trsm::NTHREADS, 0, s>>>(
+        static_cast<const trsm::BatchSys<float>*>(b->sys_dev), b->count, b->total, b->ticket, b->err);
+  trsm::count_launch();
+  return cudaGetLastError() == cudaSuccess ? TRSM_SUCCESS : TRSM_ECUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+int trsm_batch_create(const trsm_batch_item* items, int count, int dtype, trsm_batch_t* out) {
+  if (out) *out = nullptr;
+  if (!items || count < 1 || !out || (dtype != TRSM_F64 && dtype != TRSM_F32)) return TRSM_EINVAL;
+  for (int s = 0; s < count; ++s) {
+    const trsm_batch_item& it = items[s];
+    if (it.n < 1 || it.k < 1 || !it.B || !it.X || it.ldb < it.n || it.ldx < it.n || it.B == it.X)
+      return TRSM_EINVAL;
+    if (it.plan) {
+      if (dtype != TRSM_F64) return TRSM_EINVAL;
+      int64_t pn = 0;
+      trsm_plan_sizes(it.plan, &pn, nullptr, nullptr);
+      if (pn != it.n) return TRSM_EINVAL;
+    } else if (!it.L || it.ldl < it.n || !(it.n0 == 32 || it.n0 == 64)) {
+      return TRSM_EINVAL;
+    }
+  }
+  trsm_batch_s* b = new (std::nothrow) trsm_batch_s;
+  if (!b) return TRSM_ENOMEM;
+  b->dtype = dtype;
+  b->count = count;
+  cudaGetDevice(&b->device);
+  const int rc = dtype == TRSM_F64 ? build_batch<double>(items, count, b) : build_batch<float>(items, count, b);
+  if (rc != TRSM_SUCCESS) {
+    trsm_batch_destroy(b);
+    cudaGetLastError();
+    return rc;
+  }
+  *out = b;
+  return TRSM_SUCCESS;
+}
+
+int trsm_batch_run(trsm_batch_t b, void* stream) {
+  if (!b) return TRSM_EINVAL;
+  return enqueue(b, static_cast<cudaStream_t>(stream));
+}
+
+int trsm_batch_capture(trsm_batch_t b, void* stream) {
+  if (!b) return TRSM_EINVAL;
+  (void)stream;
+  // Capture on a private stream: the legacy default stream cannot be captured.
+  if (!b->capture_stream &&
+      cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return TRSM_ECUDA;
+  cudaStream_t s = b->capture_stream;
+  if (b->graph_exec) {
+    cudaGraphExecDestroy(b->graph_exec);
+    b->graph_exec = nullptr;
+  }
+  if (b->graph) {
+    cudaGraphDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return TRSM_ECUDA;
+  const int rc = enqueue(b, s);
+  e = cudaStreamEndCapture(s, &b->graph);
+  if (rc != TRSM_SUCCESS || e != cudaSuccess) {
+    cudaGetLastError();
+    return TRSM_ECUDA;
+  }
+  e = cudaGraphInstantiate(&b->graph_exec, b->graph, 0);
+  return e == cudaSuccess ? TRSM_SUCCESS : TRSM_ECUDA;
+}
+
+int trsm_batch_launch_graph(trsm_batch_t b, void* stream) {
+  if (!b || !b->graph_exec) return TRSM_EINVAL;
+  trsm::count_launch();
+  return cudaGraphLaunch(b->graph_exec, static_cast<cudaStream_t>(stream)) == cudaSuccess ? TRSM_SUCCESS
+                                                                                           : TRSM_ECUDA;
+}
+
+int trsm_batch_status(trsm_batch_t b, void* stream, int* first_bad_item, int64_t* singular_row) {
+  if (first_bad_item) *first_bad_item = -1;
+  if (singular_row) *singular_row = -1;
+  if (!b) return TRSM_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<int> st(b->count);
+  int herr = 0;
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemcpy(st.data(), b->status_dev, sizeof(int) * b->count, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&herr, b->err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return TRSM_ECUDA;
+  if (herr) return TRSM_ETIMEOUT;
+  for (int i = 0; i < b->count; ++i)
+    if (st[i] != 0) {
+      if (first_bad_item) *first_bad_item = i;
+      if (singular_row) *singular_row = INT_MAX - st[i];
+      return TRSM_ESINGULAR;
+    }
+  return TRSM_SUCCESS;
+}
+
+void trsm_batch_destroy(trsm_batch_t b) {
+  if (!b) return;
+  if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+  if (b->sys_dev) cudaFree(b->sys_dev);
+  if (b->ws) cudaFree(b->ws);
+  delete b;
+}
+
+size_t trsm_batch_workspace_bytes(trsm_batch_t b) { return b ? b->ws_bytes : 0; }
+
+}  // extern "C"

@@ -1,0 +1,126 @@
+"""Many uneven systems in one persistent launch, against the CPU oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1612_01855_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 2e-4  # FP32 arithmetic: n eps32 kappa for n <= 1024, kappa ~ 1.5
+
+
+def _dev(a, dtype):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(a, dtype=dtype).T)).cuda().t()
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _systems(count, nmax, kmax, seed, dtype=np.float64, n0s=(32, 64)):
+    import torch
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(np.rint(np.exp(rng.uniform(np.log(1), np.log(nmax)))))
+        k = int(np.rint(np.exp(rng.uniform(np.log(1), np.log(kmax)))))
+        L, B = inputs.well_conditioned(n, k, seed=seed * 1000 + i)
+        out.append({"Lh": L, "Bh": B, "L": _dev(L, dtype), "B": _dev(B, dtype),
+                    "X": torch.full((k, n), float("nan"), dtype=torch.float64 if dtype == np.float64
+                                    else torch.float32, device="cuda").t(),
+                    "n0": n0s[i % len(n0s)]})
+    return out
+
+
+def test_batch_fp64_uneven(cuda_lib):
+    import paper_1612_01855_gb300 as g
+    systems = _systems(60, 300, 70, seed=1)
+    batch = g.Batch(systems)
+    batch.run()
+    rc, item, row = batch.status()
+    assert rc == 0
+    for sy in systems:
+        want = oracle.forward_subst(sy["Lh"], sy["Bh"])
+        assert _rel(sy["X"].cpu().numpy(), want) < TOL64
+
+
+def test_batch_fp32_uneven(cuda_lib):
+    import paper_1612_01855_gb300 as g
+    systems = _systems(40, 400, 50, seed=2, dtype=np.float32)
+    batch = g.Batch(systems, dtype="f32")
+    batch.run()
+    assert batch.status()[0] == 0
+    for sy in systems:
+        want = oracle.forward_subst(sy["Lh"].astype(np.float32).astype(np.float64),
+                                    sy["Bh"].astype(np.float32).astype(np.float64))
+        assert _rel(sy["X"].cpu().numpy().astype(np.float64), want) < TOL32
+
+
+def test_batch_with_resident_plans_and_graph(cuda_lib):
+    """Items with resident plans (any n0) next to plan-less items; a captured
+    CUDA graph replays the same results."""
+    import torch
+    import paper_1612_01855_gb300 as g
+    systems = _systems(12, 700, 90, seed=3)
+    plans = []
+    for i, sy in enumerate(systems):
+        if i % 2 == 0:
+            p = g.trsm_plan(sy["L"], [32, 100, 256][i % 3])
+            plans.append(p)
+            sy["plan"] = p
+    batch = g.Batch(systems)
+    batch.run()
+    assert batch.status()[0] == 0
+    first = [sy["X"].clone() for sy in systems]
+    for sy in systems:
+        want = oracle.forward_subst(sy["Lh"], sy["Bh"])
+        assert _rel(sy["X"].cpu().numpy(), want) < TOL64
+    batch.capture()
+    for sy in systems:
+        sy["X"].fill_(float("nan"))
+    batch.launch_graph()
+    batch.launch_graph()
+    assert batch.status()[0] == 0
+    for sy, x0 in zip(systems, first):
+        assert torch.equal(sy["X"], x0)
+
+
+def test_batch_result_is_the_same_alone_and_in_the_mix(cuda_lib):
+    import torch
+    import paper_1612_01855_gb300 as g
+    systems = _systems(30, 500, 64, seed=4)
+    g.Batch(systems).run()
+    for i in (0, 7, 19):
+        sy = systems[i]
+        alone = dict(sy)
+        alone["X"] = torch.empty_like(sy["X"].t()).t()
+        b = g.Batch([alone])
+        b.run()
+        assert b.status()[0] == 0
+        assert torch.equal(alone["X"], sy["X"])
+
+
+def test_batch_reports_singular_item(cuda_lib):
+    import paper_1612_01855_gb300 as g
+    systems = _systems(6, 120, 8, seed=5)
+    bad = systems[4]
+    n = bad["Lh"].shape[0]
+    r = n // 2
+    bad["L"][r, r] = 0.0
+    rc, item, row = (lambda b: (b.run(), b.status())[1])(g.Batch(systems))
+    assert rc == -2 and item == 4 and row == r
+
+
+def test_batch_argument_errors(cuda_lib):
+    import paper_1612_01855_gb300 as g
+    systems = _systems(2, 50, 4, seed=6)
+    systems[1]["n0"] = 48  # only 32 and 64 are inverted in-launch
+    with pytest.raises(g.TrsmError):
+        g.Batch(systems)
+    systems[1]["n0"] = 32
+    systems[1]["X"] = systems[1]["B"]  # X must not alias B
+    with pytest.raises(g.TrsmError):
+        g.Batch(systems)
