@@ -184,6 +184,62 @@ def precision_study(g, torch, n, k, n0, cs, inners, s_modes, dd_cols=2, stream=N
     return out
 
 
+def batched_study(g, torch, count=4096, dtypes=("f64", "f32"), reps=5, seed=1000):
+    """Batching workload: `count` independent systems, n log-uniform in
+    [32, 1024], k log-uniform in [1, 256], diagonal U[2,3], strictly lower
+    U[-1,1]/n, B U[-1,1] (drawn on the device from a per-system seed), all
+    solved (in-launch inversion + blocked solve) by one persistent launch,
+    replayed as a CUDA graph; n0 per size bucket from the autotuner."""
+    from paper_1612_01855_gb300 import autotune
+    rng = np.random.default_rng(seed)
+    ns = np.rint(np.exp(rng.uniform(np.log(32), np.log(1024), size=count))).astype(int)
+    ks = np.rint(np.exp(rng.uniform(0.0, np.log(256), size=count))).astype(int)
+    flops = float(np.sum(ns.astype(np.float64) ** 2 * ks))
+    out = []
+    for dtype in dtypes:
+        table = autotune.tune_batch_n0(dtype)
+        tdt = torch.float64 if dtype == "f64" else torch.float32
+        gen = torch.Generator(device="cuda")
+        systems = []
+        for i, (n, k) in enumerate(zip(ns, ks)):
+            gen.manual_seed(seed + i)
+            L = torch.rand((n, n), generator=gen, device="cuda", dtype=tdt).mul_(2).sub_(1).div_(int(n))
+            L = torch.tril(L, -1)
+            L.diagonal().copy_(torch.rand(int(n), generator=gen, device="cuda", dtype=tdt).add_(2))
+            L = L.t().contiguous().t()
+            B = torch.rand((int(k), int(n)), generator=gen, device="cuda", dtype=tdt).mul_(2).sub_(1).t()
+            X = torch.empty((int(k), int(n)), device="cuda", dtype=tdt).t()
+            systems.append({"L": L, "B": B, "X": X, "n0": autotune.choose_n0(int(n), dtype, table)})
+        batch = g.Batch(systems, dtype=dtype)
+        batch.capture()
+        for _ in range(2):
+            batch.launch_graph()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            batch.launch_graph()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        rc = batch.status()[0]
+        # spot check three systems against a plain solve of the same data
+        err = 0.0
+        for i in (0, count // 2, count - 1):
+            sy = systems[i]
+            ref = torch.linalg.solve_triangular(sy["L"].double(), sy["B"].double(), upper=False)
+            err = max(err, float((sy["X"].double() - ref).abs().max() / ref.abs().max()))
+        out.append({"dtype": dtype, "systems": count, "ms_per_batch": round(ms, 3),
+                    "tflops_n2k": round(flops / (ms * 1e-3) / 1e12, 3), "status": rc,
+                    "n0_by_bucket": {f"{lo}-{hi - 1}": table[i] for i, (lo, hi) in enumerate(autotune.BUCKETS)},
+                    "workspace_gb": round(batch.workspace_bytes() / 1e9, 3),
+                    "spot_check_rel_err": err, "graph": True,
+                    "inputs": "device-generated per-system seeds (torch Philox), config-0 distributions"})
+        batch.destroy()
+        del systems
+    return out
+
+
 def run_case(args):
     """Single kernels for profiling (no JSON bench line):
     sliced:N:K       the tensor-core residual R = B - L X, twice;
@@ -402,6 +458,10 @@ def run_ours(args, rank, world, local):
     if rank == 0 and not args.no_mixed and not args.shapes:
         mixed = precision_study(g, torch, 16384, 4096, 256, [2], ["tf32"], [False, True], dd_cols=2)
 
+    batched = None
+    if rank == 0 and not args.no_batched and not args.shapes:
+        batched = batched_study(g, torch)
+
     if args.precision and rank == 0:
         for rec in precision_study(g, torch, 16384, 4096, 256, [2, 4, 6], ["tf32", "bf16"], [False, True]):
             print(json.dumps({"precision_study": True, **rec}), flush=True)
@@ -449,6 +509,7 @@ def run_ours(args, rank, world, local):
                          "traffic": None},
             "parity_max_rel_err": err,
             "mixed_precision": mixed,
+            "batched": batched,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "gpu_launches": launches,
@@ -469,6 +530,7 @@ def main():
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision refinement figure")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-systems figure")
     ap.add_argument("--precision", action="store_true", help="print the full c x inner x s-step study")
     ap.add_argument("--case", default="", help="profiling case: sliced:N:K, mixed:N:K:N0, engine:M:N:K")
     ap.add_argument("--shapes", default="", help="override workload, e.g. 6144:1024:256 (not a bench line)")

@@ -2,15 +2,19 @@
 //
 // Every system is Algorithm It-Inv-TRSM (Section 6.2) on its own L, B, X;
 // the systems differ in n, k and block size.  One kernel serves all of
-// them: each CTA repeatedly takes the next ticket of a global counter, and
-// tickets enumerate the systems one after another, each as
+// them: each CTA repeatedly takes the next ticket of a global counter.  The
+// tasks of a system are
 //   INV(b)          invert diagonal block b (only when the system has no plan:
 //                   Algorithm RecTriInv with one level, n0 <= 64)
 //   wave l:  S(l, r, j)        X_l[r, j]  = L~_ll[r, :] W_l[:, j]
 //            U(i, r, j, l)     W_i[r, j] -= L_il[r, :] X_l[:, j]      (i > l)
-// with the same dependency counters as the single-system kernel: a task's
-// dependencies always hold smaller tickets (same system, earlier position),
-// so the scheme cannot deadlock whatever the residency.  The first update
+// with the same dependency counters as the single-system kernel.  Tickets
+// run phase-major: phase 0 holds the INV tasks of every system, phase
+// l + 1 wave l of every system that has one.  The tickets in flight at any
+// time therefore belong to many systems at the same stage instead of one
+// system's dependency chain, and every dependency of a task (same system,
+// earlier phase or earlier in its wave) still holds a smaller ticket: the
+// scheme cannot deadlock whatever the residency.  The first update
 // of a tile reads B instead of the working copy W, so no copy launch is
 // needed and a whole batch is one memset plus one kernel (and so one CUDA
 // graph).  The arithmetic type T is double or float.
@@ -49,7 +53,6 @@ struct BatchSys {
   int64_t n, k, n0;
   int N, R, Rlast, C;
   int64_t total_rt;
-  int64_t task0;        // first ticket of the system
   int64_t inv_tasks;    // N when the system inverts its own blocks, else 0
   int* wdone;           // [total_rt * C]
   int* xdone;           // [N * C]
@@ -121,9 +124,17 @@ __device__ void leaf_invert_warp(const T* __restrict__ A, int64_t lda, int m, T*
     for (int c = 0; c < m; ++c) out[static_cast<int64_t>(c) * ldo + lane] = ls[lane][c];
 }
 
+// One (phase, system) range of tickets.
+struct PhaseEntry {
+  int64_t first;  // first ticket
+  int sys;        // system index
+  int phase;      // 0: INV tasks, l + 1: wave l
+};
+
 template <class T>
-__global__ void __launch_bounds__(NTHREADS) batch_kernel(const BatchSys<T>* __restrict__ sys, int nsys,
-                                                        int64_t total, unsigned long long* ticket, int* err) {
+__global__ void __launch_bounds__(NTHREADS, 4) batch_kernel(const BatchSys<T>* __restrict__ sys,
+                                                           const PhaseEntry* __restrict__ ent, int nent,
+                                                           int64_t total, unsigned long long* ticket, int* err) {
   __shared__ TileSmemT<T> sm;
   __shared__ T ls[2][32][33];
   __shared__ long long s_ticket;
@@ -135,15 +146,16 @@ __global__ void __launch_bounds__(NTHREADS) batch_kernel(const BatchSys<T>* __re
     __syncthreads();
     const int64_t t = s_ticket;
     if (t >= total) break;
-    int lo = 0, hi = nsys - 1;
+    int lo = 0, hi = nent - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
-      if (sys[mid].task0 <= t) lo = mid;
+      if (ent[mid].first <= t) lo = mid;
       else hi = mid - 1;
     }
-    const BatchSys<T>& a = sys[lo];
-    int64_t o = t - a.task0;
-    if (o < a.inv_tasks) {
+    const PhaseEntry pe = ent[lo];
+    const BatchSys<T>& a = sys[pe.sys];
+    int64_t o = t - pe.first;
+    if (pe.phase == 0) {
       // ---- INV(b): diagonal block b of order m <= 64 ----
       const int b = static_cast<int>(o);
       const int64_t s0 = static_cast<int64_t>(b) * a.n0;
@@ -189,18 +201,7 @@ __global__ void __launch_bounds__(NTHREADS) batch_kernel(const BatchSys<T>* __re
       if (tid == 0) atomicAdd(a.invdone + b, 1);
       continue;
     }
-    o -= a.inv_tasks;
-    int l = 0;
-    {
-      int l0 = 0, l1 = a.N - 1;
-      while (l0 < l1) {
-        const int mid = (l0 + l1 + 1) >> 1;
-        if (wave_first(mid, a.R, a.total_rt, a.C) <= o) l0 = mid;
-        else l1 = mid - 1;
-      }
-      l = l0;
-    }
-    o -= wave_first(l, a.R, a.total_rt, a.C);
+    const int l = pe.phase - 1;
     const int Rl = (l == a.N - 1) ? a.Rlast : a.R;
     const int64_t s0 = static_cast<int64_t>(l) * a.n0;
     const int64_t ml = imin64(a.n0, a.n - s0);
@@ -299,7 +300,9 @@ struct trsm_batch_s {
   int dtype = TRSM_F64;
   int count = 0;
   int device = 0;
-  void* sys_dev = nullptr;   // BatchSys<T>[count]
+  void* sys_dev = nullptr;   // BatchSys<T>[count], then the phase entries
+  void* ent_dev = nullptr;
+  int nent = 0;
   void* ws = nullptr;        // W, inverses, scratch, counters
   size_t ws_bytes = 0;
   size_t counters_off = 0;   // counters, statuses, ticket, error: zeroed by every run
@@ -325,7 +328,6 @@ int build_batch(const trsm_batch_item* items, int count, trsm_batch_s* b) {
     size_t W, inv, tsc;
   };
   std::vector<Off> offs(count);
-  int64_t task = 0;
   for (int s = 0; s < count; ++s) {
     const trsm_batch_item& it = items[s];
     BatchSys<T>& a = sys[s];
@@ -346,8 +348,6 @@ int build_batch(const trsm_batch_item* items, int count, trsm_batch_s* b) {
     a.C = static_cast<int>((a.k + trsm::TILE - 1) / trsm::TILE);
     a.total_rt = static_cast<int64_t>(a.N - 1) * a.R + a.Rlast;
     a.inv_tasks = planned ? 0 : a.N;
-    a.task0 = task;
-    task += a.inv_tasks + trsm::wave_first(a.N - 1, a.R, a.total_rt, a.C) + static_cast<int64_t>(a.Rlast) * a.C;
     a.ldw = trsm::align4b(a.n);
     offs[s].W = off;
     off = trsm::al256(off + sizeof(T) * a.ldw * a.k);
@@ -412,10 +412,37 @@ int build_batch(const trsm_batch_item* items, int count, trsm_batch_s* b) {
     a.invdone = a.xdone + static_cast<int64_t>(a.N) * a.C;
     a.status = b->status_dev + s;
   }
+  // phase-major ticket ranges
+  int maxN = 0;
+  for (int s = 0; s < count; ++s) maxN = std::max(maxN, sys[s].N);
+  std::vector<trsm::PhaseEntry> ent;
+  int64_t task = 0;
+  for (int p = 0; p <= maxN; ++p) {
+    for (int s = 0; s < count; ++s) {
+      const BatchSys<T>& a = sys[s];
+      int64_t cntp = 0;
+      if (p == 0) {
+        cntp = a.inv_tasks;
+      } else if (p - 1 < a.N) {
+        const int l = p - 1;
+        const int Rl = (l == a.N - 1) ? a.Rlast : a.R;
+        const int64_t below = std::max<int64_t>(0, a.total_rt - static_cast<int64_t>(l + 1) * a.R);
+        cntp = (static_cast<int64_t>(Rl) + below) * a.C;
+      }
+      if (cntp > 0) {
+        ent.push_back(trsm::PhaseEntry{task, s, p});
+        task += cntp;
+      }
+    }
+  }
   b->total = task;
-  e = cudaMalloc(&b->sys_dev, sizeof(BatchSys<T>) * count);
+  b->nent = static_cast<int>(ent.size());
+  e = cudaMalloc(&b->sys_dev, sizeof(BatchSys<T>) * count + sizeof(trsm::PhaseEntry) * ent.size());
   if (e == cudaSuccess)
     e = cudaMemcpy(b->sys_dev, sys.data(), sizeof(BatchSys<T>) * count, cudaMemcpyHostToDevice);
+  b->ent_dev = reinterpret_cast<unsigned char*>(b->sys_dev) + sizeof(BatchSys<T>) * count;
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->ent_dev, ent.data(), sizeof(trsm::PhaseEntry) * ent.size(), cudaMemcpyHostToDevice);
   int per_sm = 0;
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trsm::batch_kernel<T>, trsm::NTHREADS, 0);
@@ -434,10 +461,12 @@ int enqueue(trsm_batch_s* b, cudaStream_t s) {
   if (e != cudaSuccess) return TRSM_ECUDA;
   if (b->dtype == TRSM_F64)
     trsm::batch_kernel<double><<<b->grid, trsm::NTHREADS, 0, s>>>(
-        static_cast<const trsm::BatchSys<double>*>(b->sys_dev), b->count, b->total, b->ticket, b->err);
+        static_cast<const trsm::BatchSys<double>*>(b->sys_dev), static_cast<const trsm::PhaseEntry*>(b->ent_dev),
+        b->nent, b->total, b->ticket, b->err);
   else
     trsm::batch_kernel<float><<<b->grid, trsm::NTHREADS, 0, s>>>(
-        static_cast<const trsm::BatchSys<float>*>(b->sys_dev), b->count, b->total, b->ticket, b->err);
+        static_cast<const trsm::BatchSys<float>*>(b->sys_dev), static_cast<const trsm::PhaseEntry*>(b->ent_dev),
+        b->nent, b->total, b->ticket, b->err);
   trsm::count_launch();
   return cudaGetLastError() == cudaSuccess ? TRSM_SUCCESS : TRSM_ECUDA;
 }
