@@ -240,6 +240,52 @@ def batched_study(g, torch, count=4096, dtypes=("f64", "f32"), reps=5, seed=1000
     return out
 
 
+def serving_study(g, torch, nL=256, rates=(100, 300, 600, 1200), per_rate=300, seed=2000,
+                  budget_gb=150.0):
+    """Serving workload: nL resident L (n log-uniform in [64, 8192],
+    diagonal U[2,3], strictly lower U[-1,1]/n, drawn on the device), each
+    planned once; Poisson request streams at the given rates, each request a
+    B with k log-uniform in [1, 2048] for a random resident L; continuous
+    batching under an HBM budget.  Reports solves/s and p50/p99 latency."""
+    from paper_1612_01855_gb300.serve import Request, Server
+    rng = np.random.default_rng(seed)
+    ns = np.rint(np.exp(rng.uniform(np.log(64), np.log(8192), size=nL))).astype(int)
+    gen = torch.Generator(device="cuda")
+    plans = []
+    t0 = time.perf_counter()
+    for i, n in enumerate(ns):
+        gen.manual_seed(seed + i)
+        L = torch.rand((int(n), int(n)), generator=gen, device="cuda", dtype=torch.float64).mul_(2).sub_(1).div_(int(n))
+        L = torch.tril(L, -1)
+        L.diagonal().copy_(torch.rand(int(n), generator=gen, device="cuda", dtype=torch.float64).add_(2))
+        L = L.t().contiguous().t()
+        plans.append(g.trsm_plan(L, 256 if n >= 1024 else 64))
+        del L
+    plan_s = time.perf_counter() - t0
+    out = {"resident_L": nL, "plan_seconds": round(plan_s, 2),
+           "resident_gb": round(sum(8.0 * p.n * p.n for p in plans) / 1e9, 2), "budget_gb": budget_gb,
+           "rates": []}
+    for rate in rates:
+        reqs = []
+        t = 0.0
+        for rid in range(per_rate):
+            t += rng.exponential(1.0 / rate)
+            lid = int(rng.integers(0, nL))
+            k = int(np.rint(np.exp(rng.uniform(0.0, np.log(2048)))))
+            gen.manual_seed(seed * 7 + rid)
+            B = torch.rand((k, int(ns[lid])), generator=gen, device="cuda", dtype=torch.float64).mul_(2).sub_(1).t()
+            reqs.append(Request(rid, lid, B, t))
+        torch.cuda.synchronize()
+        srv = Server(plans, budget_bytes=int(budget_gb * 1e9), streams=2, max_batch=64)
+        st = srv.run_trace(reqs)
+        st["offered_rate"] = rate
+        out["rates"].append({k: (round(v, 4) if isinstance(v, float) else v) for k, v in st.items()})
+        del reqs, srv
+    for p in plans:
+        p.destroy()
+    return out
+
+
 def run_case(args):
     """Single kernels for profiling (no JSON bench line):
     sliced:N:K       the tensor-core residual R = B - L X, twice;
@@ -462,6 +508,10 @@ def run_ours(args, rank, world, local):
     if rank == 0 and not args.no_batched and not args.shapes:
         batched = batched_study(g, torch)
 
+    serving = None
+    if rank == 0 and not args.no_serving and not args.shapes:
+        serving = serving_study(g, torch)
+
     if args.precision and rank == 0:
         for rec in precision_study(g, torch, 16384, 4096, 256, [2, 4, 6], ["tf32", "bf16"], [False, True]):
             print(json.dumps({"precision_study": True, **rec}), flush=True)
@@ -510,6 +560,7 @@ def run_ours(args, rank, world, local):
             "parity_max_rel_err": err,
             "mixed_precision": mixed,
             "batched": batched,
+            "serving": serving,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "gpu_launches": launches,
@@ -531,6 +582,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision refinement figure")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-systems figure")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving figure")
     ap.add_argument("--precision", action="store_true", help="print the full c x inner x s-step study")
     ap.add_argument("--case", default="", help="profiling case: sliced:N:K, mixed:N:K:N0, engine:M:N:K")
     ap.add_argument("--shapes", default="", help="override workload, e.g. 6144:1024:256 (not a bench line)")

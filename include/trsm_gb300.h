@@ -183,6 +183,17 @@ typedef struct trsm_batch_s* trsm_batch_t;
  * TRSM_ECUDA. */
 int trsm_batch_create(const trsm_batch_item* items, int count, int dtype, trsm_batch_t* out);
 
+/* Allocation-free form for a caller-managed arena (e.g. a server that
+ * admits work against a memory budget): trsm_batch_workspace_size gives the
+ * bytes the items need (task tables included); trsm_batch_create_ws lays
+ * the batch out in ws_dev (256-byte aligned, >= that size, owned by the
+ * caller and not freed by trsm_batch_destroy) and uploads its tables on
+ * `stream`.  A batch made this way must run on the same stream (or after
+ * it).  Same errors as trsm_batch_create. */
+int trsm_batch_workspace_size(const trsm_batch_item* items, int count, int dtype, size_t* bytes);
+int trsm_batch_create_ws(const trsm_batch_item* items, int count, int dtype, void* ws_dev, size_t ws_bytes,
+                         void* stream, trsm_batch_t* out);
+
 /* Enqueues one solve of every item (asynchronous). */
 int trsm_batch_run(trsm_batch_t b, void* stream);
 

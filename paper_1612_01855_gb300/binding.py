@@ -56,6 +56,9 @@ SIGNATURES = {
     "trsm_solve_mixed": (_int, [_vp, _dp, _i64, _i64, _dp, _i64, _int, _int, ctypes.c_double,
                                 ctypes.POINTER(_int), ctypes.POINTER(ctypes.c_double), _vp]),
     "trsm_batch_create": (_int, [ctypes.POINTER(BatchItem), _int, _int, ctypes.POINTER(_vp)]),
+    "trsm_batch_workspace_size": (_int, [ctypes.POINTER(BatchItem), _int, _int, ctypes.POINTER(ctypes.c_size_t)]),
+    "trsm_batch_create_ws": (_int, [ctypes.POINTER(BatchItem), _int, _int, _vp, ctypes.c_size_t, _vp,
+                                    ctypes.POINTER(_vp)]),
     "trsm_batch_run": (_int, [_vp, _vp]),
     "trsm_batch_capture": (_int, [_vp, _vp]),
     "trsm_batch_launch_graph": (_int, [_vp, _vp]),
@@ -360,7 +363,32 @@ class Batch:
     (trsm_batch_*).  `systems` is a list of dicts with keys L (or plan), B,
     X (CUDA tensors, column-major) and n0 (32 or 64, plan-less items)."""
 
-    def __init__(self, systems, dtype="f64"):
+    def __init__(self, systems, dtype="f64", arena=None):
+        """arena: optional uint8 CUDA tensor to lay the batch out in (no
+        allocation); it must hold workspace_size(systems) bytes."""
+        torch = _torch()
+        items = self._items(systems, dtype)
+        h = ctypes.c_void_p()
+        code = TRSM_F64 if dtype == "f64" else TRSM_F32
+        if arena is None:
+            _check(load_library().trsm_batch_create(items, len(systems), code, ctypes.byref(h)), "trsm_batch_create")
+        else:
+            _check(load_library().trsm_batch_create_ws(items, len(systems), code, ctypes.c_void_p(arena.data_ptr()),
+                                                       arena.numel(), self._s(), ctypes.byref(h)),
+                   "trsm_batch_create_ws")
+            self._keep.append(arena)
+        self._h = h
+
+    @staticmethod
+    def workspace_size(systems, dtype="f64"):
+        b = Batch.__new__(Batch)
+        items = b._items(systems, dtype)
+        out = ctypes.c_size_t()
+        _check(load_library().trsm_batch_workspace_size(items, len(systems), TRSM_F64 if dtype == "f64" else TRSM_F32,
+                                                        ctypes.byref(out)), "trsm_batch_workspace_size")
+        return out.value
+
+    def _items(self, systems, dtype):
         torch = _torch()
         items = (BatchItem * len(systems))()
         self._keep = []
@@ -383,10 +411,7 @@ class Batch:
                 self._keep.append(L)
             it.B, it.ldb, it.X, it.ldx, it.n, it.k = B.data_ptr(), _ld(B), X.data_ptr(), _ld(X), n, k
             self._keep += [B, X]
-        h = ctypes.c_void_p()
-        _check(load_library().trsm_batch_create(items, len(systems), TRSM_F64 if dtype == "f64" else TRSM_F32,
-                                                ctypes.byref(h)), "trsm_batch_create")
-        self._h = h
+        return items
 
     def _s(self):
         torch = _torch()

@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <cstring>
 #include <new>
 #include <vector>
 
@@ -303,8 +304,10 @@ struct trsm_batch_s {
   void* sys_dev = nullptr;   // BatchSys<T>[count], then the phase entries
   void* ent_dev = nullptr;
   int nent = 0;
-  void* ws = nullptr;        // W, inverses, scratch, counters
+  void* ws = nullptr;        // W, inverses, scratch, counters, task tables
   size_t ws_bytes = 0;
+  bool owns_ws = true;
+  std::vector<unsigned char> host_tables;
   size_t counters_off = 0;   // counters, statuses, ticket, error: zeroed by every run
   int* status_dev = nullptr; // [count]
   unsigned long long* ticket = nullptr;
@@ -319,7 +322,8 @@ struct trsm_batch_s {
 namespace {
 
 template <class T>
-int build_batch(const trsm_batch_item* items, int count, trsm_batch_s* b) {
+int build_batch(const trsm_batch_item* items, int count, trsm_batch_s* b, void* user_ws, size_t user_bytes,
+                cudaStream_t stream, size_t* size_only) {
   using trsm::BatchSys;
   std::vector<BatchSys<T>> sys(count);
   // pass 1: sizes and workspace layout
@@ -356,6 +360,16 @@ int build_batch(const trsm_batch_item* items, int count, trsm_batch_s* b) {
     offs[s].tsc = off;
     if (!planned && a.n0 > 32) off = trsm::al256(off + sizeof(T) * a.N * 1024);
   }
+  // task table and phase entries (uploaded once at creation), kept before
+  // the counters: every run zeroes [counters_off, ws_bytes)
+  int maxN = 0;
+  for (int s = 0; s < count; ++s) maxN = std::max(maxN, sys[s].N);
+  size_t nent_max = 0;
+  for (int s = 0; s < count; ++s) nent_max += static_cast<size_t>(sys[s].N) + (sys[s].inv_tasks > 0 ? 1 : 0);
+  const size_t table_off = off;
+  off = trsm::al256(off + sizeof(BatchSys<T>) * count);
+  const size_t ent_off = off;
+  off = trsm::al256(off + sizeof(trsm::PhaseEntry) * nent_max);
   b->counters_off = off;
   size_t cnt = 0;
   std::vector<size_t> coff(count);
@@ -368,9 +382,21 @@ int build_batch(const trsm_batch_item* items, int count, trsm_batch_s* b) {
   off = trsm::al256(off + sizeof(int) * count);
   const size_t ticket_off = off;
   off = trsm::al256(off + sizeof(unsigned long long) + sizeof(int));
+  if (size_only) {
+    *size_only = off;
+    return TRSM_SUCCESS;
+  }
   b->ws_bytes = off;
-  cudaError_t e = cudaMalloc(&b->ws, b->ws_bytes);
-  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? TRSM_ENOMEM : TRSM_ECUDA;
+  cudaError_t e = cudaSuccess;
+  if (user_ws) {
+    if (user_bytes < off || (reinterpret_cast<uintptr_t>(user_ws) & 255)) return TRSM_EINVAL;
+    b->ws = user_ws;
+    b->owns_ws = false;
+  } else {
+    e = cudaMalloc(&b->ws, b->ws_bytes);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? TRSM_ENOMEM : TRSM_ECUDA;
+    b->owns_ws = true;
+  }
   unsigned char* ws = static_cast<unsigned char*>(b->ws);
   int* cbase = reinterpret_cast<int*>(ws + b->counters_off);
   b->status_dev = reinterpret_cast<int*>(ws + status_off);
@@ -413,8 +439,6 @@ int build_batch(const trsm_batch_item* items, int count, trsm_batch_s* b) {
     a.status = b->status_dev + s;
   }
   // phase-major ticket ranges
-  int maxN = 0;
-  for (int s = 0; s < count; ++s) maxN = std::max(maxN, sys[s].N);
   std::vector<trsm::PhaseEntry> ent;
   int64_t task = 0;
   for (int p = 0; p <= maxN; ++p) {
@@ -437,12 +461,18 @@ int build_batch(const trsm_batch_item* items, int count, trsm_batch_s* b) {
   }
   b->total = task;
   b->nent = static_cast<int>(ent.size());
-  e = cudaMalloc(&b->sys_dev, sizeof(BatchSys<T>) * count + sizeof(trsm::PhaseEntry) * ent.size());
+  b->sys_dev = ws + table_off;
+  b->ent_dev = ws + ent_off;
+  // the host copies stay in the batch until it is destroyed, so the
+  // asynchronous uploads may complete after this call returns
+  b->host_tables.resize(sizeof(BatchSys<T>) * count + sizeof(trsm::PhaseEntry) * ent.size());
+  memcpy(b->host_tables.data(), sys.data(), sizeof(BatchSys<T>) * count);
+  memcpy(b->host_tables.data() + sizeof(BatchSys<T>) * count, ent.data(), sizeof(trsm::PhaseEntry) * ent.size());
+  e = cudaMemcpyAsync(b->sys_dev, b->host_tables.data(), sizeof(BatchSys<T>) * count, cudaMemcpyHostToDevice,
+                      stream);
   if (e == cudaSuccess)
-    e = cudaMemcpy(b->sys_dev, sys.data(), sizeof(BatchSys<T>) * count, cudaMemcpyHostToDevice);
-  b->ent_dev = reinterpret_cast<unsigned char*>(b->sys_dev) + sizeof(BatchSys<T>) * count;
-  if (e == cudaSuccess)
-    e = cudaMemcpy(b->ent_dev, ent.data(), sizeof(trsm::PhaseEntry) * ent.size(), cudaMemcpyHostToDevice);
+    e = cudaMemcpyAsync(b->ent_dev, b->host_tables.data() + sizeof(BatchSys<T>) * count,
+                        sizeof(trsm::PhaseEntry) * ent.size(), cudaMemcpyHostToDevice, stream);
   int per_sm = 0;
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trsm::batch_kernel<T>, trsm::NTHREADS, 0);
@@ -475,9 +505,8 @@ int enqueue(trsm_batch_s* b, cudaStream_t s) {
 
 extern "C" {
 
-int trsm_batch_create(const trsm_batch_item* items, int count, int dtype, trsm_batch_t* out) {
-  if (out) *out = nullptr;
-  if (!items || count < 1 || !out || (dtype != TRSM_F64 && dtype != TRSM_F32)) return TRSM_EINVAL;
+static int validate_items(const trsm_batch_item* items, int count, int dtype) {
+  if (!items || count < 1 || (dtype != TRSM_F64 && dtype != TRSM_F32)) return TRSM_EINVAL;
   for (int s = 0; s < count; ++s) {
     const trsm_batch_item& it = items[s];
     if (it.n < 1 || it.k < 1 || !it.B || !it.X || it.ldb < it.n || it.ldx < it.n || it.B == it.X)
@@ -491,12 +520,22 @@ int trsm_batch_create(const trsm_batch_item* items, int count, int dtype, trsm_b
       return TRSM_EINVAL;
     }
   }
+  return TRSM_SUCCESS;
+}
+
+static int create_impl(const trsm_batch_item* items, int count, int dtype, void* ws, size_t ws_bytes,
+                       cudaStream_t stream, trsm_batch_t* out) {
+  if (out) *out = nullptr;
+  if (!out) return TRSM_EINVAL;
+  int rc = validate_items(items, count, dtype);
+  if (rc != TRSM_SUCCESS) return rc;
   trsm_batch_s* b = new (std::nothrow) trsm_batch_s;
   if (!b) return TRSM_ENOMEM;
   b->dtype = dtype;
   b->count = count;
   cudaGetDevice(&b->device);
-  const int rc = dtype == TRSM_F64 ? build_batch<double>(items, count, b) : build_batch<float>(items, count, b);
+  rc = dtype == TRSM_F64 ? build_batch<double>(items, count, b, ws, ws_bytes, stream, nullptr)
+                         : build_batch<float>(items, count, b, ws, ws_bytes, stream, nullptr);
   if (rc != TRSM_SUCCESS) {
     trsm_batch_destroy(b);
     cudaGetLastError();
@@ -504,6 +543,27 @@ int trsm_batch_create(const trsm_batch_item* items, int count, int dtype, trsm_b
   }
   *out = b;
   return TRSM_SUCCESS;
+}
+
+int trsm_batch_create(const trsm_batch_item* items, int count, int dtype, trsm_batch_t* out) {
+  const int rc = create_impl(items, count, dtype, nullptr, 0, nullptr, out);
+  if (rc == TRSM_SUCCESS && cudaStreamSynchronize(nullptr) != cudaSuccess) return TRSM_ECUDA;
+  return rc;
+}
+
+int trsm_batch_workspace_size(const trsm_batch_item* items, int count, int dtype, size_t* bytes) {
+  if (!bytes) return TRSM_EINVAL;
+  int rc = validate_items(items, count, dtype);
+  if (rc != TRSM_SUCCESS) return rc;
+  trsm_batch_s probe;
+  return dtype == TRSM_F64 ? build_batch<double>(items, count, &probe, nullptr, 0, nullptr, bytes)
+                           : build_batch<float>(items, count, &probe, nullptr, 0, nullptr, bytes);
+}
+
+int trsm_batch_create_ws(const trsm_batch_item* items, int count, int dtype, void* ws_dev, size_t ws_bytes,
+                         void* stream, trsm_batch_t* out) {
+  if (!ws_dev) return TRSM_EINVAL;
+  return create_impl(items, count, dtype, ws_dev, ws_bytes, static_cast<cudaStream_t>(stream), out);
 }
 
 int trsm_batch_run(trsm_batch_t b, void* stream) {
@@ -572,8 +632,7 @@ void trsm_batch_destroy(trsm_batch_t b) {
   if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
-  if (b->sys_dev) cudaFree(b->sys_dev);
-  if (b->ws) cudaFree(b->ws);
+  if (b->ws && b->owns_ws) cudaFree(b->ws);
   delete b;
 }
 

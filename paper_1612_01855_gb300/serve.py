@@ -1,0 +1,220 @@
+"""Continuous-batching solve server over resident plans.
+
+Each L is planned once (`trsm_plan`: its inverted diagonal blocks stay in
+HBM), so a request — a right-hand side B for one of the resident L — only
+pays for the blocked solve (Algorithm It-Inv-TRSM, Section 6.2).  The loop:
+
+* requests wait in arrival order;
+* whenever one of `streams` launch slots is free, requests are admitted from
+  the head of the queue while their memory (B, X and the batch's share of
+  the workspace) fits in the HBM budget next to the resident plans, and the
+  admitted requests run as ONE persistent batched launch (`trsm_batch_*`
+  with resident plans, laid out in an arena from torch's caching allocator:
+  no device allocation by the library);
+* batches run on different streams overlap on the device; a request that
+  arrives while others are on the GPU is admitted as soon as a slot and
+  memory free up;
+* latency = completion seen by the host - arrival.
+
+The result of a request does not depend on which other requests share its
+batch: every tile's updates are applied in a fixed order.
+"""
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import binding
+
+
+class AdmissionError(ValueError):
+    pass
+
+
+class Admission:
+    """HBM budget bookkeeping (host only): resident bytes are fixed, each
+    admitted request holds its bytes until released."""
+
+    def __init__(self, budget_bytes, resident_bytes=0):
+        if resident_bytes > budget_bytes:
+            raise AdmissionError("resident plans exceed the HBM budget")
+        self.budget = int(budget_bytes)
+        self.resident = int(resident_bytes)
+        self.in_use = 0
+        self.peak = 0
+
+    def fits(self, nbytes):
+        return self.resident + self.in_use + nbytes <= self.budget
+
+    def check_request(self, nbytes):
+        """A request larger than the whole free budget can never run."""
+        if self.resident + nbytes > self.budget:
+            raise AdmissionError(f"request needs {nbytes} bytes, budget leaves {self.budget - self.resident}")
+
+    def take(self, nbytes):
+        if not self.fits(nbytes):
+            return False
+        self.in_use += nbytes
+        self.peak = max(self.peak, self.in_use)
+        return True
+
+    def release(self, nbytes):
+        self.in_use -= nbytes
+        if self.in_use < 0:
+            raise AdmissionError("released more than admitted")
+
+
+@dataclass
+class Request:
+    rid: int
+    lid: int
+    B: object            # CUDA tensor, column-major n x k, float64
+    arrival: float       # seconds (host clock)
+    X: object = None
+    t_admit: float = None
+    t_done: float = None
+    cancelled: bool = False
+
+    @property
+    def latency(self):
+        return None if self.t_done is None else self.t_done - self.arrival
+
+
+@dataclass
+class _InFlight:
+    batch: object
+    event: object
+    reqs: list
+    nbytes: int
+    arena: object = field(default=None)
+
+
+class Server:
+    def __init__(self, plans, budget_bytes, streams=2, max_batch=64):
+        self.plans = plans
+        resident = sum(8 * p.n * p.n for p in plans)
+        self.adm = Admission(budget_bytes, resident)
+        self.pending = deque()
+        self.inflight = []
+        self.done = []
+        self.nstreams = streams
+        self.streams = None  # created at the first dispatch (host-side logic runs without a GPU)
+        self.busy = [False] * streams
+        self.max_batch = max_batch
+        self.launches = 0
+
+    @staticmethod
+    def request_bytes(n, k):
+        # B and X, the working copy W inside the batch workspace, counters
+        return 3 * 8 * n * k + 4 * ((n + 31) // 32) * ((k + 31) // 32) * 2 + 4096
+
+    def submit(self, req):
+        plan = self.plans[req.lid]
+        if req.B.shape[0] != plan.n:
+            raise AdmissionError(f"request {req.rid}: B has {req.B.shape[0]} rows, L has {plan.n}")
+        self.adm.check_request(self.request_bytes(plan.n, req.B.shape[1]))
+        self.pending.append(req)
+
+    def cancel(self, rid):
+        """Drops a request that has not been admitted yet."""
+        for r in self.pending:
+            if r.rid == rid:
+                r.cancelled = True
+                self.pending.remove(r)
+                return True
+        return False
+
+    def poll(self):
+        now = time.perf_counter()
+        still = []
+        for f in self.inflight:
+            if f.event.query():
+                now = time.perf_counter()
+                with self._torch().cuda.stream(self.streams[f.slot]):
+                    rc = f.batch.status()[0]  # the stream has completed: no wait
+                for r in f.reqs:
+                    r.t_done = now
+                    r.status = rc
+                    self.done.append(r)
+                f.batch.destroy()
+                self.adm.release(f.nbytes)
+                self.busy[f.slot] = False
+            else:
+                still.append(f)
+        self.inflight = still
+
+    @staticmethod
+    def _torch():
+        import torch
+        return torch
+
+    def dispatch(self):
+        import torch
+        if self.streams is None:
+            self.streams = [torch.cuda.Stream() for _ in range(self.nstreams)]
+        for slot in range(len(self.streams)):
+            if self.busy[slot] or not self.pending:
+                continue
+            take, nbytes = [], 0
+            while self.pending and len(take) < self.max_batch:
+                r = self.pending[0]
+                b = self.request_bytes(self.plans[r.lid].n, r.B.shape[1])
+                if not self.adm.fits(nbytes + b):
+                    break
+                take.append(self.pending.popleft())
+                nbytes += b
+            if not take:
+                continue
+            self.adm.take(nbytes)
+            stream = self.streams[slot]
+            with torch.cuda.stream(stream):
+                systems = []
+                for r in take:
+                    n, k = r.B.shape
+                    r.X = torch.empty((k, n), dtype=torch.float64, device="cuda").t()
+                    r.t_admit = time.perf_counter()
+                    systems.append({"plan": self.plans[r.lid], "B": r.B, "X": r.X})
+                ws = binding.Batch.workspace_size(systems)
+                arena = torch.empty(ws + 256, dtype=torch.uint8, device="cuda")
+                off = (-arena.data_ptr()) % 256
+                batch = binding.Batch(systems, arena=arena[off:off + ws])
+                batch.run()
+                ev = torch.cuda.Event()
+                ev.record(stream)
+            f = _InFlight(batch, ev, take, nbytes, arena)
+            f.slot = slot
+            self.busy[slot] = True
+            self.inflight.append(f)
+            self.launches += 1
+
+    def drain(self):
+        while self.pending or self.inflight:
+            self.poll()
+            self.dispatch()
+
+    def run_trace(self, requests, idle_sleep=20e-6):
+        """Feeds requests at their arrival times (seconds from now) and runs
+        the loop until all are done.  Returns a stats dict."""
+        t0 = time.perf_counter()
+        order = sorted(requests, key=lambda r: r.arrival)
+        for r in order:
+            r.arrival += t0
+        i = 0
+        while i < len(order) or self.pending or self.inflight:
+            now = time.perf_counter()
+            while i < len(order) and order[i].arrival <= now:
+                self.submit(order[i])
+                i += 1
+            self.poll()
+            self.dispatch()
+            if i < len(order) and not self.inflight:
+                time.sleep(max(0.0, min(idle_sleep, order[i].arrival - time.perf_counter())))
+        t1 = time.perf_counter()
+        lat = np.array([r.latency for r in order if r.latency is not None])
+        flops = float(sum(self.plans[r.lid].n ** 2 * r.B.shape[1] for r in order))
+        return {"requests": len(order), "seconds": t1 - t0, "solves_per_s": len(order) / (t1 - t0),
+                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "mean_ms": float(lat.mean() * 1e3), "tflops_n2k": flops / (t1 - t0) / 1e12,
+                "batches": self.launches, "peak_inflight_gb": self.adm.peak / 1e9,
+                "statuses_ok": all(getattr(r, "status", 0) == 0 for r in order)}

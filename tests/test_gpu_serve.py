@@ -1,0 +1,73 @@
+"""The continuous-batching server on the GPU: every served result equals
+the single-request solve of the same right-hand side (the result does not
+depend on the batch it shared), and memory admission holds."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1612_01855_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(a, dtype=np.float64).T)).cuda().t()
+
+
+def _setup(nL=5, seed=0):
+    import paper_1612_01855_gb300 as g
+    rng = np.random.default_rng(seed)
+    Ls, plans = [], []
+    for i in range(nL):
+        n = int(rng.integers(40, 700))
+        L = inputs.well_conditioned_L(n, seed=100 + i)
+        Ls.append(L)
+        plans.append(g.trsm_plan(_dev(L), [32, 64, 128][i % 3]))
+    return Ls, plans
+
+
+def _requests(Ls, count, rate, seed):
+    from paper_1612_01855_gb300.serve import Request
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    reqs, host = [], []
+    for rid in range(count):
+        t += rng.exponential(1.0 / rate)
+        lid = int(rng.integers(0, len(Ls)))
+        k = int(np.rint(np.exp(rng.uniform(0, np.log(96)))))
+        B = inputs.rhs(Ls[lid].shape[0], k, seed=seed * 1000 + rid)
+        reqs.append(Request(rid, lid, _dev(B), t))
+        host.append(B)
+    return reqs, host
+
+
+def test_served_results_match_single_solves(cuda_lib):
+    import torch
+    import paper_1612_01855_gb300 as g
+    from paper_1612_01855_gb300.serve import Server
+    Ls, plans = _setup()
+    reqs, host = _requests(Ls, 48, rate=4000.0, seed=1)
+    srv = Server(plans, budget_bytes=40 * 2**30, streams=2, max_batch=16)
+    stats = srv.run_trace(reqs)
+    assert stats["statuses_ok"] and stats["requests"] == 48
+    assert stats["batches"] < 48  # requests shared launches
+    for r, B in zip(reqs, host):
+        alone = g.trsm_solve(plans[r.lid], r.B)
+        g.trsm_sync_status(plans[r.lid])
+        assert torch.equal(alone, r.X), r.rid                  # same alone and in the mix
+        want = oracle.forward_subst(Ls[r.lid], B)
+        assert np.max(np.abs(r.X.cpu().numpy() - want)) <= 1e-12 * np.max(np.abs(want))
+
+
+def test_server_respects_tight_budget(cuda_lib):
+    from paper_1612_01855_gb300.serve import Server
+    Ls, plans = _setup(3, seed=2)
+    reqs, _ = _requests(Ls, 30, rate=10000.0, seed=3)
+    resident = sum(8 * p.n * p.n for p in plans)
+    budget = resident + 3 * max(Server.request_bytes(p.n, 96) for p in plans)
+    srv = Server(plans, budget_bytes=budget, streams=2, max_batch=64)
+    stats = srv.run_trace(reqs)
+    assert stats["statuses_ok"]
+    assert srv.adm.peak + resident <= budget
+    assert all(r.X is not None and r.t_done is not None for r in reqs)

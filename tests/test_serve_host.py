@@ -1,0 +1,48 @@
+"""Host-side logic of the solve server (no GPU): HBM-budget admission,
+malformed and oversized requests, cancellation."""
+import pytest
+
+from paper_1612_01855_gb300.serve import Admission, AdmissionError, Request, Server
+
+
+class _Plan:
+    def __init__(self, n):
+        self.n = n
+
+
+class _B:
+    def __init__(self, n, k):
+        self.shape = (n, k)
+
+
+def test_admission_budget_accounting():
+    a = Admission(1000, resident_bytes=400)
+    assert a.take(300) and a.in_use == 300
+    assert not a.take(301)          # would exceed 1000
+    assert a.take(300) and a.peak == 600
+    a.release(300)
+    assert a.fits(300) and not a.fits(301)
+    with pytest.raises(AdmissionError):
+        a.release(10_000)
+
+
+def test_admission_rejects_impossible_requests():
+    with pytest.raises(AdmissionError):
+        Admission(100, resident_bytes=200)
+    a = Admission(1000, resident_bytes=900)
+    with pytest.raises(AdmissionError):
+        a.check_request(200)
+
+
+def test_server_validates_and_cancels_without_gpu():
+    plans = [_Plan(64), _Plan(128)]
+    srv = Server(plans, budget_bytes=10**9)
+    srv.submit(Request(0, 1, _B(128, 4), 0.0))
+    srv.submit(Request(1, 0, _B(64, 2), 0.0))
+    with pytest.raises(AdmissionError):          # wrong number of rows for L #0
+        srv.submit(Request(2, 0, _B(65, 2), 0.0))
+    tight = Server(plans, budget_bytes=8 * (64 * 64 + 128 * 128) + 1000)
+    with pytest.raises(AdmissionError):          # can never fit next to the plans
+        tight.submit(Request(3, 1, _B(128, 1000), 0.0))
+    assert srv.cancel(0) and not srv.cancel(0)
+    assert [r.rid for r in srv.pending] == [1]
