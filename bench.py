@@ -240,6 +240,33 @@ def batched_study(g, torch, count=4096, dtypes=("f64", "f32"), reps=5, seed=1000
     return out
 
 
+def schedules_study(g, torch, dev_in, outs, shapes, n0s, reps=3, stream=None):
+    """Solve time of the three schedules of the blocked solve on the bench
+    shapes (plan reused; solve only): the dependency-driven persistent kernel,
+    the paper's right-looking loop with a look-ahead stream, and Rec-TRSM."""
+    out = []
+    for (Ld, Bd), X, (n, k), n0 in zip(dev_in, outs, shapes, n0s):
+        p = g.trsm_plan(Ld, n0)
+        rec = {"n": n, "k": k, "n0": n0}
+        for sched in ("dag", "right-looking", "recursive"):
+            g.trsm_solve_schedule(p, Bd, X=X, schedule=sched)
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(reps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                g.trsm_solve_schedule(p, Bd, X=X, schedule=sched)
+                b.record()
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+            ms = statistics.median(ts)
+            rec[sched] = {"solve_ms": round(ms, 3), "tflops": round(float(n) * n * k / (ms * 1e-3) / 1e12, 4)}
+        g.trsm_sync_status(p)
+        p.destroy()
+        out.append(rec)
+    return out
+
+
 def serving_study(g, torch, nL=256, rates=(100, 300, 600, 1200), per_rate=300, seed=2000,
                   budget_gb=150.0):
     """Serving workload: nL resident L (n log-uniform in [64, 8192],
@@ -512,6 +539,10 @@ def run_ours(args, rank, world, local):
     if rank == 0 and not args.no_serving and not args.shapes:
         serving = serving_study(g, torch)
 
+    schedules = None
+    if rank == 0 and not args.no_schedules:
+        schedules = schedules_study(g, torch, dev_in, outs, shapes, n0s)
+
     if args.precision and rank == 0:
         for rec in precision_study(g, torch, 16384, 4096, 256, [2, 4, 6], ["tf32", "bf16"], [False, True]):
             print(json.dumps({"precision_study": True, **rec}), flush=True)
@@ -561,6 +592,7 @@ def run_ours(args, rank, world, local):
             "mixed_precision": mixed,
             "batched": batched,
             "serving": serving,
+            "schedules": schedules,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "gpu_launches": launches,
@@ -583,6 +615,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision refinement figure")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-systems figure")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving figure")
+    ap.add_argument("--no-schedules", action="store_true", help="skip the solve-schedule comparison")
     ap.add_argument("--precision", action="store_true", help="print the full c x inner x s-step study")
     ap.add_argument("--case", default="", help="profiling case: sliced:N:K, mixed:N:K:N0, engine:M:N:K")
     ap.add_argument("--shapes", default="", help="override workload, e.g. 6144:1024:256 (not a bench line)")

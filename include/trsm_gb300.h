@@ -85,6 +85,27 @@ int trsm_plan(const double* L_dev, int64_t n, int64_t ldl, int64_t n0, void* str
 int trsm_solve(trsm_handle_t h, const double* B_dev, int64_t k, int64_t ldb, double* X_dev,
                int64_t ldx, void* stream);
 
+/* trsm_solve_schedule — trsm_solve with a chosen schedule of the same
+ * arithmetic (all read the plan's L~; results agree to rounding):
+ *   TRSM_SCHED_DAG            the default: one persistent kernel, tile tasks
+ *                             ordered by dependency counters (trsm_solve);
+ *   TRSM_SCHED_RIGHT_LOOKING  Algorithm It-Inv-TRSM (Section 6.2) as
+ *                             written, with the update accumulator B~ and the
+ *                             subtraction of one block row per step; the next
+ *                             block row's update runs first, the rest of the
+ *                             trailing update on a second stream (look-ahead);
+ *   TRSM_SCHED_RECURSIVE      Algorithm Rec-TRSM (Section 4): halve on block
+ *                             boundaries, X1 = Rec(L11,B1), B2 -= L21 X1,
+ *                             X2 = Rec(L22,B2); the base case X = L^-1 B uses
+ *                             the plan's inverted diagonal block.
+ * B_dev must not alias X_dev for the last two.  Asynchronous; allocates its
+ * workspace stream-ordered.  Errors as trsm_solve. */
+#define TRSM_SCHED_DAG 0
+#define TRSM_SCHED_RIGHT_LOOKING 1
+#define TRSM_SCHED_RECURSIVE 2
+int trsm_solve_schedule(trsm_handle_t h, const double* B_dev, int64_t k, int64_t ldb, double* X_dev,
+                        int64_t ldx, int schedule, void* stream);
+
 /* Workspace-explicit form of trsm_solve: the caller passes device memory
  * `ws_dev` of at least trsm_solve_workspace_size(h, k) bytes (256-byte
  * aligned); nothing is allocated.  Concurrent calls must not share ws_dev. */

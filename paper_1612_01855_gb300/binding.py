@@ -49,6 +49,7 @@ _pi64 = ctypes.POINTER(ctypes.c_int64)
 SIGNATURES = {
     "trsm_plan": (_int, [_dp, _i64, _i64, _i64, _vp, ctypes.POINTER(_vp)]),
     "trsm_solve": (_int, [_vp, _dp, _i64, _i64, _dp, _i64, _vp]),
+    "trsm_solve_schedule": (_int, [_vp, _dp, _i64, _i64, _dp, _i64, _int, _vp]),
     "trsm_solve_workspace_size": (_int, [_vp, _i64, ctypes.POINTER(ctypes.c_size_t)]),
     "trsm_solve_ws": (_int, [_vp, _dp, _i64, _i64, _dp, _i64, _vp, ctypes.c_size_t, _vp]),
     "trsm_solve_noalloc": (_int, [_vp, _dp, _i64, _i64, _dp, _i64, _vp]),
@@ -275,6 +276,26 @@ def trsm_solve_mixed(plan, B, X=None, residual="sliced", max_iter=30, tol=1e-14,
         return X, it.value, upd.value
     _check(rc, "trsm_solve_mixed")
     return X, it.value, upd.value
+
+
+SCHEDULES = {"dag": 0, "right-looking": 1, "recursive": 2}
+
+
+def trsm_solve_schedule(plan, B, X=None, schedule="dag"):
+    """trsm_solve with a chosen schedule: "dag" (default persistent
+    kernel), "right-looking" (the paper's B~ loop with look-ahead) or
+    "recursive" (Rec-TRSM).  Asynchronous."""
+    torch = _torch()
+    B = _dev_matrix(B, "B")
+    n, k = B.shape
+    if X is None:
+        X = torch.empty((k, n), dtype=torch.float64, device=B.device).t()
+    else:
+        X = _dev_matrix(X, "X")
+    _check(load_library().trsm_solve_schedule(plan.handle, ctypes.c_void_p(B.data_ptr()), k, _ld(B),
+                                              ctypes.c_void_p(X.data_ptr()), _ld(X), SCHEDULES[schedule],
+                                              _stream(B)), "trsm_solve_schedule")
+    return X
 
 
 def trsm_solve_workspace_size(plan, k):
