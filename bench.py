@@ -126,7 +126,8 @@ def cpu_oracle_rate(data, shapes, budget_s, max_cols=None):
     return flops / secs / 1e12, "; ".join(desc), cores
 
 
-def precision_study(g, torch, n, k, n0, cs, inners, s_modes, dd_cols=2, stream=None, quick=False):
+def precision_study(g, torch, n, k, n0, cs, inners, s_modes, dd_cols=2, stream=None, quick=False,
+                    residuals=("sliced",)):
     """Mixed-precision refinement on the graded-diagonal workload (diagonal
     geomspace(1, 10^-c), permuted): time, iterations and forward error
     against the double-double oracle on sampled columns, beside the FP64
@@ -162,18 +163,18 @@ def precision_study(g, torch, n, k, n0, cs, inners, s_modes, dd_cols=2, stream=N
                "fp64_fwd_err": ferr(X64), "dd_reference_finite": ref_ok, "mixed": []}
         for inner in inners:
             g.trsm_plan_mixed(plan, Ld, inner)
-            for s32 in s_modes:
-                X, it, upd = g.trsm_solve_mixed(plan, Bd, residual="sliced", max_iter=30, tol=1e-12,
+            for s32, res in ((a, b) for a in s_modes for b in residuals):
+                X, it, upd = g.trsm_solve_mixed(plan, Bd, residual=res, max_iter=30, tol=1e-12,
                                                 raise_on_noconv=False, s_fp32=s32)
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                X, it, upd = g.trsm_solve_mixed(plan, Bd, X=X, residual="sliced", max_iter=30, tol=1e-12,
+                X, it, upd = g.trsm_solve_mixed(plan, Bd, X=X, residual=res, max_iter=30, tol=1e-12,
                                                 raise_on_noconv=False, s_fp32=s32)
                 torch.cuda.synchronize()
                 tm = (time.perf_counter() - t0) * 1e3
                 fe = ferr(X)
                 rec["mixed"].append({"inner": inner, "s_step": "fp32" if s32 else "fp64",
-                                     "residual": "sliced-bf16", "ms": round(tm, 2),
+                                     "residual": res, "ms": round(tm, 2),
                                      "tflops_equiv": round(float(n) * n * k / (tm * 1e-3) / 1e12, 3),
                                      "iterations": it, "last_update": upd, "fwd_err": fe,
                                      "converged": bool(fe is not None and fe <= 1e-10),
@@ -345,7 +346,7 @@ def run_case(args):
             for _ in range(2):
                 rc = lib.trsm_residual_sliced(ctypes.c_void_p(L.data_ptr()), n, n, ctypes.c_void_p(X.data_ptr()), k,
                                               n, ctypes.c_void_p(B.data_ptr()), n, ctypes.c_void_p(R.data_ptr()),
-                                              n, ctypes.c_void_p(err.data_ptr()), s)
+                                              n, dims[2] if len(dims) > 2 else 7, ctypes.c_void_p(err.data_ptr()), s)
                 assert rc == 0
         else:
             plan = g.trsm_plan(L, dims[2])
@@ -529,7 +530,7 @@ def run_ours(args, rank, world, local):
 
     mixed = None
     if rank == 0 and not args.no_mixed and not args.shapes:
-        mixed = precision_study(g, torch, 16384, 4096, 256, [2], ["tf32"], [False, True], dd_cols=2)
+        mixed = precision_study(g, torch, 16384, 4096, 256, [2], ["tf32", "bf16x3"], [False, True], dd_cols=2)
 
     batched = None
     if rank == 0 and not args.no_batched and not args.shapes:
@@ -544,7 +545,8 @@ def run_ours(args, rank, world, local):
         schedules = schedules_study(g, torch, dev_in, outs, shapes, n0s)
 
     if args.precision and rank == 0:
-        for rec in precision_study(g, torch, 16384, 4096, 256, [2, 4, 6], ["tf32", "bf16"], [False, True]):
+        for rec in precision_study(g, torch, 16384, 4096, 256, [2, 4, 6], ["tf32", "bf16", "bf16x3"],
+                                   [False, True], residuals=("sliced", "adaptive")):
             print(json.dumps({"precision_study": True, **rec}), flush=True)
 
     if args.sweep and rank == 0:
@@ -617,7 +619,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving figure")
     ap.add_argument("--no-schedules", action="store_true", help="skip the solve-schedule comparison")
     ap.add_argument("--precision", action="store_true", help="print the full c x inner x s-step study")
-    ap.add_argument("--case", default="", help="profiling case: sliced:N:K, mixed:N:K:N0, engine:M:N:K")
+    ap.add_argument("--case", default="", help="profiling case: sliced:N:K[:PLANES], mixed:N:K:N0, engine:M:N:K")
     ap.add_argument("--shapes", default="", help="override workload, e.g. 6144:1024:256 (not a bench line)")
     args = ap.parse_args()
     rank, world, local = dist_env()

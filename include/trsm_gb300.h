@@ -45,9 +45,16 @@ extern "C" {
 /* Low-precision formats of the mixed-precision solve (tensor-core updates). */
 #define TRSM_INNER_BF16 1
 #define TRSM_INNER_TF32 2
+/* split bf16: every operand is hi + lo bf16 planes and the update takes the
+ * three products hi*hi + hi*lo + lo*hi (about 16 significant bits per factor
+ * at 1.5x the tensor work of tf32): the inner solve contracts the error far
+ * faster on ill-conditioned systems */
+#define TRSM_INNER_BF16X3 3
 /* Residual of the mixed-precision solve. */
-#define TRSM_RESIDUAL_SLICED 0 /* FP64-class, bf16 tensor cores, integer digit slices */
-#define TRSM_RESIDUAL_FP64 1   /* FP64 fused multiply-add                              */
+#define TRSM_RESIDUAL_SLICED 0   /* FP64-class, bf16 tensor cores, 7 integer digit planes */
+#define TRSM_RESIDUAL_FP64 1     /* FP64 fused multiply-add                                */
+#define TRSM_RESIDUAL_SLICED8 2  /* as SLICED with 8 digit planes: ~2^-49 instead of ~2^-43 */
+#define TRSM_RESIDUAL_ADAPTIVE 3 /* SLICED until the updates stagnate above tol, then SLICED8 */
 /* Flag or-ed into `residual`: apply the FP64 inverses of the diagonal blocks
  * in FP32 arithmetic inside the inner solve (default: FP64 arithmetic). */
 #define TRSM_SOLVE_S_FP32 0x100
@@ -139,9 +146,10 @@ int trsm_solve_noalloc(trsm_handle_t h, const double* B_dev, int64_t k, int64_t 
  * (no counterpart in the paper, which works in exact arithmetic; the block
  * structure is its Algorithm It-Inv-TRSM):
  *   - the off-diagonal block columns L(T_{i+1}, S_i) in `inner` precision
- *     (TRSM_INNER_BF16 or TRSM_INNER_TF32), for the tensor-core updates;
+ *     (TRSM_INNER_BF16, TRSM_INNER_TF32 or TRSM_INNER_BF16X3), for the
+ *     tensor-core updates;
  *   - the original diagonal blocks and diagonal of L in FP64;
- *   - seven 6-bit integer digit planes of the strictly lower L, for the
+ *   - eight 6-bit integer digit planes of the strictly lower L, for the
  *     FP64-class residual.
  *   L_dev : the same matrix the plan was made from (n x n, ldl >= n).
  * Synchronous.  Errors: TRSM_EINVAL, TRSM_ENOMEM, TRSM_ECUDA. */
@@ -156,9 +164,15 @@ int trsm_plan_mixed(trsm_handle_t h, const double* L_dev, int64_t ldl, int inner
  * D_i = L~_ii W_i with the FP64 inverse (FP64 arithmetic), then the trailing
  * update W(T_{i+1}) -= L(T_{i+1}, S_i) D_i as one tcgen05 GEMM in the plan's
  * inner precision with FP32 accumulation (W is the FP32 copy of R).
- *   residual : TRSM_RESIDUAL_SLICED or TRSM_RESIDUAL_FP64 (the latter needs
- *              n0 a multiple of 32 when there is more than one block),
- *              optionally or-ed with TRSM_SOLVE_S_FP32.
+ *   residual : TRSM_RESIDUAL_SLICED, _SLICED8, _ADAPTIVE or _FP64 (the
+ *              latter needs n0 a multiple of 32 when there is more than one
+ *              block), optionally or-ed with TRSM_SOLVE_S_FP32.  The
+ *              residual's accuracy sets the attainable error: about
+ *              cond * 2^-43 (SLICED), cond * 2^-49 (SLICED8), cond * 2^-53
+ *              (FP64), with cond the componentwise condition of the system
+ *              (the sliced residuals are componentwise only within a
+ *              2048-row chunk of X: a solution whose entries span many
+ *              orders of magnitude inside a chunk sees a normwise bound).
  *   max_iter : >= 1 inner solves at most; tol >= 0.
  *   iters, last_update (may be NULL): inner solves done, and the last
  *              max|D| / max|X|.

@@ -15,28 +15,32 @@ extern "C" {
 #endif
 
 /* Engine self-test: C = A * B^T on the tensor cores.
- *   tf32 = 0: A (M x K) and B (N x K) are bf16, row-major (K contiguous),
- *             K a multiple of 8; tf32 = 1: fp32 read as tf32, K a multiple of 4.
+ *   mode = 0: A (M x K) and B (N x K) are bf16, row-major (K contiguous),
+ *             K a multiple of 8;
+ *   mode = 1: fp32 read as tf32, K a multiple of 4;
+ *   mode = 2: split bf16: A is two bf16 planes (hi, lo) of M x K, one after
+ *             the other, B two planes of N x K; C = Ah Bh^T + Ah Bl^T +
+ *             Al Bh^T; K a multiple of 8.
  *   C_dev: fp32, column-major M x N (leading dimension M), overwritten.
  *   err_dev: device int, set to 1 if a pipeline wait gave up (never in
  *            correct operation).  Asynchronous on `stream`. */
-int trsm_tc_gemm_selftest(int tf32, const void* A_dev, const void* B_dev, float* C_dev, int64_t M,
+int trsm_tc_gemm_selftest(int mode, const void* A_dev, const void* B_dev, float* C_dev, int64_t M,
                           int64_t N, int64_t K, int* err_dev, void* stream);
 
 /* FP64-class residual R = B - tril(L) X on the BF16 tensor cores: the
- * strictly lower L and X are split into seven 6-bit integer digit planes
- * per (row, 2048-wide chunk of K) with a power-of-two exponent each; the
- * digit-pair products with s + u <= 6 are accumulated in FP32 per chunk
- * (exactly for s + u <= 3) and combined in float-float arithmetic
- * (error-free splitting after Ozaki, Ogita, Oishi & Rump 2012); the
- * diagonal of L is applied in FP64.  Relative error about 2^-40 of
- * (|L| |X|).
+ * strictly lower L and X are split into `planes` (7 or 8) 6-bit integer
+ * digit planes per (row, 2048-wide chunk of K) with a power-of-two exponent
+ * each; the digit-pair products with s + u <= planes - 1 are accumulated in
+ * FP32 per chunk (exactly for s + u <= 3) and combined in float-float
+ * arithmetic (error-free splitting after Ozaki, Ogita, Oishi & Rump 2012);
+ * the diagonal of L is applied in FP64.  Relative error about 2^-43
+ * (7 planes) or 2^-49 (8 planes) of (|B| + |L| |X|).
  *   L_dev n x n column-major (lower triangle read), X_dev, B_dev, R_dev
  *   n x k column-major.  Allocates its slice buffers stream-ordered.
- *   Asynchronous; err_dev as for the self-test. */
+ *   Asynchronous; err_dev as for the self-test; -1 for bad arguments. */
 int trsm_residual_sliced(const double* L_dev, int64_t n, int64_t ldl, const double* X_dev, int64_t k,
                          int64_t ldx, const double* B_dev, int64_t ldb, double* R_dev, int64_t ldr,
-                         int* err_dev, void* stream);
+                         int planes, int* err_dev, void* stream);
 
 #ifdef __cplusplus
 }

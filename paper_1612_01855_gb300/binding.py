@@ -27,8 +27,11 @@ TRSM_ENOSCRATCH = -6
 TRSM_ENOCONV = -7
 TRSM_INNER_BF16 = 1
 TRSM_INNER_TF32 = 2
+TRSM_INNER_BF16X3 = 3
 TRSM_RESIDUAL_SLICED = 0
 TRSM_RESIDUAL_FP64 = 1
+TRSM_RESIDUAL_SLICED8 = 2
+TRSM_RESIDUAL_ADAPTIVE = 3
 TRSM_SOLVE_S_FP32 = 0x100
 
 TRSM_F64 = 0
@@ -78,7 +81,7 @@ SIGNATURES = {
     "trsm_launch_count": (_i64, [_int]),
     "trsm_fp64_peak": (_int, [_int, ctypes.POINTER(ctypes.c_double), _vp]),
     "trsm_tc_gemm_selftest": (_int, [_int, _vp, _vp, _vp, _i64, _i64, _i64, _vp, _vp]),
-    "trsm_residual_sliced": (_int, [_dp, _i64, _i64, _dp, _i64, _i64, _dp, _i64, _dp, _i64, _vp, _vp]),
+    "trsm_residual_sliced": (_int, [_dp, _i64, _i64, _dp, _i64, _i64, _dp, _i64, _dp, _i64, _int, _vp, _vp]),
 }
 
 _lib = None
@@ -244,9 +247,10 @@ def trsm_solve_noalloc(plan, B, X):
 
 
 def trsm_plan_mixed(plan, L, inner="tf32"):
-    """Adds the mixed-precision data (inner = "bf16" or "tf32") to a plan made from L."""
+    """Adds the mixed-precision data (inner = "bf16", "tf32" or "bf16x3", the
+    split-bf16 update) to a plan made from L."""
     L = _dev_matrix(L, "L")
-    code = {"bf16": TRSM_INNER_BF16, "tf32": TRSM_INNER_TF32}[inner]
+    code = {"bf16": TRSM_INNER_BF16, "tf32": TRSM_INNER_TF32, "bf16x3": TRSM_INNER_BF16X3}[inner]
     _check(load_library().trsm_plan_mixed(plan.handle, ctypes.c_void_p(L.data_ptr()), _ld(L), code,
                                           _stream(L)), "trsm_plan_mixed")
     plan.inner = inner
@@ -266,7 +270,8 @@ def trsm_solve_mixed(plan, B, X=None, residual="sliced", max_iter=30, tol=1e-14,
         X = _dev_matrix(X, "X")
     it = ctypes.c_int()
     upd = ctypes.c_double()
-    code = {"sliced": TRSM_RESIDUAL_SLICED, "fp64": TRSM_RESIDUAL_FP64}[residual]
+    code = {"sliced": TRSM_RESIDUAL_SLICED, "fp64": TRSM_RESIDUAL_FP64, "sliced8": TRSM_RESIDUAL_SLICED8,
+            "adaptive": TRSM_RESIDUAL_ADAPTIVE}[residual]
     if s_fp32:
         code |= TRSM_SOLVE_S_FP32
     rc = load_library().trsm_solve_mixed(plan.handle, ctypes.c_void_p(B.data_ptr()), k, _ld(B),

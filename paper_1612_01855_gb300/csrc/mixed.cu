@@ -14,11 +14,13 @@
 // inner_solve is the right-looking form of Algorithm It-Inv-TRSM: for every
 // block row i, D_i = L~_ii W_i with the FP64 inverse of the diagonal block
 // (DFMA tile kernel), then W(T_{i+1}) -= L(T_{i+1}, S_i) D_i as one
-// tcgen05 GEMM with bf16 or tf32 operands and FP32 accumulation; W is the
-// FP32 working copy of R.
+// tcgen05 GEMM with bf16, tf32 or split bf16 (hi + lo planes, three
+// products) operands and FP32 accumulation; W is the FP32 working copy of R.
 //
 // The residual is either the digit-sliced tensor-core product of sliced.cu
-// (about 2^-40 relative to |L||X|) or a plain FP64 DFMA product.
+// (seven planes: about 2^-40 relative to |L||X|; eight: about 2^-46; or
+// seven until the updates stagnate above tol, then eight) or a plain FP64
+// DFMA product.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -62,36 +64,54 @@ __host__ __device__ inline int64_t panel_off(int64_t i, int64_t n, int64_t n0, i
   return n0p * (i * n - n0 * (i * (i + 1) / 2));
 }
 
-template <bool kTf32>
+// Storage of the low-precision operands: kMode 0 bf16, 1 tf32 (in fp32
+// storage, rounded to tf32 with round-to-nearest-away), 2 split bf16 (two
+// planes, hi = bf16(v) and lo = bf16(v - hi), `plane` elements apart).
+template <int kMode>
 struct LowP;
 template <>
-struct LowP<false> {
+struct LowP<0> {
   using T = __nv_bfloat16;
-  __device__ static T from(double v) { return __double2bfloat16(v); }
+  static constexpr int kPlanes = 1;
+  __device__ static void put(T* p, int64_t, double v) { *p = __double2bfloat16(v); }
 };
 template <>
-struct LowP<true> {
-  using T = float;  // tf32 kept in fp32 storage, rounded to tf32 (round-to-nearest-away)
-  __device__ static T from(double v) {
+struct LowP<1> {
+  using T = float;
+  static constexpr int kPlanes = 1;
+  __device__ static void put(T* p, int64_t, double v) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(static_cast<float>(v)));
-    return __uint_as_float(r);
+    *p = __uint_as_float(r);
+  }
+};
+template <>
+struct LowP<2> {
+  using T = __nv_bfloat16;
+  static constexpr int kPlanes = 2;
+  __device__ static void put(T* p, int64_t plane, double v) {
+    const T hi = __double2bfloat16(v);
+    p[0] = hi;
+    p[plane] = __double2bfloat16(v - static_cast<double>(__bfloat162float(hi)));
   }
 };
 
-template <bool kTf32>
+inline int mode_of(int inner) { return inner == TRSM_INNER_TF32 ? 1 : inner == TRSM_INNER_BF16X3 ? 2 : 0; }
+inline size_t mode_bytes(int mode) { return mode == 0 ? 2 : 4; }  // bytes per element, all planes
+
+template <int kMode>
 __global__ void pack_panels_kernel(const double* __restrict__ L, int64_t ldl, int64_t n, int64_t n0,
-                                   int64_t n0p, typename LowP<kTf32>::T* __restrict__ out) {
+                                   int64_t n0p, typename LowP<kMode>::T* __restrict__ out) {
   const int64_t i = blockIdx.y;  // block column, 0 .. N-2
   const int64_t rows = n - (i + 1) * n0;
   if (rows <= 0) return;
-  typename LowP<kTf32>::T* P = out + panel_off(i, n, n0, n0p);
+  typename LowP<kMode>::T* P = out + LowP<kMode>::kPlanes * panel_off(i, n, n0, n0p);
   const int64_t total = rows * n0p;
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
        e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t r = e / n0p, c = e % n0p;
     const double v = (c < n0) ? L[(i * n0 + c) * ldl + (i + 1) * n0 + r] : 0.0;
-    P[e] = LowP<kTf32>::from(v);
+    LowP<kMode>::put(P + e, total, v);
   }
 }
 
@@ -119,10 +139,10 @@ __global__ void to_float_kernel(const double* __restrict__ R, int64_t ldr, float
 // rounded, to Dt (the B operand of the next update GEMM).  L~_ii is lower
 // triangular, so row tile r costs (r + 1) K chunks: each CTA takes the
 // pair of row tiles (p, R - 1 - p), which all cost the same.
-template <bool kTf32, class TC>
+template <int kMode, class TC>
 __device__ __forceinline__ void s_tile(const double* __restrict__ Lt, int64_t ldt, const float* __restrict__ W,
                                        int64_t ldw, double* __restrict__ D, int64_t ldd,
-                                       typename LowP<kTf32>::T* __restrict__ Dt, int64_t n0p, int64_t s0, int m,
+                                       typename LowP<kMode>::T* __restrict__ Dt, int64_t n0p, int64_t s0, int m,
                                        int64_t k, int r, int j, TileSmemT<TC>& sm) {
   const int mr = min(TILE, m - r * TILE);
   const int nc = static_cast<int>(imin64(TILE, k - static_cast<int64_t>(j) * TILE));
@@ -143,24 +163,24 @@ __device__ __forceinline__ void s_tile(const double* __restrict__ Lt, int64_t ld
       const int64_t row = static_cast<int64_t>(r) * TILE + rr;
       const double v = static_cast<double>(acc[a][b]);
       D[col * ldd + s0 + row] = v;
-      Dt[col * n0p + row] = LowP<kTf32>::from(v);
+      LowP<kMode>::put(Dt + col * n0p + row, k * n0p, v);
     }
   }
 }
 
 // TC = double: FP64 DFMA with the FP64 inverses (the default); TC = float:
 // FFMA with the inverses rounded to FP32 (TRSM_SOLVE_S_FP32).
-template <bool kTf32, class TC>
+template <int kMode, class TC>
 __global__ void __launch_bounds__(NTHREADS) s_step_kernel(const double* __restrict__ Lt, int64_t ldt,
                                                           const float* __restrict__ W, int64_t ldw,
                                                           double* __restrict__ D, int64_t ldd,
-                                                          typename LowP<kTf32>::T* __restrict__ Dt,
+                                                          typename LowP<kMode>::T* __restrict__ Dt,
                                                           int64_t n0p, int64_t s0, int m, int64_t k) {
   __shared__ TileSmemT<TC> sm;
   const int R = (m + TILE - 1) / TILE;
   const int p = blockIdx.x, j = blockIdx.y;
-  s_tile<kTf32, TC>(Lt, ldt, W, ldw, D, ldd, Dt, n0p, s0, m, k, p, j, sm);
-  if (R - 1 - p != p) s_tile<kTf32, TC>(Lt, ldt, W, ldw, D, ldd, Dt, n0p, s0, m, k, R - 1 - p, j, sm);
+  s_tile<kMode, TC>(Lt, ldt, W, ldw, D, ldd, Dt, n0p, s0, m, k, p, j, sm);
+  if (R - 1 - p != p) s_tile<kMode, TC>(Lt, ldt, W, ldw, D, ldd, Dt, n0p, s0, m, k, R - 1 - p, j, sm);
 }
 
 // max that keeps a NaN once it has been seen (fmax would drop it)
@@ -253,7 +273,8 @@ dim3 grid_nk(int64_t n, int64_t k) {
 using trsm::MixedPlan;
 
 extern "C" int trsm_plan_mixed(trsm_handle_t h, const double* L_dev, int64_t ldl, int inner, void* stream) {
-  if (!h || !L_dev || ldl < h->n || (inner != TRSM_INNER_BF16 && inner != TRSM_INNER_TF32))
+  if (!h || !L_dev || ldl < h->n ||
+      (inner != TRSM_INNER_BF16 && inner != TRSM_INNER_TF32 && inner != TRSM_INNER_BF16X3))
     return TRSM_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   trsm::mixed_release(h);
@@ -261,10 +282,10 @@ extern "C" int trsm_plan_mixed(trsm_handle_t h, const double* L_dev, int64_t ldl
   if (!mp) return TRSM_ENOMEM;
   h->mixed = mp;
   const int64_t n = h->n, n0 = h->n0, N = h->N;
-  const bool tf32 = inner == TRSM_INNER_TF32;
+  const int mode = trsm::mode_of(inner);
   mp->inner = inner;
   mp->n0p = (n0 + 7) / 8 * 8;
-  const size_t esz = tf32 ? 4 : 2;
+  const size_t esz = trsm::mode_bytes(mode);
   const size_t panel_elems = static_cast<size_t>(trsm::panel_off(N - 1, n, n0, mp->n0p));
   cudaError_t e = cudaSuccess;
   if (panel_elems > 0) e = cudaMalloc(&mp->panels, esz * panel_elems);
@@ -278,12 +299,14 @@ extern "C" int trsm_plan_mixed(trsm_handle_t h, const double* L_dev, int64_t ldl
   if (e == cudaSuccess && panel_elems > 0) {
     dim3 grid(static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((n * mp->n0p + 255) / 256, 1024))),
               static_cast<unsigned>(N - 1));
-    if (tf32)
-      trsm::pack_panels_kernel<true><<<grid, 256, 0, s>>>(L_dev, ldl, n, n0, mp->n0p,
-                                                          static_cast<float*>(mp->panels));
+    if (mode == 1)
+      trsm::pack_panels_kernel<1><<<grid, 256, 0, s>>>(L_dev, ldl, n, n0, mp->n0p, static_cast<float*>(mp->panels));
+    else if (mode == 2)
+      trsm::pack_panels_kernel<2><<<grid, 256, 0, s>>>(L_dev, ldl, n, n0, mp->n0p,
+                                                       static_cast<__nv_bfloat16*>(mp->panels));
     else
-      trsm::pack_panels_kernel<false><<<grid, 256, 0, s>>>(L_dev, ldl, n, n0, mp->n0p,
-                                                           static_cast<__nv_bfloat16*>(mp->panels));
+      trsm::pack_panels_kernel<0><<<grid, 256, 0, s>>>(L_dev, ldl, n, n0, mp->n0p,
+                                                       static_cast<__nv_bfloat16*>(mp->panels));
     trsm::count_launch();
     e = cudaGetLastError();
   }
@@ -314,16 +337,18 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
   if (!h || !h->mixed || k < 0 || max_iter < 1 || !(tol >= 0.0)) return TRSM_EINVAL;
   const bool s32 = (residual & TRSM_SOLVE_S_FP32) != 0;
   residual &= ~TRSM_SOLVE_S_FP32;
-  if (residual != TRSM_RESIDUAL_SLICED && residual != TRSM_RESIDUAL_FP64) return TRSM_EINVAL;
+  if (residual != TRSM_RESIDUAL_SLICED && residual != TRSM_RESIDUAL_FP64 && residual != TRSM_RESIDUAL_SLICED8 &&
+      residual != TRSM_RESIDUAL_ADAPTIVE)
+    return TRSM_EINVAL;
   if (k == 0) return TRSM_SUCCESS;
   if (!B_dev || !X_dev || ldb < h->n || ldx < h->n || B_dev == X_dev) return TRSM_EINVAL;
   if (residual == TRSM_RESIDUAL_FP64 && h->n0 % trsm::TILE != 0 && h->N > 1) return TRSM_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   MixedPlan* mp = h->mixed;
-  const bool tf32 = mp->inner == TRSM_INNER_TF32;
+  const int mode = trsm::mode_of(mp->inner);
   const int64_t n = h->n, n0 = h->n0, N = h->N, n0p = mp->n0p;
   const int64_t ld = trsm::align4(n);
-  const size_t esz = tf32 ? 4 : 2;
+  const size_t esz = trsm::mode_bytes(mode);
 
   // workspace: R, D (FP64), W (FP32), Dt (low precision), X digit planes, norms, error word
   size_t off = 0;
@@ -358,6 +383,9 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
   if (e == cudaSuccess) e = cudaMemset2DAsync(X_dev, sizeof(double) * ldx, 0, sizeof(double) * n, k, s);
   if (e == cudaSuccess) e = trsm::copy_panel(B_dev, ldb, R, ld, n, k, s);
   double best = HUGE_VAL, prev = HUGE_VAL;
+  // digit planes of the sliced residual: the adaptive mode starts with seven
+  // and moves to eight when the updates stagnate above tol
+  int planes = residual == TRSM_RESIDUAL_SLICED8 ? 8 : 7;
   int it = 0;
   for (it = 1; it <= max_iter && e == cudaSuccess; ++it) {
     // ---- D = inner_solve(R) ----
@@ -368,17 +396,23 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
       const int m = static_cast<int>(std::min(n0, n - s0));
       const int R = (m + trsm::TILE - 1) / trsm::TILE;
       dim3 g(static_cast<unsigned>((R + 1) / 2), static_cast<unsigned>((k + trsm::TILE - 1) / trsm::TILE));
-      if (tf32 && !s32)
-        trsm::s_step_kernel<true, double><<<g, trsm::NTHREADS, 0, s>>>(h->Lt, h->ldt, W, ld, D, ld,
-                                                                        static_cast<float*>(Dt), n0p, s0, m, k);
-      else if (tf32)
-        trsm::s_step_kernel<true, float><<<g, trsm::NTHREADS, 0, s>>>(h->Lt, h->ldt, W, ld, D, ld,
-                                                                       static_cast<float*>(Dt), n0p, s0, m, k);
+      if (mode == 1 && !s32)
+        trsm::s_step_kernel<1, double><<<g, trsm::NTHREADS, 0, s>>>(h->Lt, h->ldt, W, ld, D, ld,
+                                                                     static_cast<float*>(Dt), n0p, s0, m, k);
+      else if (mode == 1)
+        trsm::s_step_kernel<1, float><<<g, trsm::NTHREADS, 0, s>>>(h->Lt, h->ldt, W, ld, D, ld,
+                                                                    static_cast<float*>(Dt), n0p, s0, m, k);
+      else if (mode == 2 && !s32)
+        trsm::s_step_kernel<2, double><<<g, trsm::NTHREADS, 0, s>>>(
+            h->Lt, h->ldt, W, ld, D, ld, static_cast<__nv_bfloat16*>(Dt), n0p, s0, m, k);
+      else if (mode == 2)
+        trsm::s_step_kernel<2, float><<<g, trsm::NTHREADS, 0, s>>>(
+            h->Lt, h->ldt, W, ld, D, ld, static_cast<__nv_bfloat16*>(Dt), n0p, s0, m, k);
       else if (!s32)
-        trsm::s_step_kernel<false, double><<<g, trsm::NTHREADS, 0, s>>>(
+        trsm::s_step_kernel<0, double><<<g, trsm::NTHREADS, 0, s>>>(
             h->Lt, h->ldt, W, ld, D, ld, static_cast<__nv_bfloat16*>(Dt), n0p, s0, m, k);
       else
-        trsm::s_step_kernel<false, float><<<g, trsm::NTHREADS, 0, s>>>(
+        trsm::s_step_kernel<0, float><<<g, trsm::NTHREADS, 0, s>>>(
             h->Lt, h->ldt, W, ld, D, ld, static_cast<__nv_bfloat16*>(Dt), n0p, s0, m, k);
       trsm::count_launch();
       e = cudaGetLastError();
@@ -386,7 +420,12 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
         const int64_t rows = n - (i + 1) * n0;
         const unsigned char* P =
             static_cast<const unsigned char*>(mp->panels) + esz * trsm::panel_off(i, n, n0, n0p);
-        e = trsm::tc::gemm_lowp(tf32, P, n0p, Dt, n0p, W + (i + 1) * n0, ld, rows, k, n0p, -1.f, 1.f, err, s);
+        if (mode == 2)
+          e = trsm::tc::gemm_split_bf16(P, n0p, rows * n0p, Dt, n0p, k * n0p, W + (i + 1) * n0, ld, rows, k, n0p,
+                                        -1.f, 1.f, err, s);
+        else
+          e = trsm::tc::gemm_lowp(mode == 1, P, n0p, Dt, n0p, W + (i + 1) * n0, ld, rows, k, n0p, -1.f, 1.f, err,
+                                  s);
       }
     }
     // ---- X += D ----
@@ -418,21 +457,27 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
     // floor) and further sweeps cannot improve X.  Accept the iterate when
     // that floor is small, otherwise report non-convergence.
     if (it >= 2 && ratio > 0.5 * prev) {
-      if (ratio > 1e-10) rc = TRSM_ENOCONV;
-      break;
+      if (residual == TRSM_RESIDUAL_ADAPTIVE && planes == 7) {
+        planes = 8;  // lower the residual's floor and keep refining
+        prev = HUGE_VAL;
+      } else {
+        if (ratio > 1e-10) rc = TRSM_ENOCONV;
+        break;
+      }
+    } else {
+      prev = ratio;
     }
-    prev = ratio;
     best = std::min(best, ratio);
     if (it == max_iter) {
       rc = TRSM_ENOCONV;
       break;
     }
     // ---- R = B - L X ----
-    if (residual == TRSM_RESIDUAL_SLICED) {
+    if (residual != TRSM_RESIDUAL_FP64) {
       e = trsm::slice_rows(X_dev, ldx, Xs, s);
       if (e == cudaSuccess)
         e = trsm::sliced_residual(mp->Ls, mp->diag, 0, Xs, X_dev, ldx, B_dev, ldb, R, ld, ws + oPart, true,
-                                  err, s);
+                                  planes, err, s);
     } else {
       dim3 g(static_cast<unsigned>((n + trsm::TILE - 1) / trsm::TILE),
              static_cast<unsigned>((k + trsm::TILE - 1) / trsm::TILE));

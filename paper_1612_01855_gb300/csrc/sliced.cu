@@ -7,27 +7,35 @@
 //   * every row of the strictly lower L (and every column of X) is cut along
 //     K into chunks of KC = 2048 elements; each (row, chunk) gets a
 //     power-of-two exponent e with max|a| < 2^e, and a / 2^e, rounded to
-//     42 fraction bits, is written as seven balanced base-64 digits
-//     d_0..d_6 (|d_0| <= 64, |d_s| <= 32 for s >= 1); plane s stores
-//     d_s 2^(-6s), exact in bf16, so that a = 2^(e-6) sum_s plane_s(a);
-//   * the tensor core multiplies plane pairs (s, u) with s + u <= 6 (28
-//     pairs, A plane fixed for consecutive MMAs) into five FP32 groups:
-//     d = s + u = 0, 1, 2, 3 each alone, and d >= 4 together.  Within one
-//     K chunk the sums of groups 0..3 are integer multiples of 2^(-6d)
-//     below 2^24 units (group 0: 2048 * 64^2 = 2^23; d = 1..3: at most
-//     2048 * 2^10 * (d + 3) <= 1.26e7 < 2^24 = 1.68e7), so they are exact;
-//     group 4 is 2^-24 of the total, and the FP32 rounding of its running
-//     sum stays near 2^-42 of the total;
-//   * after each chunk the epilogue adds the four groups in float-float
+//     48 fraction bits, is written as eight balanced base-64 digits
+//     d_0..d_7 (|d_0| <= 64, |d_s| <= 32 for s >= 1); plane s stores
+//     d_s 2^(-6s), exact in bf16, so that a = 2^(e-6) sum_s plane_s(a).
+//     The first P planes (P = 7 or 8) are themselves a P-digit expansion
+//     exact to 2^(e-6P-1);
+//   * the tensor core multiplies plane pairs (s, u) with s + u <= P - 1
+//     (28 pairs for P = 7, 36 for P = 8, A plane fixed for consecutive
+//     MMAs) into FP32 groups: each d = s + u below a cut-off alone, the rest
+//     together.  Within one K chunk the sum of a single d is an integer
+//     multiple of 2^(-6d) below 2^24 units (d = 0: 2048 * 64^2 = 2^23;
+//     d = 1..4: at most 2048 * 2^10 * (d + 3) <= 1.47e7 < 2^24 = 1.68e7),
+//     so it is exact.  The combined group is rounded to FP32 once per MMA
+//     (128 times per chunk):
+//       P = 7: d = 0..3 alone, d >= 4 together (2^-24 of the total), 96
+//              columns per tile: about 2^-41 of |L| |X| from those
+//              roundings, the fast variant;
+//       P = 8: d = 0..4 alone, d >= 5 together (2^-30 of the total), 80
+//              columns per tile: below 2^-47;
+//   * after each chunk the epilogue adds the six groups in float-float
 //     arithmetic (about 48 bits), scales by 2^(eL + eX - 12) and
 //     accumulates (in a float-float partial buffer when a tile has more than
 //     one chunk); finally R = B - diag(L) X - (hi + lo) in FP64.
 // The diagonal of L stays out of the digit planes (it would set the row
 // exponents and push the off-diagonal entries into the low digits).  Each
-// digit expansion is exact to 2^(e-43), dropped pairs (s + u > 6) are below
-// 2^(eL+eX-41) per product, so entries much smaller than their (row, chunk)
-// maximum carry fewer significant bits; on the workloads here the residual
-// is accurate to about 2^-40 relative to |L| |X|.
+// P-digit expansion is exact to 2^(e-6P-1), dropped pairs (s + u >= P) are
+// below 2^(eL+eX-6P+1) per product, so entries much smaller than their
+// (row, chunk) maximum carry fewer significant bits; on the workloads here
+// the residual is accurate to about 2^-40 (P = 7) or 2^-46 (P = 8) relative
+// to |L| |X|.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -43,64 +51,73 @@ namespace sliced {
 
 using tc::TileCfg;
 
-constexpr int BN = 96;
-constexpr int NG = 5;  // groups d = 0, 1, 2, 3 and d >= 4
-// bf16, 128-byte rows (64 elements of K per stage), one 196 KB stage of
-// 7 + 7 planes: the 28 pairs of one stage keep the tensor core busy long
-// enough that a deeper ring buys little, and two stages do not fit.  Five
-// groups of 96 FP32 columns fill 480 of the 512 TMEM columns.
-using Cfg = TileCfg<false, BN, kSlices, kSlices, NG, 1, 128>;
-static_assert(kChunk % Cfg::KB == 0, "chunk must be a whole number of stages");
+// bf16, 128-byte rows (64 elements of K per stage), one stage of P + P
+// planes (196 KB for P = 7, 208 KB for P = 8): the pairs of one stage keep
+// the tensor core busy long enough that a deeper ring buys little, and two
+// stages do not fit.  NG groups of BN FP32 columns fill 480 of the 512 TMEM
+// columns.
+template <int P>
+struct Shape {
+  static constexpr int BN = P == 7 ? 96 : 80;
+  static constexpr int NG = P == 7 ? 5 : 6;  // the last group holds every d >= NG - 1
+};
+template <int P>
+using Cfg = TileCfg<false, Shape<P>::BN, P, P, Shape<P>::NG, 1, 128>;
+static_assert(kChunk % Cfg<7>::KB == 0 && Cfg<7>::KB == Cfg<8>::KB, "chunk must be a whole number of stages");
+static_assert(Cfg<8>::SMEM_BYTES <= 227 * 1024 && Cfg<7>::SMEM_BYTES <= 227 * 1024, "stage exceeds shared memory");
 
-// Digit pairs (s, u), s + u <= kSlices - 1, in s-major order (the A plane
-// stays the same for consecutive MMAs, which the tensor core streams
-// faster), group min(s + u, 4).
+// Digit pairs (s, u), s + u <= P - 1, in s-major order (the A plane stays
+// the same for consecutive MMAs, which the tensor core streams faster),
+// group min(s + u, NG - 1).
+template <int P>
 struct DigitPairs {
-  static constexpr int N = kSlices * (kSlices + 1) / 2;
+  static constexpr int N = P * (P + 1) / 2;
   __device__ static constexpr int s_of(int p) {
-    int s = 0, cnt = kSlices;
+    int s = 0, cnt = P;
     while (p >= cnt) {
       p -= cnt;
       ++s;
-      cnt = kSlices - s;
+      cnt = P - s;
     }
     return s;
   }
   __device__ static constexpr int u_of(int p) {
-    int s = 0, cnt = kSlices;
+    int s = 0, cnt = P;
     while (p >= cnt) {
       p -= cnt;
       ++s;
-      cnt = kSlices - s;
+      cnt = P - s;
     }
     return p;
   }
   __device__ static constexpr int a(int p) { return s_of(p); }
   __device__ static constexpr int b(int p) { return u_of(p); }
-  __device__ static constexpr int g(int p) { return s_of(p) + u_of(p) < 4 ? s_of(p) + u_of(p) : 4; }
+  __device__ static constexpr int g(int p) {
+    return s_of(p) + u_of(p) < Shape<P>::NG - 1 ? s_of(p) + u_of(p) : Shape<P>::NG - 1;
+  }
 };
 
 // ---------------------------------------------------------------- slicing
 // One warp per (row, chunk): rows hold K contiguous FP64 values (stride ld
-// between rows).  Writes kSlices bf16 digit planes (plane stride plane_elems,
+// between rows).  Writes kPlanes bf16 digit planes (plane stride plane_elems,
 // row stride kp) and the chunk exponent.  Each lane converts four
 // consecutive elements and stores four digits per plane at once.
-// Balanced base-64 digits of round(a 2^(42 - e)) (|.| < 2^42 because
+// Balanced base-64 digits of round(a 2^(48 - e)) (|.| <= 2^48 because
 // |a| < 2^e), computed from the bit fields of `a` with integer operations
 // only (GB300's FP64 pipe is narrow): a = +-m 2^(E - 1075) with m the
 // 53-bit significand, so the rounded value is m shifted right by
-// (1075 - E) - (42 - e) bits, rounded to nearest.
-__device__ __forceinline__ void digits_of(double a, int e, float (&dig)[kSlices]) {
+// (1075 - E) - (48 - e) bits, rounded to nearest.
+__device__ __forceinline__ void digits_of(double a, int e, float (&dig)[kPlanes]) {
   const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(a));
   const int E = static_cast<int>((bits >> 52) & 0x7FF);
   unsigned long long m = bits & ((1ull << 52) - 1);
   if (E != 0) m |= 1ull << 52;
-  const int rsh = (1075 - (E != 0 ? E : 1)) - (6 * kSlices - e);  // >= 11 when |a| < 2^e
+  const int rsh = (1075 - (E != 0 ? E : 1)) - (kDigitBits * kPlanes - e);  // >= 5 when |a| < 2^e
   long long v = 0;
   if (rsh < 64) v = static_cast<long long>((m + (1ull << (rsh - 1))) >> rsh);
   if (bits >> 63) v = -v;
 #pragma unroll
-  for (int s = kSlices - 1; s >= 1; --s) {
+  for (int s = kPlanes - 1; s >= 1; --s) {
     long long rem = v & 63;
     if (rem >= 32) rem -= 64;
     v = (v - rem) >> kDigitBits;
@@ -141,11 +158,11 @@ __global__ void slice_rows_kernel(const double* __restrict__ src, int64_t ld, in
   const int64_t kw1 = (c == nch - 1) ? kp : k1;
   __nv_bfloat16* drow = dst + r * kp;
   for (int64_t k = k0 + 4 * lane; k < kw1; k += 128) {
-    float dig[4][kSlices];
+    float dig[4][kPlanes];
 #pragma unroll
     for (int q = 0; q < 4; ++q) digits_of((k + q < K) ? p[k + q] : 0.0, e, dig[q]);
 #pragma unroll
-    for (int s = 0; s < kSlices; ++s) {
+    for (int s = 0; s < kPlanes; ++s) {
       const float w = __int_as_float((127 - kDigitBits * s) << 23);
       __nv_bfloat162 lo2 = __floats2bfloat162_rn(dig[0][s] * w, dig[1][s] * w);
       __nv_bfloat162 hi2 = __floats2bfloat162_rn(dig[2][s] * w, dig[3][s] * w);
@@ -196,6 +213,7 @@ __device__ __forceinline__ void ff_add(float& h, float& l, float bh, float bl) {
   l = e - (h - s);
 }
 
+template <int BN>
 struct ResidualEpi {
   const double* B;
   int64_t ldb;
@@ -222,8 +240,8 @@ struct ResidualEpi {
   __device__ void k_range(int tm, int, int& kb0, int& kb1, int& chunk) const {
     const int kend = lower ? min(K, (tm + 1) * 128) : K;
     kb0 = 0;
-    kb1 = (kend + Cfg::KB - 1) / Cfg::KB;
-    chunk = kChunk / Cfg::KB;
+    kb1 = (kend + Cfg<7>::KB - 1) / Cfg<7>::KB;
+    chunk = kChunk / Cfg<7>::KB;
   }
   __device__ void init(State&) const {}
   __device__ void group(State& st, int, int, int, int, int, int g, const float (&v)[16]) const {
@@ -294,7 +312,7 @@ struct ResidualEpi {
 size_t sliced_operand_bytes(int64_t rows, int64_t K) {
   const int64_t kp = (K + 7) / 8 * 8;
   const int64_t nch = (K + kChunk - 1) / kChunk;
-  size_t b = sizeof(__nv_bfloat16) * static_cast<size_t>(kSlices) * rows * kp;
+  size_t b = sizeof(__nv_bfloat16) * static_cast<size_t>(kPlanes) * rows * kp;
   b = (b + 255) / 256 * 256;
   b += sizeof(int16_t) * static_cast<size_t>(rows) * nch;
   return (b + 255) / 256 * 256;
@@ -307,7 +325,7 @@ SlicedOperand sliced_operand_view(void* base, int64_t rows, int64_t K) {
   o.kp = (K + 7) / 8 * 8;
   o.nch = (K + kChunk - 1) / kChunk;
   o.digits = static_cast<__nv_bfloat16*>(base);
-  size_t b = sizeof(__nv_bfloat16) * static_cast<size_t>(kSlices) * rows * o.kp;
+  size_t b = sizeof(__nv_bfloat16) * static_cast<size_t>(kPlanes) * rows * o.kp;
   b = (b + 255) / 256 * 256;
   o.ex = reinterpret_cast<int16_t*>(static_cast<unsigned char*>(base) + b);
   return o;
@@ -335,52 +353,75 @@ cudaError_t slice_lower_rows(const double* L, int64_t ldl, int64_t n, const Slic
 
 size_t sliced_partial_bytes(int64_t n, int64_t k) { return sizeof(float2) * static_cast<size_t>(n) * k; }
 
-cudaError_t sliced_residual(const SlicedOperand& Ls, const double* L, int64_t ldl, const SlicedOperand& Xs,
-                            const double* X, int64_t ldx, const double* B, int64_t ldb, double* R,
-                            int64_t ldr, void* partial, bool lower, int* err, cudaStream_t s) {
-  using sliced::Cfg;
+namespace {
+
+struct ResidualArgs {
+  const double* B;
+  int64_t ldb;
+  const double* L;
+  int64_t ldl;
+  const double* X;
+  int64_t ldx;
+  double* R;
+  int64_t ldr;
+  void* partial;
+  bool lower;
+};
+
+template <int P>
+cudaError_t launch_residual(const SlicedOperand& Ls, const SlicedOperand& Xs, const ResidualArgs& a, int* err,
+                            cudaStream_t s) {
+  using C = sliced::Cfg<P>;
+  constexpr int BN = sliced::Shape<P>::BN;
   CUtensorMap ma, mb;
-  if (!tc::make_kmajor_map(&ma, Ls.digits, false, Ls.kp, Ls.rows, Ls.kp, kSlices, Ls.rows * Ls.kp, 128,
-                           kSlices, 128))
+  if (!tc::make_kmajor_map(&ma, Ls.digits, false, Ls.kp, Ls.rows, Ls.kp, kPlanes, Ls.rows * Ls.kp, 128, P, 128))
     return cudaErrorInvalidValue;
-  if (!tc::make_kmajor_map(&mb, Xs.digits, false, Xs.kp, Xs.rows, Xs.kp, kSlices, Xs.rows * Xs.kp,
-                           sliced::BN, kSlices, 128))
+  if (!tc::make_kmajor_map(&mb, Xs.digits, false, Xs.kp, Xs.rows, Xs.kp, kPlanes, Xs.rows * Xs.kp, BN, P, 128))
     return cudaErrorInvalidValue;
-  sliced::ResidualEpi epi;
-  epi.B = B;
-  epi.ldb = ldb;
-  epi.Ld = L;
-  epi.ldl = ldl;
-  epi.X = X;
-  epi.ldx = ldx;
-  epi.R = R;
-  epi.ldr = ldr;
-  epi.part = static_cast<float2*>(partial);
+  sliced::ResidualEpi<BN> epi;
+  epi.B = a.B;
+  epi.ldb = a.ldb;
+  epi.Ld = a.L;
+  epi.ldl = a.ldl;
+  epi.X = a.X;
+  epi.ldx = a.ldx;
+  epi.R = a.R;
+  epi.ldr = a.ldr;
+  epi.part = static_cast<float2*>(a.partial);
   epi.eA = Ls.ex;
   epi.eB = Xs.ex;
   epi.nch = Ls.nch;
   epi.M = static_cast<int>(Ls.rows);
   epi.N = static_cast<int>(Xs.rows);
   epi.K = static_cast<int>(Ls.K);
-  epi.lower = lower ? 1 : 0;
-  auto kern = tc::tc_tile_kernel<Cfg, sliced::DigitPairs, sliced::ResidualEpi>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(Cfg::SMEM_BYTES));
+  epi.lower = a.lower ? 1 : 0;
+  auto kern = tc::tc_tile_kernel<C, sliced::DigitPairs<P>, sliced::ResidualEpi<BN>>;
+  cudaError_t e =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(C::SMEM_BYTES));
   if (e != cudaSuccess) return e;
-  dim3 grid(static_cast<unsigned>((Ls.rows + 127) / 128),
-            static_cast<unsigned>((Xs.rows + sliced::BN - 1) / sliced::BN));
-  kern<<<grid, 192, Cfg::SMEM_BYTES, s>>>(ma, mb, epi, err);
+  dim3 grid(static_cast<unsigned>((Ls.rows + 127) / 128), static_cast<unsigned>((Xs.rows + BN - 1) / BN));
+  kern<<<grid, 192, C::SMEM_BYTES, s>>>(ma, mb, epi, err);
   count_launch();
   return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t sliced_residual(const SlicedOperand& Ls, const double* L, int64_t ldl, const SlicedOperand& Xs,
+                            const double* X, int64_t ldx, const double* B, int64_t ldb, double* R,
+                            int64_t ldr, void* partial, bool lower, int planes, int* err, cudaStream_t s) {
+  if (planes != 7 && planes != 8) return cudaErrorInvalidValue;
+  const ResidualArgs a{B, ldb, L, ldl, X, ldx, R, ldr, partial, lower};
+  return planes == 8 ? launch_residual<8>(Ls, Xs, a, err, s) : launch_residual<7>(Ls, Xs, a, err, s);
 }
 
 }  // namespace trsm
 
 extern "C" int trsm_residual_sliced(const double* L_dev, int64_t n, int64_t ldl, const double* X_dev,
                                     int64_t k, int64_t ldx, const double* B_dev, int64_t ldb,
-                                    double* R_dev, int64_t ldr, int* err_dev, void* stream) {
+                                    double* R_dev, int64_t ldr, int planes, int* err_dev, void* stream) {
   if (!L_dev || !X_dev || !B_dev || !R_dev || !err_dev || n < 1 || k < 1 || ldl < n || ldx < n ||
-      ldb < n || ldr < n)
+      ldb < n || ldr < n || (planes != 7 && planes != 8))
     return -1;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t lb = trsm::sliced_operand_bytes(n, n);
@@ -396,7 +437,7 @@ extern "C" int trsm_residual_sliced(const double* L_dev, int64_t n, int64_t ldl,
   if (e == cudaSuccess) e = trsm::slice_rows(X_dev, ldx, Xs, s);
   if (e == cudaSuccess)
     e = trsm::sliced_residual(Ls, L_dev, ldl, Xs, X_dev, ldx, B_dev, ldb, R_dev, ldr, buf + lb + xb + tb,
-                              true, err_dev, s);
+                              true, planes, err_dev, s);
   cudaFreeAsync(buf, s);
   if (e != cudaSuccess) {
     cudaGetLastError();

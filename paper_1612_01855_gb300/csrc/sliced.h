@@ -6,15 +6,15 @@
 
 namespace trsm {
 
-constexpr int kSlices = 7;     // base-64 digits per value
+constexpr int kPlanes = 8;     // base-64 digit planes stored per value
 constexpr int kDigitBits = 6;  // bits per digit
 constexpr int kChunk = 2048;   // K elements per exactly-summed chunk
 
-// kSlices digit planes of a rows x K operand (K-major: each row's K digits
+// kPlanes digit planes of a rows x K operand (K-major: each row's K digits
 // contiguous, row stride kp = K rounded up to 8), plus one int16 exponent
 // per (row, chunk of kChunk along K).
 struct SlicedOperand {
-  __nv_bfloat16* digits = nullptr;  // [kSlices][rows][kp]
+  __nv_bfloat16* digits = nullptr;  // [kPlanes][rows][kp]
   int16_t* ex = nullptr;            // [rows][nch]
   int64_t rows = 0, K = 0, kp = 0, nch = 0;
 };
@@ -37,9 +37,11 @@ size_t sliced_partial_bytes(int64_t n, int64_t k);
 // (Ls: n x n), the diagonal read from L in FP64 (L[i*ldl + i]; ldl = 0
 // reads a vector of the diagonal), and X by its sliced columns (Xs: k rows
 // of length n) plus X itself; R, B column-major n x k.  `partial` holds
-// sliced_partial_bytes(n, k) of scratch.
+// sliced_partial_bytes(n, k) of scratch.  `planes` (7 or 8) is the number of
+// leading digit planes multiplied: 7 gives about 2^-43 of |B| + |L| |X|, 8
+// about 2^-49 for 9/7 of the tensor-core work.
 cudaError_t sliced_residual(const SlicedOperand& Ls, const double* L, int64_t ldl, const SlicedOperand& Xs,
                             const double* X, int64_t ldx, const double* B, int64_t ldb, double* R,
-                            int64_t ldr, void* partial, bool lower, int* err, cudaStream_t s);
+                            int64_t ldr, void* partial, bool lower, int planes, int* err, cudaStream_t s);
 
 }  // namespace trsm

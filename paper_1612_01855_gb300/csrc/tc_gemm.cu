@@ -107,7 +107,49 @@ cudaError_t plain_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, f
   return cudaGetLastError();
 }
 
+// Split operands A = Ah + Al, B = Bh + Bl (bf16 planes): A B^T is taken as
+// Ah Bh^T + Ah Bl^T + Al Bh^T; the dropped Al Bl^T is 2^-16 of the product,
+// below what the other three terms carry (about 16 significant bits each
+// factor).  All three accumulate into one FP32 group.
+struct SplitPairs {
+  static constexpr int N = 3;
+  __device__ static constexpr int a(int p) { return p == 2 ? 1 : 0; }
+  __device__ static constexpr int b(int p) { return p == 1 ? 1 : 0; }
+  __device__ static constexpr int g(int) { return 0; }
+};
+
+template <int BN, int STAGES>
+cudaError_t split_gemm(const void* A, int64_t lda, int64_t a_plane, const void* B, int64_t ldb, int64_t b_plane,
+                       float* C, int64_t ldc, int64_t M, int64_t N, int64_t K, float alpha, float beta, int* err,
+                       cudaStream_t s) {
+  using Cfg = TileCfg<false, BN, 2, 2, 1, STAGES>;
+  CUtensorMap ma, mb;
+  if (!make_kmajor_map(&ma, A, false, K, M, lda, 2, a_plane, 128, 2, 128)) return cudaErrorInvalidValue;
+  if (!make_kmajor_map(&mb, B, false, K, N, ldb, 2, b_plane, BN, 2, 128)) return cudaErrorInvalidValue;
+  StoreF32Epi<BN> epi{C, ldc, static_cast<int>(M), static_cast<int>(N),
+                      static_cast<int>((K + Cfg::KB - 1) / Cfg::KB), alpha, beta};
+  auto kern = tc_tile_kernel<Cfg, SplitPairs, StoreF32Epi<BN>>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(Cfg::SMEM_BYTES));
+  if (e != cudaSuccess) return e;
+  dim3 grid(static_cast<unsigned>((M + 127) / 128), static_cast<unsigned>((N + BN - 1) / BN));
+  kern<<<grid, 192, Cfg::SMEM_BYTES, s>>>(ma, mb, epi, err);
+  count_launch();
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t gemm_split_bf16(const void* A, int64_t lda, int64_t a_plane, const void* B, int64_t ldb,
+                            int64_t b_plane, float* C, int64_t ldc, int64_t M, int64_t N, int64_t K, float alpha,
+                            float beta, int* err, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+  // a stage is 64 KB at BN = 128; short K (the blocked solve's updates)
+  // takes 48 KB stages at BN = 64 so that two CTAs share an SM
+  const int kb = static_cast<int>((K * 2 + 127) / 128);
+  if (kb <= 8) return split_gemm<64, 2>(A, lda, a_plane, B, ldb, b_plane, C, ldc, M, N, K, alpha, beta, err, s);
+  return split_gemm<128, 3>(A, lda, a_plane, B, ldb, b_plane, C, ldc, M, N, K, alpha, beta, err, s);
+}
 
 cudaError_t gemm_lowp(bool tf32, const void* A, int64_t lda, const void* B, int64_t ldb, float* C,
                       int64_t ldc, int64_t M, int64_t N, int64_t K, float alpha, float beta, int* err,
@@ -127,14 +169,15 @@ cudaError_t gemm_lowp(bool tf32, const void* A, int64_t lda, const void* B, int6
 }  // namespace tc
 }  // namespace trsm
 
-extern "C" int trsm_tc_gemm_selftest(int tf32, const void* A_dev, const void* B_dev, float* C_dev,
+extern "C" int trsm_tc_gemm_selftest(int mode, const void* A_dev, const void* B_dev, float* C_dev,
                                      int64_t M, int64_t N, int64_t K, int* err_dev, void* stream) {
-  if (!A_dev || !B_dev || !C_dev || !err_dev || M < 1 || N < 1 || K < 1) return -1;
-  if ((tf32 && K % 4) || (!tf32 && K % 8)) return -1;  // TMA: 16-byte row strides
+  if (!A_dev || !B_dev || !C_dev || !err_dev || M < 1 || N < 1 || K < 1 || mode < 0 || mode > 2) return -1;
+  if ((mode == 1 && K % 4) || (mode != 1 && K % 8)) return -1;  // TMA: 16-byte row strides
   if (((uintptr_t)A_dev | (uintptr_t)B_dev) & 15) return -1;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaError_t e = trsm::tc::gemm_lowp(tf32 != 0, A_dev, K, B_dev, K, C_dev, M, M, N, K, 1.f, 0.f,
-                                      err_dev, s);
+  cudaError_t e =
+      mode == 2 ? trsm::tc::gemm_split_bf16(A_dev, K, M * K, B_dev, K, N * K, C_dev, M, M, N, K, 1.f, 0.f, err_dev, s)
+                : trsm::tc::gemm_lowp(mode == 1, A_dev, K, B_dev, K, C_dev, M, M, N, K, 1.f, 0.f, err_dev, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return -4;

@@ -25,5 +25,13 @@ cudaError_t gemm_lowp(bool tf32, const void* A, int64_t lda, const void* B, int6
                       int64_t ldc, int64_t M, int64_t N, int64_t K, float alpha, float beta, int* err,
                       cudaStream_t s);
 
+// As gemm_lowp with split bf16 operands: A is two planes (hi, lo) of
+// M x K, a_plane elements apart, and B two planes of N x K, b_plane apart;
+// C = alpha (Ah Bh^T + Ah Bl^T + Al Bh^T) + beta C, about 16 significant
+// bits per factor instead of 8.
+cudaError_t gemm_split_bf16(const void* A, int64_t lda, int64_t a_plane, const void* B, int64_t ldb,
+                            int64_t b_plane, float* C, int64_t ldc, int64_t M, int64_t N, int64_t K, float alpha,
+                            float beta, int* err, cudaStream_t s);
+
 }  // namespace tc
 }  // namespace trsm

@@ -48,3 +48,41 @@ def test_engine_gemm(cuda_lib, tf32, M, N, K):
     # inputs are exact in the MMA; only FP32 accumulation order differs
     assert np.all(np.isfinite(got))
     assert np.max(np.abs(got - want) / (scale + 1e-30)) < 2e-6
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (300, 200, 520), (1024, 512, 1024), (129, 257, 200),
+                                   (256, 64, 256)])
+def test_engine_split_bf16_gemm(cuda_lib, M, N, K):
+    """Split bf16 operands (hi + lo planes): C = Ah Bh^T + Ah Bl^T + Al Bh^T."""
+    import torch
+    rng = np.random.default_rng(M * N + K)
+    A = rng.uniform(-1, 1, size=(M, K))
+    B = rng.uniform(-1, 1, size=(N, K))
+
+    def split(X):
+        hi = torch.from_numpy(X).to(torch.bfloat16)
+        lo = torch.from_numpy(X - hi.double().numpy()).to(torch.bfloat16)
+        return hi, lo
+
+    Ah, Al = split(A)
+    Bh, Bl = split(B)
+    At = torch.stack([Ah, Al]).contiguous().cuda()  # [2][M][K]
+    Bt = torch.stack([Bh, Bl]).contiguous().cuda()
+    C = torch.full((N, M), float("nan"), dtype=torch.float32, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = cuda_lib.trsm_tc_gemm_selftest(2, ctypes.c_void_p(At.data_ptr()), ctypes.c_void_p(Bt.data_ptr()),
+                                        ctypes.c_void_p(C.data_ptr()), M, N, K, ctypes.c_void_p(err.data_ptr()), s)
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert err.item() == 0
+    got = C.cpu().numpy().T.astype(np.float64)
+    ah, al, bh, bl = (t.double().numpy() for t in (Ah, Al, Bh, Bl))
+    three = ah @ bh.T + ah @ bl.T + al @ bh.T
+    scale = np.abs(A) @ np.abs(B).T
+    # the three products exactly, up to FP32 accumulation
+    assert np.max(np.abs(got - three) / scale) < 2e-6
+    # against the unsplit FP64 product: the dropped lo*lo term and the
+    # representation hi + lo (about 2^-16 each), far below bf16's 2^-8
+    rel = np.max(np.abs(got - A @ B.T) / scale)
+    assert rel < 2.0 ** -14, rel

@@ -18,7 +18,7 @@ def _rel(a, b):
     return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
 
 
-@pytest.mark.parametrize("inner", ["tf32", "bf16"])
+@pytest.mark.parametrize("inner", ["tf32", "bf16", "bf16x3"])
 @pytest.mark.parametrize("residual,s32", [("sliced", False), ("fp64", False), ("sliced", True)])
 @pytest.mark.parametrize("n,k,n0", [(1024, 64, 128), (1000, 37, 64), (300, 5, 300)])
 def test_mixed_well_conditioned(cuda_lib, inner, residual, s32, n, k, n0):
@@ -35,7 +35,7 @@ def test_mixed_well_conditioned(cuda_lib, inner, residual, s32, n, k, n0):
     print(f"mixed {inner}/{residual} n={n} k={k} n0={n0}: {iters} iterations, last update {upd:.2e}, rel err {err:.2e}")
     # the refinement's limit is the residual's accuracy: ~2^-40 of |L||X| (sliced), ~n eps (fp64)
     assert err < (5e-12 if residual == "sliced" else 1e-13)
-    assert iters <= (12 if inner == "tf32" else 25)
+    assert iters <= {"tf32": 12, "bf16": 25, "bf16x3": 6}[inner]
 
 
 def test_mixed_graded_diagonal_forward_error(cuda_lib):
@@ -55,6 +55,54 @@ def test_mixed_graded_diagonal_forward_error(cuda_lib):
     fp64 = _rel(oracle.forward_subst(L, B), ref)
     print(f"graded c=2: {iters} iterations, forward error {err:.2e} (FP64 oracle: {fp64:.2e})")
     assert err < 1e-10
+
+
+def test_mixed_residual_planes_set_the_floor(cuda_lib):
+    """Diagonal graded from 1 to 1e-3 (componentwise condition ~1e3): the
+    refinement stops at the condition times the residual's accuracy.  Seven
+    digit planes (~2^-44) leave it near 1e-10; eight (~2^-49), alone or after
+    seven stagnate, reach well below, against the double-double
+    substitution."""
+    import paper_1612_01855_gb300 as g
+    n, k, n0 = 2048, 8, 128
+    L, B = inputs.graded_diagonal(n, k, 3, seed=5)
+    Ld = _dev(L)
+    plan = g.trsm_plan(Ld, n0)
+    g.trsm_plan_mixed(plan, Ld, "tf32")
+    hi, lo = oracle.forward_subst_dd(L, B)
+    ref = hi + lo
+    errs = {}
+    for res in ("sliced", "sliced8", "adaptive"):
+        X, iters, upd = g.trsm_solve_mixed(plan, _dev(B), residual=res, max_iter=40, tol=1e-16,
+                                           raise_on_noconv=False)
+        errs[res] = (_rel(X.cpu().numpy(), ref), iters, upd)
+    print(f"graded c=3 n={n}: {errs}")
+    for res in ("sliced8", "adaptive"):
+        assert errs[res][0] < 1e-11
+        assert errs[res][0] < 0.25 * errs["sliced"][0]
+    assert errs["adaptive"][1] > errs["sliced"][1]  # it went on after seven planes stagnated
+
+
+def test_mixed_split_inner_reaches_the_floor(cuda_lib):
+    """Diagonal graded from 1 to 1e-3: the split-bf16 update (about 16 bits
+    per factor) reaches the eight-plane residual's floor in no more sweeps
+    than tf32 (11 bits)."""
+    import paper_1612_01855_gb300 as g
+    n, k, n0 = 2048, 8, 128
+    L, B = inputs.graded_diagonal(n, k, 3, seed=5)
+    Ld = _dev(L)
+    hi, lo = oracle.forward_subst_dd(L, B)
+    ref = hi + lo
+    out = {}
+    for inner in ("tf32", "bf16x3"):
+        plan = g.trsm_plan(Ld, n0)
+        g.trsm_plan_mixed(plan, Ld, inner)
+        X, iters, upd = g.trsm_solve_mixed(plan, _dev(B), residual="sliced8", max_iter=40, tol=1e-12,
+                                           raise_on_noconv=False)
+        out[inner] = (_rel(X.cpu().numpy(), ref), iters, upd)
+    print(f"graded c=3 n={n}, eight planes: {out}")
+    assert out["bf16x3"][0] < 1e-11
+    assert out["bf16x3"][1] <= out["tf32"][1]
 
 
 def test_mixed_overflowing_solution_is_reported(cuda_lib):

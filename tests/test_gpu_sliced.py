@@ -44,9 +44,10 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(np.asarray(a, dtype=np.float64).T)).cuda().t()
 
 
+@pytest.mark.parametrize("planes", [7, 8])
 @pytest.mark.parametrize("n,k,kind", [(1024, 8, "well"), (1500, 5, "well"), (700, 17, "graded2"),
                                       (2100, 3, "well"), (130, 64, "well")])
-def test_sliced_residual_accuracy(cuda_lib, n, k, kind):
+def test_sliced_residual_accuracy(cuda_lib, n, k, kind, planes):
     import torch
     lib = cuda_lib
     if kind == "well":
@@ -62,18 +63,21 @@ def test_sliced_residual_accuracy(cuda_lib, n, k, kind):
     rc = lib.trsm_residual_sliced(ctypes.c_void_p(Ld.data_ptr()), n, Ld.stride(1),
                                   ctypes.c_void_p(Xd.data_ptr()), k, Xd.stride(1),
                                   ctypes.c_void_p(Bd.data_ptr()), Bd.stride(1),
-                                  ctypes.c_void_p(Rd.data_ptr()), Rd.stride(1),
+                                  ctypes.c_void_p(Rd.data_ptr()), Rd.stride(1), planes,
                                   ctypes.c_void_p(err.data_ptr()), s)
     assert rc == 0
     torch.cuda.synchronize()
     assert err.item() == 0
     R = Rd.cpu().numpy()
     Rref = exact_residual(L, X, B)
-    scale = np.abs(np.tril(L)) @ np.abs(X)
+    # componentwise measure |B| + |L||X|: the final FP64 rounding of R is
+    # relative to |B - L X|, which |L||X| alone does not bound when X is small
+    scale = np.abs(B) + np.abs(np.tril(L)) @ np.abs(X)
     rel = np.max(np.abs(R - Rref) / scale)
     assert np.all(np.isfinite(R))
-    # 7 digits of 6 bits: each factor exact to 2^-43 of its (row, chunk) maximum,
-    # dropped digit pairs below 2^-41 per product; relative to |L||X| the max
-    # error stays near 2^-41 (2^-39 when a small diagonal shrinks |L||X|)
-    print(f"sliced residual n={n} k={k} {kind}: max rel err {rel:.3e} (2^{np.log2(rel):.1f})")
-    assert rel < 2.0 ** -38, rel
+    # P digits of 6 bits: each factor exact to 2^-(6P+1) of its (row, chunk)
+    # maximum, dropped digit pairs below 2^-(6P-1) per product; relative to
+    # |B| + |L||X| the max error stays near 2^-43 for P = 7 and 2^-48 for
+    # P = 8 (two bits more when a small diagonal shrinks |L||X|)
+    print(f"sliced residual P={planes} n={n} k={k} {kind}: max rel err {rel:.3e} (2^{np.log2(rel):.1f})")
+    assert rel < 2.0 ** (-40 if planes == 7 else -45), rel
