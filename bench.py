@@ -32,6 +32,37 @@ SWEEP_N0 = [64, 128, 256, 512, 1024, None]  # None = n (full inversion)
 NOMINAL_SM_MHZ = 2070.0
 SMS = 152
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one
+# it_inv_solve_kernel launch per bench shape, from one ncu capture each
+# (profiles/it_inv_solve_kernel_dram_bench_shapes.md).  They describe the
+# kernel source they were taken from; once solve.cu or fp64_tile.cuh changes
+# the figures no longer apply and the bench reports traffic as null.
+SOLVE_TRAFFIC_SHA256 = "ac43148b6e70e67167d687ac19c28b360971cabce804014c5f9be919a9f3e9c4"
+SOLVE_TRAFFIC = {(16384, 256, 256): 1552345856 + 234781696,
+                 (8192, 8192, 512): 5679589376 + 4524160256,
+                 (2048, 131072, 2048): 3338127104 + 2148346624}
+
+
+def solve_source_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("solve.cu", "fp64_tile.cuh"):
+        with open(os.path.join(ROOT, "paper_1612_01855_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def solve_traffic(shapes, n0s):
+    """Mean DRAM bytes per solve launch over the step's shapes, the per-shape
+    figures and the algorithmic bytes 8 (n^2/2 + 2 n k) beside them; None
+    when the counters do not describe this kernel source or these shapes."""
+    keys = [(n, k, n0) for (n, k), n0 in zip(shapes, n0s)]
+    if solve_source_sha256() != SOLVE_TRAFFIC_SHA256 or any(key not in SOLVE_TRAFFIC for key in keys):
+        return None, None
+    by_shape = {f"{n}x{k}": {"dram_bytes": SOLVE_TRAFFIC[(n, k, n0)],
+                             "algorithmic_bytes": int(8 * (n * n / 2 + 2 * n * k))} for n, k, n0 in keys}
+    return sum(SOLVE_TRAFFIC[key] for key in keys) / len(keys), by_shape
+
 
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
@@ -185,6 +216,29 @@ def precision_study(g, torch, n, k, n0, cs, inners, s_modes, dd_cols=2, stream=N
     return out
 
 
+def batch_systems(torch, count, dtype, seed, choose_n0):
+    """The batching workload: `count` systems, n log-uniform in [32, 1024], k
+    log-uniform in [1, 256], diagonal U[2,3], strictly lower U[-1,1]/n, B
+    U[-1,1], each drawn on the device from seed + index.  Returns (systems,
+    sum of n^2 k)."""
+    rng = np.random.default_rng(seed)
+    ns = np.rint(np.exp(rng.uniform(np.log(32), np.log(1024), size=count))).astype(int)
+    ks = np.rint(np.exp(rng.uniform(0.0, np.log(256), size=count))).astype(int)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    gen = torch.Generator(device="cuda")
+    systems = []
+    for i, (n, k) in enumerate(zip(ns, ks)):
+        gen.manual_seed(seed + i)
+        L = torch.rand((n, n), generator=gen, device="cuda", dtype=tdt).mul_(2).sub_(1).div_(int(n))
+        L = torch.tril(L, -1)
+        L.diagonal().copy_(torch.rand(int(n), generator=gen, device="cuda", dtype=tdt).add_(2))
+        L = L.t().contiguous().t()
+        B = torch.rand((int(k), int(n)), generator=gen, device="cuda", dtype=tdt).mul_(2).sub_(1).t()
+        X = torch.empty((int(k), int(n)), device="cuda", dtype=tdt).t()
+        systems.append({"L": L, "B": B, "X": X, "n0": choose_n0(int(n))})
+    return systems, float(np.sum(ns.astype(np.float64) ** 2 * ks))
+
+
 def batched_study(g, torch, count=4096, dtypes=("f64", "f32"), reps=5, seed=1000):
     """Batching workload: `count` independent systems, n log-uniform in
     [32, 1024], k log-uniform in [1, 256], diagonal U[2,3], strictly lower
@@ -192,25 +246,10 @@ def batched_study(g, torch, count=4096, dtypes=("f64", "f32"), reps=5, seed=1000
     solved (in-launch inversion + blocked solve) by one persistent launch,
     replayed as a CUDA graph; n0 per size bucket from the autotuner."""
     from paper_1612_01855_gb300 import autotune
-    rng = np.random.default_rng(seed)
-    ns = np.rint(np.exp(rng.uniform(np.log(32), np.log(1024), size=count))).astype(int)
-    ks = np.rint(np.exp(rng.uniform(0.0, np.log(256), size=count))).astype(int)
-    flops = float(np.sum(ns.astype(np.float64) ** 2 * ks))
     out = []
     for dtype in dtypes:
         table = autotune.tune_batch_n0(dtype)
-        tdt = torch.float64 if dtype == "f64" else torch.float32
-        gen = torch.Generator(device="cuda")
-        systems = []
-        for i, (n, k) in enumerate(zip(ns, ks)):
-            gen.manual_seed(seed + i)
-            L = torch.rand((n, n), generator=gen, device="cuda", dtype=tdt).mul_(2).sub_(1).div_(int(n))
-            L = torch.tril(L, -1)
-            L.diagonal().copy_(torch.rand(int(n), generator=gen, device="cuda", dtype=tdt).add_(2))
-            L = L.t().contiguous().t()
-            B = torch.rand((int(k), int(n)), generator=gen, device="cuda", dtype=tdt).mul_(2).sub_(1).t()
-            X = torch.empty((int(k), int(n)), device="cuda", dtype=tdt).t()
-            systems.append({"L": L, "B": B, "X": X, "n0": autotune.choose_n0(int(n), dtype, table)})
+        systems, flops = batch_systems(torch, count, dtype, seed, lambda n: autotune.choose_n0(n, dtype, table))
         batch = g.Batch(systems, dtype=dtype)
         batch.capture()
         for _ in range(2):
@@ -316,9 +355,12 @@ def serving_study(g, torch, nL=256, rates=(100, 300, 600, 1200), per_rate=300, s
 
 def run_case(args):
     """Single kernels for profiling (no JSON bench line):
-    sliced:N:K       the tensor-core residual R = B - L X, twice;
+    sliced:N:K[:P]   the tensor-core residual R = B - L X with P (7 or 8)
+                     digit planes, twice;
     mixed:N:K:N0     one mixed-precision refined solve (graded diagonal, c = 2);
-    engine:M:N:K     the bf16 tensor-core GEMM self-test, twice."""
+    engine:M:N:K     the bf16 tensor-core GEMM self-test, twice;
+    batch:COUNT:BITS one batched launch of COUNT systems of the batching
+                     workload in FP64 (BITS = 64) or FP32 (32), twice."""
     import ctypes
     import torch
     import paper_1612_01855_gb300 as g
@@ -361,6 +403,14 @@ def run_case(args):
             assert lib.trsm_tc_gemm_selftest(0, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(Bm.data_ptr()),
                                              ctypes.c_void_p(C.data_ptr()), M, N, K,
                                              ctypes.c_void_p(err.data_ptr()), s) == 0
+    elif kind == "batch":
+        dtype = "f64" if dims[1] == 64 else "f32"
+        systems, _ = batch_systems(torch, dims[0], dtype, 1000, lambda n: 32 if n < 256 else 64)
+        batch = g.Batch(systems, dtype=dtype)
+        for _ in range(2):
+            batch.run()
+        assert batch.status()[0] == 0
+        batch.destroy()
     else:
         raise SystemExit(f"unknown case {kind}")
     torch.cuda.synchronize()
@@ -572,6 +622,7 @@ def run_ours(args, rank, world, local):
                                   "solve_tflops": n * n * k / (sm_ * 1e-3) / 1e12}), flush=True)
 
     if rank == 0:
+        traffic, traffic_by_shape = solve_traffic(shapes, n0s)
         line = {
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -589,7 +640,9 @@ def run_ours(args, rank, world, local):
                          "peak_source": "measured DFMA throughput (trsm_fp64_peak) in this run; "
                                         f"nominal {SMS} SMs x 2 DFMA/clk x 2 flop x {NOMINAL_SM_MHZ:.0f} MHz"
                                         f" = {SMS * 4 * NOMINAL_SM_MHZ / 1e6:.3f}",
-                         "traffic": None},
+                         "traffic": traffic,
+                         "traffic_unit": "bytes per launch (mean over the step's three solve launches)",
+                         "traffic_by_shape": traffic_by_shape},
             "parity_max_rel_err": err,
             "mixed_precision": mixed,
             "batched": batched,
@@ -619,7 +672,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving figure")
     ap.add_argument("--no-schedules", action="store_true", help="skip the solve-schedule comparison")
     ap.add_argument("--precision", action="store_true", help="print the full c x inner x s-step study")
-    ap.add_argument("--case", default="", help="profiling case: sliced:N:K[:PLANES], mixed:N:K:N0, engine:M:N:K")
+    ap.add_argument("--case", default="", help="profiling case: sliced:N:K[:PLANES], mixed:N:K:N0, engine:M:N:K, batch:COUNT:BITS")
     ap.add_argument("--shapes", default="", help="override workload, e.g. 6144:1024:256 (not a bench line)")
     args = ap.parse_args()
     rank, world, local = dist_env()

@@ -16,8 +16,8 @@
 // solve of block row i+1 (a natural look-ahead).
 //
 // Scheduling: each CTA repeatedly takes the next task ticket from a global
-// counter.  Tickets follow wave order (wave l = all S(l,.,.) then all
-// U(.,.,.,l)), so every dependency of a task carries a smaller ticket and is
+// counter.  Tickets follow wave order (wave l = all S(l,.,.), column tile
+// major, then all U(.,.,.,l), row tile major), so every dependency of a task carries a smaller ticket and is
 // held by a CTA that is already running: the scheme cannot deadlock,
 // whatever number of CTAs is resident.  Waits are bounded (time and
 // iteration limits); a wait that runs out sets an error word, every CTA then
@@ -125,9 +125,13 @@ __global__ void __launch_bounds__(NTHREADS) it_inv_solve_kernel(const SolveArgs 
     double acc[TM][TN];
     zero_acc(acc);
     if (o < (int64_t)Rl * a.C) {
-      // ---- S(l, r, j), largest r first (they carry the most work) ----
-      const int r = Rl - 1 - (int)(o / a.C);
-      const int j = (int)(o % a.C);
+      // ---- S(l, r, j): column tile by column tile, and within one the
+      // largest r first (they carry the most work).  The row tiles of a
+      // column tile run together and share W_l[:, j] in L2: with k large
+      // (thousands of column tiles) a row-tile-major order streamed all of
+      // W_l from DRAM once per row tile.
+      const int r = Rl - 1 - (int)(o % Rl);
+      const int j = (int)(o / Rl);
       if (tid == 0) {
         bool ok = true;
         if (l > 0) {
