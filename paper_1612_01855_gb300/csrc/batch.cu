@@ -77,7 +77,7 @@ __device__ bool wait_geq_b(const int* p, int target, int* err) {
   unsigned ns = 64;
   for (long long it = 0; it < kWaitIters; ++it) {
     __nanosleep(ns);
-    if (ns < 2048) ns <<= 1;
+    if (ns < 512) ns <<= 1;  // tasks last microseconds: poll at least every 0.5 us
     if (ld_acquire_b(p) >= target) return true;
     if (*(volatile int*)err != 0) return false;
     if (gtime() - t0 > kWaitNs) break;
@@ -133,27 +133,51 @@ struct PhaseEntry {
 };
 
 template <class T>
-__global__ void __launch_bounds__(NTHREADS, 4) batch_kernel(const BatchSys<T>* __restrict__ sys,
+__global__ void __launch_bounds__(NTHREADS, 8) batch_kernel(const BatchSys<T>* __restrict__ sys,
                                                            const PhaseEntry* __restrict__ ent, int nent,
                                                            int64_t total, unsigned long long* ticket, int* err) {
-  __shared__ TileSmemT<T> sm;
-  __shared__ T ls[2][32][33];
+  // The leaf inversions (ls) and the tile products (sm) of a task run one
+  // after the other, so they share their shared memory: 17 KB per CTA in
+  // FP64 leaves room for eight CTAs per SM.
+  __shared__ union {
+    TileSmemT<T> tile;
+    T leaf[2][32][33];
+  } shm;
+  TileSmemT<T>& sm = shm.tile;
+  T(*ls)[32][33] = shm.leaf;
   __shared__ long long s_ticket;
-  __shared__ int s_ok;
+  __shared__ int s_ok, s_ent;
   const int tid = threadIdx.x;
   const int ty = tid >> 4, tx = tid & 15;
+  // (Requesting the next ticket ahead, to hide the atomic's round trip,
+  // measured slower: a task another CTA waits on then sits behind the
+  // holder's current task.)
+  int e = 0;  // entry of the previous ticket (tickets only grow per CTA)
   for (;;) {
-    if (tid == 0) s_ticket = static_cast<long long>(atomicAdd(ticket, 1ULL));
+    if (tid == 0) {
+      const long long cur = static_cast<long long>(atomicAdd(ticket, 1ULL));
+      s_ticket = cur;
+      if (cur < total) {
+        // entry of cur: gallop forward from the previous one, then bisect
+        int lo = e, step = 1;
+        while (lo + step < nent && ent[lo + step].first <= cur) {
+          lo += step;
+          step <<= 1;
+        }
+        int hi = min(lo + step, nent) - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (ent[mid].first <= cur) lo = mid;
+          else hi = mid - 1;
+        }
+        e = lo;
+        s_ent = lo;
+      }
+    }
     __syncthreads();
     const int64_t t = s_ticket;
     if (t >= total) break;
-    int lo = 0, hi = nent - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (ent[mid].first <= t) lo = mid;
-      else hi = mid - 1;
-    }
-    const PhaseEntry pe = ent[lo];
+    const PhaseEntry pe = ent[s_ent];
     const BatchSys<T>& a = sys[pe.sys];
     int64_t o = t - pe.first;
     if (pe.phase == 0) {
