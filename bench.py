@@ -566,7 +566,9 @@ def run_ours(args, rank, world, local):
             e2e_step()
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / max(1, args.steps)
-        h2d = sum(8 * (n * n + n * k) for n, k in shapes)
+        # the lower trapezoid of each block column of L, then B
+        h2d = sum(8 * (sum((n - b0) * min(n0, n - b0) for b0 in range(0, n, n0)) + n * k)
+                  for (n, k), n0 in zip(shapes, n0s))
         d2h = sum(8 * n * k for n, k in shapes)
         e2e = {"value": flops_step * world / e2e_s / 1e12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

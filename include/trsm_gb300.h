@@ -249,8 +249,15 @@ size_t trsm_batch_workspace_bytes(trsm_batch_t b);
 
 /* trsm_host — the whole method (trsm_plan + trsm_solve) on HOST buffers:
  * copies L and B to the device, plans, solves, copies X back and waits.
+ * Only the lower trapezoid of each n0-wide block column of L is copied
+ * (about half of L), straight into the plan's L~.  When B and X are large
+ * against the number of block rows (16 n k bytes above 2.5e8 per block row,
+ * k >= 4096) the columns of B go in four chunks: the solve of one chunk
+ * overlaps the copy of the next one in and of the previous one out (two
+ * extra streams).
  *   L_host (n x n, ldl), B_host (n x k, ldb), X_host (n x k, ldx), all
- *   column-major host memory; pinned memory makes the copies asynchronous.
+ *   column-major host memory; pinned memory makes the copies asynchronous
+ *   and lets them overlap.  X_host may alias B_host (same ld).
  * Synchronous.  Errors as trsm_plan and trsm_solve. */
 int trsm_host(const double* L_host, int64_t n, int64_t ldl, int64_t n0, const double* B_host,
               int64_t k, int64_t ldb, double* X_host, int64_t ldx, void* stream);

@@ -173,30 +173,99 @@ int trsm_host(const double* L_host, int64_t n, int64_t ldl, int64_t n0, const do
   if (!L_host || n < 1 || ldl < n || n0 < 1 || k < 0) return TRSM_EINVAL;
   if (k > 0 && (!B_host || !X_host || ldb < n || ldx < n)) return TRSM_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  double *dL = nullptr, *dB = nullptr;
-  const int64_t ld = align4(n);
-  cudaError_t e = cudaMallocAsync((void**)&dL, sizeof(double) * (size_t)ld * (size_t)n, s);
-  if (e == cudaSuccess && k > 0)
-    e = cudaMallocAsync((void**)&dB, sizeof(double) * (size_t)ld * (size_t)k, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpy2DAsync(dL, sizeof(double) * ld, L_host, sizeof(double) * ldl,
-                          sizeof(double) * n, (size_t)n, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess && k > 0)
-    e = cudaMemcpy2DAsync(dB, sizeof(double) * ld, B_host, sizeof(double) * ldb,
-                          sizeof(double) * n, (size_t)k, cudaMemcpyHostToDevice, s);
+  if (n0 > n) n0 = n;
+  t_singular = -1;
+  // The plan is built in place from the host copy: only the lower trapezoid
+  // of every block column crosses the link (rows from the block's first row
+  // down), straight into L~, and the strictly upper part of each diagonal
+  // block is zeroed on the device.
+  trsm_plan_s* h = new (std::nothrow) trsm_plan_s;
+  if (!h) return TRSM_ENOMEM;
+  h->n = n;
+  h->n0 = n0;
+  h->N = (n + n0 - 1) / n0;
+  h->ldt = align4(n);
+  cudaGetDevice(&h->device);
+  const int64_t ld = h->ldt;
+  double* dB = nullptr;
+  cudaStream_t cin = nullptr, cout = nullptr;
+  // B and X may move in four column chunks: the solve of chunk c overlaps
+  // the copy of chunk c + 1 in and of chunk c - 1 out, hiding 3/4 of the
+  // copies, but every extra solve launch pays the tail of its last block
+  // rows (measured on GB300: ~0.3 ms per block row; copies at ~200 GB/s).
+  // Chunk only when the hidden copy time beats that: bytes of B and X above
+  // 2.5e8 per block row (e.g. n = 2048, k = 131072 with one block row: yes;
+  // n = 8192, k = 8192 with 16 block rows: no).
+  const double bx_bytes = 16.0 * (double)n * (double)k;
+  const int64_t nchunk = (k >= 4096 && bx_bytes > 2.5e8 * (double)h->N) ? 4 : 1;
+  const int64_t kc = nchunk > 1 ? ((k + nchunk - 1) / nchunk + 31) / 32 * 32 : k;
+  std::vector<cudaEvent_t> ev_in, ev_done;
+  // L~ lives only for this call: stream-ordered allocation (the pool keeps
+  // the memory between calls instead of a synchronous cudaMalloc/cudaFree)
+  double* Lt = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&Lt, sizeof(double) * (size_t)ld * (size_t)n, s);
+  h->Lt = Lt;
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(int), s);
+  if (e == cudaSuccess && k > 0) e = cudaMallocAsync((void**)&dB, sizeof(double) * (size_t)ld * (size_t)k, s);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cin, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cout, cudaStreamNonBlocking);
+  for (int64_t c = 0; c * kc < k && e == cudaSuccess; ++c) {
+    cudaEvent_t a = nullptr, d = nullptr;
+    e = cudaEventCreateWithFlags(&a, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&d, cudaEventDisableTiming);
+    ev_in.push_back(a);
+    ev_done.push_back(d);
+  }
+  // L: block column b, rows [b n0, n)
+  for (int64_t b0 = 0; b0 < n && e == cudaSuccess; b0 += n0) {
+    const int64_t w = std::min(n0, n - b0);
+    e = cudaMemcpy2DAsync(h->Lt + b0 * ld + b0, sizeof(double) * ld, L_host + b0 * ldl + b0, sizeof(double) * ldl,
+                          sizeof(double) * (n - b0), (size_t)w, cudaMemcpyHostToDevice, s);
+  }
+  // B chunks on their own stream (after the allocation above)
+  cudaEvent_t ready = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(ready, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cin, ready, 0);
+  for (size_t c = 0; c < ev_in.size() && e == cudaSuccess; ++c) {
+    const int64_t j0 = (int64_t)c * kc, w = std::min(kc, k - j0);
+    e = cudaMemcpy2DAsync(dB + j0 * ld, sizeof(double) * ld, B_host + j0 * ldb, sizeof(double) * ldb,
+                          sizeof(double) * n, (size_t)w, cudaMemcpyHostToDevice, cin);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_in[c], cin);
+  }
+  if (e == cudaSuccess) e = trsm::zero_upper_blocks(h->Lt, ld, n, n0, s);
   int rc = from_cuda(e);
-  trsm_handle_t h = nullptr;
-  if (rc == TRSM_SUCCESS) rc = trsm_plan(dL, n, ld, n0, stream, &h);
-  if (rc == TRSM_SUCCESS && k > 0) rc = trsm_solve(h, dB, k, ld, dB, ld, stream);
-  if (rc == TRSM_SUCCESS && k > 0)
-    rc = from_cuda(cudaMemcpy2DAsync(X_host, sizeof(double) * ldx, dB, sizeof(double) * ld,
-                                     sizeof(double) * n, (size_t)k, cudaMemcpyDeviceToHost, s));
+  if (rc == TRSM_SUCCESS) rc = invert_and_check(h->Lt, ld, diag_blocks(n, n0, ld, false), s);
+  for (size_t c = 0; c < ev_in.size() && rc == TRSM_SUCCESS; ++c) {
+    const int64_t j0 = (int64_t)c * kc, w = std::min(kc, k - j0);
+    rc = from_cuda(cudaStreamWaitEvent(s, ev_in[c], 0));
+    if (rc == TRSM_SUCCESS) rc = trsm_solve(h, dB + j0 * ld, w, ld, dB + j0 * ld, ld, stream);
+    if (rc == TRSM_SUCCESS) rc = from_cuda(cudaEventRecord(ev_done[c], s));
+    if (rc == TRSM_SUCCESS) rc = from_cuda(cudaStreamWaitEvent(cout, ev_done[c], 0));
+    if (rc == TRSM_SUCCESS)
+      rc = from_cuda(cudaMemcpy2DAsync(X_host + j0 * ldx, sizeof(double) * ldx, dB + j0 * ld, sizeof(double) * ld,
+                                       sizeof(double) * n, (size_t)w, cudaMemcpyDeviceToHost, cout));
+  }
+  // every stream drains before anything is freed
+  cudaError_t e2 = cudaSuccess;
+  if (cin) e2 = cudaStreamSynchronize(cin);
+  if (cout) {
+    cudaError_t e3 = cudaStreamSynchronize(cout);
+    if (e2 == cudaSuccess) e2 = e3;
+  }
   if (rc == TRSM_SUCCESS) rc = trsm_sync_status(h, stream);
-  if (h) trsm_destroy(h);
   if (dB) cudaFreeAsync(dB, s);
-  if (dL) cudaFreeAsync(dL, s);
-  cudaError_t e2 = cudaStreamSynchronize(s);
-  if (rc == TRSM_SUCCESS) rc = from_cuda(e2);
+  if (Lt) cudaFreeAsync(Lt, s);
+  h->Lt = nullptr;
+  cudaError_t e4 = cudaStreamSynchronize(s);
+  if (rc == TRSM_SUCCESS) rc = from_cuda(e2 != cudaSuccess ? e2 : e4);
+  for (auto x : ev_in) if (x) cudaEventDestroy(x);
+  for (auto x : ev_done) if (x) cudaEventDestroy(x);
+  if (ready) cudaEventDestroy(ready);
+  if (cin) cudaStreamDestroy(cin);
+  if (cout) cudaStreamDestroy(cout);
+  trsm_destroy(h);
   return rc;
 }
 

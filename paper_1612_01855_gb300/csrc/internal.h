@@ -51,6 +51,9 @@ cudaError_t pack_diag_blocks(const double* L, int64_t ldl, double* P, int64_t n,
                              cudaStream_t s);
 
 // W (n x k, ldw) = B (n x k, ldb).
+// Zeroes the strictly upper part of the n0 x n0 diagonal blocks of Lt.
+cudaError_t zero_upper_blocks(double* Lt, int64_t ldt, int64_t n, int64_t n0, cudaStream_t s);
+
 cudaError_t copy_panel(const double* B, int64_t ldb, double* W, int64_t ldw, int64_t n,
                        int64_t k, cudaStream_t s);
 

@@ -232,10 +232,23 @@ struct ResidualEpi {
   struct State {
     float ph[16], pl[16];
   };
-  // With a triangular L the last row tiles carry the longest K ranges: run
-  // them first so that they do not form the tail of the launch.
-  __device__ void tile(int& tm, int&) const {
-    if (lower) tm = static_cast<int>(gridDim.x) - 1 - tm;
+  // Launch order -> tile: groups of kGroupRows row tiles, and within a group
+  // the column tiles one after the other, so that the CTAs in flight (one
+  // per SM) cover about 16 row tiles x 10 column tiles and share their digit
+  // planes in L2 (row-tile-major order streamed every L plane once per
+  // column tile).  With a triangular L the last row tiles carry the longest
+  // K ranges: their groups run first so that they do not form the tail.
+  static constexpr int kGroupRows = 16;
+  __device__ void tile(int& tm, int& tn) const {
+    const int R = static_cast<int>(gridDim.x), C = static_cast<int>(gridDim.y);
+    const int lin = tm + R * tn;
+    const int grp = lin / (kGroupRows * C);
+    const int g0 = grp * kGroupRows;
+    const int gsz = min(kGroupRows, R - g0);
+    const int idx = lin - g0 * C;
+    const int r = g0 + idx % gsz;
+    tn = idx / gsz;
+    tm = lower ? R - 1 - r : r;
   }
   __device__ void k_range(int tm, int, int& kb0, int& kb1, int& chunk) const {
     const int kend = lower ? min(K, (tm + 1) * 128) : K;

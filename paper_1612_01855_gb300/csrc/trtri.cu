@@ -319,6 +319,25 @@ cudaError_t pack_diag_blocks(const double* L, int64_t ldl, double* P, int64_t n,
   return cudaGetLastError();
 }
 
+// Zeroes the strictly upper part of every n0 x n0 diagonal block of Lt
+// (what a copy of the lower trapezoid of each block column brings along).
+__global__ void zero_upper_blocks_kernel(double* __restrict__ Lt, int64_t ldt, int64_t n, int64_t n0) {
+  const int64_t nb = (n + n0 - 1) / n0;
+  for (int64_t bc = blockIdx.y; bc < nb * n0; bc += gridDim.y) {
+    const int64_t b = bc / n0, c = bc % n0, s0 = b * n0;
+    if (s0 + c >= n) continue;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < c; r += (int64_t)gridDim.x * blockDim.x)
+      Lt[(s0 + c) * ldt + s0 + r] = 0.0;
+  }
+}
+
+cudaError_t zero_upper_blocks(double* Lt, int64_t ldt, int64_t n, int64_t n0, cudaStream_t s) {
+  const int64_t nb = (n + n0 - 1) / n0;
+  zero_upper_blocks_kernel<<<grid2d(n0, nb * n0), 256, 0, s>>>(Lt, ldt, n, n0);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t copy_panel(const double* B, int64_t ldb, double* W, int64_t ldw, int64_t n, int64_t k,
                        cudaStream_t s) {
   copy_panel_kernel<<<grid2d(n, k), 256, 0, s>>>(B, ldb, W, ldw, n, k);

@@ -208,6 +208,29 @@ def test_host_buffers_through_c_abi(cuda_lib):
     assert rel_err(X, oracle.forward_subst(L, B)) < TOL
 
 
+@pytest.mark.parametrize("n,k,n0", [(1000, 4100, 96), (513, 5000, 513), (300, 4096, 32), (64, 1, 100),
+                                    (1500, 40000, 1500), (600, 90001, 300)])
+def test_host_buffers_chunked_and_trapezoid(cuda_lib, n, k, n0):
+    """The host path copies only the lower trapezoid of each block column of
+    L (NaN above the diagonal must not leak in), pipelines B and X in column
+    chunks when they are large against the block rows (the last two cases),
+    honours leading dimensions > n and may solve in place (X aliasing B)."""
+    import paper_1612_01855_gb300 as g
+    L, B = inputs.well_conditioned(n, k, seed=n + k)
+    ldl, ldb = n + 3, n + 5
+    Lh = np.full((ldl, n), np.nan, order="F")
+    Lh[:n, :n] = np.where(np.tri(n, dtype=bool), L, np.nan)
+    Bh = np.full((ldb, k), np.nan, order="F")
+    Bh[:n] = B
+    g.trsm_host_ptr(Lh.ctypes.data, n, ldl, n0, Bh.ctypes.data, k, ldb, Bh.ctypes.data, ldb)
+    X = Bh[:n]
+    cols = np.unique(np.linspace(0, k - 1, 9).astype(int))
+    want = oracle.forward_subst_columns(np.tril(L), B, cols)
+    assert np.all(np.isfinite(X))
+    assert rel_err(X[:, cols], want) < TOL
+    assert np.all(np.isnan(Bh[n:]))  # rows beyond n untouched
+
+
 FULL_SIZES = [(16384, 256, 256), (8192, 8192, 512), (2048, 131072, 2048)]
 
 
