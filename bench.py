@@ -308,12 +308,16 @@ def schedules_study(g, torch, dev_in, outs, shapes, n0s, reps=3, stream=None):
 
 
 def serving_study(g, torch, nL=256, rates=(100, 300, 600, 1200), per_rate=300, seed=2000,
-                  budget_gb=150.0):
+                  budget_gb=150.0, mixed_min_n=2048):
     """Serving workload: nL resident L (n log-uniform in [64, 8192],
     diagonal U[2,3], strictly lower U[-1,1]/n, drawn on the device), each
     planned once; Poisson request streams at the given rates, each request a
     B with k log-uniform in [1, 2048] for a random resident L; continuous
-    batching under an HBM budget.  Reports solves/s and p50/p99 latency."""
+    batching under an HBM budget.  The L with n >= mixed_min_n also carry a
+    mixed-precision plan (split-bf16 updates), and half of the requests on
+    them ask for the refined mixed-precision solve (tol 1e-12) instead of
+    FP64.  Reports solves/s and p50/p99 latency, overall and for the mixed
+    requests."""
     from paper_1612_01855_gb300.serve import Request, Server
     rng = np.random.default_rng(seed)
     ns = np.rint(np.exp(rng.uniform(np.log(64), np.log(8192), size=nL))).astype(int)
@@ -327,10 +331,13 @@ def serving_study(g, torch, nL=256, rates=(100, 300, 600, 1200), per_rate=300, s
         L.diagonal().copy_(torch.rand(int(n), generator=gen, device="cuda", dtype=torch.float64).add_(2))
         L = L.t().contiguous().t()
         plans.append(g.trsm_plan(L, 256 if n >= 1024 else 64))
+        if n >= mixed_min_n:
+            g.trsm_plan_mixed(plans[-1], L, "bf16x3")
         del L
     plan_s = time.perf_counter() - t0
     out = {"resident_L": nL, "plan_seconds": round(plan_s, 2),
-           "resident_gb": round(sum(8.0 * p.n * p.n for p in plans) / 1e9, 2), "budget_gb": budget_gb,
+           "mixed_plans": int(sum(1 for n in ns if n >= mixed_min_n)),
+           "resident_gb": round(sum(p.device_bytes() for p in plans) / 1e9, 2), "budget_gb": budget_gb,
            "rates": []}
     for rate in rates:
         reqs = []
@@ -341,12 +348,22 @@ def serving_study(g, torch, nL=256, rates=(100, 300, 600, 1200), per_rate=300, s
             k = int(np.rint(np.exp(rng.uniform(0.0, np.log(2048)))))
             gen.manual_seed(seed * 7 + rid)
             B = torch.rand((k, int(ns[lid])), generator=gen, device="cuda", dtype=torch.float64).mul_(2).sub_(1).t()
-            reqs.append(Request(rid, lid, B, t))
+            mixed = bool(ns[lid] >= mixed_min_n and rng.random() < 0.5)
+            reqs.append(Request(rid, lid, B, t, mixed=mixed))
         torch.cuda.synchronize()
         srv = Server(plans, budget_bytes=int(budget_gb * 1e9), streams=2, max_batch=64)
         st = srv.run_trace(reqs)
         st["offered_rate"] = rate
         out["rates"].append({k: (round(v, 4) if isinstance(v, float) else v) for k, v in st.items()})
+        # accuracy of a few served requests of each kind against a plain FP64 solve
+        errs = {"fp64": 0.0, "mixed": 0.0}
+        for r in [x for x in reqs if not x.mixed][:3] + [x for x in reqs if x.mixed][:3]:
+            ref = g.trsm_solve(plans[r.lid], r.B)
+            g.trsm_sync_status(plans[r.lid])
+            e = float((r.X - ref).abs().max() / ref.abs().max())
+            key = "mixed" if r.mixed else "fp64"
+            errs[key] = max(errs[key], e)
+        out["rates"][-1]["max_rel_diff_vs_fp64_solve"] = errs
         del reqs, srv
     for p in plans:
         p.destroy()

@@ -282,6 +282,12 @@ void trsm_destroy(trsm_handle_t h);
 int trsm_plan_sizes(trsm_handle_t h, int64_t* n, int64_t* n0, int64_t* nblocks);
 const double* trsm_plan_lt(trsm_handle_t h, int64_t* ldt);
 
+/* Device bytes the plan holds: L~ and, after trsm_plan_mixed, the
+ * mixed-precision data (panels, digit planes, diagonal blocks).  0 for a
+ * null handle.  No counterpart in the paper: memory accounting for callers
+ * that admit work against an HBM budget. */
+size_t trsm_plan_device_bytes(trsm_handle_t h);
+
 /* Waits for `stream` and returns the device status of the last solve
  * enqueued with this plan: TRSM_SUCCESS or TRSM_ETIMEOUT. */
 int trsm_sync_status(trsm_handle_t h, void* stream);

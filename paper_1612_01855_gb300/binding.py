@@ -73,6 +73,7 @@ SIGNATURES = {
     "trtri_blocks": (_int, [_dp, _i64, _i64, _i64, _dp, _vp]),
     "trsm_destroy": (None, [_vp]),
     "trsm_plan_sizes": (_int, [_vp, _pi64, _pi64, _pi64]),
+    "trsm_plan_device_bytes": (ctypes.c_size_t, [_vp]),
     "trsm_plan_lt": (_vp, [_vp, _pi64]),
     "trsm_sync_status": (_int, [_vp, _vp]),
     "trsm_singular_index": (_i64, []),
@@ -170,6 +171,10 @@ class Plan:
     @property
     def handle(self):
         return self._h
+
+    def device_bytes(self):
+        """Device bytes held by the plan (L~ and any mixed-precision data)."""
+        return int(load_library().trsm_plan_device_bytes(self._h))
 
     def lt(self):
         """L~ as a torch tensor view (n x n, column-major) of the plan's memory."""

@@ -292,6 +292,11 @@ void trsm_destroy(trsm_handle_t h) {
   delete h;
 }
 
+size_t trsm_plan_device_bytes(trsm_handle_t h) {
+  if (!h) return 0;
+  return sizeof(double) * (size_t)h->ldt * (size_t)h->n + sizeof(int) + trsm::mixed_bytes(h);
+}
+
 int trsm_plan_sizes(trsm_handle_t h, int64_t* n, int64_t* n0, int64_t* nblocks) {
   if (!h) return TRSM_EINVAL;
   if (n) *n = h->n;

@@ -23,6 +23,8 @@ struct trsm_plan_s {
 namespace trsm {
 
 // Frees the mixed-precision part of a plan (no-op when absent).
+// Device bytes of the plan's mixed-precision data (0 without it).
+size_t mixed_bytes(const trsm_plan_s* h);
 void mixed_release(trsm_plan_s* h);
 
 // A diagonal block to invert in place: top-left element at A + off, order m;

@@ -44,7 +44,10 @@ struct MixedPlan {
   double* dblk = nullptr;   // the original diagonal blocks of L, N x n0 x n0 (FP64 residual)
   void* lsl = nullptr;      // digit planes of the strictly lower L
   SlicedOperand Ls;
+  size_t bytes = 0;         // device bytes held by the fields above
 };
+
+size_t mixed_bytes(const trsm_plan_s* h) { return (h && h->mixed) ? h->mixed->bytes : 0; }
 
 void mixed_release(trsm_plan_s* h) {
   if (!h || !h->mixed) return;
@@ -294,6 +297,7 @@ extern "C" int trsm_plan_mixed(trsm_handle_t h, const double* L_dev, int64_t ldl
     e = cudaMalloc(reinterpret_cast<void**>(&mp->dblk), sizeof(double) * static_cast<size_t>(N * n0 * n0));
   const size_t lbytes = trsm::sliced_operand_bytes(n, n);
   if (e == cudaSuccess) e = cudaMalloc(&mp->lsl, lbytes);
+  mp->bytes = esz * panel_elems + sizeof(double) * n + sizeof(double) * static_cast<size_t>(N * n0 * n0) + lbytes;
   double* tmp = nullptr;
   if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&tmp), sizeof(double) * n * n, s);
   if (e == cudaSuccess && panel_elems > 0) {

@@ -16,11 +16,19 @@ pays for the blocked solve (Algorithm It-Inv-TRSM, Section 6.2).  The loop:
   memory free up;
 * latency = completion seen by the host - arrival.
 
-The result of a request does not depend on which other requests share its
-batch: every tile's updates are applied in a fixed order.
+A request may instead ask for the mixed-precision solve refined to a
+tolerance (`mixed=True`; its plan needs `trsm_plan_mixed`).  That solve
+decides on the host when to stop refining, so it cannot join a persistent
+batch: it takes a launch slot alone and runs in a worker thread on the
+slot's stream (the C call releases the interpreter lock), while the other
+slots keep serving batches.
+
+The result of a FP64 request does not depend on which other requests share
+its batch: every tile's updates are applied in a fixed order.
 """
 import time
 from collections import deque
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -75,6 +83,10 @@ class Request:
     t_admit: float = None
     t_done: float = None
     cancelled: bool = False
+    mixed: bool = False  # mixed-precision solve refined to `tol` (max|D| / max|X|)
+    tol: float = 1e-12
+    status: int = None
+    iterations: int = None
 
     @property
     def latency(self):
@@ -88,13 +100,20 @@ class _InFlight:
     reqs: list
     nbytes: int
     arena: object = field(default=None)
+    future: object = None  # a mixed-precision request's worker
+
+
+def _has_mixed_data(plan):
+    return getattr(plan, "inner", None) is not None
 
 
 class Server:
-    def __init__(self, plans, budget_bytes, streams=2, max_batch=64):
+    def __init__(self, plans, budget_bytes, streams=2, max_batch=64, mixed_residual="adaptive"):
         self.plans = plans
-        resident = sum(8 * p.n * p.n for p in plans)
+        resident = sum(self.plan_bytes(p) for p in plans)
         self.adm = Admission(budget_bytes, resident)
+        self.mixed_residual = mixed_residual
+        self.pool = None
         self.pending = deque()
         self.inflight = []
         self.done = []
@@ -105,7 +124,18 @@ class Server:
         self.launches = 0
 
     @staticmethod
-    def request_bytes(n, k):
+    def plan_bytes(plan):
+        """Device bytes a resident plan holds (the library's count when the
+        plan can tell, else L~ alone)."""
+        f = getattr(plan, "device_bytes", None)
+        return f() if f is not None else 8 * plan.n * plan.n
+
+    @staticmethod
+    def request_bytes(n, k, mixed=False):
+        if mixed:
+            # X, and the refinement's workspace: R, D (FP64), W (FP32), the
+            # eight digit planes of X (bf16), the float-float partial sums
+            return (8 + 8 + 8 + 4 + 16 + 8) * n * k + (1 << 16)
         # B and X, the working copy W inside the batch workspace, counters
         return 3 * 8 * n * k + 4 * ((n + 31) // 32) * ((k + 31) // 32) * 2 + 4096
 
@@ -113,7 +143,10 @@ class Server:
         plan = self.plans[req.lid]
         if req.B.shape[0] != plan.n:
             raise AdmissionError(f"request {req.rid}: B has {req.B.shape[0]} rows, L has {plan.n}")
-        self.adm.check_request(self.request_bytes(plan.n, req.B.shape[1]))
+        if req.mixed and not _has_mixed_data(plan):
+            raise AdmissionError(f"request {req.rid}: mixed precision asked for, but L #{req.lid} has no "
+                                 "mixed-precision plan (trsm_plan_mixed)")
+        self.adm.check_request(self.request_bytes(plan.n, req.B.shape[1], req.mixed))
         self.pending.append(req)
 
     def cancel(self, rid):
@@ -129,6 +162,17 @@ class Server:
         now = time.perf_counter()
         still = []
         for f in self.inflight:
+            if f.future is not None:
+                if not f.future.done():
+                    still.append(f)
+                    continue
+                r = f.reqs[0]
+                r.t_done = time.perf_counter()
+                r.status, r.iterations = f.future.result()
+                self.done.append(r)
+                self.adm.release(f.nbytes)
+                self.busy[f.slot] = False
+                continue
             if f.event.query():
                 now = time.perf_counter()
                 with self._torch().cuda.stream(self.streams[f.slot]):
@@ -149,6 +193,18 @@ class Server:
         import torch
         return torch
 
+    def _solve_mixed(self, slot, r):
+        """Worker: one refined mixed-precision solve on the slot's stream.
+        Returns (status, iterations)."""
+        import torch
+        with torch.cuda.stream(self.streams[slot]):
+            try:
+                _, it, _ = binding.trsm_solve_mixed(self.plans[r.lid], r.B, X=r.X, residual=self.mixed_residual,
+                                                    tol=r.tol)
+                return 0, it
+            except binding.TrsmError as e:
+                return e.code, None
+
     def dispatch(self):
         import torch
         if self.streams is None:
@@ -156,8 +212,26 @@ class Server:
         for slot in range(len(self.streams)):
             if self.busy[slot] or not self.pending:
                 continue
+            head = self.pending[0]
+            if head.mixed:
+                b = self.request_bytes(self.plans[head.lid].n, head.B.shape[1], True)
+                if not self.adm.take(b):
+                    continue
+                r = self.pending.popleft()
+                n, k = r.B.shape
+                with torch.cuda.stream(self.streams[slot]):
+                    r.X = torch.empty((k, n), dtype=torch.float64, device="cuda").t()
+                r.t_admit = time.perf_counter()
+                if self.pool is None:
+                    self.pool = ThreadPoolExecutor(max_workers=self.nstreams)
+                f = _InFlight(None, None, [r], b, future=self.pool.submit(self._solve_mixed, slot, r))
+                f.slot = slot
+                self.busy[slot] = True
+                self.inflight.append(f)
+                self.launches += 1
+                continue
             take, nbytes = [], 0
-            while self.pending and len(take) < self.max_batch:
+            while self.pending and len(take) < self.max_batch and not self.pending[0].mixed:
                 r = self.pending[0]
                 b = self.request_bytes(self.plans[r.lid].n, r.B.shape[1])
                 if not self.adm.fits(nbytes + b):
@@ -211,10 +285,20 @@ class Server:
             if i < len(order) and not self.inflight:
                 time.sleep(max(0.0, min(idle_sleep, order[i].arrival - time.perf_counter())))
         t1 = time.perf_counter()
+        if self.pool is not None:
+            self.pool.shutdown(wait=True)
+            self.pool = None
         lat = np.array([r.latency for r in order if r.latency is not None])
         flops = float(sum(self.plans[r.lid].n ** 2 * r.B.shape[1] for r in order))
-        return {"requests": len(order), "seconds": t1 - t0, "solves_per_s": len(order) / (t1 - t0),
-                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-                "mean_ms": float(lat.mean() * 1e3), "tflops_n2k": flops / (t1 - t0) / 1e12,
-                "batches": self.launches, "peak_inflight_gb": self.adm.peak / 1e9,
-                "statuses_ok": all(getattr(r, "status", 0) == 0 for r in order)}
+        out = {"requests": len(order), "seconds": t1 - t0, "solves_per_s": len(order) / (t1 - t0),
+               "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+               "mean_ms": float(lat.mean() * 1e3), "tflops_n2k": flops / (t1 - t0) / 1e12,
+               "batches": self.launches, "peak_inflight_gb": self.adm.peak / 1e9,
+               "statuses_ok": all(r.status == 0 for r in order)}
+        mixed = [r for r in order if r.mixed and r.latency is not None]
+        if mixed:
+            ml = np.array([r.latency for r in mixed])
+            out["mixed"] = {"requests": len(mixed), "p50_ms": float(np.percentile(ml, 50) * 1e3),
+                            "p99_ms": float(np.percentile(ml, 99) * 1e3),
+                            "mean_iterations": float(np.mean([r.iterations or 0 for r in mixed]))}
+        return out

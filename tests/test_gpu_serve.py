@@ -71,3 +71,25 @@ def test_server_respects_tight_budget(cuda_lib):
     assert stats["statuses_ok"]
     assert srv.adm.peak + resident <= budget
     assert all(r.X is not None and r.t_done is not None for r in reqs)
+
+
+def test_server_mixes_fp64_and_refined_requests(cuda_lib):
+    """Half the requests ask for the mixed-precision solve (split-bf16
+    updates, refined on the tensor cores): they run alone on a slot's worker
+    thread next to the FP64 batches; every result matches the oracle."""
+    import paper_1612_01855_gb300 as g
+    from paper_1612_01855_gb300.serve import Server
+    Ls, plans = _setup(4, seed=7)
+    for L, p in zip(Ls, plans):
+        g.trsm_plan_mixed(p, _dev(L), "bf16x3")
+    reqs, host = _requests(Ls, 40, rate=3000.0, seed=9)
+    for r in reqs:
+        r.mixed = r.rid % 2 == 1
+    srv = Server(plans, budget_bytes=40 * 2**30, streams=2, max_batch=16)
+    stats = srv.run_trace(reqs)
+    assert stats["statuses_ok"] and stats["requests"] == 40
+    assert stats["mixed"]["requests"] == 20 and stats["mixed"]["mean_iterations"] >= 2
+    for r, B in zip(reqs, host):
+        want = oracle.forward_subst(Ls[r.lid], B)
+        assert np.max(np.abs(r.X.cpu().numpy() - want)) <= 1e-12 * np.max(np.abs(want)), (r.rid, r.mixed)
+    assert all(p.device_bytes() > 8 * p.n * p.n for p in plans)  # L~ plus the mixed data

@@ -46,3 +46,15 @@ def test_server_validates_and_cancels_without_gpu():
         tight.submit(Request(3, 1, _B(128, 1000), 0.0))
     assert srv.cancel(0) and not srv.cancel(0)
     assert [r.rid for r in srv.pending] == [1]
+
+
+def test_mixed_requests_need_a_mixed_plan():
+    plans = [_Plan(64), _Plan(128)]
+    plans[1].inner = "bf16x3"  # as set by trsm_plan_mixed
+    srv = Server(plans, budget_bytes=10**9)
+    with pytest.raises(AdmissionError):
+        srv.submit(Request(0, 0, _B(64, 4), 0.0, mixed=True))
+    srv.submit(Request(1, 1, _B(128, 4), 0.0, mixed=True))
+    assert [r.rid for r in srv.pending] == [1]
+    # the refinement's workspace is larger than the FP64 batch share
+    assert Server.request_bytes(128, 4, mixed=True) > Server.request_bytes(128, 4)
