@@ -42,60 +42,23 @@
 
 #include "internal.h"
 #include "sliced.h"
-#include "tc_gemm.cuh"
+#include "tc_engine.cuh"
 #include "tc_host.h"
 #include "trsm_gb300_engine.h"
 
 namespace trsm {
 namespace sliced {
 
-using tc::TileCfg;
-
-// bf16, 128-byte rows (64 elements of K per stage), one stage of P + P
-// planes (196 KB for P = 7, 208 KB for P = 8): the pairs of one stage keep
-// the tensor core busy long enough that a deeper ring buys little, and two
-// stages do not fit.  NG groups of BN FP32 columns fill 480 of the 512 TMEM
-// columns.
+// Tile shape per plane count: BN columns of the residual per CTA, NG FP32
+// accumulator groups of BN TMEM columns each (480 of the 512 columns).
+// K advances in steps of 64 bf16 (one 128-byte swizzled row).
 template <int P>
 struct Shape {
   static constexpr int BN = P == 7 ? 96 : 80;
   static constexpr int NG = P == 7 ? 5 : 6;  // the last group holds every d >= NG - 1
 };
-template <int P>
-using Cfg = TileCfg<false, Shape<P>::BN, P, P, Shape<P>::NG, 1, 128>;
-static_assert(kChunk % Cfg<7>::KB == 0 && Cfg<7>::KB == Cfg<8>::KB, "chunk must be a whole number of stages");
-static_assert(Cfg<8>::SMEM_BYTES <= 227 * 1024 && Cfg<7>::SMEM_BYTES <= 227 * 1024, "stage exceeds shared memory");
-
-// Digit pairs (s, u), s + u <= P - 1, in s-major order (the A plane stays
-// the same for consecutive MMAs, which the tensor core streams faster),
-// group min(s + u, NG - 1).
-template <int P>
-struct DigitPairs {
-  static constexpr int N = P * (P + 1) / 2;
-  __device__ static constexpr int s_of(int p) {
-    int s = 0, cnt = P;
-    while (p >= cnt) {
-      p -= cnt;
-      ++s;
-      cnt = P - s;
-    }
-    return s;
-  }
-  __device__ static constexpr int u_of(int p) {
-    int s = 0, cnt = P;
-    while (p >= cnt) {
-      p -= cnt;
-      ++s;
-      cnt = P - s;
-    }
-    return p;
-  }
-  __device__ static constexpr int a(int p) { return s_of(p); }
-  __device__ static constexpr int b(int p) { return u_of(p); }
-  __device__ static constexpr int g(int p) {
-    return s_of(p) + u_of(p) < Shape<P>::NG - 1 ? s_of(p) + u_of(p) : Shape<P>::NG - 1;
-  }
-};
+constexpr int kStepK = 64;
+static_assert(kChunk % kStepK == 0, "chunk must be a whole number of K steps");
 
 // ---------------------------------------------------------------- slicing
 // One warp per (row, chunk): rows hold K contiguous FP64 values (stride ld
@@ -253,8 +216,8 @@ struct ResidualEpi {
   __device__ void k_range(int tm, int, int& kb0, int& kb1, int& chunk) const {
     const int kend = lower ? min(K, (tm + 1) * 128) : K;
     kb0 = 0;
-    kb1 = (kend + Cfg<7>::KB - 1) / Cfg<7>::KB;
-    chunk = kChunk / Cfg<7>::KB;
+    kb1 = (kend + kStepK - 1) / kStepK;
+    chunk = kChunk / kStepK;
   }
   __device__ void init(State&) const {}
   __device__ void group(State& st, int, int, int, int, int, int g, const float (&v)[16]) const {
@@ -318,6 +281,194 @@ struct ResidualEpi {
     }
   }
 };
+
+
+// ---------------------------------------------------------------- kernel
+// The residual's own tcgen05 kernel.  All P + P planes of one 64-wide K
+// step take 196-208 KB of shared memory, so a ring over whole K steps has
+// one stage and every load is exposed (measured: about 24k cycles per step
+// against 6.7k of MMA work).  Here a stage holds a group of A planes
+// [s0, s1) with the B planes they pair with (u <= P - 1 - s0): at most
+// 112 KB, so two stages are in flight.  The groups (P = 7: {0}, {1, 2},
+// {3 .. 6}; P = 8: {0}, {1, 2}, {3, 4, 5}, {6, 7}) keep the stages near
+// 100 KB and at least 6 plane pairs each, and read 316 (P = 7) or 348
+// (P = 8) KB per K step against 196 and 208 for the whole step at once.
+// The items of a chunk run block by block (kBlkSteps K steps), within a
+// block group by group and within a group step by step, so the B planes
+// that several groups share are re-read from L2 within the block.  Roles as
+// in the generic engine: warp 0 lane 0 loads (one TMA per plane), warp 1
+// owns TMEM and issues the MMAs, warps 2-5 run the epilogue.
+constexpr int kBlkSteps = 4;
+
+template <int P>
+struct Stream {
+  static constexpr int BN = Shape<P>::BN;
+  static constexpr int NG = Shape<P>::NG;
+  static constexpr int kGroups = 3;
+  static constexpr uint32_t A_SL = 128u * 128u;
+  static constexpr uint32_t B_SL = static_cast<uint32_t>(BN) * 128u;
+  __host__ __device__ static constexpr int begin(int gi) {
+    return P == 7 ? (gi == 0 ? 0 : gi == 1 ? 1 : 3) : (gi == 0 ? 0 : gi == 1 ? 2 : 4);
+  }
+  __host__ __device__ static constexpr int end(int gi) { return gi + 1 < kGroups ? begin(gi + 1) : P; }
+  __host__ __device__ static constexpr uint32_t bytes(int gi) {
+    return static_cast<uint32_t>(end(gi) - begin(gi)) * A_SL + static_cast<uint32_t>(P - begin(gi)) * B_SL;
+  }
+  static constexpr uint32_t max2(uint32_t a, uint32_t b) { return a > b ? a : b; }
+  static constexpr uint32_t SLOT = max2(max2(bytes(0), bytes(1)), bytes(2));
+  static constexpr size_t SMEM_BYTES = 2 * static_cast<size_t>(SLOT) + 1024;
+  static constexpr uint32_t TMEM_COLS = 512;
+  static_assert(SLOT % 1024 == 0 && B_SL % 1024 == 0, "swizzled tiles need 1024-byte alignment");
+  static_assert(NG * BN <= 512, "accumulators exceed tensor memory");
+  static_assert(SMEM_BYTES <= 227 * 1024, "two stages exceed shared memory");
+};
+
+// Visits the items (chunk c, plane group gi, K step j) of a tile in issue
+// order; the last item of a chunk is flagged.
+template <int NGROUPS, class F>
+__device__ __forceinline__ void for_items(int kb0, int kb1, int chunk, F&& f) {
+  int i = 0;
+  for (int cb0 = kb0, c = 0; cb0 < kb1; cb0 += chunk, ++c) {
+    const int cb1 = min(kb1, cb0 + chunk);
+    for (int b0 = cb0; b0 < cb1; b0 += kBlkSteps) {
+      const int b1 = min(cb1, b0 + kBlkSteps);
+      for (int gi = 0; gi < NGROUPS; ++gi)
+        for (int j = b0; j < b1; ++j) {
+          if (!f(i, c, gi, j, j + 1 == cb1 && gi == NGROUPS - 1)) return;
+          ++i;
+        }
+    }
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(192)
+    stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                  const ResidualEpi<Stream<P>::BN> epi, int* err) {
+  using S = Stream<P>;
+  constexpr int BN = S::BN;
+  constexpr int NG = S::NG;
+  constexpr uint32_t IDESC = tc::idesc_m128(BN, false);
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~static_cast<uintptr_t>(1023));
+  __shared__ uint64_t full_bar[2], empty_bar[2], tfull_bar, tempty_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int abort_sh;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int tm = blockIdx.x, tn = blockIdx.y;
+  epi.tile(tm, tn);
+  int kb0 = 0, kb1 = 0, chunk = 1;
+  epi.k_range(tm, tn, kb0, kb1, chunk);
+  const int nkb = kb1 > kb0 ? kb1 - kb0 : 0;
+  const int nchunks = nkb > 0 ? (nkb + chunk - 1) / chunk : 0;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < 2; ++q) {
+      tc::mbar_init(&full_bar[q], 1);
+      tc::mbar_init(&empty_bar[q], 1);
+    }
+    tc::mbar_init(&tfull_bar, 1);
+    tc::mbar_init(&tempty_bar, 4);
+    abort_sh = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(&tmem_base_sh, S::TMEM_COLS);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tbase = tmem_base_sh;
+  volatile int* abort_flag = &abort_sh;
+
+  if (warp == 0) {
+    if (lane == 0 && nkb > 0) {
+      tc::prefetch_map(&mapA);
+      tc::prefetch_map(&mapB);
+      for_items<S::kGroups>(kb0, kb1, chunk, [&](int i, int, int gi, int j, bool) {
+        const int q = i & 1;
+        if (i >= 2 && !tc::mbar_wait(&empty_bar[q], ((i >> 1) + 1) & 1, abort_flag)) return false;
+        uint8_t* sa = smem + static_cast<size_t>(q) * S::SLOT;
+        const int s0 = S::begin(gi), s1 = S::end(gi);
+        tc::mbar_arrive_expect_tx(&full_bar[q], S::bytes(gi));
+        const int kx = j * kStepK;
+        for (int sp = s0; sp < s1; ++sp)
+          tc::tma_load_3d(sa + (sp - s0) * S::A_SL, &mapA, &full_bar[q], kx, tm * 128, sp);
+        uint8_t* sb = sa + (s1 - s0) * S::A_SL;
+        for (int u = 0; u < P - s0; ++u) tc::tma_load_3d(sb + u * S::B_SL, &mapB, &full_bar[q], kx, tn * BN, u);
+        return true;
+      });
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && nkb > 0) {
+      uint32_t started = 0;
+      int cur = -1;
+      for_items<S::kGroups>(kb0, kb1, chunk, [&](int i, int c, int gi, int, bool last_of_chunk) {
+        if (c != cur) {
+          if (c > 0 && !tc::mbar_wait(&tempty_bar, (c - 1) & 1, abort_flag)) return false;
+          tc::tc_fence_after();
+          started = 0;
+          cur = c;
+        }
+        const int q = i & 1;
+        if (!tc::mbar_wait(&full_bar[q], (i >> 1) & 1, abort_flag)) return false;
+        tc::tc_fence_after();
+        const uint32_t sa = tc::smem_u32(smem + static_cast<size_t>(q) * S::SLOT);
+        const int s0 = S::begin(gi), s1 = S::end(gi);
+        const uint32_t sb = sa + static_cast<uint32_t>(s1 - s0) * S::A_SL;
+        for (int sp = s0; sp < s1; ++sp) {
+          const uint64_t ad = tc::desc_kmajor<128>(sa + static_cast<uint32_t>(sp - s0) * S::A_SL);
+          for (int u = 0; u < P - sp; ++u) {
+            const int g = sp + u < NG - 1 ? sp + u : NG - 1;
+            const uint64_t bd = tc::desc_kmajor<128>(sb + u * S::B_SL);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+              tc::mma<false>(tbase + static_cast<uint32_t>(g * BN), ad + 2u * kk, bd + 2u * kk, IDESC,
+                             ((started >> g) & 1u) | (kk > 0 ? 1u : 0u));
+            started |= 1u << g;
+          }
+        }
+        tc::mma_commit(&empty_bar[q]);
+        if (last_of_chunk) tc::mma_commit(&tfull_bar);
+        return true;
+      });
+    }
+  } else {
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    typename ResidualEpi<BN>::State st;
+    epi.init(st);
+    for (int c = 0; c < nchunks; ++c) {
+      if (!tc::mbar_wait(&tfull_bar, c & 1, abort_flag)) break;
+      tc::tc_fence_after();
+#pragma unroll
+      for (int sl = 0; sl < BN / 16; ++sl) {
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+          uint32_t r[16];
+          tc::tmem_ld16(tbase + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(g * BN + sl * 16), r);
+          tc::tmem_wait_ld();
+          float v[16];
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) v[jj] = __uint_as_float(r[jj]);
+          epi.group(st, tm, tn, c, row, sl, g, v);
+        }
+        epi.slab_done(st, tm, tn, c, row, sl);
+      }
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&tempty_bar);
+    }
+    epi.finish(st, tm, tn, nchunks, row);
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tbase, S::TMEM_COLS);
+  }
+  if (threadIdx.x == 0 && abort_sh) atomicExch(err, 1);
+}
 
 }  // namespace sliced
 
@@ -384,12 +535,12 @@ struct ResidualArgs {
 template <int P>
 cudaError_t launch_residual(const SlicedOperand& Ls, const SlicedOperand& Xs, const ResidualArgs& a, int* err,
                             cudaStream_t s) {
-  using C = sliced::Cfg<P>;
+  using St = sliced::Stream<P>;
   constexpr int BN = sliced::Shape<P>::BN;
   CUtensorMap ma, mb;
-  if (!tc::make_kmajor_map(&ma, Ls.digits, false, Ls.kp, Ls.rows, Ls.kp, kPlanes, Ls.rows * Ls.kp, 128, P, 128))
+  if (!tc::make_kmajor_map(&ma, Ls.digits, false, Ls.kp, Ls.rows, Ls.kp, kPlanes, Ls.rows * Ls.kp, 128, 1, 128))
     return cudaErrorInvalidValue;
-  if (!tc::make_kmajor_map(&mb, Xs.digits, false, Xs.kp, Xs.rows, Xs.kp, kPlanes, Xs.rows * Xs.kp, BN, P, 128))
+  if (!tc::make_kmajor_map(&mb, Xs.digits, false, Xs.kp, Xs.rows, Xs.kp, kPlanes, Xs.rows * Xs.kp, BN, 1, 128))
     return cudaErrorInvalidValue;
   sliced::ResidualEpi<BN> epi;
   epi.B = a.B;
@@ -408,12 +559,12 @@ cudaError_t launch_residual(const SlicedOperand& Ls, const SlicedOperand& Xs, co
   epi.N = static_cast<int>(Xs.rows);
   epi.K = static_cast<int>(Ls.K);
   epi.lower = a.lower ? 1 : 0;
-  auto kern = tc::tc_tile_kernel<C, sliced::DigitPairs<P>, sliced::ResidualEpi<BN>>;
+  auto kern = sliced::stream_kernel<P>;
   cudaError_t e =
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(C::SMEM_BYTES));
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(St::SMEM_BYTES));
   if (e != cudaSuccess) return e;
   dim3 grid(static_cast<unsigned>((Ls.rows + 127) / 128), static_cast<unsigned>((Xs.rows + BN - 1) / BN));
-  kern<<<grid, 192, C::SMEM_BYTES, s>>>(ma, mb, epi, err);
+  kern<<<grid, 192, St::SMEM_BYTES, s>>>(ma, mb, epi, err);
   count_launch();
   return cudaGetLastError();
 }
