@@ -29,6 +29,11 @@ SHAPES = [(16384, 256), (8192, 8192), (2048, 131072)]
 # package); the paper's a-priori rule for p = 1 is n0 ~ min(sqrt(n k), n).
 DEFAULT_N0 = {(16384, 256): 256, (8192, 8192): 512, (2048, 131072): 2048}
 SWEEP_N0 = [64, 128, 256, 512, 1024, None]  # None = n (full inversion)
+# Block size of the mixed-precision figure (n = 16384, k = 4096).  Larger
+# blocks suit the mixed path: fewer, longer tensor-core updates, and the
+# diagonal multiplies run in FP32 (measured: 163 / 137 / 131 / 135 ms at
+# n0 = 256 / 512 / 1024 / 2048, tf32 with FP32 diagonal multiplies).
+MIXED_N0 = 1024
 NOMINAL_SM_MHZ = 2070.0
 SMS = 152
 
@@ -374,7 +379,9 @@ def run_case(args):
     """Single kernels for profiling (no JSON bench line):
     sliced:N:K[:P]   the tensor-core residual R = B - L X with P (7 or 8)
                      digit planes, twice;
-    mixed:N:K:N0     one mixed-precision refined solve (graded diagonal, c = 2);
+    mixed:N:K:N0[:I[:S]]  one mixed-precision refined solve (graded diagonal,
+                     c = 2); inner I = 0 tf32, 1 bf16, 2 split bf16; S = 1 for
+                     the FP32 diagonal-block multiply;
     engine:M:N:K     the bf16 tensor-core GEMM self-test, twice;
     batch:COUNT:BITS one batched launch of COUNT systems of the batching
                      workload in FP64 (BITS = 64) or FP32 (32), twice."""
@@ -408,9 +415,11 @@ def run_case(args):
                                               n, dims[2] if len(dims) > 2 else 7, ctypes.c_void_p(err.data_ptr()), s)
                 assert rc == 0
         else:
+            inner = ("tf32", "bf16", "bf16x3")[dims[3]] if len(dims) > 3 else "tf32"
             plan = g.trsm_plan(L, dims[2])
-            g.trsm_plan_mixed(plan, L, "tf32")
-            g.trsm_solve_mixed(plan, B, max_iter=30, tol=1e-12, raise_on_noconv=False)
+            g.trsm_plan_mixed(plan, L, inner)
+            g.trsm_solve_mixed(plan, B, max_iter=30, tol=1e-12, raise_on_noconv=False,
+                               s_fp32=len(dims) > 4 and dims[4] == 1)
     elif kind == "engine":
         M, N, K = dims
         A = torch.randn(M, K, device="cuda").to(torch.bfloat16)
@@ -599,7 +608,10 @@ def run_ours(args, rank, world, local):
 
     mixed = None
     if rank == 0 and not args.no_mixed and not args.shapes:
-        mixed = precision_study(g, torch, 16384, 4096, 256, [2], ["tf32", "bf16x3"], [False, True], dd_cols=2)
+        # FP32 diagonal multiplies at the mixed path's block size, and the
+        # FP64 ones at the FP64 path's block size (where they cost least)
+        mixed = (precision_study(g, torch, 16384, 4096, MIXED_N0, [2], ["tf32", "bf16x3"], [True], dd_cols=2) +
+                 precision_study(g, torch, 16384, 4096, 256, [2], ["tf32"], [False], dd_cols=2))
 
     batched = None
     if rank == 0 and not args.no_batched and not args.shapes:
@@ -614,7 +626,7 @@ def run_ours(args, rank, world, local):
         schedules = schedules_study(g, torch, dev_in, outs, shapes, n0s)
 
     if args.precision and rank == 0:
-        for rec in precision_study(g, torch, 16384, 4096, 256, [2, 4, 6], ["tf32", "bf16", "bf16x3"],
+        for rec in precision_study(g, torch, 16384, 4096, MIXED_N0, [2, 4, 6], ["tf32", "bf16", "bf16x3"],
                                    [False, True], residuals=("sliced", "adaptive")):
             print(json.dumps({"precision_study": True, **rec}), flush=True)
 
@@ -691,7 +703,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving figure")
     ap.add_argument("--no-schedules", action="store_true", help="skip the solve-schedule comparison")
     ap.add_argument("--precision", action="store_true", help="print the full c x inner x s-step study")
-    ap.add_argument("--case", default="", help="profiling case: sliced:N:K[:PLANES], mixed:N:K:N0, engine:M:N:K, batch:COUNT:BITS")
+    ap.add_argument("--case", default="", help="profiling case: sliced:N:K[:PLANES], mixed:N:K:N0[:INNER[:S32]], engine:M:N:K, batch:COUNT:BITS")
     ap.add_argument("--shapes", default="", help="override workload, e.g. 6144:1024:256 (not a bench line)")
     args = ap.parse_args()
     rank, world, local = dist_env()
