@@ -53,6 +53,7 @@ struct BatchSys {
   int64_t ldx;
   int64_t n, k, n0;
   int N, R, Rlast, C;
+  int cw;               // columns per column tile: 8, 16 or 32 (narrow B wastes less of a tile)
   int64_t total_rt;
   int64_t inv_tasks;    // N when the system inverts its own blocks, else 0
   int* wdone;           // [total_rt * C]
@@ -123,6 +124,121 @@ __device__ void leaf_invert_warp(const T* __restrict__ A, int64_t lda, int m, T*
   // the m x m leaf only: the output block may be narrower than 32 (n < 32)
   if (lane < m)
     for (int c = 0; c < m; ++c) out[static_cast<int64_t>(c) * ldo + lane] = ls[lane][c];
+}
+
+// acc += A(rows [0,m), K [kbeg,kend)) * B(K [kbeg,kend), cols [0,nc)) for a
+// TILE x CW output tile (CW = 8, 16 or 32) on 128 threads: thread (ty, tx)
+// = (tid / (CW/2), tid % (CW/2)) owns rows ty*(CW/8) .. and columns 2 tx,
+// 2 tx + 1; CW = 32 is the layout of the generic tile.  Narrow tiles let
+// systems with few right-hand sides skip most of the padded columns.
+template <int CW>
+struct NarrowMap {
+  static constexpr int TX = CW / 2;
+  static constexpr int TMR = CW / 8;  // rows per thread
+  __device__ static int row(int i) { return (threadIdx.x / TX) * TMR + i; }
+  __device__ static int col(int j) { return (threadIdx.x % TX) * 2 + j; }
+};
+
+template <class TC, bool kAMutable, bool kBMutable, int CW>
+__device__ __forceinline__ void tile_mma_cw(const TC* __restrict__ A, int64_t lda, const TC* __restrict__ B,
+                                            int64_t ldb, int m, int nc, int64_t kbeg, int64_t kend,
+                                            TileSmemT<TC>& sm, TC (&acc)[TM][TN]) {
+  using Mp = NarrowMap<CW>;
+  const int tid = threadIdx.x;
+  for (int64_t k0 = kbeg; k0 < kend; k0 += KCH) {
+#pragma unroll
+    for (int it = 0; it < (KCH * TILE) / NTHREADS; ++it) {
+      const int r = tid & 31;
+      const int kk = (tid >> 5) + 4 * it;
+      const int64_t t = k0 + kk;
+      TC v = TC(0);
+      if (r < m && t < kend) v = ld_raw<kAMutable>(A + t * lda + r);
+      sm.a[kk][r] = v;
+    }
+#pragma unroll
+    for (int it = 0; it < (KCH * CW) / NTHREADS; ++it) {
+      const int kk = tid & 31;
+      const int c = (tid >> 5) + 4 * it;
+      const int64_t t = k0 + kk;
+      TC v = TC(0);
+      if (c < nc && t < kend) v = ld_raw<kBMutable>(B + static_cast<int64_t>(c) * ldb + t);
+      sm.b[kk][c] = v;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < KCH; ++kk) {
+      TC av[Mp::TMR], bv[2];
+#pragma unroll
+      for (int i = 0; i < Mp::TMR; ++i) av[i] = sm.a[kk][Mp::row(i)];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) bv[j] = sm.b[kk][Mp::col(j)];
+#pragma unroll
+      for (int i = 0; i < Mp::TMR; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+}
+
+// X_l[r, j] = L~_ll[r, :] W_l[:, j] (the first block row reads B).
+template <class T, int CW>
+__device__ __forceinline__ void s_body(const BatchSys<T>& a, int l, int r, int j, int64_t s0, int64_t ml,
+                                       TileSmemT<T>& sm) {
+  using Mp = NarrowMap<CW>;
+  T acc[TM][TN];
+  zero_acc(acc);
+  const int m = static_cast<int>(imin64(TILE, ml - static_cast<int64_t>(r) * TILE));
+  const int nc = static_cast<int>(imin64(CW, a.k - static_cast<int64_t>(j) * CW));
+  const int64_t kend = imin64(static_cast<int64_t>(r + 1) * TILE, ml);
+  const T* Ainv = a.Linv + l * a.inv_bstride + r * TILE;
+  if (l == 0)
+    tile_mma_cw<T, true, false, CW>(Ainv, a.ldinv, a.B + static_cast<int64_t>(j) * CW * a.ldb, a.ldb, m, nc, 0, kend,
+                                    sm, acc);
+  else
+    tile_mma_cw<T, true, true, CW>(Ainv, a.ldinv, a.W + static_cast<int64_t>(j) * CW * a.ldw + s0, a.ldw, m, nc, 0,
+                                   kend, sm, acc);
+  const int64_t row0 = s0 + static_cast<int64_t>(r) * TILE;
+#pragma unroll
+  for (int i = 0; i < Mp::TMR; ++i) {
+    const int rr = Mp::row(i);
+    if (rr >= m) continue;
+#pragma unroll
+    for (int jj = 0; jj < 2; ++jj) {
+      const int cc = Mp::col(jj);
+      if (cc >= nc) continue;
+      __stcg(a.X + (static_cast<int64_t>(j) * CW + cc) * a.ldx + row0 + rr, acc[i][jj]);
+    }
+  }
+}
+
+// W_i[r, j] -= L_il[r, :] X_l[:, j] (the first update of a tile starts from B).
+template <class T, int CW>
+__device__ __forceinline__ void u_body(const BatchSys<T>& a, int l, int i, int r, int j, int64_t s0, int64_t ml,
+                                       TileSmemT<T>& sm) {
+  using Mp = NarrowMap<CW>;
+  T acc[TM][TN];
+  zero_acc(acc);
+  const int64_t si = static_cast<int64_t>(i) * a.n0;
+  const int64_t mi = imin64(a.n0, a.n - si);
+  const int64_t row0 = si + static_cast<int64_t>(r) * TILE;
+  const int m = static_cast<int>(imin64(TILE, mi - static_cast<int64_t>(r) * TILE));
+  const int nc = static_cast<int>(imin64(CW, a.k - static_cast<int64_t>(j) * CW));
+  tile_mma_cw<T, false, true, CW>(a.Loff + s0 * a.ldoff + row0, a.ldoff,
+                                  a.X + static_cast<int64_t>(j) * CW * a.ldx + s0, a.ldx, m, nc, 0, ml, sm, acc);
+#pragma unroll
+  for (int ii = 0; ii < Mp::TMR; ++ii) {
+    const int rr = Mp::row(ii);
+    if (rr >= m) continue;
+#pragma unroll
+    for (int jj = 0; jj < 2; ++jj) {
+      const int cc = Mp::col(jj);
+      if (cc >= nc) continue;
+      const int64_t col = static_cast<int64_t>(j) * CW + cc;
+      const T base = (l == 0) ? a.B[col * a.ldb + row0 + rr] : __ldcg(a.W + col * a.ldw + row0 + rr);
+      __stcg(a.W + col * a.ldw + row0 + rr, base - acc[ii][jj]);
+    }
+  }
 }
 
 // One (phase, system) range of tickets.
@@ -230,8 +346,6 @@ __global__ void __launch_bounds__(NTHREADS, 8) batch_kernel(const BatchSys<T>* _
     const int Rl = (l == a.N - 1) ? a.Rlast : a.R;
     const int64_t s0 = static_cast<int64_t>(l) * a.n0;
     const int64_t ml = imin64(a.n0, a.n - s0);
-    T acc[TM][TN];
-    zero_acc(acc);
     if (o < static_cast<int64_t>(Rl) * a.C) {
       // ---- S(l, r, j) ----
       const int r = Rl - 1 - static_cast<int>(o / a.C);
@@ -247,28 +361,9 @@ __global__ void __launch_bounds__(NTHREADS, 8) batch_kernel(const BatchSys<T>* _
       }
       __syncthreads();
       if (!s_ok) break;
-      const int m = static_cast<int>(imin64(TILE, ml - static_cast<int64_t>(r) * TILE));
-      const int nc = static_cast<int>(imin64(TILE, a.k - static_cast<int64_t>(j) * TILE));
-      const int64_t kend = imin64(static_cast<int64_t>(r + 1) * TILE, ml);
-      const T* Ainv = a.Linv + l * a.inv_bstride + r * TILE;
-      if (l == 0)
-        tile_mma<T, true, false>(Ainv, a.ldinv, a.B + static_cast<int64_t>(j) * TILE * a.ldb, a.ldb, m, nc, 0,
-                                 kend, sm, acc);
-      else
-        tile_mma<T, true, true>(Ainv, a.ldinv, a.W + static_cast<int64_t>(j) * TILE * a.ldw + s0, a.ldw, m, nc, 0,
-                                kend, sm, acc);
-      const int64_t row0 = s0 + static_cast<int64_t>(r) * TILE;
-#pragma unroll
-      for (int i = 0; i < TM; ++i) {
-        const int rr = ty * TM + i;
-        if (rr >= m) continue;
-#pragma unroll
-        for (int jj = 0; jj < TN; ++jj) {
-          const int cc = tx * TN + jj;
-          if (cc >= nc) continue;
-          __stcg(a.X + (static_cast<int64_t>(j) * TILE + cc) * a.ldx + row0 + rr, acc[i][jj]);
-        }
-      }
+      if (a.cw == 8) s_body<T, 8>(a, l, r, j, s0, ml, sm);
+      else if (a.cw == 16) s_body<T, 16>(a, l, r, j, s0, ml, sm);
+      else s_body<T, 32>(a, l, r, j, s0, ml, sm);
       __threadfence();
       __syncthreads();
       if (tid == 0) atomicAdd(a.xdone + static_cast<int64_t>(l) * a.C + j, 1);
@@ -286,27 +381,9 @@ __global__ void __launch_bounds__(NTHREADS, 8) batch_kernel(const BatchSys<T>* _
       }
       __syncthreads();
       if (!s_ok) break;
-      const int64_t si = static_cast<int64_t>(i) * a.n0;
-      const int64_t mi = imin64(a.n0, a.n - si);
-      const int64_t row0 = si + static_cast<int64_t>(r) * TILE;
-      const int m = static_cast<int>(imin64(TILE, mi - static_cast<int64_t>(r) * TILE));
-      const int nc = static_cast<int>(imin64(TILE, a.k - static_cast<int64_t>(j) * TILE));
-      tile_mma<T, false, true>(a.Loff + s0 * a.ldoff + row0, a.ldoff,
-                               a.X + static_cast<int64_t>(j) * TILE * a.ldx + s0, a.ldx, m, nc, 0, ml, sm, acc);
-#pragma unroll
-      for (int ii = 0; ii < TM; ++ii) {
-        const int rr = ty * TM + ii;
-        if (rr >= m) continue;
-#pragma unroll
-        for (int jj = 0; jj < TN; ++jj) {
-          const int cc = tx * TN + jj;
-          if (cc >= nc) continue;
-          const int64_t col = static_cast<int64_t>(j) * TILE + cc;
-          // the first update of a tile starts from B, the others from W
-          const T base = (l == 0) ? a.B[col * a.ldb + row0 + rr] : __ldcg(a.W + col * a.ldw + row0 + rr);
-          __stcg(a.W + col * a.ldw + row0 + rr, base - acc[ii][jj]);
-        }
-      }
+      if (a.cw == 8) u_body<T, 8>(a, l, i, r, j, s0, ml, sm);
+      else if (a.cw == 16) u_body<T, 16>(a, l, i, r, j, s0, ml, sm);
+      else u_body<T, 32>(a, l, i, r, j, s0, ml, sm);
       __threadfence();
       __syncthreads();
       if (tid == 0) atomicAdd(a.wdone + q * a.C + j, 1);
@@ -373,7 +450,8 @@ int build_batch(const trsm_batch_item* items, int count, trsm_batch_s* b, void* 
     a.R = static_cast<int>((a.n0 + trsm::TILE - 1) / trsm::TILE);
     const int64_t mlast = a.n - static_cast<int64_t>(a.N - 1) * a.n0;
     a.Rlast = static_cast<int>((mlast + trsm::TILE - 1) / trsm::TILE);
-    a.C = static_cast<int>((a.k + trsm::TILE - 1) / trsm::TILE);
+    a.cw = a.k <= 8 ? 8 : a.k <= 16 ? 16 : trsm::TILE;
+    a.C = static_cast<int>((a.k + a.cw - 1) / a.cw);
     a.total_rt = static_cast<int64_t>(a.N - 1) * a.R + a.Rlast;
     a.inv_tasks = planned ? 0 : a.N;
     a.ldw = trsm::align4b(a.n);
