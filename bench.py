@@ -69,6 +69,22 @@ def solve_traffic(shapes, n0s):
     return sum(SOLVE_TRAFFIC[key] for key in keys) / len(keys), by_shape
 
 
+def max_over_ranks(value, device):
+    """The largest `value` over all ranks of the process group (the timing
+    rule for replicas: the job lasts as long as its slowest rank)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_step, world, ms_per_step):
+    """Whole-job rate of `world` replicas that each process units_per_step
+    per step in ms_per_step (the max over ranks): weak scaling, no exchange."""
+    return units_per_step * world / (ms_per_step * 1e-3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -539,12 +555,10 @@ def run_ours(args, rank, world, local):
     clk = clocks.stop()
     total_ms = e0.elapsed_time(e1)
     if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, "cuda")
     ms_per_step = total_ms / args.steps
     flops_step = sum(float(n) * n * k for n, k in shapes)
-    value = flops_step * world / (ms_per_step * 1e-3) / 1e12
+    value = replica_throughput(flops_step, world, ms_per_step) / 1e12
 
     per_shape = []
     solve_ms_tot, solve_flops_tot = 0.0, 0.0
