@@ -42,6 +42,19 @@ int trsm_residual_sliced(const double* L_dev, int64_t n, int64_t ldl, const doub
                          int64_t ldx, const double* B_dev, int64_t ldb, double* R_dev, int64_t ldr,
                          int planes, int* err_dev, void* stream);
 
+/* Failure-detection self-test (no counterpart in the paper): launches one
+ * small kernel whose wait can never be satisfied, with a time limit of
+ * limit_us microseconds (1 .. 2e6), and reports what the library would:
+ *   kind = 0: a dependency-counter wait, the routine of the blocked and
+ *             batched solve kernels, on a counter nothing raises;
+ *   kind = 1: an mbarrier wait, the routine of the tcgen05 kernels, on a
+ *             barrier that never gets its arrival, in a CTA holding tensor
+ *             memory (freed before it returns).
+ * Returns TRSM_ETIMEOUT when the wait ran out and the kernel drained (the
+ * expected outcome: the device stays usable), TRSM_SUCCESS if it did not,
+ * TRSM_EINVAL or TRSM_ECUDA.  Synchronous on `stream`. */
+int trsm_wait_selftest(int kind, int64_t limit_us, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

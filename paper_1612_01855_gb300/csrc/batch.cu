@@ -28,6 +28,7 @@
 
 #include "fp64_tile.cuh"
 #include "internal.h"
+#include "wait.cuh"
 #include "trsm_gb300.h"
 
 namespace trsm {
@@ -62,29 +63,9 @@ struct BatchSys {
   int* status;          // per-system status word: 0, or INT_MAX - first singular row
 };
 
-__device__ __forceinline__ int ld_acquire_b(const int* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ long long gtime() {
-  long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
+// Tasks last microseconds: poll at least every 0.5 us.
 __device__ bool wait_geq_b(const int* p, int target, int* err) {
-  if (ld_acquire_b(p) >= target) return true;
-  const long long t0 = gtime();
-  unsigned ns = 64;
-  for (long long it = 0; it < kWaitIters; ++it) {
-    __nanosleep(ns);
-    if (ns < 512) ns <<= 1;  // tasks last microseconds: poll at least every 0.5 us
-    if (ld_acquire_b(p) >= target) return true;
-    if (*(volatile int*)err != 0) return false;
-    if (gtime() - t0 > kWaitNs) break;
-  }
-  atomicCAS(err, 0, 1);
-  return false;
+  return wait_geq_bounded(p, target, err, 1, kWaitNs, kWaitIters, 512) > 0;
 }
 
 __host__ __device__ __forceinline__ int64_t wave_first(int64_t l, int64_t R, int64_t total_rt, int64_t C) {

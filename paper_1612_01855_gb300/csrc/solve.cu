@@ -26,6 +26,7 @@
 
 #include "fp64_tile.cuh"
 #include "internal.h"
+#include "wait.cuh"
 
 namespace trsm {
 
@@ -55,34 +56,13 @@ struct SolveArgs {
   int* status;  // sticky status word of the plan, read by trsm_sync_status
 };
 
-__device__ __forceinline__ int ld_acquire(const int* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ long long global_ns() {
-  long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
 // Thread 0 only: wait until *p >= target.  Returns false if the kernel is
-// draining (error set by anyone) or the wait ran out (sets the error).
+// draining (error set by anyone) or the wait ran out (sets the error and the
+// plan's sticky status).
 __device__ bool wait_geq(const int* p, int target, int* err, int* status) {
-  if (ld_acquire(p) >= target) return true;
-  const long long t0 = global_ns();
-  unsigned ns = 64;
-  for (long long it = 0; it < kWaitLimitIters; ++it) {
-    __nanosleep(ns);
-    if (ns < 2048) ns <<= 1;
-    if (ld_acquire(p) >= target) return true;
-    if (*(volatile int*)err != 0) return false;
-    if (global_ns() - t0 > kWaitLimitNs) break;
-  }
-  atomicCAS(err, 0, kErrTimeout);
-  atomicOr(status, kErrTimeout);
-  return false;
+  const int r = wait_geq_bounded(p, target, err, kErrTimeout, kWaitLimitNs, kWaitLimitIters, 2048);
+  if (r < 0) atomicOr(status, kErrTimeout);
+  return r > 0;
 }
 
 // First ticket of wave l (l < N).  Waves 0..l-1 each hold R S-tasks per

@@ -63,18 +63,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 // Waits for the phase with the given parity to complete.  Returns false if
 // the abort flag is raised or the spin limit is reached (then it raises the
 // flag itself so that every role of the CTA drains).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+__device__ __forceinline__ bool mbar_wait_limit(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                                long long limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = globaltimer_ns();
   for (uint32_t i = 1; i < kMbarSpinLimit; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((i & 255u) == 0) {
       if (*abort_flag) return false;
-      if (globaltimer_ns() - t0 > kMbarWaitNs) break;
+      if (globaltimer_ns() - t0 > limit_ns) break;
     }
   }
   *abort_flag = 1;
   return false;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  return mbar_wait_limit(bar, parity, abort_flag, kMbarWaitNs);
 }
 
 // 3-D TMA tile load (coordinates: x = K offset in elements, y = row, z = slice).
