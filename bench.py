@@ -572,17 +572,24 @@ def run_ours(args, rank, world, local):
                           "tflops": round(float(n) * n * k / ((plan_ms + solve_ms) * 1e-3) / 1e12, 4)})
     solve_achieved = solve_flops_tot / (solve_ms_tot * 1e-3) / 1e12
 
-    # parity check of this run's results on a few sampled columns (oracle)
-    err = None
+    # parity check of this run's results on a few sampled columns (oracle),
+    # and their backward error ||B - L X|| / (||L|| ||X||) (infinity norm)
+    err, bwd = None, None
     if rank == 0 and not args.no_check:
         import oracle
-        errs = []
-        for (L, B), X in zip(data, outs):
+        errs, bwds = [], []
+        for (L, B), X, (Ld, Bd) in zip(data, outs, dev_in):
             cols = np.array([0, B.shape[1] // 2, B.shape[1] - 1])
             want = oracle.forward_subst_columns(L, B, cols)
-            got = X[:, torch.from_numpy(cols).cuda()].cpu().numpy()
+            ci = torch.from_numpy(cols).cuda()
+            got = X[:, ci].cpu().numpy()
             errs.append(float(np.max(np.abs(got - want)) / np.max(np.abs(want))))
-        err = max(errs)
+            Lt = torch.tril(Ld)
+            Xs = X[:, ci]
+            r = (Bd[:, ci] - Lt @ Xs).abs().max().item()
+            bwds.append(r / (Lt.abs().sum(dim=1).max().item() * Xs.abs().max().item()))
+            del Lt
+        err, bwd = max(errs), max(bwds)
 
     # end to end through the C ABI with host buffers (pinned), copies timed
     e2e = None
@@ -689,6 +696,7 @@ def run_ours(args, rank, world, local):
                          "traffic_unit": "bytes per launch (mean over the step's three solve launches)",
                          "traffic_by_shape": traffic_by_shape},
             "parity_max_rel_err": err,
+            "backward_err": bwd,
             "mixed_precision": mixed,
             "batched": batched,
             "serving": serving,

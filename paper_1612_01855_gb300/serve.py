@@ -168,7 +168,10 @@ class Server:
                     continue
                 r = f.reqs[0]
                 r.t_done = time.perf_counter()
-                r.status, r.iterations = f.future.result()
+                try:
+                    r.status, r.iterations = f.future.result()
+                except Exception:  # a failure outside the library (e.g. the runtime): report, keep serving
+                    r.status, r.iterations = binding.TRSM_ECUDA, None
                 self.done.append(r)
                 self.adm.release(f.nbytes)
                 self.busy[f.slot] = False

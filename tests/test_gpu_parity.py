@@ -244,12 +244,18 @@ def test_full_size_sampled_columns(cuda_lib, n, k, n0):
     cols = np.sort(np.random.default_rng(5).choice(k, size=min(6, k), replace=False))
     want = oracle.forward_subst_columns(L, B, cols)
     Ld = dev(L)
-    del L
     p = g.trsm_plan(Ld, n0)
-    del Ld
     Bd = dev(B)
     Xd = g.trsm_solve(p, Bd, X=Bd)
     g.trsm_sync_status(p)
     got = Xd[:, torch.from_numpy(cols).cuda()].cpu().numpy()
     assert rel_err(got, want) < TOL
     assert torch.isfinite(Xd).all().item()
+    # backward error of the sampled columns, ||B - L X|| / (||L|| ||X||) in
+    # the infinity norm, within 10 n eps (the defining equation L X = B)
+    Xs = torch.from_numpy(got).cuda()
+    Bs = torch.from_numpy(np.ascontiguousarray(B[:, cols])).cuda()
+    Lt = torch.tril(Ld)
+    r = (Bs - Lt @ Xs).abs().max().item()
+    bwd = r / (Lt.abs().sum(dim=1).max().item() * Xs.abs().max().item())
+    assert bwd <= 10 * n * np.finfo(np.float64).eps, bwd
