@@ -69,6 +69,21 @@ def solve_traffic(shapes, n0s):
     return sum(SOLVE_TRAFFIC[key] for key in keys) / len(keys), by_shape
 
 
+def measured_peaks():
+    """bf16 tensor peaks (burst, sustained) in TFLOP/s from MEASURED_PEAKS.json
+    when present, else the fallback figures of an earlier GB300 measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["bf16_tflops"]), float(d["bf16_tflops_sustained"]), "measured (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, 1700.0, "fallback (earlier GB300 measurement)"
+
+
+# FP32 FFMA: 128 lanes per SM per clock, 2 flops each (no measured figure)
+FFMA_PEAK_NOMINAL = SMS * 128 * 2 * NOMINAL_SM_MHZ * 1e6 / 1e12
+
+
 def max_over_ranks(value, device):
     """The largest `value` over all ranks of the process group (the timing
     rule for replicas: the job lasts as long as its slowest rank)."""
@@ -237,6 +252,49 @@ def precision_study(g, torch, n, k, n0, cs, inners, s_modes, dd_cols=2, stream=N
     return out
 
 
+def residual_roofline(g, torch, n=16384, k=4096, reps=3):
+    """The sliced FP64-class residual (the mixed path's dominant kernel) at
+    n = 16384, k = 4096: bf16 MMA flops (P(P+1)/2 plane pairs x 2 x n^2/2 x k)
+    per call / CUDA-event time, against the bf16 tensor peak.  The call
+    slices L and X too, so the fraction is a lower bound for the kernel."""
+    import ctypes
+    lib = g.load_library()
+    L = torch.tril(torch.rand(n, n, dtype=torch.float64, device="cuda") * 2 - 1) / n
+    L.diagonal().copy_(2 + torch.rand(n, dtype=torch.float64, device="cuda"))
+    L = L.t().contiguous().t()
+    X = (torch.rand(k, n, dtype=torch.float64, device="cuda") * 2 - 1).t()
+    B = (torch.rand(k, n, dtype=torch.float64, device="cuda") * 2 - 1).t()
+    R = torch.empty(k, n, dtype=torch.float64, device="cuda").t()
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    burst, _, src = measured_peaks()
+    out = {}
+    for planes in (7, 8):
+        def call():
+            return lib.trsm_residual_sliced(ctypes.c_void_p(L.data_ptr()), n, n, ctypes.c_void_p(X.data_ptr()), k, n,
+                                            ctypes.c_void_p(B.data_ptr()), n, ctypes.c_void_p(R.data_ptr()), n,
+                                            planes, ctypes.c_void_p(err.data_ptr()), s)
+        assert call() == 0
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            call()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        ms = statistics.median(ts)
+        flops = planes * (planes + 1) / 2 * float(n) * n * k
+        achieved = flops / (ms * 1e-3) / 1e12
+        out[f"planes{planes}"] = {"bound": "tensor", "kernel": "sliced stream_kernel (slicing of L and X included)",
+                                  "ms": round(ms, 3), "achieved": round(achieved, 1), "peak": burst,
+                                  "unit": "TFLOP/s", "frac": round(achieved / burst, 4), "peak_source": src,
+                                  "err_flag": int(err.item())}
+    del L, X, B, R
+    return out
+
+
 def batch_systems(torch, count, dtype, seed, choose_n0):
     """The batching workload: `count` systems, n log-uniform in [32, 1024], k
     log-uniform in [1, 256], diagonal U[2,3], strictly lower U[-1,1]/n, B
@@ -260,7 +318,7 @@ def batch_systems(torch, count, dtype, seed, choose_n0):
     return systems, float(np.sum(ns.astype(np.float64) ** 2 * ks))
 
 
-def batched_study(g, torch, count=4096, dtypes=("f64", "f32"), reps=5, seed=1000):
+def batched_study(g, torch, count=4096, dtypes=("f64", "f32"), reps=5, seed=1000, fp64_peak=None):
     """Batching workload: `count` independent systems, n log-uniform in
     [32, 1024], k log-uniform in [1, 256], diagonal U[2,3], strictly lower
     U[-1,1]/n, B U[-1,1] (drawn on the device from a per-system seed), all
@@ -290,8 +348,14 @@ def batched_study(g, torch, count=4096, dtypes=("f64", "f32"), reps=5, seed=1000
             sy = systems[i]
             ref = torch.linalg.solve_triangular(sy["L"].double(), sy["B"].double(), upper=False)
             err = max(err, float((sy["X"].double() - ref).abs().max() / ref.abs().max()))
+        achieved = flops / (ms * 1e-3) / 1e12
+        peak, src = ((fp64_peak, "measured DFMA throughput") if dtype == "f64" and fp64_peak
+                     else (FFMA_PEAK_NOMINAL, f"nominal FFMA: {SMS} SMs x 128 lanes x 2 flop x {NOMINAL_SM_MHZ:.0f} MHz"))
         out.append({"dtype": dtype, "systems": count, "ms_per_batch": round(ms, 3),
-                    "tflops_n2k": round(flops / (ms * 1e-3) / 1e12, 3), "status": rc,
+                    "tflops_n2k": round(achieved, 3), "status": rc,
+                    "roofline": {"bound": "alu", "kernel": "batch_kernel", "achieved": round(achieved, 4),
+                                 "peak": round(peak, 4), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                                 "peak_source": src},
                     "n0_by_bucket": {f"{lo}-{hi - 1}": table[i] for i, (lo, hi) in enumerate(autotune.BUCKETS)},
                     "workspace_gb": round(batch.workspace_bytes() / 1e9, 3),
                     "spot_check_rel_err": err, "graph": True,
@@ -301,7 +365,7 @@ def batched_study(g, torch, count=4096, dtypes=("f64", "f32"), reps=5, seed=1000
     return out
 
 
-def schedules_study(g, torch, dev_in, outs, shapes, n0s, reps=3, stream=None):
+def schedules_study(g, torch, dev_in, outs, shapes, n0s, reps=3, stream=None, fp64_peak=None):
     """Solve time of the three schedules of the blocked solve on the bench
     shapes (plan reused; solve only): the dependency-driven persistent kernel,
     the paper's right-looking loop with a look-ahead stream, and Rec-TRSM."""
@@ -321,7 +385,10 @@ def schedules_study(g, torch, dev_in, outs, shapes, n0s, reps=3, stream=None):
                 torch.cuda.synchronize()
                 ts.append(a.elapsed_time(b))
             ms = statistics.median(ts)
-            rec[sched] = {"solve_ms": round(ms, 3), "tflops": round(float(n) * n * k / (ms * 1e-3) / 1e12, 4)}
+            tf = float(n) * n * k / (ms * 1e-3) / 1e12
+            rec[sched] = {"solve_ms": round(ms, 3), "tflops": round(tf, 4)}
+            if fp64_peak:
+                rec[sched]["frac_of_measured_dfma"] = round(tf / fp64_peak, 4)
         g.trsm_sync_status(p)
         p.destroy()
         out.append(rec)
@@ -628,6 +695,9 @@ def run_ours(args, rank, world, local):
                "sample": sample + " (forward substitution, FP64, OpenMP over columns)"}
 
     mixed = None
+    residual = None
+    if rank == 0 and not args.no_mixed and not args.shapes:
+        residual = residual_roofline(g, torch)
     if rank == 0 and not args.no_mixed and not args.shapes:
         # FP32 diagonal multiplies at the mixed path's block size, and the
         # FP64 ones at the FP64 path's block size (where they cost least)
@@ -636,7 +706,7 @@ def run_ours(args, rank, world, local):
 
     batched = None
     if rank == 0 and not args.no_batched and not args.shapes:
-        batched = batched_study(g, torch)
+        batched = batched_study(g, torch, fp64_peak=fp64_peak)
 
     serving = None
     if rank == 0 and not args.no_serving and not args.shapes:
@@ -644,7 +714,7 @@ def run_ours(args, rank, world, local):
 
     schedules = None
     if rank == 0 and not args.no_schedules:
-        schedules = schedules_study(g, torch, dev_in, outs, shapes, n0s)
+        schedules = schedules_study(g, torch, dev_in, outs, shapes, n0s, fp64_peak=fp64_peak)
 
     if args.precision and rank == 0:
         for rec in precision_study(g, torch, 16384, 4096, MIXED_N0, [2, 4, 6], ["tf32", "bf16", "bf16x3"],
@@ -698,6 +768,7 @@ def run_ours(args, rank, world, local):
             "parity_max_rel_err": err,
             "backward_err": bwd,
             "mixed_precision": mixed,
+            "residual_roofline": residual,
             "batched": batched,
             "serving": serving,
             "schedules": schedules,
