@@ -10,11 +10,14 @@
 //            U(i, r, j, l)     W_i[r, j] -= L_il[r, :] X_l[:, j]      (i > l)
 // with the same dependency counters as the single-system kernel.  Tickets
 // run phase-major: phase 0 holds the INV tasks of every system, phase
-// l + 1 wave l of every system that has one.  The tickets in flight at any
-// time therefore belong to many systems at the same stage instead of one
-// system's dependency chain, and every dependency of a task (same system,
-// earlier phase or earlier in its wave) still holds a smaller ticket: the
-// scheme cannot deadlock whatever the residency.  The first update
+// l + 1 wave l of every system that has one, first the S tasks of all
+// those systems, then their U tasks.  The tickets in flight at any time
+// therefore belong to many systems at the same stage instead of one
+// system's dependency chain, and a U task rarely waits: the S tasks it
+// needs were handed out a whole sweep over the systems earlier.  Every
+// dependency of a task (same system, earlier phase, or the S part of its
+// phase) holds a smaller ticket: the scheme cannot deadlock whatever the
+// residency.  The first update
 // of a tile reads B instead of the working copy W, so no copy launch is
 // needed and a whole batch is one memset plus one kernel (and so one CUDA
 // graph).  The arithmetic type T is double or float.
@@ -222,11 +225,12 @@ __device__ __forceinline__ void u_body(const BatchSys<T>& a, int l, int i, int r
   }
 }
 
-// One (phase, system) range of tickets.
+// One (phase, part, system) range of tickets.
 struct PhaseEntry {
   int64_t first;  // first ticket
   int sys;        // system index
   int phase;      // 0: INV tasks, l + 1: wave l
+  int part;       // wave l: 0 = its S tasks, 1 = its U tasks
 };
 
 template <class T>
@@ -327,7 +331,7 @@ __global__ void __launch_bounds__(NTHREADS, 8) batch_kernel(const BatchSys<T>* _
     const int Rl = (l == a.N - 1) ? a.Rlast : a.R;
     const int64_t s0 = static_cast<int64_t>(l) * a.n0;
     const int64_t ml = imin64(a.n0, a.n - s0);
-    if (o < static_cast<int64_t>(Rl) * a.C) {
+    if (pe.part == 0) {
       // ---- S(l, r, j) ----
       const int r = Rl - 1 - static_cast<int>(o / a.C);
       const int j = static_cast<int>(o % a.C);
@@ -350,7 +354,7 @@ __global__ void __launch_bounds__(NTHREADS, 8) batch_kernel(const BatchSys<T>* _
       if (tid == 0) atomicAdd(a.xdone + static_cast<int64_t>(l) * a.C + j, 1);
     } else {
       // ---- U(i, r, j, l) ----
-      const int64_t o2 = o - static_cast<int64_t>(Rl) * a.C;
+      const int64_t o2 = o;
       const int64_t q = static_cast<int64_t>(l + 1) * a.R + o2 / a.C;
       const int j = static_cast<int>(o2 % a.C);
       const int i = static_cast<int>(imin64(q / a.R, a.N - 1));
@@ -448,7 +452,7 @@ int build_batch(const trsm_batch_item* items, int count, trsm_batch_s* b, void* 
   int maxN = 0;
   for (int s = 0; s < count; ++s) maxN = std::max(maxN, sys[s].N);
   size_t nent_max = 0;
-  for (int s = 0; s < count; ++s) nent_max += static_cast<size_t>(sys[s].N) + (sys[s].inv_tasks > 0 ? 1 : 0);
+  for (int s = 0; s < count; ++s) nent_max += 2 * static_cast<size_t>(sys[s].N) + (sys[s].inv_tasks > 0 ? 1 : 0);
   const size_t table_off = off;
   off = trsm::al256(off + sizeof(BatchSys<T>) * count);
   const size_t ent_off = off;
@@ -525,20 +529,22 @@ int build_batch(const trsm_batch_item* items, int count, trsm_batch_s* b, void* 
   std::vector<trsm::PhaseEntry> ent;
   int64_t task = 0;
   for (int p = 0; p <= maxN; ++p) {
-    for (int s = 0; s < count; ++s) {
-      const BatchSys<T>& a = sys[s];
-      int64_t cntp = 0;
-      if (p == 0) {
-        cntp = a.inv_tasks;
-      } else if (p - 1 < a.N) {
-        const int l = p - 1;
-        const int Rl = (l == a.N - 1) ? a.Rlast : a.R;
-        const int64_t below = std::max<int64_t>(0, a.total_rt - static_cast<int64_t>(l + 1) * a.R);
-        cntp = (static_cast<int64_t>(Rl) + below) * a.C;
-      }
-      if (cntp > 0) {
-        ent.push_back(trsm::PhaseEntry{task, s, p});
-        task += cntp;
+    for (int part = 0; part < (p == 0 ? 1 : 2); ++part) {
+      for (int s = 0; s < count; ++s) {
+        const BatchSys<T>& a = sys[s];
+        int64_t cntp = 0;
+        if (p == 0) {
+          cntp = a.inv_tasks;
+        } else if (p - 1 < a.N) {
+          const int l = p - 1;
+          const int Rl = (l == a.N - 1) ? a.Rlast : a.R;
+          const int64_t below = std::max<int64_t>(0, a.total_rt - static_cast<int64_t>(l + 1) * a.R);
+          cntp = (part == 0 ? static_cast<int64_t>(Rl) : below) * a.C;
+        }
+        if (cntp > 0) {
+          ent.push_back(trsm::PhaseEntry{task, s, p, part});
+          task += cntp;
+        }
       }
     }
   }
