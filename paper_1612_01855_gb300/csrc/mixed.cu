@@ -186,6 +186,90 @@ __global__ void __launch_bounds__(NTHREADS) s_step_kernel(const double* __restri
   if (R - 1 - p != p) s_tile<kMode, TC>(Lt, ldt, W, ldw, D, ldd, Dt, n0p, s0, m, k, R - 1 - p, j, sm);
 }
 
+// The same step in FP32 arithmetic (TRSM_SOLVE_S_FP32), register-blocked
+// for the FFMA pipes: a 64 x 64 output tile per CTA of 256 threads, 4 x 4
+// outputs per thread, K staged through shared memory in chunks of 32 and
+// read back as float4 (16 FMAs per 8 loads; the generic 32 x 32 tile
+// makes 8 per 6).
+constexpr int kS32Tile = 64;
+constexpr int kS32Chunk = 32;
+constexpr int kS32Threads = 256;
+struct S32Smem {
+  float a[kS32Chunk][kS32Tile + 4];  // a[kk][row]: rows 16-byte aligned for float4 reads
+  float b[kS32Chunk][kS32Tile + 4];  // b[kk][col]
+};
+
+template <int kMode>
+__device__ __forceinline__ void s32_tile(const double* __restrict__ Lt, int64_t ldt, const float* __restrict__ W,
+                                         int64_t ldw, double* __restrict__ D, int64_t ldd,
+                                         typename LowP<kMode>::T* __restrict__ Dt, int64_t n0p, int64_t s0, int m,
+                                         int64_t k, int r, int j, S32Smem& sm) {
+  const int tid = threadIdx.x;
+  const int ty = tid >> 4, tx = tid & 15;
+  const int mr = min(kS32Tile, m - r * kS32Tile);
+  const int nc = static_cast<int>(imin64(kS32Tile, k - static_cast<int64_t>(j) * kS32Tile));
+  const int kend = min((r + 1) * kS32Tile, m);  // L~_ii is lower triangular
+  const double* A = Lt + s0 * ldt + s0 + static_cast<int64_t>(r) * kS32Tile;  // A(row, t) = A[t ldt + row]
+  const float* B = W + static_cast<int64_t>(j) * kS32Tile * ldw + s0;         // B(t, col) = B[col ldw + t]
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[i][c] = 0.f;
+  for (int k0 = 0; k0 < kend; k0 += kS32Chunk) {
+#pragma unroll
+    for (int it = 0; it < (kS32Tile * kS32Chunk) / kS32Threads; ++it) {
+      const int row = tid & 63, kk = (tid >> 6) + 4 * it, t = k0 + kk;
+      sm.a[kk][row] = (row < mr && t < kend) ? static_cast<float>(A[static_cast<int64_t>(t) * ldt + row]) : 0.f;
+    }
+#pragma unroll
+    for (int it = 0; it < (kS32Tile * kS32Chunk) / kS32Threads; ++it) {
+      const int kk = tid & 31, col = (tid >> 5) + 8 * it, t = k0 + kk;
+      sm.b[kk][col] = (col < nc && t < kend) ? B[static_cast<int64_t>(col) * ldw + t] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < kS32Chunk; ++kk) {
+      const float4 av = *reinterpret_cast<const float4*>(&sm.a[kk][ty * 4]);
+      const float4 bv = *reinterpret_cast<const float4*>(&sm.b[kk][tx * 4]);
+      const float a4[4] = {av.x, av.y, av.z, av.w}, b4[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[i][c] = fmaf(a4[i], b4[c], acc[i][c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int rr = ty * 4 + i;
+    if (rr >= mr) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int cc = tx * 4 + c;
+      if (cc >= nc) continue;
+      const int64_t col = static_cast<int64_t>(j) * kS32Tile + cc;
+      const int64_t row = static_cast<int64_t>(r) * kS32Tile + rr;
+      const double v = static_cast<double>(acc[i][c]);
+      D[col * ldd + s0 + row] = v;
+      LowP<kMode>::put(Dt + col * n0p + row, k * n0p, v);
+    }
+  }
+}
+
+template <int kMode>
+__global__ void __launch_bounds__(kS32Threads) s_step32_kernel(const double* __restrict__ Lt, int64_t ldt,
+                                                               const float* __restrict__ W, int64_t ldw,
+                                                               double* __restrict__ D, int64_t ldd,
+                                                               typename LowP<kMode>::T* __restrict__ Dt,
+                                                               int64_t n0p, int64_t s0, int m, int64_t k) {
+  __shared__ __align__(16) S32Smem sm;
+  const int R = (m + kS32Tile - 1) / kS32Tile;
+  const int p = blockIdx.x, j = blockIdx.y;
+  s32_tile<kMode>(Lt, ldt, W, ldw, D, ldd, Dt, n0p, s0, m, k, p, j, sm);
+  if (R - 1 - p != p) s32_tile<kMode>(Lt, ldt, W, ldw, D, ldd, Dt, n0p, s0, m, k, R - 1 - p, j, sm);
+}
+
 // max that keeps a NaN once it has been seen (fmax would drop it)
 __device__ __forceinline__ double nanmax(double m, double v) { return (v > m || isnan(v)) ? v : m; }
 
@@ -400,23 +484,37 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
       const int m = static_cast<int>(std::min(n0, n - s0));
       const int R = (m + trsm::TILE - 1) / trsm::TILE;
       dim3 g(static_cast<unsigned>((R + 1) / 2), static_cast<unsigned>((k + trsm::TILE - 1) / trsm::TILE));
+      const int R32 = (m + trsm::kS32Tile - 1) / trsm::kS32Tile;
+      dim3 g32(static_cast<unsigned>((R32 + 1) / 2), static_cast<unsigned>((k + trsm::kS32Tile - 1) / trsm::kS32Tile));
+      // the 64 x 64 FP32 tile pays off from 512-row blocks; smaller blocks
+      // give it too few CTAs (measured: n0 = 256 slower, 1024 faster)
+      const bool wide = m >= 512;
       if (mode == 1 && !s32)
         trsm::s_step_kernel<1, double><<<g, trsm::NTHREADS, 0, s>>>(h->Lt, h->ldt, W, ld, D, ld,
                                                                      static_cast<float*>(Dt), n0p, s0, m, k);
-      else if (mode == 1)
+      else if (mode == 1 && !wide)
         trsm::s_step_kernel<1, float><<<g, trsm::NTHREADS, 0, s>>>(h->Lt, h->ldt, W, ld, D, ld,
+                                                                    static_cast<float*>(Dt), n0p, s0, m, k);
+      else if (mode == 1)
+        trsm::s_step32_kernel<1><<<g32, trsm::kS32Threads, 0, s>>>(h->Lt, h->ldt, W, ld, D, ld,
                                                                     static_cast<float*>(Dt), n0p, s0, m, k);
       else if (mode == 2 && !s32)
         trsm::s_step_kernel<2, double><<<g, trsm::NTHREADS, 0, s>>>(
             h->Lt, h->ldt, W, ld, D, ld, static_cast<__nv_bfloat16*>(Dt), n0p, s0, m, k);
-      else if (mode == 2)
+      else if (mode == 2 && !wide)
         trsm::s_step_kernel<2, float><<<g, trsm::NTHREADS, 0, s>>>(
+            h->Lt, h->ldt, W, ld, D, ld, static_cast<__nv_bfloat16*>(Dt), n0p, s0, m, k);
+      else if (mode == 2)
+        trsm::s_step32_kernel<2><<<g32, trsm::kS32Threads, 0, s>>>(
             h->Lt, h->ldt, W, ld, D, ld, static_cast<__nv_bfloat16*>(Dt), n0p, s0, m, k);
       else if (!s32)
         trsm::s_step_kernel<0, double><<<g, trsm::NTHREADS, 0, s>>>(
             h->Lt, h->ldt, W, ld, D, ld, static_cast<__nv_bfloat16*>(Dt), n0p, s0, m, k);
-      else
+      else if (!wide)
         trsm::s_step_kernel<0, float><<<g, trsm::NTHREADS, 0, s>>>(
+            h->Lt, h->ldt, W, ld, D, ld, static_cast<__nv_bfloat16*>(Dt), n0p, s0, m, k);
+      else
+        trsm::s_step32_kernel<0><<<g32, trsm::kS32Threads, 0, s>>>(
             h->Lt, h->ldt, W, ld, D, ld, static_cast<__nv_bfloat16*>(Dt), n0p, s0, m, k);
       trsm::count_launch();
       e = cudaGetLastError();

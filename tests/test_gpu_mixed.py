@@ -38,6 +38,24 @@ def test_mixed_well_conditioned(cuda_lib, inner, residual, s32, n, k, n0):
     assert iters <= {"tf32": 12, "bf16": 25, "bf16x3": 6}[inner]
 
 
+@pytest.mark.parametrize("inner", ["tf32", "bf16x3"])
+@pytest.mark.parametrize("n,k,n0", [(1500, 70, 600), (2048, 33, 1024), (1100, 130, 512)])
+def test_mixed_wide_blocks_fp32_diagonal_multiply(cuda_lib, inner, n, k, n0):
+    """Blocks of 512 rows and more take the 64 x 64 register-blocked FP32
+    diagonal multiply (ragged last blocks the 32 x 32 tile)."""
+    import paper_1612_01855_gb300 as g
+    L, B = inputs.well_conditioned(n, k, seed=n + 3 * k)
+    Ld = _dev(L)
+    plan = g.trsm_plan(Ld, n0)
+    g.trsm_plan_mixed(plan, Ld, inner)
+    X, iters, upd = g.trsm_solve_mixed(plan, _dev(B), residual="sliced", max_iter=40, tol=1e-15,
+                                       raise_on_noconv=False, s_fp32=True)
+    err = _rel(X.cpu().numpy(), oracle.forward_subst(L, B))
+    print(f"mixed {inner}/s32 n={n} k={k} n0={n0}: {iters} iterations, rel err {err:.2e}")
+    assert err < 5e-12
+    assert iters <= 12
+
+
 def test_mixed_graded_diagonal_forward_error(cuda_lib):
     """Diagonal graded from 1 to 1e-2: forward error against the
     double-double substitution stays below 1e-10."""
