@@ -42,10 +42,10 @@ SMS = 152
 # (profiles/it_inv_solve_kernel_dram_bench_shapes.md).  They describe the
 # kernel source they were taken from; once solve.cu or fp64_tile.cuh changes
 # the figures no longer apply and the bench reports traffic as null.
-SOLVE_TRAFFIC_SHA256 = "5ce0f8d4e49acdf07958222c94c780b4315e25617d723b5e884105dbca12c5de"
-SOLVE_TRAFFIC = {(16384, 256, 256): 1310468864 + 220226560,
-                 (8192, 8192, 512): 5600246528 + 4522664704,
-                 (2048, 131072, 2048): 3350170112 + 2148292864}
+SOLVE_TRAFFIC_SHA256 = "1b10bcd32c87a0a41972ba56e8f8083faf7da9229e5723ae1281f62ca03d8e2a"
+SOLVE_TRAFFIC = {(16384, 256, 256): 1120057344 + 64409856,
+                 (8192, 8192, 512): 5455504384 + 4520425216,
+                 (2048, 131072, 2048): 2200583168 + 2126338304}
 
 
 def solve_source_sha256():

@@ -97,14 +97,43 @@ __global__ void __launch_bounds__(NTHREADS) it_inv_solve_kernel(const SolveArgs 
       if (wave_start(mid, a.R, a.total_rt, a.C) <= t) lo = mid;
       else hi = mid - 1;
     }
-    const int l = lo;
-    const int64_t o = t - wave_start(l, a.R, a.total_rt, a.C);
-    const int Rl = (l == a.N - 1) ? a.Rlast : a.R;
+    // The tickets of wave lw span [S(lw) | Unear(lw) | Ufar(lw)], Unear being
+    // the updates of block row lw + 1 and Ufar those below it.  They are
+    // handed out in the order S(0), Unear(0), S(1), Ufar(0), Unear(1), S(2),
+    // Ufar(1), ...: each wave's far updates move behind the next wave's S
+    // tasks, which start as soon as their near updates are done instead of
+    // after the whole trailing update.  Every dependency still has a smaller
+    // ticket (S(l+1) needs Unear(l) and the Ufar of earlier waves; Unear(l+1)
+    // and Ufar(l+1) need Ufar(l) on their rows).
+    const int lw = lo;
+    auto rt = [&](int b) { return b == a.N - 1 ? a.Rlast : a.R; };
+    const int64_t ws = wave_start(lw, a.R, a.total_rt, a.C);
+    const int64_t sz = (int64_t)rt(lw) * a.C;
+    const int64_t nz = (lw + 1 < a.N) ? (int64_t)rt(lw + 1) * a.C : 0;
+    int l;
+    bool is_s;
+    int64_t o;  // S tasks: offset in S(l); U tasks: offset in the wave's U tickets (near first)
+    if (t < ws + sz && lw == 0) {
+      l = 0, is_s = true, o = t;
+    } else if (t < ws + sz) {
+      const int64_t far_prev = (a.total_rt - (int64_t)lw * a.R - rt(lw)) * a.C;  // Ufar(lw - 1)
+      const int64_t p = t - ws + far_prev;
+      if (p < sz) l = lw, is_s = true, o = p;
+      else l = lw - 1, is_s = false, o = (int64_t)rt(lw) * a.C + (p - sz);
+    } else if (t < ws + sz + nz) {
+      l = lw, is_s = false, o = t - ws - sz;
+    } else {
+      const int64_t p = t - ws - sz - nz;
+      const int64_t sz_next = (lw + 1 < a.N) ? (int64_t)rt(lw + 1) * a.C : 0;
+      if (p < sz_next) l = lw + 1, is_s = true, o = p;
+      else l = lw, is_s = false, o = nz + (p - sz_next);
+    }
+    const int Rl = rt(l);
     const int64_t s0 = (int64_t)l * a.n0;             // first row of block l
     const int64_t ml = imin64(a.n0, a.n - s0);           // |S_l|
     double acc[TM][TN];
     zero_acc(acc);
-    if (o < (int64_t)Rl * a.C) {
+    if (is_s) {
       // ---- S(l, r, j): column tile by column tile, and within one the
       // largest r first (they carry the most work).  The row tiles of a
       // column tile run together and share W_l[:, j] in L2: with k large
@@ -145,7 +174,7 @@ __global__ void __launch_bounds__(NTHREADS) it_inv_solve_kernel(const SolveArgs 
       if (tid == 0) atomicAdd(a.xdone + (int64_t)l * a.C + j, 1);
     } else {
       // ---- U(i, r, j, l) ----
-      const int64_t o2 = o - (int64_t)Rl * a.C;
+      const int64_t o2 = o;
       const int64_t q = (int64_t)(l + 1) * a.R + o2 / a.C;  // global row tile
       const int j = (int)(o2 % a.C);
       const int i = (int)imin64(q / a.R, a.N - 1);
@@ -264,7 +293,7 @@ cudaError_t solve_enqueue(const double* Lt, int64_t ldt, int64_t n, int64_t n0, 
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, it_inv_solve_kernel, NTHREADS, 0);
   if (e != cudaSuccess) return e;
-  per_sm = std::max(1, std::min(per_sm, 8));
+  per_sm = std::max(1, std::min(per_sm, 4));
   int64_t grid = (int64_t)device_sm_count() * per_sm;
   grid = std::max<int64_t>(1, std::min<int64_t>(grid, ntasks));
   it_inv_solve_kernel<<<(unsigned)grid, NTHREADS, 0, s>>>(a);
