@@ -201,9 +201,9 @@ def cpu_oracle_rate(data, shapes, budget_s, max_cols=None):
 def precision_study(g, torch, n, k, n0, cs, inners, s_modes, dd_cols=2, stream=None, quick=False,
                     residuals=("sliced",)):
     """Mixed-precision refinement on the graded-diagonal workload (diagonal
-    geomspace(1, 10^-c), permuted): time, iterations and forward error
-    against the double-double oracle on sampled columns, beside the FP64
-    solve of the same system."""
+    geomspace(1, 10^-c), permuted): time, iterations, forward error against
+    the double-double oracle and backward error ||B - L X|| / (||L|| ||X||)
+    on sampled columns, beside the FP64 solve of the same system."""
     import oracle
     from paper_1612_01855_gb300 import inputs
     out = []
@@ -222,6 +222,17 @@ def precision_study(g, torch, n, k, n0, cs, inners, s_modes, dd_cols=2, stream=N
                 return None
             return float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
 
+        Lt_abs_rowsum = torch.tril(Ld).abs().sum(dim=1).max().item()
+
+        def berr(X):
+            """||B - L X|| / (||L|| ||X||) on the sampled columns (infinity norm)."""
+            ci = torch.from_numpy(cols).cuda()
+            Xs = X[:, ci]
+            if not torch.isfinite(Xs).all():
+                return None
+            r = (Bd[:, ci] - torch.tril(Ld) @ Xs).abs().max().item()
+            return r / (Lt_abs_rowsum * Xs.abs().max().item())
+
         plan = g.trsm_plan(Ld, n0)
         X64 = g.trsm_solve(plan, Bd)
         g.trsm_sync_status(plan)
@@ -232,7 +243,7 @@ def precision_study(g, torch, n, k, n0, cs, inners, s_modes, dd_cols=2, stream=N
         torch.cuda.synchronize()
         t64 = e0.elapsed_time(e1)
         rec = {"c": c, "n": n, "k": k, "n0": n0, "fp64_solve_ms": round(t64, 2),
-               "fp64_fwd_err": ferr(X64), "dd_reference_finite": ref_ok, "mixed": []}
+               "fp64_fwd_err": ferr(X64), "fp64_bwd_err": berr(X64), "dd_reference_finite": ref_ok, "mixed": []}
         for inner in inners:
             g.trsm_plan_mixed(plan, Ld, inner)
             for s32, res in ((a, b) for a in s_modes for b in residuals):
@@ -248,7 +259,7 @@ def precision_study(g, torch, n, k, n0, cs, inners, s_modes, dd_cols=2, stream=N
                 rec["mixed"].append({"inner": inner, "s_step": "fp32" if s32 else "fp64",
                                      "residual": res, "ms": round(tm, 2),
                                      "tflops_equiv": round(float(n) * n * k / (tm * 1e-3) / 1e12, 3),
-                                     "iterations": it, "last_update": upd, "fwd_err": fe,
+                                     "iterations": it, "last_update": upd, "fwd_err": fe, "bwd_err": berr(X),
                                      "converged": bool(fe is not None and fe <= 1e-10),
                                      "speedup_vs_fp64": round(t64 / tm, 3)})
         plan.destroy()
@@ -319,7 +330,9 @@ def batch_systems(torch, count, dtype, seed, choose_n0):
         L = L.t().contiguous().t()
         B = torch.rand((int(k), int(n)), generator=gen, device="cuda", dtype=tdt).mul_(2).sub_(1).t()
         X = torch.empty((int(k), int(n)), device="cuda", dtype=tdt).t()
-        systems.append({"L": L, "B": B, "X": X, "n0": choose_n0(int(n))})
+        c = choose_n0(int(n))
+        n0, tile = c if isinstance(c, tuple) else (c, 0)
+        systems.append({"L": L, "B": B, "X": X, "n0": n0, "tile_cols": tile})
     return systems, float(np.sum(ns.astype(np.float64) ** 2 * ks))
 
 
@@ -332,8 +345,8 @@ def batched_study(g, torch, count=4096, dtypes=("f64", "f32"), reps=5, seed=1000
     from paper_1612_01855_gb300 import autotune
     out = []
     for dtype in dtypes:
-        table = autotune.tune_batch_n0(dtype)
-        systems, flops = batch_systems(torch, count, dtype, seed, lambda n: autotune.choose_n0(n, dtype, table))
+        table = autotune.tune_batch(dtype)
+        systems, flops = batch_systems(torch, count, dtype, seed, lambda n: autotune.choose(n, dtype, table))
         batch = g.Batch(systems, dtype=dtype)
         batch.capture()
         for _ in range(2):
@@ -361,7 +374,9 @@ def batched_study(g, torch, count=4096, dtypes=("f64", "f32"), reps=5, seed=1000
                     "roofline": {"bound": "alu", "kernel": "batch_kernel", "achieved": round(achieved, 4),
                                  "peak": round(peak, 4), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
                                  "peak_source": src},
-                    "n0_by_bucket": {f"{lo}-{hi - 1}": table[i] for i, (lo, hi) in enumerate(autotune.BUCKETS)},
+                    "n0_by_bucket": {f"{lo}-{hi - 1}": table[i][0] for i, (lo, hi) in enumerate(autotune.BUCKETS)},
+                    "tile_cols_by_bucket": {f"{lo}-{hi - 1}": (table[i][1] or "by k")
+                                            for i, (lo, hi) in enumerate(autotune.BUCKETS)},
                     "workspace_gb": round(batch.workspace_bytes() / 1e9, 3),
                     "spot_check_rel_err": err, "graph": True,
                     "inputs": "device-generated per-system seeds (torch Philox), config-0 distributions"})
@@ -394,6 +409,7 @@ def schedules_study(g, torch, dev_in, outs, shapes, n0s, reps=3, stream=None, fp
             rec[sched] = {"solve_ms": round(ms, 3), "tflops": round(tf, 4)}
             if fp64_peak:
                 rec[sched]["frac_of_measured_dfma"] = round(tf / fp64_peak, 4)
+        rec["autotuned"] = min(("dag", "right-looking", "recursive"), key=lambda x: rec[x]["solve_ms"])
         g.trsm_sync_status(p)
         p.destroy()
         out.append(rec)

@@ -206,6 +206,8 @@ typedef struct trsm_batch_item {
   int64_t ldx;
   int64_t n, k;
   int64_t n0;           /* 32 or 64 when plan == NULL (ignored otherwise)      */
+  int64_t tile_cols;    /* columns per output tile: 8, 16 or 32; 0 = by k
+                           (8 for k <= 8, 16 for k <= 16, else 32)            */
 } trsm_batch_item;
 
 typedef struct trsm_batch_s* trsm_batch_t;

@@ -1,11 +1,18 @@
-"""Block-size autotuner for batches of small systems.
+"""Autotuning of the batched and the single-system solve.
 
 The paper chooses n0 a priori from its cost model (Section 8; with one
-processor its three-dimensional rule gives n0 ~ min(sqrt(n k), n)); on one
-GPU the choice that matters is the in-launch inversion block of the
-batched solve (32 or 64) per size bucket.  `tune_batch_n0` times both
-candidates on synthetic systems of each bucket through the batched C ABI
-and keeps the faster; `choose_n0` maps a system to its bucket's choice.
+processor its three-dimensional rule gives n0 ~ min(sqrt(n k), n)).  On one
+GPU the choices that matter are measured instead:
+
+* batches (`tune_batch`): per size bucket, the in-launch inversion block
+  n0 (32 or 64) and the output tile shape (32-wide column tiles, or column
+  tiles narrowed to k by the library: 8 for k <= 8, 16 for k <= 16) -- each
+  candidate timed on synthetic systems of that bucket through the batched
+  C ABI, the fastest kept; `choose` maps a system to its bucket's choice;
+* single systems (`tune_schedule`): the schedule of the blocked solve
+  (dependency-driven kernel, right-looking loop with look-ahead, Rec-TRSM)
+  timed on the system itself.
+
 Results are cached per (dtype, bucket) for the process.
 """
 import math
@@ -16,7 +23,8 @@ from . import binding
 
 # size buckets by n (log2 ranges), as in the batching workload n in [32, 1024]
 BUCKETS = [(1, 64), (64, 128), (128, 256), (256, 512), (512, 1025)]
-CANDIDATES = (32, 64)
+N0_CANDIDATES = (32, 64)
+TILE_CANDIDATES = (0, 32)  # 0: column tiles narrowed to k by the library
 _cache = {}
 
 
@@ -52,9 +60,22 @@ def _synthetic(count, lo, hi, kmax, dtype, seed):
     return systems
 
 
-def tune_batch_n0(dtype="f64", count=96, kmax=256, reps=3, seed=7):
-    """Measures n0 = 32 and 64 per bucket; returns {bucket index: n0}."""
+def _time(fn, reps):
     import torch
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def tune_batch(dtype="f64", count=96, kmax=256, reps=3, seed=7):
+    """Times every (n0, tile) candidate per bucket; returns {bucket index:
+    (n0, tile_cols)} with the fastest candidate that ran without error."""
     out = {}
     for bi, (lo, hi) in enumerate(BUCKETS):
         key = (dtype, bi)
@@ -62,29 +83,43 @@ def tune_batch_n0(dtype="f64", count=96, kmax=256, reps=3, seed=7):
             out[bi] = _cache[key]
             continue
         systems = _synthetic(count, max(lo, 1), hi, kmax, dtype, seed + bi)
-        best, best_t = None, float("inf")
-        for n0 in CANDIDATES:
-            for sy in systems:
-                sy["n0"] = n0
-            b = binding.Batch(systems, dtype=dtype)
-            b.run()
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            for _ in range(reps):
-                b.run()
-            e1.record()
-            torch.cuda.synchronize()
-            t = e0.elapsed_time(e1) / reps
-            rc = b.status()[0]
-            b.destroy()
-            if rc == 0 and t < best_t:
-                best, best_t = n0, t
+        best, best_t = (32, 0), float("inf")
+        for n0 in N0_CANDIDATES:
+            for tile in TILE_CANDIDATES:
+                for sy in systems:
+                    sy["n0"], sy["tile_cols"] = n0, tile
+                b = binding.Batch(systems, dtype=dtype)
+                t = _time(b.run, reps)
+                rc = b.status()[0]
+                b.destroy()
+                if rc == 0 and t < best_t:
+                    best, best_t = (n0, tile), t
         _cache[key] = best
         out[bi] = best
     return out
 
 
-def choose_n0(n, dtype="f64", table=None):
+def tune_batch_n0(dtype="f64", **kw):
+    """The block-size part of tune_batch: {bucket index: n0}."""
+    return {bi: v[0] for bi, v in tune_batch(dtype, **kw).items()}
+
+
+def choose(n, dtype="f64", table=None):
+    """(n0, tile_cols) for a system of order n from its bucket's tuned choice."""
     table = table if table is not None else {bi: v for (dt, bi), v in _cache.items() if dt == dtype}
-    return table.get(bucket_of(n), 32)
+    return table.get(bucket_of(n), (32, 0))
+
+
+def choose_n0(n, dtype="f64", table=None):
+    v = choose(n, dtype, table)
+    return v[0] if isinstance(v, tuple) else v
+
+
+def tune_schedule(plan, B, X=None, reps=2):
+    """Times the three schedules of the blocked solve on this system;
+    returns (fastest name, {name: ms})."""
+    times = {}
+    for sched in binding.SCHEDULES:
+        times[sched] = _time(lambda: binding.trsm_solve_schedule(plan, B, X=X, schedule=sched), reps)
+    binding.trsm_sync_status(plan)
+    return min(times, key=times.get), times

@@ -43,7 +43,7 @@ class BatchItem(ctypes.Structure):
     _fields_ = [("L", ctypes.c_void_p), ("ldl", ctypes.c_int64), ("plan", ctypes.c_void_p),
                 ("B", ctypes.c_void_p), ("ldb", ctypes.c_int64), ("X", ctypes.c_void_p),
                 ("ldx", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int64),
-                ("n0", ctypes.c_int64)]
+                ("n0", ctypes.c_int64), ("tile_cols", ctypes.c_int64)]
 
 
 # Every symbol the header declares, with (restype, argtypes).
@@ -393,7 +393,8 @@ def launch_count(reset=False):
 class Batch:
     """Many independent systems solved by one persistent launch
     (trsm_batch_*).  `systems` is a list of dicts with keys L (or plan), B,
-    X (CUDA tensors, column-major) and n0 (32 or 64, plan-less items)."""
+    X (CUDA tensors, column-major), n0 (32 or 64, plan-less items) and
+    optionally tile_cols (8, 16 or 32 columns per output tile; default: by k)."""
 
     def __init__(self, systems, dtype="f64", arena=None):
         """arena: optional uint8 CUDA tensor to lay the batch out in (no
@@ -442,6 +443,7 @@ class Batch:
                 it.L, it.ldl, it.n0 = L.data_ptr(), _ld(L), int(sy.get("n0", 32))
                 self._keep.append(L)
             it.B, it.ldb, it.X, it.ldx, it.n, it.k = B.data_ptr(), _ld(B), X.data_ptr(), _ld(X), n, k
+            it.tile_cols = int(sy.get("tile_cols", 0))
             self._keep += [B, X]
         return items
 

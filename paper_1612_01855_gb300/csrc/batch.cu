@@ -435,7 +435,7 @@ int build_batch(const trsm_batch_item* items, int count, trsm_batch_s* b, void* 
     a.R = static_cast<int>((a.n0 + trsm::TILE - 1) / trsm::TILE);
     const int64_t mlast = a.n - static_cast<int64_t>(a.N - 1) * a.n0;
     a.Rlast = static_cast<int>((mlast + trsm::TILE - 1) / trsm::TILE);
-    a.cw = a.k <= 8 ? 8 : a.k <= 16 ? 16 : trsm::TILE;
+    a.cw = it.tile_cols != 0 ? static_cast<int>(it.tile_cols) : a.k <= 8 ? 8 : a.k <= 16 ? 16 : trsm::TILE;
     a.C = static_cast<int>((a.k + a.cw - 1) / a.cw);
     a.total_rt = static_cast<int64_t>(a.N - 1) * a.R + a.Rlast;
     a.inv_tasks = planned ? 0 : a.N;
@@ -600,6 +600,7 @@ static int validate_items(const trsm_batch_item* items, int count, int dtype) {
     const trsm_batch_item& it = items[s];
     if (it.n < 1 || it.k < 1 || !it.B || !it.X || it.ldb < it.n || it.ldx < it.n || it.B == it.X)
       return TRSM_EINVAL;
+    if (!(it.tile_cols == 0 || it.tile_cols == 8 || it.tile_cols == 16 || it.tile_cols == 32)) return TRSM_EINVAL;
     if (it.plan) {
       if (dtype != TRSM_F64) return TRSM_EINVAL;
       int64_t pn = 0;

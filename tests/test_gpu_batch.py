@@ -124,3 +124,38 @@ def test_batch_argument_errors(cuda_lib):
     systems[1]["X"] = systems[1]["B"]  # X must not alias B
     with pytest.raises(g.TrsmError):
         g.Batch(systems)
+
+
+def test_batch_tile_shapes_give_identical_results(cuda_lib):
+    """8-, 16- and 32-wide column tiles only change which thread computes
+    which output, not the order of any sum: results are bitwise equal."""
+    import torch
+    import paper_1612_01855_gb300 as g
+    systems = _systems(24, 400, 40, seed=8)
+    ref = None
+    for tile in (0, 8, 16, 32):
+        for sy in systems:
+            sy["tile_cols"] = tile
+            sy["X"].fill_(float("nan"))
+        b = g.Batch(systems)
+        b.run()
+        assert b.status()[0] == 0
+        got = [sy["X"].clone() for sy in systems]
+        if ref is None:
+            ref = got
+            for sy in systems:
+                assert _rel(sy["X"].cpu().numpy(), oracle.forward_subst(sy["Lh"], sy["Bh"])) < TOL64
+        else:
+            assert all(torch.equal(a, c) for a, c in zip(ref, got)), tile
+    systems[0]["tile_cols"] = 12
+    with pytest.raises(g.TrsmError):
+        g.Batch(systems)
+
+
+def test_autotuner_choices(cuda_lib):
+    from paper_1612_01855_gb300 import autotune
+    table = autotune.tune_batch("f64", count=12, kmax=32, reps=1)
+    assert set(table) == set(range(len(autotune.BUCKETS)))
+    for n0, tile in table.values():
+        assert n0 in autotune.N0_CANDIDATES and tile in autotune.TILE_CANDIDATES
+    assert autotune.choose(700, "f64", table) == table[autotune.bucket_of(700)]

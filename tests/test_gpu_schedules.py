@@ -42,3 +42,17 @@ def test_schedules_agree_and_are_deterministic(cuda_lib):
     ref = xs["dag"].cpu().numpy()
     for s, x in xs.items():
         assert np.max(np.abs(x.cpu().numpy() - ref)) / np.max(np.abs(ref)) < TOL, s
+
+
+def test_schedule_autotuner_picks_a_correct_fastest(cuda_lib):
+    import paper_1612_01855_gb300 as g
+    from paper_1612_01855_gb300 import autotune
+    L, B = inputs.well_conditioned(1024, 48, seed=11)
+    p = g.trsm_plan(_dev(L), 128)
+    Bd = _dev(B)
+    best, times = autotune.tune_schedule(p, Bd)
+    assert best in times and times[best] == min(times.values())
+    X = g.trsm_solve_schedule(p, Bd, schedule=best)
+    g.trsm_sync_status(p)
+    want = oracle.forward_subst(L, B)
+    assert np.max(np.abs(X.cpu().numpy() - want)) / np.max(np.abs(want)) < TOL

@@ -58,3 +58,11 @@ def test_mixed_requests_need_a_mixed_plan():
     assert [r.rid for r in srv.pending] == [1]
     # the refinement's workspace is larger than the FP64 batch share
     assert Server.request_bytes(128, 4, mixed=True) > Server.request_bytes(128, 4)
+
+
+def test_autotune_buckets_and_paper_rule():
+    from paper_1612_01855_gb300 import autotune
+    assert [autotune.bucket_of(n) for n in (1, 63, 64, 255, 256, 1024, 5000)] == [0, 0, 1, 2, 3, 4, 4]
+    assert autotune.paper_rule_n0(16384, 256) == 2048 and autotune.paper_rule_n0(100, 10000) == 100
+    table = {0: (32, 0), 1: (64, 32)}
+    assert autotune.choose(100, table=table) == (64, 32) and autotune.choose(900, table=table) == (32, 0)
