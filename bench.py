@@ -722,7 +722,8 @@ def run_ours(args, rank, world, local):
     if rank == 0 and not args.no_mixed and not args.shapes:
         # FP32 diagonal multiplies at the mixed path's block size, and the
         # FP64 ones at the FP64 path's block size (where they cost least)
-        mixed = (precision_study(g, torch, 16384, 4096, MIXED_N0, [2], ["tf32", "bf16x3"], [True], dd_cols=2) +
+        mixed = (precision_study(g, torch, 16384, 4096, MIXED_N0, [2], ["tf32", "bf16x3", "fp16x3"], [True],
+                                 dd_cols=2) +
                  precision_study(g, torch, 16384, 4096, 256, [2], ["tf32"], [False], dd_cols=2))
 
     batched = None
@@ -738,7 +739,7 @@ def run_ours(args, rank, world, local):
         schedules = schedules_study(g, torch, dev_in, outs, shapes, n0s, fp64_peak=fp64_peak)
 
     if args.precision and rank == 0:
-        for rec in precision_study(g, torch, 16384, 4096, MIXED_N0, [2, 4, 6], ["tf32", "bf16", "bf16x3"],
+        for rec in precision_study(g, torch, 16384, 4096, MIXED_N0, [2, 4, 6], ["tf32", "bf16", "bf16x3", "fp16x3"],
                                    [False, True], residuals=("sliced", "adaptive")):
             print(json.dumps({"precision_study": True, **rec}), flush=True)
 

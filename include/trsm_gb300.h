@@ -50,6 +50,10 @@ extern "C" {
  * at 1.5x the tensor work of tf32): the inner solve contracts the error far
  * faster on ill-conditioned systems */
 #define TRSM_INNER_BF16X3 3
+/* split fp16: hi + lo fp16 planes, three products (about 22 significant bits
+ * per factor); the panels and each block row of the correction are scaled by
+ * powers of two into fp16's range and the update undoes both */
+#define TRSM_INNER_FP16X3 4
 /* Residual of the mixed-precision solve. */
 #define TRSM_RESIDUAL_SLICED 0   /* FP64-class, bf16 tensor cores, 7 integer digit planes */
 #define TRSM_RESIDUAL_FP64 1     /* FP64 fused multiply-add                                */
@@ -146,8 +150,8 @@ int trsm_solve_noalloc(trsm_handle_t h, const double* B_dev, int64_t k, int64_t 
  * (no counterpart in the paper, which works in exact arithmetic; the block
  * structure is its Algorithm It-Inv-TRSM):
  *   - the off-diagonal block columns L(T_{i+1}, S_i) in `inner` precision
- *     (TRSM_INNER_BF16, TRSM_INNER_TF32 or TRSM_INNER_BF16X3), for the
- *     tensor-core updates;
+ *     (TRSM_INNER_BF16, TRSM_INNER_TF32, TRSM_INNER_BF16X3 or
+ *     TRSM_INNER_FP16X3), for the tensor-core updates;
  *   - the original diagonal blocks and diagonal of L in FP64;
  *   - eight 6-bit integer digit planes of the strictly lower L, for the
  *     FP64-class residual.

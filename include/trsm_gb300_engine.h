@@ -20,7 +20,8 @@ extern "C" {
  *   mode = 1: fp32 read as tf32, K a multiple of 4;
  *   mode = 2: split bf16: A is two bf16 planes (hi, lo) of M x K, one after
  *             the other, B two planes of N x K; C = Ah Bh^T + Ah Bl^T +
- *             Al Bh^T; K a multiple of 8.
+ *             Al Bh^T; K a multiple of 8;
+ *   mode = 3: the same with fp16 planes.
  *   C_dev: fp32, column-major M x N (leading dimension M), overwritten.
  *   err_dev: device int, set to 1 if a pipeline wait gave up (never in
  *            correct operation).  Asynchronous on `stream`. */

@@ -28,6 +28,7 @@ TRSM_ENOCONV = -7
 TRSM_INNER_BF16 = 1
 TRSM_INNER_TF32 = 2
 TRSM_INNER_BF16X3 = 3
+TRSM_INNER_FP16X3 = 4
 TRSM_RESIDUAL_SLICED = 0
 TRSM_RESIDUAL_FP64 = 1
 TRSM_RESIDUAL_SLICED8 = 2
@@ -253,10 +254,11 @@ def trsm_solve_noalloc(plan, B, X):
 
 
 def trsm_plan_mixed(plan, L, inner="tf32"):
-    """Adds the mixed-precision data (inner = "bf16", "tf32" or "bf16x3", the
-    split-bf16 update) to a plan made from L."""
+    """Adds the mixed-precision data (inner = "bf16", "tf32", "bf16x3" or
+    "fp16x3", the split updates) to a plan made from L."""
     L = _dev_matrix(L, "L")
-    code = {"bf16": TRSM_INNER_BF16, "tf32": TRSM_INNER_TF32, "bf16x3": TRSM_INNER_BF16X3}[inner]
+    code = {"bf16": TRSM_INNER_BF16, "tf32": TRSM_INNER_TF32, "bf16x3": TRSM_INNER_BF16X3,
+            "fp16x3": TRSM_INNER_FP16X3}[inner]
     _check(load_library().trsm_plan_mixed(plan.handle, ctypes.c_void_p(L.data_ptr()), _ld(L), code,
                                           _stream(L)), "trsm_plan_mixed")
     plan.inner = inner

@@ -14,14 +14,19 @@
 // inner_solve is the right-looking form of Algorithm It-Inv-TRSM: for every
 // block row i, D_i = L~_ii W_i with the FP64 inverse of the diagonal block
 // (DFMA tile kernel), then W(T_{i+1}) -= L(T_{i+1}, S_i) D_i as one
-// tcgen05 GEMM with bf16, tf32 or split bf16 (hi + lo planes, three
-// products) operands and FP32 accumulation; W is the FP32 working copy of R.
+// tcgen05 GEMM with bf16, tf32, split bf16 or split fp16 (hi + lo planes,
+// three products) operands and FP32 accumulation; W is the FP32 working copy
+// of R.  The fp16 planes are scaled by powers of two into fp16's range: each
+// off-diagonal panel once at plan time, each D_i after its diagonal
+// multiply (from its maximum), the GEMM undoing both through a device
+// factor on alpha.
 //
 // The residual is either the digit-sliced tensor-core product of sliced.cu
 // (seven planes: about 2^-40 relative to |L||X|; eight: about 2^-46; or
 // seven until the updates stagnate above tol, then eight) or a plain FP64
 // DFMA product.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -44,6 +49,7 @@ struct MixedPlan {
   double* dblk = nullptr;   // the original diagonal blocks of L, N x n0 x n0 (FP64 residual)
   void* lsl = nullptr;      // digit planes of the strictly lower L
   SlicedOperand Ls;
+  int* panel_exp = nullptr; // split fp16: panel i is stored times 2^panel_exp[i]
   size_t bytes = 0;         // device bytes held by the fields above
 };
 
@@ -56,6 +62,7 @@ void mixed_release(trsm_plan_s* h) {
   if (mp->diag) cudaFree(mp->diag);
   if (mp->dblk) cudaFree(mp->dblk);
   if (mp->lsl) cudaFree(mp->lsl);
+  if (mp->panel_exp) cudaFree(mp->panel_exp);
   delete mp;
   h->mixed = nullptr;
 }
@@ -99,7 +106,103 @@ struct LowP<2> {
   }
 };
 
-inline int mode_of(int inner) { return inner == TRSM_INNER_TF32 ? 1 : inner == TRSM_INNER_BF16X3 ? 2 : 0; }
+// Split fp16: the planes need a scale known only after the whole D_i is
+// formed, so the diagonal multiply writes D alone and pack_dt_f16_kernel
+// makes the planes.
+template <>
+struct LowP<3> {
+  using T = __half;
+  static constexpr int kPlanes = 2;
+  __device__ static void put(T*, int64_t, double) {}
+};
+
+inline int mode_of(int inner) {
+  return inner == TRSM_INNER_TF32 ? 1 : inner == TRSM_INNER_BF16X3 ? 2 : inner == TRSM_INNER_FP16X3 ? 3 : 0;
+}
+
+// Exponent e with |x| < 2^e for the largest |x| recorded as the bit pattern
+// of a non-negative double (0 when nothing was recorded).
+__device__ __forceinline__ int exp_above(unsigned long long bits) {
+  if (bits == 0) return 0;
+  const int E = static_cast<int>(bits >> 52);
+  return E != 0 ? E - 1022 : -1022;
+}
+
+// Largest |L| of each off-diagonal panel, as ordered bit patterns.
+__global__ void panel_max_kernel(const double* __restrict__ L, int64_t ldl, int64_t n, int64_t n0,
+                                 unsigned long long* __restrict__ pmax) {
+  const int64_t i = blockIdx.y;
+  const int64_t rows = n - (i + 1) * n0;
+  if (rows <= 0) return;
+  unsigned long long mb = 0;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < rows * n0;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = e % rows, c = e / rows;  // column-major walk over the panel
+    const unsigned long long b =
+        static_cast<unsigned long long>(__double_as_longlong(L[(i * n0 + c) * ldl + (i + 1) * n0 + r])) &
+        ~(1ull << 63);
+    mb = b > mb ? b : mb;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long b = __shfl_xor_sync(0xffffffffu, mb, o);
+    mb = b > mb ? b : mb;
+  }
+  if ((threadIdx.x & 31) == 0 && mb) atomicMax(pmax + i, mb);
+}
+
+// Split-fp16 panels: hi = fp16(v 2^s), lo = fp16(v 2^s - hi) with
+// s = 14 - e(panel maximum), so that every stored value is below 2^14.
+__global__ void pack_panels_f16_kernel(const double* __restrict__ L, int64_t ldl, int64_t n, int64_t n0, int64_t n0p,
+                                       const unsigned long long* __restrict__ pmax, __half* __restrict__ out,
+                                       int* __restrict__ panel_exp) {
+  const int64_t i = blockIdx.y;
+  const int64_t rows = n - (i + 1) * n0;
+  if (rows <= 0) return;
+  const int sc = 14 - exp_above(pmax[i]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) panel_exp[i] = sc;
+  __half* P = out + 2 * panel_off(i, n, n0, n0p);
+  const int64_t total = rows * n0p;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = e / n0p, c = e % n0p;
+    const double v = (c < n0) ? ldexp(L[(i * n0 + c) * ldl + (i + 1) * n0 + r], sc) : 0.0;
+    const __half hi = __double2half(v);
+    P[e] = hi;
+    P[total + e] = __double2half(v - static_cast<double>(__half2float(hi)));
+  }
+}
+
+// D_i (FP64, n0 x k at D + s0) into split-fp16 planes of Dt (k x n0p, K-major)
+// scaled by 2^sd, sd = 14 - e(max |D_i|); gscale = 2^-(panel_exp + sd)
+// undoes both scales in the update GEMM.
+__global__ void pack_dt_f16_kernel(const double* __restrict__ D, int64_t ldd, int64_t s0, int m, int64_t k,
+                                   int64_t n0p, const unsigned long long* __restrict__ dmax, const int* panel_exp,
+                                   __half* __restrict__ Dt, float* __restrict__ gscale) {
+  const int sd = 14 - exp_above(*dmax);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *gscale = ldexpf(1.f, -(*panel_exp + sd));
+  const int64_t plane = k * n0p;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < static_cast<int64_t>(m) * k;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t row = e % m, col = e / m;
+    const double v = ldexp(D[col * ldd + s0 + row], sd);
+    const __half hi = __double2half(v);
+    Dt[col * n0p + row] = hi;
+    Dt[plane + col * n0p + row] = __double2half(v - static_cast<double>(__half2float(hi)));
+  }
+}
+
+// Warp-level max of |v| folded into *dmax (as ordered bit patterns).
+__device__ __forceinline__ void fold_max(double local, unsigned long long* dmax) {
+  unsigned long long mb = static_cast<unsigned long long>(__double_as_longlong(fabs(local)));
+  if (isnan(local)) mb = 0x7FF8000000000000ull;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long b = __shfl_xor_sync(0xffffffffu, mb, o);
+    mb = b > mb ? b : mb;
+  }
+  if ((threadIdx.x & 31) == 0 && mb) atomicMax(dmax, mb);
+}
 inline size_t mode_bytes(int mode) { return mode == 0 ? 2 : 4; }  // bytes per element, all planes
 
 template <int kMode>
@@ -146,7 +249,7 @@ template <int kMode, class TC>
 __device__ __forceinline__ void s_tile(const double* __restrict__ Lt, int64_t ldt, const float* __restrict__ W,
                                        int64_t ldw, double* __restrict__ D, int64_t ldd,
                                        typename LowP<kMode>::T* __restrict__ Dt, int64_t n0p, int64_t s0, int m,
-                                       int64_t k, int r, int j, TileSmemT<TC>& sm) {
+                                       int64_t k, int r, int j, TileSmemT<TC>& sm, unsigned long long* dmax) {
   const int mr = min(TILE, m - r * TILE);
   const int nc = static_cast<int>(imin64(TILE, k - static_cast<int64_t>(j) * TILE));
   TC acc[TM][TN];
@@ -169,6 +272,14 @@ __device__ __forceinline__ void s_tile(const double* __restrict__ Lt, int64_t ld
       LowP<kMode>::put(Dt + col * n0p + row, k * n0p, v);
     }
   }
+  if constexpr (kMode == 3) {
+    double mx = 0.0;  // outputs outside the tile are zero
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+      for (int b = 0; b < TN; ++b) mx = fmax(mx, fabs(static_cast<double>(acc[a][b])));
+    fold_max(mx, dmax);
+  }
 }
 
 // TC = double: FP64 DFMA with the FP64 inverses (the default); TC = float:
@@ -178,12 +289,13 @@ __global__ void __launch_bounds__(NTHREADS) s_step_kernel(const double* __restri
                                                           const float* __restrict__ W, int64_t ldw,
                                                           double* __restrict__ D, int64_t ldd,
                                                           typename LowP<kMode>::T* __restrict__ Dt,
-                                                          int64_t n0p, int64_t s0, int m, int64_t k) {
+                                                          int64_t n0p, int64_t s0, int m, int64_t k,
+                                                          unsigned long long* dmax) {
   __shared__ TileSmemT<TC> sm;
   const int R = (m + TILE - 1) / TILE;
   const int p = blockIdx.x, j = blockIdx.y;
-  s_tile<kMode, TC>(Lt, ldt, W, ldw, D, ldd, Dt, n0p, s0, m, k, p, j, sm);
-  if (R - 1 - p != p) s_tile<kMode, TC>(Lt, ldt, W, ldw, D, ldd, Dt, n0p, s0, m, k, R - 1 - p, j, sm);
+  s_tile<kMode, TC>(Lt, ldt, W, ldw, D, ldd, Dt, n0p, s0, m, k, p, j, sm, dmax);
+  if (R - 1 - p != p) s_tile<kMode, TC>(Lt, ldt, W, ldw, D, ldd, Dt, n0p, s0, m, k, R - 1 - p, j, sm, dmax);
 }
 
 // The same step in FP32 arithmetic (TRSM_SOLVE_S_FP32), register-blocked
@@ -203,7 +315,7 @@ template <int kMode>
 __device__ __forceinline__ void s32_tile(const double* __restrict__ Lt, int64_t ldt, const float* __restrict__ W,
                                          int64_t ldw, double* __restrict__ D, int64_t ldd,
                                          typename LowP<kMode>::T* __restrict__ Dt, int64_t n0p, int64_t s0, int m,
-                                         int64_t k, int r, int j, S32Smem& sm) {
+                                         int64_t k, int r, int j, S32Smem& sm, unsigned long long* dmax) {
   const int tid = threadIdx.x;
   const int ty = tid >> 4, tx = tid & 15;
   const int mr = min(kS32Tile, m - r * kS32Tile);
@@ -255,6 +367,14 @@ __device__ __forceinline__ void s32_tile(const double* __restrict__ Lt, int64_t 
       LowP<kMode>::put(Dt + col * n0p + row, k * n0p, v);
     }
   }
+  if constexpr (kMode == 3) {
+    double mx = 0.0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) mx = fmax(mx, fabs(static_cast<double>(acc[i][c])));
+    fold_max(mx, dmax);
+  }
 }
 
 template <int kMode>
@@ -262,12 +382,34 @@ __global__ void __launch_bounds__(kS32Threads) s_step32_kernel(const double* __r
                                                                const float* __restrict__ W, int64_t ldw,
                                                                double* __restrict__ D, int64_t ldd,
                                                                typename LowP<kMode>::T* __restrict__ Dt,
-                                                               int64_t n0p, int64_t s0, int m, int64_t k) {
+                                                               int64_t n0p, int64_t s0, int m, int64_t k,
+                                                               unsigned long long* dmax) {
   __shared__ __align__(16) S32Smem sm;
   const int R = (m + kS32Tile - 1) / kS32Tile;
   const int p = blockIdx.x, j = blockIdx.y;
-  s32_tile<kMode>(Lt, ldt, W, ldw, D, ldd, Dt, n0p, s0, m, k, p, j, sm);
-  if (R - 1 - p != p) s32_tile<kMode>(Lt, ldt, W, ldw, D, ldd, Dt, n0p, s0, m, k, R - 1 - p, j, sm);
+  s32_tile<kMode>(Lt, ldt, W, ldw, D, ldd, Dt, n0p, s0, m, k, p, j, sm, dmax);
+  if (R - 1 - p != p) s32_tile<kMode>(Lt, ldt, W, ldw, D, ldd, Dt, n0p, s0, m, k, R - 1 - p, j, sm, dmax);
+}
+
+// Launches the diagonal-block multiply of one block row in the given
+// inner precision: FP64 (DFMA) or FP32 arithmetic; blocks of 512 rows and
+// more take the register-blocked FP32 tile, which gives smaller blocks too
+// few CTAs (measured: n0 = 256 slower, 1024 faster).
+template <int kMode>
+void launch_s_step(bool s32, const double* Lt, int64_t ldt, const float* W, int64_t ld, double* D, void* Dt,
+                   int64_t n0p, int64_t s0, int m, int64_t k, unsigned long long* dmax, cudaStream_t s) {
+  using T = typename LowP<kMode>::T;
+  T* dt = static_cast<T*>(Dt);
+  const int R = (m + TILE - 1) / TILE;
+  const dim3 g(static_cast<unsigned>((R + 1) / 2), static_cast<unsigned>((k + TILE - 1) / TILE));
+  const int R32 = (m + kS32Tile - 1) / kS32Tile;
+  const dim3 g32(static_cast<unsigned>((R32 + 1) / 2), static_cast<unsigned>((k + kS32Tile - 1) / kS32Tile));
+  if (!s32)
+    s_step_kernel<kMode, double><<<g, NTHREADS, 0, s>>>(Lt, ldt, W, ld, D, ld, dt, n0p, s0, m, k, dmax);
+  else if (m < 512)
+    s_step_kernel<kMode, float><<<g, NTHREADS, 0, s>>>(Lt, ldt, W, ld, D, ld, dt, n0p, s0, m, k, dmax);
+  else
+    s_step32_kernel<kMode><<<g32, kS32Threads, 0, s>>>(Lt, ldt, W, ld, D, ld, dt, n0p, s0, m, k, dmax);
 }
 
 // max that keeps a NaN once it has been seen (fmax would drop it)
@@ -361,7 +503,8 @@ using trsm::MixedPlan;
 
 extern "C" int trsm_plan_mixed(trsm_handle_t h, const double* L_dev, int64_t ldl, int inner, void* stream) {
   if (!h || !L_dev || ldl < h->n ||
-      (inner != TRSM_INNER_BF16 && inner != TRSM_INNER_TF32 && inner != TRSM_INNER_BF16X3))
+      (inner != TRSM_INNER_BF16 && inner != TRSM_INNER_TF32 && inner != TRSM_INNER_BF16X3 &&
+       inner != TRSM_INNER_FP16X3))
     return TRSM_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   trsm::mixed_release(h);
@@ -387,7 +530,20 @@ extern "C" int trsm_plan_mixed(trsm_handle_t h, const double* L_dev, int64_t ldl
   if (e == cudaSuccess && panel_elems > 0) {
     dim3 grid(static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((n * mp->n0p + 255) / 256, 1024))),
               static_cast<unsigned>(N - 1));
-    if (mode == 1)
+    if (mode == 3) {
+      unsigned long long* pmax = nullptr;
+      e = cudaMallocAsync(reinterpret_cast<void**>(&pmax), sizeof(unsigned long long) * N, s);
+      if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&mp->panel_exp), sizeof(int) * N);
+      if (e == cudaSuccess) e = cudaMemsetAsync(pmax, 0, sizeof(unsigned long long) * N, s);
+      if (e == cudaSuccess) {
+        trsm::panel_max_kernel<<<grid, 256, 0, s>>>(L_dev, ldl, n, n0, pmax);
+        trsm::pack_panels_f16_kernel<<<grid, 256, 0, s>>>(L_dev, ldl, n, n0, mp->n0p, pmax,
+                                                          static_cast<__half*>(mp->panels), mp->panel_exp);
+        trsm::count_launch(2);
+      }
+      if (pmax) cudaFreeAsync(pmax, s);
+      mp->bytes += sizeof(int) * N;
+    } else if (mode == 1)
       trsm::pack_panels_kernel<1><<<grid, 256, 0, s>>>(L_dev, ldl, n, n0, mp->n0p, static_cast<float*>(mp->panels));
     else if (mode == 2)
       trsm::pack_panels_kernel<2><<<grid, 256, 0, s>>>(L_dev, ldl, n, n0, mp->n0p,
@@ -454,6 +610,10 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
   off = trsm::align256(off + trsm::sliced_partial_bytes(n, k));
   const size_t oNorm = off;
   off = trsm::align256(off + 2 * sizeof(unsigned long long) + sizeof(int));
+  const size_t oDmax = off;  // per block row: max |D_i| (split fp16 scaling)
+  off = trsm::align256(off + sizeof(unsigned long long) * N);
+  const size_t oGscale = off;
+  off = trsm::align256(off + sizeof(float) * N);
   unsigned char* ws = nullptr;
   cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), off, s);
   if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? TRSM_ENOMEM : TRSM_ECUDA;
@@ -464,6 +624,8 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
   trsm::SlicedOperand Xs = trsm::sliced_operand_view(ws + oXs, k, n);
   unsigned long long* norms = reinterpret_cast<unsigned long long*>(ws + oNorm);
   int* err = reinterpret_cast<int*>(ws + oNorm + 2 * sizeof(unsigned long long));
+  unsigned long long* dmax = reinterpret_cast<unsigned long long*>(ws + oDmax);
+  float* gscale = reinterpret_cast<float*>(ws + oGscale);
 
   int rc = TRSM_SUCCESS;
   e = cudaMemsetAsync(err, 0, sizeof(int), s);
@@ -477,6 +639,8 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
   int it = 0;
   for (it = 1; it <= max_iter && e == cudaSuccess; ++it) {
     // ---- D = inner_solve(R) ----
+    e = cudaMemsetAsync(dmax, 0, sizeof(unsigned long long) * N, s);
+    if (e != cudaSuccess) break;
     trsm::to_float_kernel<<<trsm::grid_nk(n, k), 256, 0, s>>>(R, ld, W, ld, n, k);
     trsm::count_launch();
     for (int64_t i = 0; i < N && e == cudaSuccess; ++i) {
@@ -484,45 +648,29 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
       const int m = static_cast<int>(std::min(n0, n - s0));
       const int R = (m + trsm::TILE - 1) / trsm::TILE;
       dim3 g(static_cast<unsigned>((R + 1) / 2), static_cast<unsigned>((k + trsm::TILE - 1) / trsm::TILE));
-      const int R32 = (m + trsm::kS32Tile - 1) / trsm::kS32Tile;
-      dim3 g32(static_cast<unsigned>((R32 + 1) / 2), static_cast<unsigned>((k + trsm::kS32Tile - 1) / trsm::kS32Tile));
-      // the 64 x 64 FP32 tile pays off from 512-row blocks; smaller blocks
-      // give it too few CTAs (measured: n0 = 256 slower, 1024 faster)
-      const bool wide = m >= 512;
-      if (mode == 1 && !s32)
-        trsm::s_step_kernel<1, double><<<g, trsm::NTHREADS, 0, s>>>(h->Lt, h->ldt, W, ld, D, ld,
-                                                                     static_cast<float*>(Dt), n0p, s0, m, k);
-      else if (mode == 1 && !wide)
-        trsm::s_step_kernel<1, float><<<g, trsm::NTHREADS, 0, s>>>(h->Lt, h->ldt, W, ld, D, ld,
-                                                                    static_cast<float*>(Dt), n0p, s0, m, k);
-      else if (mode == 1)
-        trsm::s_step32_kernel<1><<<g32, trsm::kS32Threads, 0, s>>>(h->Lt, h->ldt, W, ld, D, ld,
-                                                                    static_cast<float*>(Dt), n0p, s0, m, k);
-      else if (mode == 2 && !s32)
-        trsm::s_step_kernel<2, double><<<g, trsm::NTHREADS, 0, s>>>(
-            h->Lt, h->ldt, W, ld, D, ld, static_cast<__nv_bfloat16*>(Dt), n0p, s0, m, k);
-      else if (mode == 2 && !wide)
-        trsm::s_step_kernel<2, float><<<g, trsm::NTHREADS, 0, s>>>(
-            h->Lt, h->ldt, W, ld, D, ld, static_cast<__nv_bfloat16*>(Dt), n0p, s0, m, k);
-      else if (mode == 2)
-        trsm::s_step32_kernel<2><<<g32, trsm::kS32Threads, 0, s>>>(
-            h->Lt, h->ldt, W, ld, D, ld, static_cast<__nv_bfloat16*>(Dt), n0p, s0, m, k);
-      else if (!s32)
-        trsm::s_step_kernel<0, double><<<g, trsm::NTHREADS, 0, s>>>(
-            h->Lt, h->ldt, W, ld, D, ld, static_cast<__nv_bfloat16*>(Dt), n0p, s0, m, k);
-      else if (!wide)
-        trsm::s_step_kernel<0, float><<<g, trsm::NTHREADS, 0, s>>>(
-            h->Lt, h->ldt, W, ld, D, ld, static_cast<__nv_bfloat16*>(Dt), n0p, s0, m, k);
-      else
-        trsm::s_step32_kernel<0><<<g32, trsm::kS32Threads, 0, s>>>(
-            h->Lt, h->ldt, W, ld, D, ld, static_cast<__nv_bfloat16*>(Dt), n0p, s0, m, k);
+      unsigned long long* dmax_i = dmax + i;
+      switch (mode) {
+        case 1: trsm::launch_s_step<1>(s32, h->Lt, h->ldt, W, ld, D, Dt, n0p, s0, m, k, dmax_i, s); break;
+        case 2: trsm::launch_s_step<2>(s32, h->Lt, h->ldt, W, ld, D, Dt, n0p, s0, m, k, dmax_i, s); break;
+        case 3: trsm::launch_s_step<3>(s32, h->Lt, h->ldt, W, ld, D, Dt, n0p, s0, m, k, dmax_i, s); break;
+        default: trsm::launch_s_step<0>(s32, h->Lt, h->ldt, W, ld, D, Dt, n0p, s0, m, k, dmax_i, s); break;
+      }
       trsm::count_launch();
       e = cudaGetLastError();
       if (e == cudaSuccess && i < N - 1) {
         const int64_t rows = n - (i + 1) * n0;
         const unsigned char* P =
             static_cast<const unsigned char*>(mp->panels) + esz * trsm::panel_off(i, n, n0, n0p);
-        if (mode == 2)
+        if (mode == 3) {
+          trsm::pack_dt_f16_kernel<<<trsm::grid_nk(m, 1).x * 8, 256, 0, s>>>(D, ld, s0, m, k, n0p, dmax_i,
+                                                                             mp->panel_exp + i,
+                                                                             static_cast<__half*>(Dt), gscale + i);
+          trsm::count_launch();
+          e = cudaGetLastError();
+          if (e == cudaSuccess)
+            e = trsm::tc::gemm_split_f16(P, n0p, rows * n0p, Dt, n0p, k * n0p, W + (i + 1) * n0, ld, rows, k, n0p,
+                                         -1.f, gscale + i, 1.f, err, s);
+        } else if (mode == 2)
           e = trsm::tc::gemm_split_bf16(P, n0p, rows * n0p, Dt, n0p, k * n0p, W + (i + 1) * n0, ld, rows, k, n0p,
                                         -1.f, 1.f, err, s);
         else

@@ -175,14 +175,16 @@ __device__ __forceinline__ uint64_t desc_kmajor(uint32_t saddr) {
 }
 
 // Instruction descriptor: FP32 accumulate, A and B K-major, M = 128.
-// BF16 inputs (kind::f16, format 1) or TF32 inputs (kind::tf32, format 2).
-__host__ __device__ constexpr uint32_t idesc_m128(int n, bool tf32) {
+// Operand format fmt (the same for A and B): 0 FP16 or 1 BF16 (kind::f16),
+// 2 TF32 (kind::tf32).
+__host__ __device__ constexpr uint32_t idesc_m128_fmt(int n, uint32_t fmt) {
   return (1u << 4)                                   // D format: F32
-         | ((tf32 ? 2u : 1u) << 7)                   // A format
-         | ((tf32 ? 2u : 1u) << 10)                  // B format
+         | (fmt << 7)                                // A format
+         | (fmt << 10)                               // B format
          | (static_cast<uint32_t>(n >> 3) << 17)     // N / 8
          | (static_cast<uint32_t>(128 >> 4) << 24);  // M / 16
 }
+__host__ __device__ constexpr uint32_t idesc_m128(int n, bool tf32) { return idesc_m128_fmt(n, tf32 ? 2u : 1u); }
 
 }  // namespace tc
 }  // namespace trsm

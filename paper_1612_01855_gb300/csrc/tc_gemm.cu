@@ -62,6 +62,7 @@ struct StoreF32Epi {
   int64_t ldc;
   int M, N, nkb;
   float alpha, beta;
+  const float* scale = nullptr;  // optional device factor on alpha (set by an earlier kernel)
   struct State {};
   __device__ void tile(int&, int&) const {}
   __device__ void k_range(int, int, int& kb0, int& kb1, int& chunk) const {
@@ -75,13 +76,14 @@ struct StoreF32Epi {
     if (r >= M) return;
     float* base = C + static_cast<int64_t>(tn * BN + sl * 16) * ldc + r;
     const int ncol = min(16, N - (tn * BN + sl * 16));
+    const float a = scale ? alpha * __ldg(scale) : alpha;
     // all loads of the slab first, so that their latencies overlap
     float old[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) old[j] = (beta != 0.f && j < ncol) ? base[static_cast<int64_t>(j) * ldc] : 0.f;
 #pragma unroll
     for (int j = 0; j < 16; ++j)
-      if (j < ncol) base[static_cast<int64_t>(j) * ldc] = alpha * v[j] + beta * old[j];
+      if (j < ncol) base[static_cast<int64_t>(j) * ldc] = a * v[j] + beta * old[j];
   }
   __device__ void slab_done(State&, int, int, int, int, int) const {}
   __device__ void finish(State&, int, int, int, int) const {}
@@ -118,16 +120,17 @@ struct SplitPairs {
   __device__ static constexpr int g(int) { return 0; }
 };
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, bool kFp16 = false>
 cudaError_t split_gemm(const void* A, int64_t lda, int64_t a_plane, const void* B, int64_t ldb, int64_t b_plane,
                        float* C, int64_t ldc, int64_t M, int64_t N, int64_t K, float alpha, float beta, int* err,
-                       cudaStream_t s) {
-  using Cfg = TileCfg<false, BN, 2, 2, 1, STAGES>;
+                       cudaStream_t s, const float* scale = nullptr) {
+  // the tensor maps only move 2-byte elements: bf16 and fp16 planes alike
+  using Cfg = TileCfg<false, BN, 2, 2, 1, STAGES, 128, kFp16>;
   CUtensorMap ma, mb;
   if (!make_kmajor_map(&ma, A, false, K, M, lda, 2, a_plane, 128, 2, 128)) return cudaErrorInvalidValue;
   if (!make_kmajor_map(&mb, B, false, K, N, ldb, 2, b_plane, BN, 2, 128)) return cudaErrorInvalidValue;
   StoreF32Epi<BN> epi{C, ldc, static_cast<int>(M), static_cast<int>(N),
-                      static_cast<int>((K + Cfg::KB - 1) / Cfg::KB), alpha, beta};
+                      static_cast<int>((K + Cfg::KB - 1) / Cfg::KB), alpha, beta, scale};
   auto kern = tc_tile_kernel<Cfg, SplitPairs, StoreF32Epi<BN>>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(Cfg::SMEM_BYTES));
@@ -151,6 +154,16 @@ cudaError_t gemm_split_bf16(const void* A, int64_t lda, int64_t a_plane, const v
   return split_gemm<128, 3>(A, lda, a_plane, B, ldb, b_plane, C, ldc, M, N, K, alpha, beta, err, s);
 }
 
+cudaError_t gemm_split_f16(const void* A, int64_t lda, int64_t a_plane, const void* B, int64_t ldb,
+                           int64_t b_plane, float* C, int64_t ldc, int64_t M, int64_t N, int64_t K, float alpha,
+                           const float* scale, float beta, int* err, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+  const int kb = static_cast<int>((K * 2 + 127) / 128);
+  if (kb <= 8)
+    return split_gemm<64, 2, true>(A, lda, a_plane, B, ldb, b_plane, C, ldc, M, N, K, alpha, beta, err, s, scale);
+  return split_gemm<128, 3, true>(A, lda, a_plane, B, ldb, b_plane, C, ldc, M, N, K, alpha, beta, err, s, scale);
+}
+
 cudaError_t gemm_lowp(bool tf32, const void* A, int64_t lda, const void* B, int64_t ldb, float* C,
                       int64_t ldc, int64_t M, int64_t N, int64_t K, float alpha, float beta, int* err,
                       cudaStream_t s) {
@@ -171,13 +184,15 @@ cudaError_t gemm_lowp(bool tf32, const void* A, int64_t lda, const void* B, int6
 
 extern "C" int trsm_tc_gemm_selftest(int mode, const void* A_dev, const void* B_dev, float* C_dev,
                                      int64_t M, int64_t N, int64_t K, int* err_dev, void* stream) {
-  if (!A_dev || !B_dev || !C_dev || !err_dev || M < 1 || N < 1 || K < 1 || mode < 0 || mode > 2) return -1;
+  if (!A_dev || !B_dev || !C_dev || !err_dev || M < 1 || N < 1 || K < 1 || mode < 0 || mode > 3) return -1;
   if ((mode == 1 && K % 4) || (mode != 1 && K % 8)) return -1;  // TMA: 16-byte row strides
   if (((uintptr_t)A_dev | (uintptr_t)B_dev) & 15) return -1;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e =
-      mode == 2 ? trsm::tc::gemm_split_bf16(A_dev, K, M * K, B_dev, K, N * K, C_dev, M, M, N, K, 1.f, 0.f, err_dev, s)
-                : trsm::tc::gemm_lowp(mode == 1, A_dev, K, B_dev, K, C_dev, M, M, N, K, 1.f, 0.f, err_dev, s);
+      mode == 3 ? trsm::tc::gemm_split_f16(A_dev, K, M * K, B_dev, K, N * K, C_dev, M, M, N, K, 1.f, nullptr, 0.f,
+                                           err_dev, s)
+      : mode == 2 ? trsm::tc::gemm_split_bf16(A_dev, K, M * K, B_dev, K, N * K, C_dev, M, M, N, K, 1.f, 0.f, err_dev, s)
+                  : trsm::tc::gemm_lowp(mode == 1, A_dev, K, B_dev, K, C_dev, M, M, N, K, 1.f, 0.f, err_dev, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return -4;

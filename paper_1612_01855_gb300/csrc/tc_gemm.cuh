@@ -20,9 +20,10 @@
 namespace trsm {
 namespace tc {
 
-template <bool kTf32_, int BN_, int NSA_, int NSB_, int NG_, int STAGES_, int ROWB_ = 128>
+template <bool kTf32_, int BN_, int NSA_, int NSB_, int NG_, int STAGES_, int ROWB_ = 128, bool kFp16_ = false>
 struct TileCfg {
   static constexpr bool kTf32 = kTf32_;
+  static constexpr uint32_t FMT = kTf32_ ? 2u : kFp16_ ? 0u : 1u;  // operand format of the MMA
   static constexpr int BN = BN_;
   static constexpr int NSA = NSA_;
   static constexpr int NSB = NSB_;
@@ -55,7 +56,7 @@ __global__ void __launch_bounds__(192)
   constexpr int STAGES = Cfg::STAGES;
   constexpr int BN = Cfg::BN;
   constexpr int NG = Cfg::NG;
-  constexpr uint32_t IDESC = idesc_m128(BN, Cfg::kTf32);
+  constexpr uint32_t IDESC = idesc_m128_fmt(BN, Cfg::FMT);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));

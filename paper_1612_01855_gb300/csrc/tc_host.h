@@ -33,5 +33,13 @@ cudaError_t gemm_split_bf16(const void* A, int64_t lda, int64_t a_plane, const v
                             int64_t b_plane, float* C, int64_t ldc, int64_t M, int64_t N, int64_t K, float alpha,
                             float beta, int* err, cudaStream_t s);
 
+// As gemm_split_bf16 with FP16 planes (about 22 significant bits per
+// factor); C = alpha * (*scale) * (Ah Bh^T + Ah Bl^T + Al Bh^T) + beta C,
+// `scale` a device float written by an earlier kernel (NULL: 1).  The
+// callers scale the planes by powers of two to keep them in FP16 range.
+cudaError_t gemm_split_f16(const void* A, int64_t lda, int64_t a_plane, const void* B, int64_t ldb,
+                           int64_t b_plane, float* C, int64_t ldc, int64_t M, int64_t N, int64_t K, float alpha,
+                           const float* scale, float beta, int* err, cudaStream_t s);
+
 }  // namespace tc
 }  // namespace trsm

@@ -50,18 +50,20 @@ def test_engine_gemm(cuda_lib, tf32, M, N, K):
     assert np.max(np.abs(got - want) / (scale + 1e-30)) < 2e-6
 
 
+@pytest.mark.parametrize("fmt", ["bf16", "fp16"])
 @pytest.mark.parametrize("M,N,K", [(128, 128, 64), (300, 200, 520), (1024, 512, 1024), (129, 257, 200),
                                    (256, 64, 256)])
-def test_engine_split_bf16_gemm(cuda_lib, M, N, K):
-    """Split bf16 operands (hi + lo planes): C = Ah Bh^T + Ah Bl^T + Al Bh^T."""
+def test_engine_split_gemm(cuda_lib, M, N, K, fmt):
+    """Split operands (hi + lo planes of bf16 or fp16): C = Ah Bh^T + Ah Bl^T + Al Bh^T."""
     import torch
     rng = np.random.default_rng(M * N + K)
     A = rng.uniform(-1, 1, size=(M, K))
     B = rng.uniform(-1, 1, size=(N, K))
+    dt = torch.bfloat16 if fmt == "bf16" else torch.float16
 
     def split(X):
-        hi = torch.from_numpy(X).to(torch.bfloat16)
-        lo = torch.from_numpy(X - hi.double().numpy()).to(torch.bfloat16)
+        hi = torch.from_numpy(X).to(dt)
+        lo = torch.from_numpy(X - hi.double().numpy()).to(dt)
         return hi, lo
 
     Ah, Al = split(A)
@@ -71,7 +73,8 @@ def test_engine_split_bf16_gemm(cuda_lib, M, N, K):
     C = torch.full((N, M), float("nan"), dtype=torch.float32, device="cuda")
     err = torch.zeros(1, dtype=torch.int32, device="cuda")
     s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    rc = cuda_lib.trsm_tc_gemm_selftest(2, ctypes.c_void_p(At.data_ptr()), ctypes.c_void_p(Bt.data_ptr()),
+    rc = cuda_lib.trsm_tc_gemm_selftest(2 if fmt == "bf16" else 3, ctypes.c_void_p(At.data_ptr()),
+                                        ctypes.c_void_p(Bt.data_ptr()),
                                         ctypes.c_void_p(C.data_ptr()), M, N, K, ctypes.c_void_p(err.data_ptr()), s)
     assert rc == 0
     torch.cuda.synchronize()
@@ -85,4 +88,4 @@ def test_engine_split_bf16_gemm(cuda_lib, M, N, K):
     # against the unsplit FP64 product: the dropped lo*lo term and the
     # representation hi + lo (about 2^-16 each), far below bf16's 2^-8
     rel = np.max(np.abs(got - A @ B.T) / scale)
-    assert rel < 2.0 ** -14, rel
+    assert rel < (2.0 ** -14 if fmt == "bf16" else 2.0 ** -19), rel

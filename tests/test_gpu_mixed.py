@@ -18,7 +18,7 @@ def _rel(a, b):
     return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
 
 
-@pytest.mark.parametrize("inner", ["tf32", "bf16", "bf16x3"])
+@pytest.mark.parametrize("inner", ["tf32", "bf16", "bf16x3", "fp16x3"])
 @pytest.mark.parametrize("residual,s32", [("sliced", False), ("fp64", False), ("sliced", True)])
 @pytest.mark.parametrize("n,k,n0", [(1024, 64, 128), (1000, 37, 64), (300, 5, 300)])
 def test_mixed_well_conditioned(cuda_lib, inner, residual, s32, n, k, n0):
@@ -35,10 +35,10 @@ def test_mixed_well_conditioned(cuda_lib, inner, residual, s32, n, k, n0):
     print(f"mixed {inner}/{residual} n={n} k={k} n0={n0}: {iters} iterations, last update {upd:.2e}, rel err {err:.2e}")
     # the refinement's limit is the residual's accuracy: ~2^-40 of |L||X| (sliced), ~n eps (fp64)
     assert err < (5e-12 if residual == "sliced" else 1e-13)
-    assert iters <= {"tf32": 12, "bf16": 25, "bf16x3": 6}[inner]
+    assert iters <= {"tf32": 12, "bf16": 25, "bf16x3": 6, "fp16x3": 6}[inner]
 
 
-@pytest.mark.parametrize("inner", ["tf32", "bf16x3"])
+@pytest.mark.parametrize("inner", ["tf32", "bf16x3", "fp16x3"])
 @pytest.mark.parametrize("n,k,n0", [(1500, 70, 600), (2048, 33, 1024), (1100, 130, 512)])
 def test_mixed_wide_blocks_fp32_diagonal_multiply(cuda_lib, inner, n, k, n0):
     """Blocks of 512 rows and more take the 64 x 64 register-blocked FP32
@@ -102,9 +102,9 @@ def test_mixed_residual_planes_set_the_floor(cuda_lib):
 
 
 def test_mixed_split_inner_reaches_the_floor(cuda_lib):
-    """Diagonal graded from 1 to 1e-3: the split-bf16 update (about 16 bits
-    per factor) reaches the eight-plane residual's floor in no more sweeps
-    than tf32 (11 bits)."""
+    """Diagonal graded from 1 to 1e-3: the split updates (bf16: about 16
+    bits per factor; fp16, scaled into range: about 22) reach the eight-plane
+    residual's floor in no more sweeps than tf32 (11 bits)."""
     import paper_1612_01855_gb300 as g
     n, k, n0 = 2048, 8, 128
     L, B = inputs.graded_diagonal(n, k, 3, seed=5)
@@ -112,15 +112,16 @@ def test_mixed_split_inner_reaches_the_floor(cuda_lib):
     hi, lo = oracle.forward_subst_dd(L, B)
     ref = hi + lo
     out = {}
-    for inner in ("tf32", "bf16x3"):
+    for inner in ("tf32", "bf16x3", "fp16x3"):
         plan = g.trsm_plan(Ld, n0)
         g.trsm_plan_mixed(plan, Ld, inner)
         X, iters, upd = g.trsm_solve_mixed(plan, _dev(B), residual="sliced8", max_iter=40, tol=1e-12,
                                            raise_on_noconv=False)
         out[inner] = (_rel(X.cpu().numpy(), ref), iters, upd)
     print(f"graded c=3 n={n}, eight planes: {out}")
-    assert out["bf16x3"][0] < 1e-11
-    assert out["bf16x3"][1] <= out["tf32"][1]
+    for split in ("bf16x3", "fp16x3"):
+        assert out[split][0] < 1e-11
+        assert out[split][1] <= out["tf32"][1]
 
 
 def test_mixed_overflowing_solution_is_reported(cuda_lib):
