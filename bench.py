@@ -423,7 +423,7 @@ def serving_study(g, torch, nL=256, rates=(100, 300, 600, 1200), per_rate=300, s
     planned once; Poisson request streams at the given rates, each request a
     B with k log-uniform in [1, 2048] for a random resident L; continuous
     batching under an HBM budget.  The L with n >= mixed_min_n also carry a
-    mixed-precision plan (split-bf16 updates), and half of the requests on
+    mixed-precision plan (split-fp16 updates), and half of the requests on
     them ask for the refined mixed-precision solve (tol 1e-12) instead of
     FP64.  Reports solves/s and p50/p99 latency, overall and for the mixed
     requests."""
@@ -441,7 +441,7 @@ def serving_study(g, torch, nL=256, rates=(100, 300, 600, 1200), per_rate=300, s
         L = L.t().contiguous().t()
         plans.append(g.trsm_plan(L, 256 if n >= 1024 else 64))
         if n >= mixed_min_n:
-            g.trsm_plan_mixed(plans[-1], L, "bf16x3")
+            g.trsm_plan_mixed(plans[-1], L, "fp16x3")
         del L
     plan_s = time.perf_counter() - t0
     out = {"resident_L": nL, "plan_seconds": round(plan_s, 2),
