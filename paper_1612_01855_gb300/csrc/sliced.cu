@@ -167,6 +167,15 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
+// x 2^n, as ldexpf: one multiply by an exact power of two when 2^n is a
+// normal float (the product is then rounded once, like ldexpf's result),
+// the library call out of line otherwise.
+__device__ __noinline__ float scale2_slow(float x, int n) { return ldexpf(x, n); }
+__device__ __forceinline__ float scale2(float x, int n) {
+  if (n >= -126 && n <= 127) return x * __int_as_float((n + 127) << 23);
+  return scale2_slow(x, n);
+}
+
 // (h, l) += (bh, bl) in float-float arithmetic.
 __device__ __forceinline__ void ff_add(float& h, float& l, float bh, float bl) {
   float s, e;
@@ -251,16 +260,18 @@ struct ResidualEpi {
     for (int j = 0; j < 16; ++j) {
       if (j >= ncol) continue;
       const int sc = ea + eb[j] - 2 * kDigitBits;
-      float h = ldexpf(st.ph[j], sc), l = ldexpf(st.pl[j], sc);
+      float h = scale2(st.ph[j], sc), l = scale2(st.pl[j], sc);
       ff_add(h, l, o[j].x, o[j].y);
       base[static_cast<int64_t>(j) * M] = make_float2(h, l);
     }
   }
-  __device__ void finish(State&, int tm, int tn, int nchunks, int row) const {
+  // Final R for the columns of slabs [sl0, sl1) of the tile.
+  __device__ void finish(State&, int tm, int tn, int nchunks, int row, int sl0, int sl1) const {
     const int grow = tm * 128 + row;
     if (grow >= M) return;
     const double dg = Ld[static_cast<int64_t>(grow) * ldl + grow];
-    for (int c0 = 0; c0 < BN; c0 += 16) {
+#pragma unroll 1
+    for (int c0 = sl0 * 16; c0 < sl1 * 16; c0 += 16) {
       const int col0 = tn * BN + c0;
       const int ncol = min(16, N - col0);
       if (ncol <= 0) break;
@@ -297,7 +308,7 @@ struct ResidualEpi {
 // block group by group and within a group step by step, so the B planes
 // that several groups share are re-read from L2 within the block.  Roles as
 // in the generic engine: warp 0 lane 0 loads (one TMA per plane), warp 1
-// owns TMEM and issues the MMAs, warps 2-5 run the epilogue.
+// owns TMEM and issues the MMAs, warps 2-9 run the epilogue.
 constexpr int kBlkSteps = 4;
 
 template <int P>
@@ -318,6 +329,11 @@ struct Stream {
   static constexpr uint32_t SLOT = max2(max2(bytes(0), bytes(1)), bytes(2));
   static constexpr size_t SMEM_BYTES = 2 * static_cast<size_t>(SLOT) + 1024;
   static constexpr uint32_t TMEM_COLS = 512;
+  // Epilogue warps: two per TMEM lane quadrant, each draining half of the
+  // slabs, so that the MMAs, which wait for the drain at every chunk
+  // boundary, stand idle half as long as with one warp per quadrant.
+  static constexpr int kEpiWarps = 8;
+  static constexpr int kThreads = 64 + 32 * kEpiWarps;
   static_assert(SLOT % 1024 == 0 && B_SL % 1024 == 0, "swizzled tiles need 1024-byte alignment");
   static_assert(NG * BN <= 512, "accumulators exceed tensor memory");
   static_assert(SMEM_BYTES <= 227 * 1024, "two stages exceed shared memory");
@@ -342,7 +358,7 @@ __device__ __forceinline__ void for_items(int kb0, int kb1, int chunk, F&& f) {
 }
 
 template <int P>
-__global__ void __launch_bounds__(192)
+__global__ void __launch_bounds__(Stream<P>::kThreads, 1)
     stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                   const ResidualEpi<Stream<P>::BN> epi, int* err) {
   using S = Stream<P>;
@@ -368,7 +384,7 @@ __global__ void __launch_bounds__(192)
       tc::mbar_init(&empty_bar[q], 1);
     }
     tc::mbar_init(&tfull_bar, 1);
-    tc::mbar_init(&tempty_bar, 4);
+    tc::mbar_init(&tempty_bar, S::kEpiWarps);
     abort_sh = 0;
     tc::fence_mbar_init();
   }
@@ -435,15 +451,21 @@ __global__ void __launch_bounds__(192)
       });
     }
   } else {
-    const int q = warp & 3;
+    const int q = warp & 3;  // the TMEM lane quadrant this warp may read
     const int row = q * 32 + lane;
+    constexpr int kSlabs = BN / 16, kShares = S::kEpiWarps / 4;
+    constexpr int kPer = (kSlabs + kShares - 1) / kShares;
+    const int sl0 = ((warp - 2) / 4) * kPer, sl1 = min(kSlabs, sl0 + kPer);
     typename ResidualEpi<BN>::State st;
     epi.init(st);
     for (int c = 0; c < nchunks; ++c) {
       if (!tc::mbar_wait(&tfull_bar, c & 1, abort_flag)) break;
       tc::tc_fence_after();
-#pragma unroll
-      for (int sl = 0; sl < BN / 16; ++sl) {
+      // one slab at a time in a loop: unrolled over the slabs the epilogue
+      // is far larger than the instruction cache, and every chunk boundary
+      // then refetches it from L2 while the MMAs wait
+#pragma unroll 1
+      for (int sl = sl0; sl < sl1; ++sl) {
 #pragma unroll
         for (int g = 0; g < NG; ++g) {
           uint32_t r[16];
@@ -460,7 +482,7 @@ __global__ void __launch_bounds__(192)
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&tempty_bar);
     }
-    epi.finish(st, tm, tn, nchunks, row);
+    epi.finish(st, tm, tn, nchunks, row, sl0, sl1);
   }
   __syncthreads();
   if (warp == 1) {
@@ -564,7 +586,7 @@ cudaError_t launch_residual(const SlicedOperand& Ls, const SlicedOperand& Xs, co
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(St::SMEM_BYTES));
   if (e != cudaSuccess) return e;
   dim3 grid(static_cast<unsigned>((Ls.rows + 127) / 128), static_cast<unsigned>((Xs.rows + BN - 1) / BN));
-  kern<<<grid, 192, St::SMEM_BYTES, s>>>(ma, mb, epi, err);
+  kern<<<grid, St::kThreads, St::SMEM_BYTES, s>>>(ma, mb, epi, err);
   count_launch();
   return cudaGetLastError();
 }

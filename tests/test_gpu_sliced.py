@@ -46,7 +46,8 @@ def _dev(a):
 
 @pytest.mark.parametrize("planes", [7, 8])
 @pytest.mark.parametrize("n,k,kind", [(1024, 8, "well"), (1500, 5, "well"), (700, 17, "graded2"),
-                                      (2100, 3, "well"), (130, 64, "well")])
+                                      (2100, 3, "well"), (130, 64, "well"), (100, 9, "well"),
+                                      (300, 40, "graded2")])
 def test_sliced_residual_accuracy(cuda_lib, n, k, kind, planes):
     import torch
     lib = cuda_lib
