@@ -484,7 +484,8 @@ def run_case(args):
     sliced:N:K[:P]   the tensor-core residual R = B - L X with P (7 or 8)
                      digit planes, twice;
     mixed:N:K:N0[:I[:S]]  one mixed-precision refined solve (graded diagonal,
-                     c = 2); inner I = 0 tf32, 1 bf16, 2 split bf16; S = 1 for
+                     c = 2); inner I = 0 tf32, 1 bf16, 2 split bf16, 3 split
+                     fp16; S = 1 for
                      the FP32 diagonal-block multiply;
     engine:M:N:K     the bf16 tensor-core GEMM self-test, twice;
     batch:COUNT:BITS one batched launch of COUNT systems of the batching
@@ -519,7 +520,7 @@ def run_case(args):
                                               n, dims[2] if len(dims) > 2 else 7, ctypes.c_void_p(err.data_ptr()), s)
                 assert rc == 0
         else:
-            inner = ("tf32", "bf16", "bf16x3")[dims[3]] if len(dims) > 3 else "tf32"
+            inner = ("tf32", "bf16", "bf16x3", "fp16x3")[dims[3]] if len(dims) > 3 else "tf32"
             plan = g.trsm_plan(L, dims[2])
             g.trsm_plan_mixed(plan, L, inner)
             g.trsm_solve_mixed(plan, B, max_iter=30, tol=1e-12, raise_on_noconv=False,

@@ -28,6 +28,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <type_traits>
 
 #include <algorithm>
 #include <cmath>
@@ -84,6 +85,7 @@ struct LowP<0> {
   using T = __nv_bfloat16;
   static constexpr int kPlanes = 1;
   __device__ static void put(T* p, int64_t, double v) { *p = __double2bfloat16(v); }
+  __device__ static void put(T* p, int64_t, float v) { *p = __float2bfloat16_rn(v); }
 };
 template <>
 struct LowP<1> {
@@ -92,6 +94,11 @@ struct LowP<1> {
   __device__ static void put(T* p, int64_t, double v) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(static_cast<float>(v)));
+    *p = __uint_as_float(r);
+  }
+  __device__ static void put(T* p, int64_t, float v) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
     *p = __uint_as_float(r);
   }
 };
@@ -104,6 +111,12 @@ struct LowP<2> {
     p[0] = hi;
     p[plane] = __double2bfloat16(v - static_cast<double>(__bfloat162float(hi)));
   }
+  // an FP32 value: the same planes without the FP64 pipe (v - hi is exact in FP32)
+  __device__ static void put(T* p, int64_t plane, float v) {
+    const T hi = __float2bfloat16_rn(v);
+    p[0] = hi;
+    p[plane] = __float2bfloat16_rn(v - __bfloat162float(hi));
+  }
 };
 
 // Split fp16: the planes need a scale known only after the whole D_i is
@@ -114,6 +127,7 @@ struct LowP<3> {
   using T = __half;
   static constexpr int kPlanes = 2;
   __device__ static void put(T*, int64_t, double) {}
+  __device__ static void put(T*, int64_t, float) {}
 };
 
 inline int mode_of(int inner) {
@@ -173,22 +187,39 @@ __global__ void pack_panels_f16_kernel(const double* __restrict__ L, int64_t ldl
   }
 }
 
+// x 2^n, exact: an add to the exponent field when x and the result are
+// normal doubles (integer work only: GB300's FP64 pipe is narrow), ldexp out
+// of line otherwise (subnormal, inf or nan, or a result outside the normal
+// range).
+__device__ __noinline__ double scale_pow2_slow(double x, int n) { return ldexp(x, n); }
+__device__ __forceinline__ double scale_pow2(double x, int n) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  const int E = static_cast<int>((b >> 52) & 0x7FF);
+  if (E != 0 && E != 0x7FF && E + n >= 1 && E + n <= 0x7FE)
+    return __longlong_as_double(static_cast<long long>(b + (static_cast<unsigned long long>(n) << 52)));
+  if ((b << 1) == 0) return x;  // +-0
+  return scale_pow2_slow(x, n);
+}
+
 // D_i (FP64, n0 x k at D + s0) into split-fp16 planes of Dt (k x n0p, K-major)
 // scaled by 2^sd, sd = 14 - e(max |D_i|); gscale = 2^-(panel_exp + sd)
-// undoes both scales in the update GEMM.
+// undoes both scales in the update GEMM.  hi = fp16(v), lo = fp16(v - hi)
+// with v rounded once to FP32 first: v - hi is then exact in FP32 and
+// hi + lo keeps 22 bits of v.  Rows on threadIdx.x (coalesced in D and in
+// Dt), columns on blockIdx.y.
 __global__ void pack_dt_f16_kernel(const double* __restrict__ D, int64_t ldd, int64_t s0, int m, int64_t k,
                                    int64_t n0p, const unsigned long long* __restrict__ dmax, const int* panel_exp,
                                    __half* __restrict__ Dt, float* __restrict__ gscale) {
   const int sd = 14 - exp_above(*dmax);
-  if (blockIdx.x == 0 && threadIdx.x == 0) *gscale = ldexpf(1.f, -(*panel_exp + sd));
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *gscale = ldexpf(1.f, -(*panel_exp + sd));
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= m) return;
   const int64_t plane = k * n0p;
-  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < static_cast<int64_t>(m) * k;
-       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t row = e % m, col = e / m;
-    const double v = ldexp(D[col * ldd + s0 + row], sd);
-    const __half hi = __double2half(v);
+  for (int64_t col = blockIdx.y; col < k; col += gridDim.y) {
+    const float vf = __double2float_rn(scale_pow2(D[col * ldd + s0 + row], sd));
+    const __half hi = __float2half_rn(vf);
     Dt[col * n0p + row] = hi;
-    Dt[plane + col * n0p + row] = __double2half(v - static_cast<double>(__half2float(hi)));
+    Dt[plane + col * n0p + row] = __float2half_rn(vf - __half2float(hi));
   }
 }
 
@@ -267,18 +298,20 @@ __device__ __forceinline__ void s_tile(const double* __restrict__ Lt, int64_t ld
       if (cc >= nc) continue;
       const int64_t col = static_cast<int64_t>(j) * TILE + cc;
       const int64_t row = static_cast<int64_t>(r) * TILE + rr;
-      const double v = static_cast<double>(acc[a][b]);
-      D[col * ldd + s0 + row] = v;
-      LowP<kMode>::put(Dt + col * n0p + row, k * n0p, v);
+      D[col * ldd + s0 + row] = static_cast<double>(acc[a][b]);
+      LowP<kMode>::put(Dt + col * n0p + row, k * n0p, acc[a][b]);  // in the accumulator's type
     }
   }
   if constexpr (kMode == 3) {
-    double mx = 0.0;  // outputs outside the tile are zero
+    TC mx = TC(0);  // outputs outside the tile are zero; a NaN never replaces the maximum (as fmax)
 #pragma unroll
     for (int a = 0; a < TM; ++a)
 #pragma unroll
-      for (int b = 0; b < TN; ++b) mx = fmax(mx, fabs(static_cast<double>(acc[a][b])));
-    fold_max(mx, dmax);
+      for (int b = 0; b < TN; ++b) {
+        const TC v = acc[a][b] < TC(0) ? -acc[a][b] : acc[a][b];
+        mx = v > mx ? v : mx;
+      }
+    fold_max(static_cast<double>(mx), dmax);
   }
 }
 
@@ -362,18 +395,23 @@ __device__ __forceinline__ void s32_tile(const double* __restrict__ Lt, int64_t 
       if (cc >= nc) continue;
       const int64_t col = static_cast<int64_t>(j) * kS32Tile + cc;
       const int64_t row = static_cast<int64_t>(r) * kS32Tile + rr;
-      const double v = static_cast<double>(acc[i][c]);
-      D[col * ldd + s0 + row] = v;
-      LowP<kMode>::put(Dt + col * n0p + row, k * n0p, v);
+      D[col * ldd + s0 + row] = static_cast<double>(acc[i][c]);
+      LowP<kMode>::put(Dt + col * n0p + row, k * n0p, acc[i][c]);
     }
   }
   if constexpr (kMode == 3) {
-    double mx = 0.0;
+    // in the accumulator's own type (FP32 here keeps the FP64 pipe free);
+    // like fmax, a NaN never replaces the running maximum
+    using A = typename std::remove_reference<decltype(acc[0][0])>::type;
+    A mx = A(0);
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) mx = fmax(mx, fabs(static_cast<double>(acc[i][c])));
-    fold_max(mx, dmax);
+      for (int c = 0; c < 4; ++c) {
+        const A a = acc[i][c] < A(0) ? -acc[i][c] : acc[i][c];
+        mx = a > mx ? a : mx;
+      }
+    fold_max(static_cast<double>(mx), dmax);
   }
 }
 
@@ -412,29 +450,35 @@ void launch_s_step(bool s32, const double* Lt, int64_t ldt, const float* W, int6
     s_step32_kernel<kMode><<<g32, kS32Threads, 0, s>>>(Lt, ldt, W, ld, D, ld, dt, n0p, s0, m, k, dmax);
 }
 
-// max that keeps a NaN once it has been seen (fmax would drop it)
-__device__ __forceinline__ double nanmax(double m, double v) { return (v > m || isnan(v)) ? v : m; }
-
-// X += D; folds max|D| and max|X| (as ordered bit patterns) into norms[0..1].
+// X += D; folds max|D| and max|X| into norms[0..1] as ordered bit patterns
+// (|v| compared as an unsigned integer: monotone for non-negative doubles,
+// and every NaN pattern lies above inf, so a NaN, once seen, stays the
+// maximum; it is stored as ~0).  Integer maxima keep the FP64 pipe for the
+// additions alone.
 __global__ void correct_kernel(double* __restrict__ X, int64_t ldx, const double* __restrict__ D,
                                int64_t ldd, int64_t n, int64_t k,
                                unsigned long long* __restrict__ norms) {
-  double dm = 0.0, xm = 0.0;
+  constexpr unsigned long long kAbs = ~(1ull << 63);
+  unsigned long long dm = 0, xm = 0;
   for (int64_t j = blockIdx.y; j < k; j += gridDim.y)
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
       const double d = D[j * ldd + i];
       const double x = X[j * ldx + i] + d;
       X[j * ldx + i] = x;
-      dm = nanmax(dm, fabs(d));
-      xm = nanmax(xm, fabs(x));
+      const unsigned long long bd = static_cast<unsigned long long>(__double_as_longlong(d)) & kAbs;
+      const unsigned long long bx = static_cast<unsigned long long>(__double_as_longlong(x)) & kAbs;
+      dm = bd > dm ? bd : dm;
+      xm = bx > xm ? bx : xm;
     }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    dm = nanmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
-    xm = nanmax(xm, __shfl_xor_sync(0xffffffffu, xm, o));
+    const unsigned long long od = __shfl_xor_sync(0xffffffffu, dm, o);
+    const unsigned long long ox = __shfl_xor_sync(0xffffffffu, xm, o);
+    dm = od > dm ? od : dm;
+    xm = ox > xm ? ox : xm;
   }
-  __shared__ double sd[32], sx[32];
+  __shared__ unsigned long long sd[32], sx[32];
   const int w = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0) {
     sd[w] = dm;
@@ -443,14 +487,12 @@ __global__ void correct_kernel(double* __restrict__ X, int64_t ldx, const double
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int i = 1; i < static_cast<int>(blockDim.x >> 5); ++i) {
-      dm = nanmax(dm, sd[i]);
-      xm = nanmax(xm, sx[i]);
+      dm = sd[i] > dm ? sd[i] : dm;
+      xm = sx[i] > xm ? sx[i] : xm;
     }
-    // NaN propagates as the largest pattern so that divergence is visible
-    const unsigned long long bd = isnan(dm) ? ~0ull : __double_as_longlong(dm);
-    const unsigned long long bx = isnan(xm) ? ~0ull : __double_as_longlong(xm);
-    atomicMax(norms, bd);
-    atomicMax(norms + 1, bx);
+    constexpr unsigned long long kInf = 0x7FF0000000000000ull;
+    atomicMax(norms, dm > kInf ? ~0ull : dm);
+    atomicMax(norms + 1, xm > kInf ? ~0ull : xm);
   }
 }
 
@@ -662,9 +704,10 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
         const unsigned char* P =
             static_cast<const unsigned char*>(mp->panels) + esz * trsm::panel_off(i, n, n0, n0p);
         if (mode == 3) {
-          trsm::pack_dt_f16_kernel<<<trsm::grid_nk(m, 1).x * 8, 256, 0, s>>>(D, ld, s0, m, k, n0p, dmax_i,
-                                                                             mp->panel_exp + i,
-                                                                             static_cast<__half*>(Dt), gscale + i);
+          const dim3 gp(static_cast<unsigned>((m + 255) / 256),
+                        static_cast<unsigned>(std::min<int64_t>(k, std::max<int64_t>(1, 2432 / ((m + 255) / 256)))));
+          trsm::pack_dt_f16_kernel<<<gp, 256, 0, s>>>(D, ld, s0, m, k, n0p, dmax_i, mp->panel_exp + i,
+                                                      static_cast<__half*>(Dt), gscale + i);
           trsm::count_launch();
           e = cudaGetLastError();
           if (e == cudaSuccess)

@@ -84,9 +84,9 @@ __device__ __forceinline__ void digits_of(double a, int e, float (&dig)[kPlanes]
     long long rem = v & 63;
     if (rem >= 32) rem -= 64;
     v = (v - rem) >> kDigitBits;
-    dig[s] = static_cast<float>(rem);
+    dig[s] = static_cast<float>(static_cast<int>(rem));  // 32-bit conversions: the 64-bit one is slow here
   }
-  dig[0] = static_cast<float>(v);  // |d_0| <= 64
+  dig[0] = static_cast<float>(static_cast<int>(v));  // |d_0| <= 64
 }
 
 __global__ void slice_rows_kernel(const double* __restrict__ src, int64_t ld, int64_t rows, int64_t K,
@@ -301,7 +301,7 @@ struct ResidualEpi {
 // against 6.7k of MMA work).  Here a stage holds a group of A planes
 // [s0, s1) with the B planes they pair with (u <= P - 1 - s0): at most
 // 112 KB, so two stages are in flight.  The groups (P = 7: {0}, {1, 2},
-// {3 .. 6}; P = 8: {0}, {1, 2}, {3, 4, 5}, {6, 7}) keep the stages near
+// {3 .. 6}; P = 8: {0, 1}, {2, 3}, {4 .. 7}) keep the stages near
 // 100 KB and at least 6 plane pairs each, and read 316 (P = 7) or 348
 // (P = 8) KB per K step against 196 and 208 for the whole step at once.
 // The items of a chunk run block by block (kBlkSteps K steps), within a

@@ -56,6 +56,29 @@ def test_mixed_wide_blocks_fp32_diagonal_multiply(cuda_lib, inner, n, k, n0):
     assert iters <= 12
 
 
+@pytest.mark.parametrize("inner", ["tf32", "bf16x3", "fp16x3"])
+@pytest.mark.parametrize("s32", [False, True])
+def test_mixed_power_of_two_scaling_is_exact(cuda_lib, inner, s32):
+    """Every scale in the refined solve (chunk exponents of the sliced
+    residual, the fp16 panel and D_i scales, the FP32 inner solve) is a power
+    of two, so solving with 2^s B gives 2^s X bit for bit while nothing leaves
+    the normal range: s = -60 and +60 keep the FP32 residuals normal."""
+    import paper_1612_01855_gb300 as g
+    n, k, n0 = 600, 7, 128
+    L, B = inputs.well_conditioned(n, k, seed=11)
+    Ld = _dev(L)
+    plan = g.trsm_plan(Ld, n0)
+    g.trsm_plan_mixed(plan, Ld, inner)
+    runs = {}
+    for sc in (0, -60, 60):
+        X, iters, upd = g.trsm_solve_mixed(plan, _dev(np.ldexp(B, sc)), residual="sliced", max_iter=40, tol=1e-13,
+                                           raise_on_noconv=False, s_fp32=s32)
+        runs[sc] = (X.cpu().numpy(), iters)
+    for sc in (-60, 60):
+        assert runs[sc][1] == runs[0][1]
+        assert np.array_equal(runs[sc][0], np.ldexp(runs[0][0], sc))
+
+
 def test_mixed_graded_diagonal_forward_error(cuda_lib):
     """Diagonal graded from 1 to 1e-2: forward error against the
     double-double substitution stays below 1e-10."""
