@@ -153,6 +153,8 @@ int trsm_solve_noalloc(trsm_handle_t h, const double* B_dev, int64_t k, int64_t 
  *     (TRSM_INNER_BF16, TRSM_INNER_TF32, TRSM_INNER_BF16X3 or
  *     TRSM_INNER_FP16X3), for the tensor-core updates;
  *   - the original diagonal blocks and diagonal of L in FP64;
+ *   - FP32 copies of the plan's inverted diagonal blocks L~_ii (n x n0
+ *     floats), for the FP32 diagonal-block multiply;
  *   - eight 6-bit integer digit planes of the strictly lower L, for the
  *     FP64-class residual.
  *   L_dev : the same matrix the plan was made from (n x n, ldl >= n).

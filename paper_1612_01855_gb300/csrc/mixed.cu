@@ -51,6 +51,7 @@ struct MixedPlan {
   void* lsl = nullptr;      // digit planes of the strictly lower L
   SlicedOperand Ls;
   int* panel_exp = nullptr; // split fp16: panel i is stored times 2^panel_exp[i]
+  float* dinv32 = nullptr;  // FP32 copies of the inverted diagonal blocks L~_ii, N x n0 x n0 (ld n0)
   size_t bytes = 0;         // device bytes held by the fields above
 };
 
@@ -64,6 +65,7 @@ void mixed_release(trsm_plan_s* h) {
   if (mp->dblk) cudaFree(mp->dblk);
   if (mp->lsl) cudaFree(mp->lsl);
   if (mp->panel_exp) cudaFree(mp->panel_exp);
+  if (mp->dinv32) cudaFree(mp->dinv32);
   delete mp;
   h->mixed = nullptr;
 }
@@ -252,6 +254,17 @@ __global__ void pack_panels_kernel(const double* __restrict__ L, int64_t ldl, in
   }
 }
 
+// FP32 copies of the inverted diagonal blocks of L~ (the FP32 diagonal
+// multiply reads them instead of rounding L~_ii again for every tile of W).
+__global__ void dinv_to_f32_kernel(const double* __restrict__ Lt, int64_t ldt, int64_t n, int64_t n0,
+                                   float* __restrict__ out) {
+  const int64_t s0 = static_cast<int64_t>(blockIdx.y) * n0;
+  const int64_t m = imin64(n0, n - s0);
+  float* o = out + s0 * n0;
+  for (int64_t t = blockIdx.x; t < m; t += gridDim.x)
+    for (int64_t r = threadIdx.x; r < m; r += blockDim.x) o[t * n0 + r] = static_cast<float>(Lt[(s0 + t) * ldt + s0 + r]);
+}
+
 __global__ void extract_diag_kernel(const double* __restrict__ L, int64_t ldl, int64_t n, int64_t n0,
                                     double* __restrict__ diag, double* __restrict__ dblk) {
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < n * n0;
@@ -276,8 +289,8 @@ __global__ void to_float_kernel(const double* __restrict__ R, int64_t ldr, float
 // rounded, to Dt (the B operand of the next update GEMM).  L~_ii is lower
 // triangular, so row tile r costs (r + 1) K chunks: each CTA takes the
 // pair of row tiles (p, R - 1 - p), which all cost the same.
-template <int kMode, class TC>
-__device__ __forceinline__ void s_tile(const double* __restrict__ Lt, int64_t ldt, const float* __restrict__ W,
+template <int kMode, class TC, class TA>
+__device__ __forceinline__ void s_tile(const TA* __restrict__ La, int64_t lda, const float* __restrict__ W,
                                        int64_t ldw, double* __restrict__ D, int64_t ldd,
                                        typename LowP<kMode>::T* __restrict__ Dt, int64_t n0p, int64_t s0, int m,
                                        int64_t k, int r, int j, TileSmemT<TC>& sm, unsigned long long* dmax) {
@@ -285,7 +298,7 @@ __device__ __forceinline__ void s_tile(const double* __restrict__ Lt, int64_t ld
   const int nc = static_cast<int>(imin64(TILE, k - static_cast<int64_t>(j) * TILE));
   TC acc[TM][TN];
   zero_acc(acc);
-  tile_mma<TC, false, false>(Lt + s0 * ldt + s0 + r * TILE, ldt, W + static_cast<int64_t>(j) * TILE * ldw + s0,
+  tile_mma<TC, false, false>(La + r * TILE, lda, W + static_cast<int64_t>(j) * TILE * ldw + s0,
                              ldw, mr, nc, 0, min((r + 1) * TILE, m), sm, acc);
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
 #pragma unroll
@@ -317,8 +330,8 @@ __device__ __forceinline__ void s_tile(const double* __restrict__ Lt, int64_t ld
 
 // TC = double: FP64 DFMA with the FP64 inverses (the default); TC = float:
 // FFMA with the inverses rounded to FP32 (TRSM_SOLVE_S_FP32).
-template <int kMode, class TC>
-__global__ void __launch_bounds__(NTHREADS) s_step_kernel(const double* __restrict__ Lt, int64_t ldt,
+template <int kMode, class TC, class TA>
+__global__ void __launch_bounds__(NTHREADS) s_step_kernel(const TA* __restrict__ La, int64_t lda,
                                                           const float* __restrict__ W, int64_t ldw,
                                                           double* __restrict__ D, int64_t ldd,
                                                           typename LowP<kMode>::T* __restrict__ Dt,
@@ -327,8 +340,8 @@ __global__ void __launch_bounds__(NTHREADS) s_step_kernel(const double* __restri
   __shared__ TileSmemT<TC> sm;
   const int R = (m + TILE - 1) / TILE;
   const int p = blockIdx.x, j = blockIdx.y;
-  s_tile<kMode, TC>(Lt, ldt, W, ldw, D, ldd, Dt, n0p, s0, m, k, p, j, sm, dmax);
-  if (R - 1 - p != p) s_tile<kMode, TC>(Lt, ldt, W, ldw, D, ldd, Dt, n0p, s0, m, k, R - 1 - p, j, sm, dmax);
+  s_tile<kMode, TC, TA>(La, lda, W, ldw, D, ldd, Dt, n0p, s0, m, k, p, j, sm, dmax);
+  if (R - 1 - p != p) s_tile<kMode, TC, TA>(La, lda, W, ldw, D, ldd, Dt, n0p, s0, m, k, R - 1 - p, j, sm, dmax);
 }
 
 // The same step in FP32 arithmetic (TRSM_SOLVE_S_FP32), register-blocked
@@ -345,7 +358,7 @@ struct S32Smem {
 };
 
 template <int kMode>
-__device__ __forceinline__ void s32_tile(const double* __restrict__ Lt, int64_t ldt, const float* __restrict__ W,
+__device__ __forceinline__ void s32_tile(const float* __restrict__ La, int64_t lda, const float* __restrict__ W,
                                          int64_t ldw, double* __restrict__ D, int64_t ldd,
                                          typename LowP<kMode>::T* __restrict__ Dt, int64_t n0p, int64_t s0, int m,
                                          int64_t k, int r, int j, S32Smem& sm, unsigned long long* dmax) {
@@ -354,7 +367,7 @@ __device__ __forceinline__ void s32_tile(const double* __restrict__ Lt, int64_t 
   const int mr = min(kS32Tile, m - r * kS32Tile);
   const int nc = static_cast<int>(imin64(kS32Tile, k - static_cast<int64_t>(j) * kS32Tile));
   const int kend = min((r + 1) * kS32Tile, m);  // L~_ii is lower triangular
-  const double* A = Lt + s0 * ldt + s0 + static_cast<int64_t>(r) * kS32Tile;  // A(row, t) = A[t ldt + row]
+  const float* A = La + static_cast<int64_t>(r) * kS32Tile;  // A(row, t) = A[t lda + row]
   const float* B = W + static_cast<int64_t>(j) * kS32Tile * ldw + s0;         // B(t, col) = B[col ldw + t]
   float acc[4][4];
 #pragma unroll
@@ -365,7 +378,7 @@ __device__ __forceinline__ void s32_tile(const double* __restrict__ Lt, int64_t 
 #pragma unroll
     for (int it = 0; it < (kS32Tile * kS32Chunk) / kS32Threads; ++it) {
       const int row = tid & 63, kk = (tid >> 6) + 4 * it, t = k0 + kk;
-      sm.a[kk][row] = (row < mr && t < kend) ? static_cast<float>(A[static_cast<int64_t>(t) * ldt + row]) : 0.f;
+      sm.a[kk][row] = (row < mr && t < kend) ? A[static_cast<int64_t>(t) * lda + row] : 0.f;
     }
 #pragma unroll
     for (int it = 0; it < (kS32Tile * kS32Chunk) / kS32Threads; ++it) {
@@ -416,7 +429,7 @@ __device__ __forceinline__ void s32_tile(const double* __restrict__ Lt, int64_t 
 }
 
 template <int kMode>
-__global__ void __launch_bounds__(kS32Threads) s_step32_kernel(const double* __restrict__ Lt, int64_t ldt,
+__global__ void __launch_bounds__(kS32Threads) s_step32_kernel(const float* __restrict__ La, int64_t lda,
                                                                const float* __restrict__ W, int64_t ldw,
                                                                double* __restrict__ D, int64_t ldd,
                                                                typename LowP<kMode>::T* __restrict__ Dt,
@@ -425,17 +438,19 @@ __global__ void __launch_bounds__(kS32Threads) s_step32_kernel(const double* __r
   __shared__ __align__(16) S32Smem sm;
   const int R = (m + kS32Tile - 1) / kS32Tile;
   const int p = blockIdx.x, j = blockIdx.y;
-  s32_tile<kMode>(Lt, ldt, W, ldw, D, ldd, Dt, n0p, s0, m, k, p, j, sm, dmax);
-  if (R - 1 - p != p) s32_tile<kMode>(Lt, ldt, W, ldw, D, ldd, Dt, n0p, s0, m, k, R - 1 - p, j, sm, dmax);
+  s32_tile<kMode>(La, lda, W, ldw, D, ldd, Dt, n0p, s0, m, k, p, j, sm, dmax);
+  if (R - 1 - p != p) s32_tile<kMode>(La, lda, W, ldw, D, ldd, Dt, n0p, s0, m, k, R - 1 - p, j, sm, dmax);
 }
 
 // Launches the diagonal-block multiply of one block row in the given
 // inner precision: FP64 (DFMA) or FP32 arithmetic; blocks of 512 rows and
 // more take the register-blocked FP32 tile, which gives smaller blocks too
-// few CTAs (measured: n0 = 256 slower, 1024 faster).
+// few CTAs (measured: n0 = 256 slower, 1024 faster).  Lt: L~ (FP64, ld
+// ldt); Lf: the FP32 copy of this block row's L~_ii (ld ldf).
 template <int kMode>
-void launch_s_step(bool s32, const double* Lt, int64_t ldt, const float* W, int64_t ld, double* D, void* Dt,
-                   int64_t n0p, int64_t s0, int m, int64_t k, unsigned long long* dmax, cudaStream_t s) {
+void launch_s_step(bool s32, const double* Lt, int64_t ldt, const float* Lf, int64_t ldf, const float* W,
+                   int64_t ld, double* D, void* Dt, int64_t n0p, int64_t s0, int m, int64_t k,
+                   unsigned long long* dmax, cudaStream_t s) {
   using T = typename LowP<kMode>::T;
   T* dt = static_cast<T*>(Dt);
   const int R = (m + TILE - 1) / TILE;
@@ -443,11 +458,12 @@ void launch_s_step(bool s32, const double* Lt, int64_t ldt, const float* W, int6
   const int R32 = (m + kS32Tile - 1) / kS32Tile;
   const dim3 g32(static_cast<unsigned>((R32 + 1) / 2), static_cast<unsigned>((k + kS32Tile - 1) / kS32Tile));
   if (!s32)
-    s_step_kernel<kMode, double><<<g, NTHREADS, 0, s>>>(Lt, ldt, W, ld, D, ld, dt, n0p, s0, m, k, dmax);
+    s_step_kernel<kMode, double, double><<<g, NTHREADS, 0, s>>>(Lt + s0 * ldt + s0, ldt, W, ld, D, ld, dt, n0p, s0,
+                                                               m, k, dmax);
   else if (m < 512)
-    s_step_kernel<kMode, float><<<g, NTHREADS, 0, s>>>(Lt, ldt, W, ld, D, ld, dt, n0p, s0, m, k, dmax);
+    s_step_kernel<kMode, float, float><<<g, NTHREADS, 0, s>>>(Lf, ldf, W, ld, D, ld, dt, n0p, s0, m, k, dmax);
   else
-    s_step32_kernel<kMode><<<g32, kS32Threads, 0, s>>>(Lt, ldt, W, ld, D, ld, dt, n0p, s0, m, k, dmax);
+    s_step32_kernel<kMode><<<g32, kS32Threads, 0, s>>>(Lf, ldf, W, ld, D, ld, dt, n0p, s0, m, k, dmax);
 }
 
 // X += D; folds max|D| and max|X| into norms[0..1] as ordered bit patterns
@@ -601,6 +617,15 @@ extern "C" int trsm_plan_mixed(trsm_handle_t h, const double* L_dev, int64_t ldl
     trsm::count_launch();
     e = cudaGetLastError();
   }
+  if (e == cudaSuccess)
+    e = cudaMalloc(reinterpret_cast<void**>(&mp->dinv32), sizeof(float) * static_cast<size_t>(N * n0 * n0));
+  if (e == cudaSuccess) {
+    mp->bytes += sizeof(float) * static_cast<size_t>(N * n0 * n0);
+    trsm::dinv_to_f32_kernel<<<dim3(static_cast<unsigned>(std::min<int64_t>(n0, 1024)), static_cast<unsigned>(N)), 256,
+                               0, s>>>(h->Lt, h->ldt, n, n0, mp->dinv32);
+    trsm::count_launch();
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) {
     mp->Ls = trsm::sliced_operand_view(mp->lsl, n, n);
     e = trsm::slice_lower_rows(L_dev, ldl, n, mp->Ls, tmp, s);
@@ -691,11 +716,12 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
       const int R = (m + trsm::TILE - 1) / trsm::TILE;
       dim3 g(static_cast<unsigned>((R + 1) / 2), static_cast<unsigned>((k + trsm::TILE - 1) / trsm::TILE));
       unsigned long long* dmax_i = dmax + i;
+      const float* Lf = mp->dinv32 + s0 * n0;  // block i of the FP32 copies
       switch (mode) {
-        case 1: trsm::launch_s_step<1>(s32, h->Lt, h->ldt, W, ld, D, Dt, n0p, s0, m, k, dmax_i, s); break;
-        case 2: trsm::launch_s_step<2>(s32, h->Lt, h->ldt, W, ld, D, Dt, n0p, s0, m, k, dmax_i, s); break;
-        case 3: trsm::launch_s_step<3>(s32, h->Lt, h->ldt, W, ld, D, Dt, n0p, s0, m, k, dmax_i, s); break;
-        default: trsm::launch_s_step<0>(s32, h->Lt, h->ldt, W, ld, D, Dt, n0p, s0, m, k, dmax_i, s); break;
+        case 1: trsm::launch_s_step<1>(s32, h->Lt, h->ldt, Lf, n0, W, ld, D, Dt, n0p, s0, m, k, dmax_i, s); break;
+        case 2: trsm::launch_s_step<2>(s32, h->Lt, h->ldt, Lf, n0, W, ld, D, Dt, n0p, s0, m, k, dmax_i, s); break;
+        case 3: trsm::launch_s_step<3>(s32, h->Lt, h->ldt, Lf, n0, W, ld, D, Dt, n0p, s0, m, k, dmax_i, s); break;
+        default: trsm::launch_s_step<0>(s32, h->Lt, h->ldt, Lf, n0, W, ld, D, Dt, n0p, s0, m, k, dmax_i, s); break;
       }
       trsm::count_launch();
       e = cudaGetLastError();

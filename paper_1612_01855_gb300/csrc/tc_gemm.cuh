@@ -50,7 +50,7 @@ struct TileCfg {
 // The pair table of a configuration: MMA i multiplies A slice pa(i) by
 // B slice pb(i) into group pg(i).
 template <class Cfg, class Pairs, class Epi>
-__global__ void __launch_bounds__(192)
+__global__ void __launch_bounds__(192, 1)
     tc_tile_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    const Epi epi, int* err) {
   constexpr int STAGES = Cfg::STAGES;
@@ -148,7 +148,9 @@ __global__ void __launch_bounds__(192)
     for (int c = 0; c < nchunks; ++c) {
       if (!mbar_wait(&tfull_bar, c & 1, abort_flag)) break;
       tc_fence_after();
-#pragma unroll
+      // a loop, not unrolled: unrolled over the slabs the drain alone is
+      // several times the instruction cache
+#pragma unroll 1
       for (int sl = 0; sl < BN / 16; ++sl) {
         // the epilogue consumes the NG groups of a 16-column slab one group
         // at a time (keeps the register footprint at 16 values per group)
