@@ -75,8 +75,10 @@ __host__ __device__ __forceinline__ int64_t wave_first(int64_t l, int64_t R, int
   return C * (l * total_rt - R * (l * (l - 1) / 2));
 }
 
+// Out of line: unrolled over the 32 columns it is most of the kernel's
+// code, and it runs only in the inversion phase.
 template <class T>
-__device__ void leaf_invert_warp(const T* __restrict__ A, int64_t lda, int m, T* __restrict__ out,
+__device__ __noinline__ void leaf_invert_warp(const T* __restrict__ A, int64_t lda, int m, T* __restrict__ out,
                                  int64_t ldo, T (*ls)[33], int* status, int64_t row0) {
   const int lane = threadIdx.x & 31;
   for (int c = 0; c < 32; ++c) {
