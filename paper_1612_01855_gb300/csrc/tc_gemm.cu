@@ -64,7 +64,21 @@ struct StoreF32Epi {
   float alpha, beta;
   const float* scale = nullptr;  // optional device factor on alpha (set by an earlier kernel)
   struct State {};
-  __device__ void tile(int&, int&) const {}
+  // Launch order -> tile: groups of kGroupRows row tiles, within a group the
+  // column tiles one after the other.  The CTAs in flight (one per SM) then
+  // cover about 16 row tiles x 10 column tiles, whose A and B panels stay
+  // in L2; in plain launch order they spanned every row tile of two or
+  // three column tiles and re-read all of A from HBM for each.
+  static constexpr int kGroupRows = 16;
+  __device__ void tile(int& tm, int& tn) const {
+    const int R = static_cast<int>(gridDim.x), C = static_cast<int>(gridDim.y);
+    const int lin = tm + R * tn;
+    const int g0 = lin / (kGroupRows * C) * kGroupRows;
+    const int gsz = min(kGroupRows, R - g0);
+    const int idx = lin - g0 * C;
+    tm = g0 + idx % gsz;
+    tn = idx / gsz;
+  }
   __device__ void k_range(int, int, int& kb0, int& kb1, int& chunk) const {
     kb0 = 0;
     kb1 = nkb;
