@@ -195,10 +195,12 @@ int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k, int64_t ld
  * systems may differ in n, k and block size.  An item either carries a
  * resident plan (its inverted blocks are reused: no inversion work) or its
  * own L, whose n0 x n0 diagonal blocks (n0 = 32 or 64) are inverted inside
- * the same launch by Algorithm RecTriInv (Section 5.1, one level).  One
- * run is one memset and one kernel, so it can be captured in a CUDA graph;
- * the results do not depend on which other items share the launch (every
- * tile's updates are applied in a fixed order). */
+ * the same launch by Algorithm RecTriInv (Section 5.1, one level).  An
+ * FP64 run is one memset and one persistent kernel of dependent tile tasks;
+ * an FP32 run is one memset and two kernels (every diagonal block inverted
+ * once, then one CTA per system and column chunk).  Either can be captured
+ * in a CUDA graph, and the results do not depend on which other items share
+ * the launch (every output's sums are taken in a fixed order). */
 #define TRSM_F64 0
 #define TRSM_F32 1
 
@@ -212,8 +214,9 @@ typedef struct trsm_batch_item {
   int64_t ldx;
   int64_t n, k;
   int64_t n0;           /* 32 or 64 when plan == NULL (ignored otherwise)      */
-  int64_t tile_cols;    /* columns per output tile: 8, 16 or 32; 0 = by k
-                           (8 for k <= 8, 16 for k <= 16, else 32)            */
+  int64_t tile_cols;    /* columns per output tile (FP32: per CTA): 8, 16
+                           or 32; 0 = by k (8 for k <= 8, 16 for k <= 16,
+                           else 32)                                           */
 } trsm_batch_item;
 
 typedef struct trsm_batch_s* trsm_batch_t;

@@ -20,7 +20,8 @@
 // residency.  The first update
 // of a tile reads B instead of the working copy W, so no copy launch is
 // needed and a whole batch is one memset plus one kernel (and so one CUDA
-// graph).  The arithmetic type T is double or float.
+// graph).  This kernel serves FP64 batches; FP32 batches take the per-system
+// kernels further down.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -81,11 +82,12 @@ template <class T>
 __device__ __noinline__ void leaf_invert_warp(const T* __restrict__ A, int64_t lda, int m, T* __restrict__ out,
                                  int64_t ldo, T (*ls)[33], int* status, int64_t row0) {
   const int lane = threadIdx.x & 31;
-  for (int c = 0; c < 32; ++c) {
-    T v = T(0);
-    if (lane < m && c < m && lane >= c) v = A[static_cast<int64_t>(c) * lda + lane];
-    ls[lane][c] = v;
-  }
+  // all 32 loads in flight before the first store (one round trip, not 32)
+  T v[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) v[c] = (lane < m && c < m && lane >= c) ? A[static_cast<int64_t>(c) * lda + lane] : T(0);
+#pragma unroll
+  for (int c = 0; c < 32; ++c) ls[lane][c] = v[c];
   __syncwarp();
   if (lane < m) {
     const T dl = ls[lane][lane];
@@ -225,6 +227,248 @@ __device__ __forceinline__ void u_body(const BatchSys<T>& a, int l, int i, int r
       __stcg(a.W + col * a.ldw + row0 + rr, base - acc[ii][jj]);
     }
   }
+}
+
+// ---------------------------------------------------------------- FP32
+// FP32 systems run as two launches with no dependency between CTAs inside
+// either.  First every diagonal block of every system is inverted, one CTA
+// per block (RecTriInv with one level, as the INV tasks), into a workspace.
+// Then one CTA per (system, chunk of cw columns) walks its system's block
+// rows in order: it forms W_l = B_l - L(S_l, 0:s0) X(0:s0, chunk) with a
+// register-blocked FP32 product whose operands are staged through shared
+// memory, and writes X_l = L~_ll W_l.  In FP32 the ticketed tasks of the
+// kernel above are short next to their dependency waits and global round
+// trips; here a unit is a whole system's chunk, and the units run longest
+// first.  Every output's sums run in a fixed order that depends neither on
+// cw nor on the other units: results are bitwise the same for any tile
+// width, alone and in a mix.
+constexpr int kSysThreads = 128;
+constexpr int kSysKC = 32;  // K chunk of the staged product
+
+struct SysUnit {
+  int sys;  // system index
+  int c0;   // first column of the chunk
+};
+
+struct SysSmem {
+  float inv[64][68];  // inv[col][row]: L~_ll, zeros above the diagonal (rows 16-byte aligned)
+  float w[64][36];    // w[row][col]: W_l for the chunk's columns
+  union {
+    struct {
+      float a[kSysKC][68];  // a[kk][row] = L(s0 + row, t0 + kk)
+      float b[kSysKC][36];  // b[kk][col] = X(t0 + kk, c0 + col)
+    } g;
+    struct {
+      float ls[2][32][33];  // leaf-inversion scratch
+      float t[32][33];      // combine: t[c][q] = L21(q, c), then T
+    } v;
+  } u;
+};
+
+// L~_ll for the diagonal block at s0 (order m <= 64) into sm.inv.
+__device__ void sys_invert(const BatchSys<float>& a, int64_t s0, int m, SysSmem& sm) {
+  const int tid = threadIdx.x, warp = tid >> 5;
+  for (int e = tid; e < 64 * 68; e += kSysThreads) (&sm.inv[0][0])[e] = 0.f;
+  __syncthreads();
+  const float* Lb = a.L + s0 * a.ldl + s0;
+  const int h = m > 32 ? 32 : m, r2 = m - h;
+  if (warp == 0) leaf_invert_warp<float>(Lb, a.ldl, h, &sm.inv[0][0], 68, sm.u.v.ls[0], a.status, s0);
+  if (warp == 1 && r2 > 0)
+    leaf_invert_warp<float>(Lb + 32 * a.ldl + 32, a.ldl, r2, &sm.inv[32][32], 68, sm.u.v.ls[1], a.status, s0 + 32);
+  if (r2 == 0) {
+    __syncthreads();
+    return;
+  }
+  {
+    float lv[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int e = tid + kSysThreads * j, c = e >> 5, q = e & 31;
+      lv[j] = (q < r2) ? Lb[static_cast<int64_t>(c) * a.ldl + 32 + q] : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int e = tid + kSysThreads * j;
+      sm.u.v.t[e >> 5][e & 31] = lv[j];
+    }
+  }
+  __syncthreads();
+  // T = -(L22^-1 L21), r2 x 32 (the paper's order: this product first)
+  float tv[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int e = tid + kSysThreads * j, r = e >> 5, c = e & 31;
+    float acc = 0.f;
+    if (r < r2)
+      for (int q = 0; q <= r; ++q) acc = fmaf(sm.inv[32 + q][32 + r], sm.u.v.t[c][q], acc);
+    tv[j] = -acc;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int e = tid + kSysThreads * j, r = e >> 5, c = e & 31;
+    sm.u.v.t[r][c] = tv[j];  // now t[r][c] = T(r, c)
+  }
+  __syncthreads();
+  // L21^-1 = T L11^-1
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int e = tid + kSysThreads * j, r = e >> 5, c = e & 31;
+    if (r < r2) {
+      float acc = 0.f;
+      for (int q = c; q < 32; ++q) acc = fmaf(sm.u.v.t[r][q], sm.inv[c][q], acc);
+      sm.inv[c][32 + r] = acc;
+    }
+  }
+  __syncthreads();
+}
+
+// One unit: columns [c0, c0 + nc) of one system.  Thread (ty, tx) owns rows
+// 4 ty .. 4 ty + 3 and columns CPT tx .. CPT tx + CPT - 1 of every block row.
+template <int CW>
+__device__ void sys_unit(const BatchSys<float>& a, int c0, SysSmem& sm) {
+  constexpr int CPT = CW / 8;
+  constexpr int NB = kSysKC * CW / kSysThreads;  // staged X values per thread and chunk
+  const int tid = threadIdx.x, ty = tid >> 3, tx = tid & 7;
+  const int nc = static_cast<int>(imin64(CW, a.k - c0));
+  for (int l = 0; l < a.N; ++l) {
+    const int64_t s0 = static_cast<int64_t>(l) * a.n0;
+    const int m = static_cast<int>(imin64(a.n0, a.n - s0));
+    {
+      // L~_ll from the workspace, every load in flight before the stores
+      const float* Li = a.Linv + static_cast<int64_t>(l) * a.inv_bstride;
+      float iv[32];
+#pragma unroll
+      for (int it = 0; it < 32; ++it) {
+        const int e = tid + kSysThreads * it, c = e >> 6, r = e & 63;
+        iv[it] = (c < m && r < m) ? Li[static_cast<int64_t>(c) * a.ldinv + r] : 0.f;
+      }
+#pragma unroll
+      for (int it = 0; it < 32; ++it) {
+        const int e = tid + kSysThreads * it;
+        sm.inv[e >> 6][e & 63] = iv[it];
+      }
+      __syncthreads();
+    }
+    float acc[4][CPT];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < CPT; ++j) acc[i][j] = 0.f;
+    // acc = L(S_l, 0:s0) X(0:s0, chunk), K in chunks of kSysKC, the next
+    // chunk's operands loaded into registers while this one is used
+    float ra[16], rb[NB];
+    auto load = [&](int64_t t0) {
+#pragma unroll
+      for (int it = 0; it < 16; ++it) {
+        const int e = tid + kSysThreads * it, kk = e >> 6, row = e & 63;
+        const int64_t t = t0 + kk;
+        ra[it] = (row < m && t < s0) ? a.L[t * a.ldl + s0 + row] : 0.f;
+      }
+#pragma unroll
+      for (int it = 0; it < NB; ++it) {
+        const int e = tid + kSysThreads * it, col = e >> 5, kk = e & 31;
+        const int64_t t = t0 + kk;
+        rb[it] = (col < nc && t < s0) ? a.X[static_cast<int64_t>(c0 + col) * a.ldx + t] : 0.f;
+      }
+    };
+    if (s0 > 0) load(0);
+    for (int64_t t0 = 0; t0 < s0; t0 += kSysKC) {
+#pragma unroll
+      for (int it = 0; it < 16; ++it) {
+        const int e = tid + kSysThreads * it;
+        sm.u.g.a[e >> 6][e & 63] = ra[it];
+      }
+#pragma unroll
+      for (int it = 0; it < NB; ++it) {
+        const int e = tid + kSysThreads * it;
+        sm.u.g.b[e & 31][e >> 5] = rb[it];
+      }
+      __syncthreads();
+      if (t0 + kSysKC < s0) load(t0 + kSysKC);
+#pragma unroll 8
+      for (int kk = 0; kk < kSysKC; ++kk) {
+        const float4 av = *reinterpret_cast<const float4*>(&sm.u.g.a[kk][ty * 4]);
+        const float a4[4] = {av.x, av.y, av.z, av.w};
+        float bv[CPT];
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) bv[j] = sm.u.g.b[kk][tx * CPT + j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < CPT; ++j) acc[i][j] = fmaf(a4[i], bv[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+    // W_l = B_l - acc (zeros outside the block and the chunk)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int row = ty * 4 + i;
+#pragma unroll
+      for (int j = 0; j < CPT; ++j) {
+        const int col = tx * CPT + j;
+        sm.w[row][col] = (row < m && col < nc)
+                             ? a.B[static_cast<int64_t>(c0 + col) * a.ldb + s0 + row] - acc[i][j]
+                             : 0.f;
+      }
+    }
+    __syncthreads();
+    // X_l = L~_ll W_l
+    float x[4][CPT];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < CPT; ++j) x[i][j] = 0.f;
+    for (int t = 0; t < m; ++t) {
+      const float4 iv = *reinterpret_cast<const float4*>(&sm.inv[t][ty * 4]);
+      const float i4[4] = {iv.x, iv.y, iv.z, iv.w};
+      float wv[CPT];
+#pragma unroll
+      for (int j = 0; j < CPT; ++j) wv[j] = sm.w[t][tx * CPT + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) x[i][j] = fmaf(i4[i], wv[j], x[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int row = ty * 4 + i;
+#pragma unroll
+      for (int j = 0; j < CPT; ++j) {
+        const int col = tx * CPT + j;
+        if (row < m && col < nc) a.X[static_cast<int64_t>(c0 + col) * a.ldx + s0 + row] = x[i][j];
+      }
+    }
+    __syncthreads();  // X_l visible to the block before the next block row reads it
+  }
+}
+
+// Diagonal block `c0` of system `sys` (the unit's fields reused) into the
+// system's inverse workspace (column-major, ld n0).
+__global__ void __launch_bounds__(kSysThreads) inv32_kernel(const BatchSys<float>* __restrict__ sys,
+                                                            const SysUnit* __restrict__ blocks) {
+  __shared__ __align__(16) SysSmem sm;
+  const SysUnit u = blocks[blockIdx.x];
+  const BatchSys<float>& a = sys[u.sys];
+  const int64_t s0 = static_cast<int64_t>(u.c0) * a.n0;
+  const int m = static_cast<int>(imin64(a.n0, a.n - s0));
+  sys_invert(a, s0, m, sm);
+  float* Li = const_cast<float*>(a.Linv) + static_cast<int64_t>(u.c0) * a.inv_bstride;
+#pragma unroll 8
+  for (int it = 0; it < 32; ++it) {
+    const int e = threadIdx.x + kSysThreads * it, c = e >> 6, r = e & 63;
+    if (c < m && r < m) Li[static_cast<int64_t>(c) * a.ldinv + r] = sm.inv[c][r];
+  }
+}
+
+__global__ void __launch_bounds__(kSysThreads, 4) sys32_kernel(const BatchSys<float>* __restrict__ sys,
+                                                            const SysUnit* __restrict__ units) {
+  __shared__ __align__(16) SysSmem sm;
+  const SysUnit u = units[blockIdx.x];
+  const BatchSys<float>& a = sys[u.sys];
+  if (a.cw == 8) sys_unit<8>(a, u.c0, sm);
+  else if (a.cw == 16) sys_unit<16>(a, u.c0, sm);
+  else sys_unit<32>(a, u.c0, sm);
 }
 
 // One (phase, part, system) range of tickets.
@@ -392,6 +636,7 @@ struct trsm_batch_s {
   void* sys_dev = nullptr;   // BatchSys<T>[count], then the phase entries
   void* ent_dev = nullptr;
   int nent = 0;
+  int ninv = 0;              // FP32: diagonal blocks, inverted by a first launch
   void* ws = nullptr;        // W, inverses, scratch, counters, task tables
   size_t ws_bytes = 0;
   bool owns_ws = true;
@@ -574,6 +819,93 @@ int build_batch(const trsm_batch_item* items, int count, trsm_batch_s* b, void* 
   return TRSM_SUCCESS;
 }
 
+// FP32 batches: the system table, one unit per (system, column chunk) in
+// decreasing order of work (n^2 times the chunk width), and the statuses.
+int build_batch32(const trsm_batch_item* items, int count, trsm_batch_s* b, void* user_ws, size_t user_bytes,
+                  cudaStream_t stream, size_t* size_only) {
+  using trsm::BatchSys;
+  std::vector<BatchSys<float>> sys(count);
+  std::vector<trsm::SysUnit> units, blocks;
+  size_t off = 0;
+  std::vector<size_t> inv_off(count);
+  for (int s = 0; s < count; ++s) {
+    const trsm_batch_item& it = items[s];
+    BatchSys<float>& a = sys[s];
+    a = BatchSys<float>{};
+    a.n = it.n;
+    a.k = it.k;
+    a.n0 = std::min<int64_t>(it.n0, it.n);
+    a.N = static_cast<int>((a.n + a.n0 - 1) / a.n0);
+    a.cw = it.tile_cols != 0 ? static_cast<int>(it.tile_cols) : a.k <= 8 ? 8 : a.k <= 16 ? 16 : 32;
+    a.C = static_cast<int>((a.k + a.cw - 1) / a.cw);
+    a.L = static_cast<const float*>(it.L);
+    a.ldl = it.ldl;
+    a.B = static_cast<const float*>(it.B);
+    a.ldb = it.ldb;
+    a.X = static_cast<float*>(it.X);
+    a.ldx = it.ldx;
+    a.ldinv = a.n0;
+    a.inv_bstride = a.n0 * a.n0;
+    inv_off[s] = off;
+    off = trsm::al256(off + sizeof(float) * a.N * a.n0 * a.n0);
+    for (int c = 0; c < a.C; ++c) units.push_back(trsm::SysUnit{s, c * a.cw});
+    for (int l = 0; l < a.N; ++l) blocks.push_back(trsm::SysUnit{s, l});
+  }
+  std::stable_sort(units.begin(), units.end(), [&](const trsm::SysUnit& x, const trsm::SysUnit& y) {
+    const BatchSys<float>& p = sys[x.sys];
+    const BatchSys<float>& q = sys[y.sys];
+    return p.n * p.n * p.cw > q.n * q.n * q.cw;
+  });
+  const size_t table_off = off;
+  off = trsm::al256(off + sizeof(BatchSys<float>) * count);
+  const size_t unit_off = off;
+  off = trsm::al256(off + sizeof(trsm::SysUnit) * (units.size() + blocks.size()));
+  b->counters_off = off;  // statuses and the error word: zeroed by every run
+  const size_t status_off = off;
+  off = trsm::al256(off + sizeof(int) * count);
+  const size_t err_off = off;
+  off = trsm::al256(off + sizeof(unsigned long long) + sizeof(int));
+  if (size_only) {
+    *size_only = off;
+    return TRSM_SUCCESS;
+  }
+  b->ws_bytes = off;
+  cudaError_t e = cudaSuccess;
+  if (user_ws) {
+    if (user_bytes < off || (reinterpret_cast<uintptr_t>(user_ws) & 255)) return TRSM_EINVAL;
+    b->ws = user_ws;
+    b->owns_ws = false;
+  } else {
+    e = cudaMalloc(&b->ws, b->ws_bytes);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? TRSM_ENOMEM : TRSM_ECUDA;
+    b->owns_ws = true;
+  }
+  unsigned char* ws = static_cast<unsigned char*>(b->ws);
+  b->status_dev = reinterpret_cast<int*>(ws + status_off);
+  b->ticket = reinterpret_cast<unsigned long long*>(ws + err_off);
+  b->err = reinterpret_cast<int*>(ws + err_off + sizeof(unsigned long long));
+  for (int s = 0; s < count; ++s) {
+    sys[s].status = b->status_dev + s;
+    sys[s].Linv = reinterpret_cast<const float*>(ws + inv_off[s]);
+  }
+  b->sys_dev = ws + table_off;
+  b->ent_dev = ws + unit_off;
+  b->nent = static_cast<int>(units.size());
+  b->total = static_cast<int64_t>(units.size());
+  b->grid = static_cast<int>(units.size());
+  b->ninv = static_cast<int>(blocks.size());
+  units.insert(units.end(), blocks.begin(), blocks.end());  // the block table follows the units
+  b->host_tables.resize(sizeof(BatchSys<float>) * count + sizeof(trsm::SysUnit) * units.size());
+  memcpy(b->host_tables.data(), sys.data(), sizeof(BatchSys<float>) * count);
+  memcpy(b->host_tables.data() + sizeof(BatchSys<float>) * count, units.data(), sizeof(trsm::SysUnit) * units.size());
+  e = cudaMemcpyAsync(b->sys_dev, b->host_tables.data(), sizeof(BatchSys<float>) * count, cudaMemcpyHostToDevice,
+                      stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->ent_dev, b->host_tables.data() + sizeof(BatchSys<float>) * count,
+                        sizeof(trsm::SysUnit) * units.size(), cudaMemcpyHostToDevice, stream);
+  return e == cudaSuccess ? TRSM_SUCCESS : TRSM_ECUDA;
+}
+
 int enqueue(trsm_batch_s* b, cudaStream_t s) {
   if (b->total == 0) return TRSM_SUCCESS;
   // counters, per-system statuses (0 = fine), ticket and error word start at zero
@@ -584,10 +916,13 @@ int enqueue(trsm_batch_s* b, cudaStream_t s) {
     trsm::batch_kernel<double><<<b->grid, trsm::NTHREADS, 0, s>>>(
         static_cast<const trsm::BatchSys<double>*>(b->sys_dev), static_cast<const trsm::PhaseEntry*>(b->ent_dev),
         b->nent, b->total, b->ticket, b->err);
-  else
-    trsm::batch_kernel<float><<<b->grid, trsm::NTHREADS, 0, s>>>(
-        static_cast<const trsm::BatchSys<float>*>(b->sys_dev), static_cast<const trsm::PhaseEntry*>(b->ent_dev),
-        b->nent, b->total, b->ticket, b->err);
+  else {
+    const auto* sys = static_cast<const trsm::BatchSys<float>*>(b->sys_dev);
+    const auto* units = static_cast<const trsm::SysUnit*>(b->ent_dev);
+    trsm::inv32_kernel<<<b->ninv, trsm::kSysThreads, 0, s>>>(sys, units + b->nent);
+    trsm::sys32_kernel<<<b->grid, trsm::kSysThreads, 0, s>>>(sys, units);
+    trsm::count_launch();
+  }
   trsm::count_launch();
   return cudaGetLastError() == cudaSuccess ? TRSM_SUCCESS : TRSM_ECUDA;
 }
@@ -627,7 +962,7 @@ static int create_impl(const trsm_batch_item* items, int count, int dtype, void*
   b->count = count;
   cudaGetDevice(&b->device);
   rc = dtype == TRSM_F64 ? build_batch<double>(items, count, b, ws, ws_bytes, stream, nullptr)
-                         : build_batch<float>(items, count, b, ws, ws_bytes, stream, nullptr);
+                         : build_batch32(items, count, b, ws, ws_bytes, stream, nullptr);
   if (rc != TRSM_SUCCESS) {
     trsm_batch_destroy(b);
     cudaGetLastError();
@@ -649,7 +984,7 @@ int trsm_batch_workspace_size(const trsm_batch_item* items, int count, int dtype
   if (rc != TRSM_SUCCESS) return rc;
   trsm_batch_s probe;
   return dtype == TRSM_F64 ? build_batch<double>(items, count, &probe, nullptr, 0, nullptr, bytes)
-                           : build_batch<float>(items, count, &probe, nullptr, 0, nullptr, bytes);
+                           : build_batch32(items, count, &probe, nullptr, 0, nullptr, bytes);
 }
 
 int trsm_batch_create_ws(const trsm_batch_item* items, int count, int dtype, void* ws_dev, size_t ws_bytes,

@@ -59,6 +59,75 @@ def test_batch_fp32_uneven(cuda_lib):
         assert _rel(sy["X"].cpu().numpy().astype(np.float64), want) < TOL32
 
 
+def test_batch_fp32_large_and_wide(cuda_lib):
+    """FP32 systems up to n = 1024 and k = 256 (many column chunks per
+    system), with n not a multiple of n0 and k not a multiple of the chunk."""
+    import paper_1612_01855_gb300 as g
+    systems = _systems(10, 1024, 256, seed=12, dtype=np.float32)
+    systems[0] = _systems(1, 2, 2, seed=13, dtype=np.float32)[0]  # n, k tiny
+    for sy in systems[1:4]:
+        sy["n0"] = 64
+    batch = g.Batch(systems, dtype="f32")
+    batch.run()
+    assert batch.status()[0] == 0
+    for sy in systems:
+        want = oracle.forward_subst(sy["Lh"].astype(np.float32).astype(np.float64),
+                                    sy["Bh"].astype(np.float32).astype(np.float64))
+        assert _rel(sy["X"].cpu().numpy().astype(np.float64), want) < TOL32
+
+
+def test_batch_fp32_tiles_mix_and_graph_are_bitwise_stable(cuda_lib):
+    """Every FP32 output is summed in one fixed order: 8-, 16- and 32-wide
+    column chunks give the same bits, a system alone equals the system in the
+    mix, and a captured graph replays the same bits."""
+    import torch
+    import paper_1612_01855_gb300 as g
+    systems = _systems(20, 600, 70, seed=9, dtype=np.float32)
+    ref = None
+    for tile in (0, 8, 16, 32):
+        for sy in systems:
+            sy["tile_cols"] = tile
+            sy["X"].fill_(float("nan"))
+        b = g.Batch(systems, dtype="f32")
+        b.run()
+        assert b.status()[0] == 0
+        got = [sy["X"].clone() for sy in systems]
+        if ref is None:
+            ref = got
+        else:
+            assert all(torch.equal(a, c) for a, c in zip(ref, got)), tile
+    for i in (2, 11):
+        alone = dict(systems[i])
+        alone["X"] = torch.empty_like(systems[i]["X"].t()).t()
+        b = g.Batch([alone], dtype="f32")
+        b.run()
+        assert b.status()[0] == 0
+        assert torch.equal(alone["X"], ref[i])
+    b = g.Batch(systems, dtype="f32")
+    b.capture()
+    for sy in systems:
+        sy["X"].fill_(float("nan"))
+    b.launch_graph()
+    b.launch_graph()
+    assert b.status()[0] == 0
+    assert all(torch.equal(sy["X"], x0) for sy, x0 in zip(systems, ref))
+
+
+def test_batch_fp32_reports_singular_item(cuda_lib):
+    """A zero pivot is reported by the first failing item and its row; a
+    later failing item does not hide it."""
+    import paper_1612_01855_gb300 as g
+    systems = _systems(8, 200, 40, seed=5, dtype=np.float32)
+    bad = next(i for i in range(2, 7) if systems[i]["Lh"].shape[0] >= 4)
+    r = systems[bad]["Lh"].shape[0] // 2
+    systems[bad]["L"][r, r] = 0.0
+    systems[7]["L"][0, 0] = 0.0
+    b = g.Batch(systems, dtype="f32")
+    b.run()
+    rc, item, row = b.status()
+    assert rc == -2 and item == bad and row == r
+
+
 def test_batch_with_resident_plans_and_graph(cuda_lib):
     """Items with resident plans (any n0) next to plan-less items; a captured
     CUDA graph replays the same results."""
