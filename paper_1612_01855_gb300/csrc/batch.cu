@@ -61,6 +61,7 @@ struct BatchSys {
   int cw;               // columns per column tile: 8, 16 or 32 (narrow B wastes less of a tile)
   int64_t total_rt;
   int64_t inv_tasks;    // N when the system inverts its own blocks, else 0
+  int inv_shared;       // 1: another part of the same item inverts the blocks (S tasks wait on invdone)
   int* wdone;           // [total_rt * C]
   int* xdone;           // [N * C]
   int* invdone;         // [N]
@@ -247,7 +248,8 @@ constexpr int kSysKC = 32;  // K chunk of the staged product
 
 struct SysUnit {
   int sys;  // system index
-  int c0;   // first column of the chunk
+  int c0;   // first column of the chunk (a block table entry: the block index)
+  int cw;   // chunk width: 8, 16 or 32
 };
 
 struct SysSmem {
@@ -466,8 +468,8 @@ __global__ void __launch_bounds__(kSysThreads, 4) sys32_kernel(const BatchSys<fl
   __shared__ __align__(16) SysSmem sm;
   const SysUnit u = units[blockIdx.x];
   const BatchSys<float>& a = sys[u.sys];
-  if (a.cw == 8) sys_unit<8>(a, u.c0, sm);
-  else if (a.cw == 16) sys_unit<16>(a, u.c0, sm);
+  if (u.cw == 8) sys_unit<8>(a, u.c0, sm);
+  else if (u.cw == 16) sys_unit<16>(a, u.c0, sm);
   else sys_unit<32>(a, u.c0, sm);
 }
 
@@ -583,7 +585,7 @@ __global__ void __launch_bounds__(NTHREADS, 8) batch_kernel(const BatchSys<T>* _
       const int j = static_cast<int>(o % a.C);
       if (tid == 0) {
         bool ok = true;
-        if (a.inv_tasks > 0) ok = wait_geq_b(a.invdone + l, 1, err);
+        if (a.inv_tasks > 0 || a.inv_shared) ok = wait_geq_b(a.invdone + l, 1, err);
         if (l > 0) {
           const int64_t q0 = static_cast<int64_t>(l) * a.R;
           for (int rr = 0; rr <= r && ok; ++rr) ok = wait_geq_b(a.wdone + (q0 + rr) * a.C + j, l, err);
@@ -654,22 +656,57 @@ struct trsm_batch_s {
 
 namespace {
 
+// An item whose k is above 32 and not a multiple of it is solved as two
+// parts: its first floor(k / 32) * 32 columns in 32-wide tiles and the rest
+// in one 8-, 16- or 32-wide tile, sharing L and the inverted blocks (only
+// the first part inverts them).  A column's arithmetic does not depend on
+// the tile it is in, so the split changes no result; it only drops most of
+// the padded columns of the last tile (on the batching workload the
+// executed multiply-adds fall by about a tenth).
+struct Part {
+  int item;      // the user's item
+  int64_t col0;  // first column of the part
+  int64_t k;     // columns in the part
+  int cw;        // tile width
+  int owner;     // part whose inverted blocks this part reads, or -1
+};
+
+std::vector<Part> split_parts(const trsm_batch_item* items, int count) {
+  std::vector<Part> parts;
+  for (int s = 0; s < count; ++s) {
+    const trsm_batch_item& it = items[s];
+    if (it.tile_cols == 0 && it.k > 32 && it.k % 32 != 0) {
+      const int64_t k32 = it.k / 32 * 32, rem = it.k - k32;
+      const int own = static_cast<int>(parts.size());
+      parts.push_back(Part{s, 0, k32, 32, -1});
+      parts.push_back(Part{s, k32, rem, rem <= 8 ? 8 : rem <= 16 ? 16 : 32, own});
+    } else {
+      const int cw = it.tile_cols != 0 ? static_cast<int>(it.tile_cols) : it.k <= 8 ? 8 : it.k <= 16 ? 16 : 32;
+      parts.push_back(Part{s, 0, it.k, cw, -1});
+    }
+  }
+  return parts;
+}
+
 template <class T>
 int build_batch(const trsm_batch_item* items, int count, trsm_batch_s* b, void* user_ws, size_t user_bytes,
                 cudaStream_t stream, size_t* size_only) {
   using trsm::BatchSys;
-  std::vector<BatchSys<T>> sys(count);
+  const std::vector<Part> parts = split_parts(items, count);
+  const int P = static_cast<int>(parts.size());
+  std::vector<BatchSys<T>> sys(P);
   // pass 1: sizes and workspace layout
   size_t off = 0;
   struct Off {
     size_t W, inv, tsc;
   };
-  std::vector<Off> offs(count);
-  for (int s = 0; s < count; ++s) {
-    const trsm_batch_item& it = items[s];
+  std::vector<Off> offs(P);
+  for (int s = 0; s < P; ++s) {
+    const Part& pt = parts[s];
+    const trsm_batch_item& it = items[pt.item];
     BatchSys<T>& a = sys[s];
     a.n = it.n;
-    a.k = it.k;
+    a.k = pt.k;
     const bool planned = it.plan != nullptr;
     int64_t n0 = planned ? 0 : it.n0;
     if (planned) {
@@ -682,32 +719,34 @@ int build_batch(const trsm_batch_item* items, int count, trsm_batch_s* b, void* 
     a.R = static_cast<int>((a.n0 + trsm::TILE - 1) / trsm::TILE);
     const int64_t mlast = a.n - static_cast<int64_t>(a.N - 1) * a.n0;
     a.Rlast = static_cast<int>((mlast + trsm::TILE - 1) / trsm::TILE);
-    a.cw = it.tile_cols != 0 ? static_cast<int>(it.tile_cols) : a.k <= 8 ? 8 : a.k <= 16 ? 16 : trsm::TILE;
+    a.cw = pt.cw;
     a.C = static_cast<int>((a.k + a.cw - 1) / a.cw);
     a.total_rt = static_cast<int64_t>(a.N - 1) * a.R + a.Rlast;
-    a.inv_tasks = planned ? 0 : a.N;
+    const bool inverts = !planned && pt.owner < 0;
+    a.inv_tasks = inverts ? a.N : 0;
+    a.inv_shared = (!planned && pt.owner >= 0) ? 1 : 0;
     a.ldw = trsm::align4b(a.n);
     offs[s].W = off;
     off = trsm::al256(off + sizeof(T) * a.ldw * a.k);
     offs[s].inv = off;
-    if (!planned) off = trsm::al256(off + sizeof(T) * a.N * a.n0 * a.n0);
+    if (inverts) off = trsm::al256(off + sizeof(T) * a.N * a.n0 * a.n0);
     offs[s].tsc = off;
-    if (!planned && a.n0 > 32) off = trsm::al256(off + sizeof(T) * a.N * 1024);
+    if (inverts && a.n0 > 32) off = trsm::al256(off + sizeof(T) * a.N * 1024);
   }
   // task table and phase entries (uploaded once at creation), kept before
   // the counters: every run zeroes [counters_off, ws_bytes)
   int maxN = 0;
-  for (int s = 0; s < count; ++s) maxN = std::max(maxN, sys[s].N);
+  for (int s = 0; s < P; ++s) maxN = std::max(maxN, sys[s].N);
   size_t nent_max = 0;
-  for (int s = 0; s < count; ++s) nent_max += 2 * static_cast<size_t>(sys[s].N) + (sys[s].inv_tasks > 0 ? 1 : 0);
+  for (int s = 0; s < P; ++s) nent_max += 2 * static_cast<size_t>(sys[s].N) + (sys[s].inv_tasks > 0 ? 1 : 0);
   const size_t table_off = off;
-  off = trsm::al256(off + sizeof(BatchSys<T>) * count);
+  off = trsm::al256(off + sizeof(BatchSys<T>) * P);
   const size_t ent_off = off;
   off = trsm::al256(off + sizeof(trsm::PhaseEntry) * nent_max);
   b->counters_off = off;
   size_t cnt = 0;
-  std::vector<size_t> coff(count);
-  for (int s = 0; s < count; ++s) {
+  std::vector<size_t> coff(P);
+  for (int s = 0; s < P; ++s) {
     coff[s] = cnt;
     cnt += static_cast<size_t>(sys[s].total_rt * sys[s].C + static_cast<int64_t>(sys[s].N) * sys[s].C + sys[s].N);
   }
@@ -737,12 +776,13 @@ int build_batch(const trsm_batch_item* items, int count, trsm_batch_s* b, void* 
   b->ticket = reinterpret_cast<unsigned long long*>(ws + ticket_off);
   b->err = reinterpret_cast<int*>(ws + ticket_off + sizeof(unsigned long long));
   // pass 2: pointers
-  for (int s = 0; s < count; ++s) {
-    const trsm_batch_item& it = items[s];
+  for (int s = 0; s < P; ++s) {
+    const Part& pt = parts[s];
+    const trsm_batch_item& it = items[pt.item];
     BatchSys<T>& a = sys[s];
-    a.B = static_cast<const T*>(it.B);
+    a.B = static_cast<const T*>(it.B) + pt.col0 * it.ldb;
     a.ldb = it.ldb;
-    a.X = static_cast<T*>(it.X);
+    a.X = static_cast<T*>(it.X) + pt.col0 * it.ldx;
     a.ldx = it.ldx;
     a.W = reinterpret_cast<T*>(ws + offs[s].W);
     if (it.plan) {
@@ -753,6 +793,16 @@ int build_batch(const trsm_batch_item* items, int count, trsm_batch_s* b, void* 
       a.inv_bstride = ldt * a.n0 + a.n0;
       a.Loff = reinterpret_cast<const T*>(Lt);
       a.ldoff = ldt;
+      a.L = nullptr;
+      a.ldl = 0;
+      a.Tsc = nullptr;
+    } else if (pt.owner >= 0) {
+      const BatchSys<T>& o = sys[pt.owner];  // set earlier in this pass
+      a.Linv = o.Linv;
+      a.ldinv = o.ldinv;
+      a.inv_bstride = o.inv_bstride;
+      a.Loff = o.Loff;
+      a.ldoff = o.ldoff;
       a.L = nullptr;
       a.ldl = 0;
       a.Tsc = nullptr;
@@ -769,15 +819,15 @@ int build_batch(const trsm_batch_item* items, int count, trsm_batch_s* b, void* 
     int* c = cbase + coff[s];
     a.wdone = c;
     a.xdone = c + a.total_rt * a.C;
-    a.invdone = a.xdone + static_cast<int64_t>(a.N) * a.C;
-    a.status = b->status_dev + s;
+    a.invdone = pt.owner >= 0 ? sys[pt.owner].invdone : a.xdone + static_cast<int64_t>(a.N) * a.C;
+    a.status = b->status_dev + pt.item;
   }
   // phase-major ticket ranges
   std::vector<trsm::PhaseEntry> ent;
   int64_t task = 0;
   for (int p = 0; p <= maxN; ++p) {
     for (int part = 0; part < (p == 0 ? 1 : 2); ++part) {
-      for (int s = 0; s < count; ++s) {
+      for (int s = 0; s < P; ++s) {
         const BatchSys<T>& a = sys[s];
         int64_t cntp = 0;
         if (p == 0) {
@@ -801,13 +851,13 @@ int build_batch(const trsm_batch_item* items, int count, trsm_batch_s* b, void* 
   b->ent_dev = ws + ent_off;
   // the host copies stay in the batch until it is destroyed, so the
   // asynchronous uploads may complete after this call returns
-  b->host_tables.resize(sizeof(BatchSys<T>) * count + sizeof(trsm::PhaseEntry) * ent.size());
-  memcpy(b->host_tables.data(), sys.data(), sizeof(BatchSys<T>) * count);
-  memcpy(b->host_tables.data() + sizeof(BatchSys<T>) * count, ent.data(), sizeof(trsm::PhaseEntry) * ent.size());
-  e = cudaMemcpyAsync(b->sys_dev, b->host_tables.data(), sizeof(BatchSys<T>) * count, cudaMemcpyHostToDevice,
+  b->host_tables.resize(sizeof(BatchSys<T>) * P + sizeof(trsm::PhaseEntry) * ent.size());
+  memcpy(b->host_tables.data(), sys.data(), sizeof(BatchSys<T>) * P);
+  memcpy(b->host_tables.data() + sizeof(BatchSys<T>) * P, ent.data(), sizeof(trsm::PhaseEntry) * ent.size());
+  e = cudaMemcpyAsync(b->sys_dev, b->host_tables.data(), sizeof(BatchSys<T>) * P, cudaMemcpyHostToDevice,
                       stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(b->ent_dev, b->host_tables.data() + sizeof(BatchSys<T>) * count,
+    e = cudaMemcpyAsync(b->ent_dev, b->host_tables.data() + sizeof(BatchSys<T>) * P,
                         sizeof(trsm::PhaseEntry) * ent.size(), cudaMemcpyHostToDevice, stream);
   int per_sm = 0;
   if (e == cudaSuccess)
@@ -848,13 +898,21 @@ int build_batch32(const trsm_batch_item* items, int count, trsm_batch_s* b, void
     a.inv_bstride = a.n0 * a.n0;
     inv_off[s] = off;
     off = trsm::al256(off + sizeof(float) * a.N * a.n0 * a.n0);
-    for (int c = 0; c < a.C; ++c) units.push_back(trsm::SysUnit{s, c * a.cw});
-    for (int l = 0; l < a.N; ++l) blocks.push_back(trsm::SysUnit{s, l});
+    // chunks of cw columns; by k, 32-wide chunks and one narrower last chunk
+    if (it.tile_cols == 0 && a.k > 32) {
+      int64_t c0 = 0;
+      for (; c0 + 32 <= a.k; c0 += 32) units.push_back(trsm::SysUnit{s, static_cast<int>(c0), 32});
+      const int64_t rem = a.k - c0;
+      if (rem > 0) units.push_back(trsm::SysUnit{s, static_cast<int>(c0), rem <= 8 ? 8 : rem <= 16 ? 16 : 32});
+    } else {
+      for (int c = 0; c < a.C; ++c) units.push_back(trsm::SysUnit{s, c * a.cw, a.cw});
+    }
+    for (int l = 0; l < a.N; ++l) blocks.push_back(trsm::SysUnit{s, l, 0});
   }
   std::stable_sort(units.begin(), units.end(), [&](const trsm::SysUnit& x, const trsm::SysUnit& y) {
     const BatchSys<float>& p = sys[x.sys];
     const BatchSys<float>& q = sys[y.sys];
-    return p.n * p.n * p.cw > q.n * q.n * q.cw;
+    return p.n * p.n * x.cw > q.n * q.n * y.cw;
   });
   const size_t table_off = off;
   off = trsm::al256(off + sizeof(BatchSys<float>) * count);

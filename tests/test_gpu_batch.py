@@ -221,6 +221,42 @@ def test_batch_tile_shapes_give_identical_results(cuda_lib):
         g.Batch(systems)
 
 
+def test_batch_column_split_is_bitwise_neutral(cuda_lib):
+    """Items with k above 32 and not a multiple of it run as a 32-wide part
+    and a narrow remainder part that shares the first part's inverted
+    blocks (or the plan): the bits equal those of 32-wide tiles throughout,
+    and a zero pivot is still reported by item and row."""
+    import torch
+    import paper_1612_01855_gb300 as g
+    systems = []
+    for i, (n, k) in enumerate([(150, 33), (300, 40), (97, 100), (64, 65), (500, 47), (33, 200)]):
+        L, B = inputs.well_conditioned(n, k, seed=2100 + i)
+        systems.append({"Lh": L, "Bh": B, "L": _dev(L, np.float64), "B": _dev(B, np.float64),
+                        "X": torch.full((k, n), float("nan"), dtype=torch.float64, device="cuda").t(),
+                        "n0": (32, 64)[i % 2]})
+    plan = g.trsm_plan(systems[4]["L"], 100)
+    systems[4]["plan"] = plan
+    got = {}
+    for tile in (0, 32):
+        for sy in systems:
+            sy["tile_cols"] = tile
+            sy["X"].fill_(float("nan"))
+        b = g.Batch(systems)
+        b.run()
+        assert b.status()[0] == 0
+        got[tile] = [sy["X"].clone() for sy in systems]
+    assert all(torch.equal(a, c) for a, c in zip(got[0], got[32]))
+    for sy, x in zip(systems, got[0]):
+        assert _rel(x.cpu().numpy(), oracle.forward_subst(sy["Lh"], sy["Bh"])) < TOL64
+    for sy in systems:
+        sy["tile_cols"] = 0
+    systems[1]["L"][200, 200] = 0.0  # n = 300, k = 40: split into 32 + 8 columns
+    b = g.Batch(systems)
+    b.run()
+    rc, item, row = b.status()
+    assert rc == -2 and item == 1 and row == 200
+
+
 def test_autotuner_choices(cuda_lib):
     from paper_1612_01855_gb300 import autotune
     table = autotune.tune_batch("f64", count=12, kmax=32, reps=1)
