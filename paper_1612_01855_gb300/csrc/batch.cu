@@ -128,12 +128,17 @@ struct NarrowMap {
   __device__ static int col(int j) { return (threadIdx.x % TX) * 2 + j; }
 };
 
+// kTriFrom >= 0: A is lower triangular from K offset kTriFrom on (the
+// diagonal chunk of an S task, A(row, kTriFrom + kk) = 0 for kk > row).
+// Warp w holds rows 8w .. 8w + 7 for every CW, so it stops that chunk after
+// 8w + 8 steps: the products it skips are zeros.
 template <class TC, bool kAMutable, bool kBMutable, int CW>
 __device__ __forceinline__ void tile_mma_cw(const TC* __restrict__ A, int64_t lda, const TC* __restrict__ B,
                                             int64_t ldb, int m, int nc, int64_t kbeg, int64_t kend,
-                                            TileSmemT<TC>& sm, TC (&acc)[TM][TN]) {
+                                            TileSmemT<TC>& sm, TC (&acc)[TM][TN], int64_t kTriFrom = -1) {
   using Mp = NarrowMap<CW>;
   const int tid = threadIdx.x;
+  const int tri_end = 8 * (tid >> 5) + 8;
   for (int64_t k0 = kbeg; k0 < kend; k0 += KCH) {
 #pragma unroll
     for (int it = 0; it < (KCH * TILE) / NTHREADS; ++it) {
@@ -154,8 +159,9 @@ __device__ __forceinline__ void tile_mma_cw(const TC* __restrict__ A, int64_t ld
       sm.b[kk][c] = v;
     }
     __syncthreads();
+    const int kk_end = (k0 == kTriFrom) ? tri_end : KCH;
 #pragma unroll 8
-    for (int kk = 0; kk < KCH; ++kk) {
+    for (int kk = 0; kk < kk_end; ++kk) {
       TC av[Mp::TMR], bv[2];
 #pragma unroll
       for (int i = 0; i < Mp::TMR; ++i) av[i] = sm.a[kk][Mp::row(i)];
@@ -181,12 +187,14 @@ __device__ __forceinline__ void s_body(const BatchSys<T>& a, int l, int r, int j
   const int nc = static_cast<int>(imin64(CW, a.k - static_cast<int64_t>(j) * CW));
   const int64_t kend = imin64(static_cast<int64_t>(r + 1) * TILE, ml);
   const T* Ainv = a.Linv + l * a.inv_bstride + r * TILE;
+  // L~_ll is lower triangular: the K chunk at r * TILE is its diagonal chunk
+  const int64_t tri = static_cast<int64_t>(r) * TILE;
   if (l == 0)
     tile_mma_cw<T, true, false, CW>(Ainv, a.ldinv, a.B + static_cast<int64_t>(j) * CW * a.ldb, a.ldb, m, nc, 0, kend,
-                                    sm, acc);
+                                    sm, acc, tri);
   else
     tile_mma_cw<T, true, true, CW>(Ainv, a.ldinv, a.W + static_cast<int64_t>(j) * CW * a.ldw + s0, a.ldw, m, nc, 0,
-                                   kend, sm, acc);
+                                   kend, sm, acc, tri);
   const int64_t row0 = s0 + static_cast<int64_t>(r) * TILE;
 #pragma unroll
   for (int i = 0; i < Mp::TMR; ++i) {
