@@ -95,13 +95,18 @@ __device__ __noinline__ void leaf_invert_warp(const T* __restrict__ A, int64_t l
     // status 0 = fine; otherwise INT_MAX - (smallest singular row)
     if (dl == T(0) || !isfinite(static_cast<double>(dl))) atomicMax(status, INT_MAX - static_cast<int>(row0 + lane));
   }
+  // the pivots' reciprocals, all at once, into the padding column: the
+  // substitution below then multiplies instead of dividing at each of its
+  // 32 dependent steps
+  ls[lane][32] = (lane < m) ? T(1) / ls[lane][lane] : T(0);
+  __syncwarp();
   T y[32];
 #pragma unroll
   for (int r = 0; r < 32; ++r) y[r] = (r == lane) ? T(1) : T(0);
 #pragma unroll
   for (int l = 0; l < 32; ++l) {
     if (l < m) {
-      y[l] = y[l] / ls[l][l];
+      y[l] = y[l] * ls[l][32];
 #pragma unroll
       for (int r = l + 1; r < 32; ++r) y[r] = fma(-ls[r][l], y[l], y[r]);
     }
