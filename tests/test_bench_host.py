@@ -1,0 +1,74 @@
+"""Host-side helpers of bench.py (no GPU): the gate on the stored DRAM
+counters, the peak figures and their fallback, the CPU-oracle baseline's
+bounded sample, replica throughput, and the parsing of the clock samples
+that decides whether a run was throttled."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import bench
+
+
+def test_solve_traffic_applies_only_to_the_captured_source(monkeypatch):
+    shapes = [(16384, 256), (8192, 8192), (2048, 131072)]
+    n0s = [256, 512, 2048]
+    monkeypatch.setattr(bench, "solve_source_sha256", lambda: bench.SOLVE_TRAFFIC_SHA256)
+    mean, by_shape = bench.solve_traffic(shapes, n0s)
+    stored = [bench.SOLVE_TRAFFIC[(n, k, n0)] for (n, k), n0 in zip(shapes, n0s)]
+    assert mean == pytest.approx(sum(stored) / 3)
+    assert by_shape["8192x8192"]["algorithmic_bytes"] == int(8 * (8192 * 8192 / 2 + 2 * 8192 * 8192))
+    assert bench.solve_traffic([(16384, 256)], [128]) == (None, None)  # shape/n0 not captured
+    monkeypatch.setattr(bench, "solve_source_sha256", lambda: "0" * 64)
+    assert bench.solve_traffic(shapes, n0s) == (None, None)  # kernel changed since the capture
+
+
+def test_measured_peaks_and_fallback(tmp_path, monkeypatch):
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"bf16_tflops": 1925.7, "bf16_tflops_sustained": 1712.9}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    burst, sustained, src = bench.measured_peaks()
+    assert (burst, sustained) == (1925.7, 1712.9) and src.startswith("measured")
+    os.remove(tmp_path / "MEASURED_PEAKS.json")
+    burst, sustained, src = bench.measured_peaks()
+    assert (burst, sustained) == (1900.0, 1700.0) and src.startswith("fallback")
+
+
+def test_cpu_oracle_rate_takes_a_bounded_sample():
+    shapes = [(64, 40), (96, 7)]
+    data = bench.make_inputs(shapes, seed=3)
+    rate, sample, cores = bench.cpu_oracle_rate(data, shapes, budget_s=0.05)
+    assert rate > 0 and cores >= 1
+    parts = sample.split("; ")
+    assert parts[0].startswith("n=64: ") and parts[1].startswith("n=96: ")
+    for part, (n, k) in zip(parts, shapes):
+        used = int(part.split(": ")[1].split(" of ")[0])
+        assert 1 <= used <= k and part.endswith(f"of {k} columns")
+
+
+def test_replica_throughput_counts_every_rank():
+    assert bench.replica_throughput(1e12, 4, 1000.0) == pytest.approx(4e12)
+    assert bench.replica_throughput(2e9, 1, 2.0) == pytest.approx(1e12)
+
+
+class _Done:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def test_clock_sampler_reads_throttle_reasons(tmp_path):
+    s = bench.ClockSampler(0)
+    s.proc, s.fh = _Done(), open(os.devnull, "w")
+    rows = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, 1965, 2070, 1380.0, 0x4, Not Active, Not Active, Not Active, Active",
+            "0, 2070, 2070, 950.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "garbage line"]
+    with open(s.path, "w") as fh:
+        fh.write("\n".join(rows) + "\n")
+    out = s.stop()
+    assert out["samples"] == 3 and out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"]
+    assert not os.path.exists(s.path)
