@@ -1,8 +1,9 @@
-// Many independent triangular systems in one persistent launch.
+// Many independent triangular systems in one run.
 //
 // Every system is Algorithm It-Inv-TRSM (Section 6.2) on its own L, B, X;
-// the systems differ in n, k and block size.  One kernel serves all of
-// them: each CTA repeatedly takes the next ticket of a global counter.  The
+// the systems differ in n, k and block size.  In FP64 one persistent kernel
+// serves all of them: each CTA repeatedly takes the next ticket of a global
+// counter.  The
 // tasks of a system are
 //   INV(b)          invert diagonal block b (only when the system has no plan:
 //                   Algorithm RecTriInv with one level, n0 <= 64)

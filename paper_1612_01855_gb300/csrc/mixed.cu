@@ -12,8 +12,10 @@
 //            R = B - L X               FP64-class residual
 //
 // inner_solve is the right-looking form of Algorithm It-Inv-TRSM: for every
-// block row i, D_i = L~_ii W_i with the FP64 inverse of the diagonal block
-// (DFMA tile kernel), then W(T_{i+1}) -= L(T_{i+1}, S_i) D_i as one
+// block row i, D_i = L~_ii W_i with the inverse of the diagonal block (in
+// FP64 on the DFMA pipe, or, with TRSM_SOLVE_S_FP32, in FP32 from FP32
+// copies of the inverses kept in the plan), then
+// W(T_{i+1}) -= L(T_{i+1}, S_i) D_i as one
 // tcgen05 GEMM with bf16, tf32, split bf16 or split fp16 (hi + lo planes,
 // three products) operands and FP32 accumulation; W is the FP32 working copy
 // of R.  The fp16 planes are scaled by powers of two into fp16's range: each
