@@ -281,8 +281,22 @@ struct SysSmem {
   } u;
 };
 
+// The inversion launch needs only the inverse and the leaf scratch: 30 KB
+// instead of 40, so seven CTAs fit per SM instead of five (two of a CTA's
+// four warps wait at the barrier during the leaf substitutions).
+struct InvSmem {
+  float inv[64][68];
+  union {
+    struct {
+      float ls[2][32][33];
+      float t[32][33];
+    } v;
+  } u;
+};
+
 // L~_ll for the diagonal block at s0 (order m <= 64) into sm.inv.
-__device__ void sys_invert(const BatchSys<float>& a, int64_t s0, int m, SysSmem& sm) {
+template <class Smem>
+__device__ void sys_invert(const BatchSys<float>& a, int64_t s0, int m, Smem& sm) {
   const int tid = threadIdx.x, warp = tid >> 5;
   for (int e = tid; e < 64 * 68; e += kSysThreads) (&sm.inv[0][0])[e] = 0.f;
   __syncthreads();
@@ -463,7 +477,7 @@ __device__ void sys_unit(const BatchSys<float>& a, int c0, SysSmem& sm) {
 // system's inverse workspace (column-major, ld n0).
 __global__ void __launch_bounds__(kSysThreads) inv32_kernel(const BatchSys<float>* __restrict__ sys,
                                                             const SysUnit* __restrict__ blocks) {
-  __shared__ __align__(16) SysSmem sm;
+  __shared__ __align__(16) InvSmem sm;
   const SysUnit u = blocks[blockIdx.x];
   const BatchSys<float>& a = sys[u.sys];
   const int64_t s0 = static_cast<int64_t>(u.c0) * a.n0;
