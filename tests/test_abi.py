@@ -73,6 +73,49 @@ def test_invalid_arguments_rejected_before_any_device_work():
     assert lib.trsm_solve(None, None, 1, 1, None, 1, None) == binding.TRSM_EINVAL
 
 
+def test_every_entry_point_checks_its_arguments_on_the_host():
+    """Null handles, bad sizes and bad modes come back as errors from the
+    host-side checks of each entry point, before any CUDA call."""
+    from paper_1612_01855_gb300 import binding
+    lib = binding.load_library()
+    E = binding.TRSM_EINVAL
+    p16 = ctypes.c_void_p(16)
+    # solves on a null plan, under every schedule and workspace form
+    for sched in (0, 1, 2, 5):
+        assert lib.trsm_solve_schedule(None, p16, 1, 8, p16, 8, sched, None) == E
+    assert lib.trsm_solve_ws(None, p16, 1, 8, p16, 8, p16, 1 << 20, None) == E
+    assert lib.trsm_solve_noalloc(None, p16, 1, 8, p16, 8, None) == E
+    assert lib.trsm_plan_mixed(None, p16, 8, binding.TRSM_INNER_TF32, None) == E
+    it = ctypes.c_int(7)
+    up = ctypes.c_double(1.0)
+    assert lib.trsm_solve_mixed(None, p16, 1, 8, p16, 8, 0, 10, 1e-12, ctypes.byref(it), ctypes.byref(up), None) == E
+    assert it.value == 0 and up.value == 0.0
+    # host-buffer entry
+    assert lib.trsm_host(None, 8, 8, 4, p16, 1, 8, p16, 8, None) == E
+    assert lib.trsm_host(p16, 0, 8, 4, p16, 1, 8, p16, 8, None) == E
+    assert lib.trsm_host(p16, 8, 8, 4, None, 1, 8, p16, 8, None) == E
+    assert lib.trsm_host(p16, 8, 8, 4, p16, -1, 8, p16, 8, None) == E
+    # plan queries on a null plan
+    assert lib.trsm_plan_device_bytes(None) == 0
+    assert lib.trsm_plan_sizes(None, None, None, None) == E
+    # batches: null handle
+    item, row = ctypes.c_int(5), ctypes.c_int64(5)
+    assert lib.trsm_batch_run(None, None) == E
+    assert lib.trsm_batch_capture(None, None) == E
+    assert lib.trsm_batch_launch_graph(None, None) == E
+    assert lib.trsm_batch_status(None, None, ctypes.byref(item), ctypes.byref(row)) == E
+    assert item.value == -1 and row.value == -1
+    assert lib.trsm_batch_workspace_bytes(None) == 0
+    lib.trsm_batch_destroy(None)
+    # engine building blocks
+    assert lib.trsm_tc_gemm_selftest(4, p16, p16, p16, 128, 128, 64, p16, None) == -1   # no mode 4
+    assert lib.trsm_tc_gemm_selftest(0, p16, p16, p16, 128, 128, 60, p16, None) == -1   # K not a multiple of 8
+    assert lib.trsm_residual_sliced(p16, 8, 8, p16, 1, 8, p16, 8, p16, 8, 6, p16, None) == -1  # 7 or 8 planes
+    assert lib.trsm_residual_sliced(None, 8, 8, p16, 1, 8, p16, 8, p16, 8, 7, p16, None) == -1
+    assert lib.trsm_wait_selftest(2, 1000, None) == E
+    assert lib.trsm_wait_selftest(0, 0, None) == E
+
+
 def _imports(path):
     src = open(path).read()
     return re.findall(r"^\s*(?:from|import)\s+([\w\.]+)", src, flags=re.M)
