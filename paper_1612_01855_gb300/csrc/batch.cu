@@ -74,10 +74,6 @@ __device__ bool wait_geq_b(const int* p, int target, int* err) {
   return wait_geq_bounded(p, target, err, 1, kWaitNs, kWaitIters, 512) > 0;
 }
 
-__host__ __device__ __forceinline__ int64_t wave_first(int64_t l, int64_t R, int64_t total_rt, int64_t C) {
-  return C * (l * total_rt - R * (l * (l - 1) / 2));
-}
-
 // Out of line: unrolled over the 32 columns it is most of the kernel's
 // code, and it runs only in the inversion phase.
 template <class T>

@@ -179,7 +179,7 @@ __global__ void pack_panels_f16_kernel(const double* __restrict__ L, int64_t ldl
   if (rows <= 0) return;
   const int sc = 14 - exp_above(pmax[i]);
   if (blockIdx.x == 0 && threadIdx.x == 0) panel_exp[i] = sc;
-  __half* P = out + 2 * panel_off(i, n, n0, n0p);
+  __half* P = out + LowP<3>::kPlanes * panel_off(i, n, n0, n0p);
   const int64_t total = rows * n0p;
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
        e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
