@@ -5,10 +5,11 @@ processor its three-dimensional rule gives n0 ~ min(sqrt(n k), n)).  On one
 GPU the choices that matter are measured instead:
 
 * batches (`tune_batch`): per size bucket, the in-launch inversion block
-  n0 (32 or 64) and the output tile shape (32-wide column tiles, or column
-  tiles narrowed to k by the library: 8 for k <= 8, 16 for k <= 16) -- each
-  candidate timed on synthetic systems of that bucket through the batched
-  C ABI, the fastest kept; `choose` maps a system to its bucket's choice;
+  n0 (32 or 64) and the output tile shape -- 32-wide column tiles, or tiles
+  fitted to k by the library (8 for k <= 8, 16 for k <= 16, and above 32
+  32-wide tiles plus one narrower tile for the remainder) -- each candidate
+  timed on synthetic systems of that bucket through the batched C ABI, the
+  fastest kept; `choose` maps a system to its bucket's choice;
 * single systems (`tune_schedule`): the schedule of the blocked solve
   (dependency-driven kernel, right-looking loop with look-ahead, Rec-TRSM)
   timed on the system itself.
@@ -24,7 +25,7 @@ from . import binding
 # size buckets by n (log2 ranges), as in the batching workload n in [32, 1024]
 BUCKETS = [(1, 64), (64, 128), (128, 256), (256, 512), (512, 1025)]
 N0_CANDIDATES = (32, 64)
-TILE_CANDIDATES = (0, 32)  # 0: column tiles narrowed to k by the library
+TILE_CANDIDATES = (0, 32)  # 0: column tiles fitted to k by the library
 _cache = {}
 
 
