@@ -5,10 +5,15 @@ for each shape (n, k) in {(16384, 256), (8192, 8192), (2048, 131072)} at its
 block size n0, trsm_plan (invert the diagonal blocks) + trsm_solve (blocked
 solve), inputs resident in HBM.  value = sum(n^2 k) / step time (TFLOP/s).
 
-Prints ONE JSON line (rank 0).  `--impl reference` times the CPU oracle
-(forward substitution, the plain definition of X = L^-1 B) on the host cores
-instead, on a bounded column sample of the same workload.  `--sweep` prints
-one extra line per (shape, n0) of the block-size sweep.
+Prints ONE compact JSON line (rank 0).  Beside the timed step it carries the
+other configurations, each measured in the same run: the block-size sweep
+(`n0_sweep`), the precision configuration at c = 2, 4, 6 (`precision`), the
+batches of uneven systems (`batched`), the serving loop (`serving`), the
+solve schedules (`schedules_ms`) and the sliced residual's roofline.
+`--details FILE` writes the full records of every study.  `--impl reference`
+times the CPU oracle (forward substitution, the plain definition of
+X = L^-1 B) on the host cores instead, on a bounded column sample of the
+same workload.
 """
 import argparse
 import json
@@ -29,17 +34,17 @@ SHAPES = [(16384, 256), (8192, 8192), (2048, 131072)]
 # package); the paper's a-priori rule for p = 1 is n0 ~ min(sqrt(n k), n).
 DEFAULT_N0 = {(16384, 256): 256, (8192, 8192): 512, (2048, 131072): 2048}
 SWEEP_N0 = [64, 128, 256, 512, 1024, None]  # None = n (full inversion)
+SCHEDULE_NAMES = ("dag", "right-looking", "recursive")
 # Block size of the mixed-precision figure (n = 16384, k = 4096).  Larger
 # blocks suit the mixed path: fewer, longer tensor-core updates, and the
 # diagonal multiplies run in FP32 (measured: 163 / 137 / 131 / 135 ms at
 # n0 = 256 / 512 / 1024 / 2048, tf32 with FP32 diagonal multiplies).
 MIXED_N0 = 1024
 NOMINAL_SM_MHZ = 2070.0
-SMS = 152
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one
-# it_inv_solve_kernel launch per bench shape, from one ncu capture each
-# (profiles/it_inv_solve_kernel_dram_bench_shapes.md).  They describe the
+# it_inv_solve_kernel launch per bench shape, from one 1-pass ncu capture of
+# each shape in the bench's launch configuration.  They describe the
 # kernel source they were taken from; once solve.cu or fp64_tile.cuh changes
 # the figures no longer apply and the bench reports traffic as null.
 SOLVE_TRAFFIC_SHA256 = "1b10bcd32c87a0a41972ba56e8f8083faf7da9229e5723ae1281f62ca03d8e2a"
@@ -80,8 +85,18 @@ def measured_peaks():
         return 1900.0, 1700.0, "fallback (earlier GB300 measurement)"
 
 
-# FP32 FFMA: 128 lanes per SM per clock, 2 flops each (no measured figure)
-FFMA_PEAK_NOMINAL = SMS * 128 * 2 * NOMINAL_SM_MHZ * 1e6 / 1e12
+def sm_count():
+    """Streaming multiprocessors of the current device."""
+    import torch
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+
+def nominal_peaks():
+    """Nominal FP64 (2 DFMA lanes per SM and clock) and FP32 (128 FFMA lanes
+    per SM and clock) rates in TFLOP/s at the nominal SM clock, for the SM
+    count of the current device."""
+    sms = sm_count()
+    return sms, sms * 2 * 2 * NOMINAL_SM_MHZ * 1e6 / 1e12, sms * 128 * 2 * NOMINAL_SM_MHZ * 1e6 / 1e12
 
 
 def max_over_ranks(value, device):
@@ -194,22 +209,24 @@ def cpu_oracle_rate(data, shapes, budget_s, max_cols=None):
             cols = min(cols * 2, k)
         flops += float(n) * n * c_used
         secs += t_used
-        desc.append(f"n={n}: {c_used} of {k} columns")
+        desc.append(f"n={n}: {c_used}/{k} cols")
     return flops / secs / 1e12, "; ".join(desc), cores
 
 
-def precision_study(g, torch, n, k, n0, cs, inners, s_modes, dd_cols=2, stream=None, quick=False,
+def precision_study(g, torch, n, k, n0, cs, inners, s_modes, dd_cols=4, stream=None, quick=False,
                     residuals=("sliced",)):
     """Mixed-precision refinement on the graded-diagonal workload (diagonal
     geomspace(1, 10^-c), permuted): time, iterations, forward error against
     the double-double oracle and backward error ||B - L X|| / (||L|| ||X||)
-    on sampled columns, beside the FP64 solve of the same system."""
+    on a seeded sample of columns, beside the FP64 solve of the same system.
+    A solve that stops without reaching the target reports its status
+    (ENOCONV), and a non-finite result or reference reports None errors."""
     import oracle
-    from paper_1612_01855_gb300 import inputs
+    from paper_1612_01855_gb300 import binding, inputs
     out = []
     for c in cs:
         L, B = inputs.graded_diagonal(n, k, c, seed=0)
-        cols = np.linspace(0, k - 1, dd_cols).astype(int)
+        cols = np.sort(np.random.default_rng(7).choice(k, size=min(dd_cols, k), replace=False))
         hi, lo = oracle.forward_subst_dd(L, B[:, cols])
         ref = hi + lo
         ref_ok = bool(np.all(np.isfinite(ref)))
@@ -243,29 +260,89 @@ def precision_study(g, torch, n, k, n0, cs, inners, s_modes, dd_cols=2, stream=N
         torch.cuda.synchronize()
         t64 = e0.elapsed_time(e1)
         rec = {"c": c, "n": n, "k": k, "n0": n0, "fp64_solve_ms": round(t64, 2),
-               "fp64_fwd_err": ferr(X64), "fp64_bwd_err": berr(X64), "dd_reference_finite": ref_ok, "mixed": []}
+               "fp64_fwd_err": ferr(X64), "fp64_bwd_err": berr(X64), "dd_reference_finite": ref_ok,
+               "sampled_columns": [int(v) for v in cols], "mixed": []}
         for inner in inners:
             g.trsm_plan_mixed(plan, Ld, inner)
             for s32, res in ((a, b) for a in s_modes for b in residuals):
-                X, it, upd = g.trsm_solve_mixed(plan, Bd, residual=res, max_iter=30, tol=1e-12,
-                                                raise_on_noconv=False, s_fp32=s32)
+                def solve(X=None):
+                    try:
+                        X, it, upd = g.trsm_solve_mixed(plan, Bd, X=X, residual=res, max_iter=30, tol=1e-12,
+                                                        raise_on_noconv=False, s_fp32=s32)
+                        return X, it, upd, 0
+                    except binding.TrsmError as e:  # e.g. a non-finite working copy
+                        return X, None, None, e.code
+                X, it, upd, rc = solve()
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                X, it, upd = g.trsm_solve_mixed(plan, Bd, X=X, residual=res, max_iter=30, tol=1e-12,
-                                                raise_on_noconv=False, s_fp32=s32)
+                X, it, upd, rc = solve(X)
                 torch.cuda.synchronize()
                 tm = (time.perf_counter() - t0) * 1e3
-                fe = ferr(X)
+                fe = ferr(X) if X is not None else None
+                converged = bool(fe is not None and fe <= 1e-10)
+                status = "ok" if converged else ("non-finite" if fe is None else "target missed")
                 rec["mixed"].append({"inner": inner, "s_step": "fp32" if s32 else "fp64",
                                      "residual": res, "ms": round(tm, 2),
                                      "tflops_equiv": round(float(n) * n * k / (tm * 1e-3) / 1e12, 3),
-                                     "iterations": it, "last_update": upd, "fwd_err": fe, "bwd_err": berr(X),
-                                     "converged": bool(fe is not None and fe <= 1e-10),
+                                     "iterations": it, "last_update": upd, "fwd_err": fe,
+                                     "bwd_err": berr(X) if X is not None else None,
+                                     "converged": converged, "status": status, "rc": rc,
                                      "speedup_vs_fp64": round(t64 / tm, 3)})
         plan.destroy()
         del Ld, Bd, X64
         out.append(rec)
     return out
+
+
+def compact_precision(recs):
+    """Short records for the bench line: per c the FP64 solve's time and
+    forward error, and per (c, inner format) the refined solve's time,
+    sweeps, forward and backward errors, speed-up over FP64 and status
+    ("ok": forward error <= 1e-10; "miss": finite but above; "nan": the
+    solution or its reference is not finite)."""
+    fp64 = {str(rec["c"]): [rec["fp64_solve_ms"], _sig(rec["fp64_fwd_err"])] for rec in recs}
+    rows = []
+    for rec in recs:
+        for m in rec["mixed"]:
+            st = "ok" if m["converged"] else ("nan" if m["fwd_err"] is None else "miss")
+            rows.append([rec["c"], m["inner"], m["ms"], m["iterations"], _sig(m["fwd_err"]), _sig(m["bwd_err"]),
+                         m["speedup_vs_fp64"], st])
+    return {"fp64": fp64, "cols": ["c", "inner", "ms", "sweeps", "fwd", "bwd", "x_fp64", "status"], "rows": rows}
+
+
+def _sig(v, digits=3):
+    """A float rounded to `digits` significant digits (None stays None)."""
+    if v is None:
+        return None
+    return float(f"{v:.{digits - 1}e}")
+
+
+def n0_sweep_study(g, torch, dev_in, outs, shapes, sweep=None):
+    """The block-size sweep: every shape x n0 in {64, 128, 256, 512, 1024,
+    n}, plan and solve each timed once with CUDA events after one untimed
+    run (n0 = n is the full inversion, Section 7.4)."""
+    stream = torch.cuda.current_stream()
+    res = {}
+    for (n, k), (Ld, Bd), X in zip(shapes, dev_in, outs):
+        rows = []
+        for n0 in (sweep or SWEEP_N0):
+            n0v = n if n0 is None else n0
+            p = g.trsm_plan(Ld, n0v)
+            g.trsm_solve(p, Bd, X=X)
+            g.trsm_sync_status(p)
+            p.destroy()
+            a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            a.record(stream)
+            p = g.trsm_plan(Ld, n0v)
+            b.record(stream)
+            g.trsm_solve(p, Bd, X=X)
+            c.record(stream)
+            g.trsm_sync_status(p)
+            p.destroy()
+            pm, sm_ = a.elapsed_time(b), b.elapsed_time(c)
+            rows.append([n0v, round(pm, 1), round(sm_, 1), round(float(n) * n * k / ((pm + sm_) * 1e-3) / 1e12, 3)])
+        res[f"{n}x{k}"] = rows
+    return res
 
 
 def residual_roofline(g, torch, n=16384, k=4096, reps=3):
@@ -336,7 +413,7 @@ def batch_systems(torch, count, dtype, seed, choose_n0):
     return systems, float(np.sum(ns.astype(np.float64) ** 2 * ks))
 
 
-def batched_study(g, torch, count=4096, dtypes=("f64", "f32"), reps=5, seed=1000, fp64_peak=None):
+def batched_study(g, torch, count=4096, dtypes=("f64", "f32"), reps=5, seed=1000, fp64_peak=None, fp32_peak=None):
     """Batching workload: `count` independent systems, n log-uniform in
     [32, 1024], k log-uniform in [1, 256], diagonal U[2,3], strictly lower
     U[-1,1]/n, B U[-1,1] (drawn on the device from a per-system seed), all
@@ -367,8 +444,10 @@ def batched_study(g, torch, count=4096, dtypes=("f64", "f32"), reps=5, seed=1000
             ref = torch.linalg.solve_triangular(sy["L"].double(), sy["B"].double(), upper=False)
             err = max(err, float((sy["X"].double() - ref).abs().max() / ref.abs().max()))
         achieved = flops / (ms * 1e-3) / 1e12
-        peak, src = ((fp64_peak, "measured DFMA throughput") if dtype == "f64" and fp64_peak
-                     else (FFMA_PEAK_NOMINAL, f"nominal FFMA: {SMS} SMs x 128 lanes x 2 flop x {NOMINAL_SM_MHZ:.0f} MHz"))
+        if dtype == "f64":
+            peak, src = fp64_peak, "measured DFMA throughput (trsm_fp64_peak) in this run"
+        else:
+            peak, src = fp32_peak, "measured FFMA throughput (trsm_fp32_peak) in this run"
         out.append({"dtype": dtype, "systems": count, "ms_per_batch": round(ms, 3),
                     "tflops_n2k": round(achieved, 3), "status": rc,
                     "roofline": {"bound": "alu", "kernel": "batch_kernel", "achieved": round(achieved, 4),
@@ -460,7 +539,7 @@ def serving_study(g, torch, nL=256, rates=(100, 300, 600, 1200), per_rate=300, s
             mixed = bool(ns[lid] >= mixed_min_n and rng.random() < 0.5)
             reqs.append(Request(rid, lid, B, t, mixed=mixed))
         torch.cuda.synchronize()
-        srv = Server(plans, budget_bytes=int(budget_gb * 1e9), streams=2, max_batch=64)
+        srv = Server(plans, budget_bytes=int(budget_gb * 1e9), streams=4, max_batch=64)
         st = srv.run_trace(reqs)
         st["offered_rate"] = rate
         out["rates"].append({k: (round(v, 4) if isinstance(v, float) else v) for k, v in st.items()})
@@ -623,6 +702,8 @@ def run_ours(args, rank, world, local):
         step()
     torch.cuda.synchronize()
     fp64_peak = g.fp64_peak(8192)
+    fp32_peak = g.fp32_peak(16384)
+    sms, fp64_nominal, fp32_nominal = nominal_peaks()
     clocks = ClockSampler(local)
     clocks.start()
     if world > 1:
@@ -706,30 +787,30 @@ def run_ours(args, rank, world, local):
         h2d = sum(8 * (sum((n - b0) * min(n0, n - b0) for b0 in range(0, n, n0)) + n * k)
                   for (n, k), n0 in zip(shapes, n0s))
         d2h = sum(8 * n * k for n, k in shapes)
-        e2e = {"value": flops_step * world / e2e_s / 1e12, "unit": "TFLOP/s",
+        e2e = {"value": round(flops_step * world / e2e_s / 1e12, 4), "unit": "TFLOP/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "ms_per_step": e2e_s * 1e3}
+               "ms_per_step": round(e2e_s * 1e3, 2)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, sample, cores = cpu_oracle_rate(data, shapes, args.cpu_budget)
-        cpu = {"value": rate, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-               "sample": sample + " (forward substitution, FP64, OpenMP over columns)"}
+        cpu = {"value": round(rate, 5), "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+               "sample": sample + " (forward subst., FP64, OpenMP)"}
 
     mixed = None
     residual = None
     if rank == 0 and not args.no_mixed and not args.shapes:
         residual = residual_roofline(g, torch)
     if rank == 0 and not args.no_mixed and not args.shapes:
-        # FP32 diagonal multiplies at the mixed path's block size, and the
-        # FP64 ones at the FP64 path's block size (where they cost least)
-        mixed = (precision_study(g, torch, 16384, 4096, MIXED_N0, [2], ["tf32", "bf16x3", "fp16x3"], [True],
-                                 dd_cols=2) +
-                 precision_study(g, torch, 16384, 4096, 256, [2], ["tf32"], [False], dd_cols=2))
+        # config 2 at c = 2, 4, 6: split fp16 and tf32 updates, FP32
+        # diagonal multiplies, the adaptive residual, at the mixed path's
+        # block size
+        mixed = precision_study(g, torch, 16384, 4096, MIXED_N0, [2, 4, 6], ["fp16x3", "tf32"], [True],
+                                residuals=("adaptive",))
 
     batched = None
     if rank == 0 and not args.no_batched and not args.shapes:
-        batched = batched_study(g, torch, fp64_peak=fp64_peak)
+        batched = batched_study(g, torch, fp64_peak=fp64_peak, fp32_peak=fp32_peak)
 
     serving = None
     if rank == 0 and not args.no_serving and not args.shapes:
@@ -739,35 +820,23 @@ def run_ours(args, rank, world, local):
     if rank == 0 and not args.no_schedules:
         schedules = schedules_study(g, torch, dev_in, outs, shapes, n0s, fp64_peak=fp64_peak)
 
+    sweep = None
+    if rank == 0 and not args.no_sweep and not args.shapes:
+        sweep = n0_sweep_study(g, torch, dev_in, outs, shapes)
+
     if args.precision and rank == 0:
         for rec in precision_study(g, torch, 16384, 4096, MIXED_N0, [2, 4, 6], ["tf32", "bf16", "bf16x3", "fp16x3"],
                                    [False, True], residuals=("sliced", "adaptive")):
             print(json.dumps({"precision_study": True, **rec}), flush=True)
 
-    if args.sweep and rank == 0:
-        for (L, B), (n, k), (Ld, Bd), X in zip(data, shapes, dev_in, outs):
-            for n0 in SWEEP_N0:
-                n0v = n if n0 is None else n0
-                for _ in range(2):
-                    p = g.trsm_plan(Ld, n0v)
-                    g.trsm_solve(p, Bd, X=X)
-                    g.trsm_sync_status(p)
-                    p.destroy()
-                a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-                a.record(stream)
-                p = g.trsm_plan(Ld, n0v)
-                b.record(stream)
-                g.trsm_solve(p, Bd, X=X)
-                c.record(stream)
-                g.trsm_sync_status(p)
-                p.destroy()
-                pm, sm_ = a.elapsed_time(b), b.elapsed_time(c)
-                print(json.dumps({"sweep": True, "n": n, "k": k, "n0": n0v, "plan_ms": pm,
-                                  "solve_ms": sm_, "tflops": n * n * k / ((pm + sm_) * 1e-3) / 1e12,
-                                  "solve_tflops": n * n * k / (sm_ * 1e-3) / 1e12}), flush=True)
-
     if rank == 0:
         traffic, traffic_by_shape = solve_traffic(shapes, n0s)
+        details = {"per_shape": per_shape, "traffic_by_shape": traffic_by_shape, "mixed_precision": mixed,
+                   "residual_roofline": residual, "batched": batched, "serving": serving,
+                   "schedules": schedules, "n0_sweep": sweep}
+        if args.details:
+            with open(args.details, "w") as fh:
+                json.dump(details, fh, indent=1)
         line = {
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -778,29 +847,43 @@ def run_ours(args, rank, world, local):
                        "n0": {f"{n}x{k}": n0 for (n, k), n0 in zip(shapes, n0s)},
                        "flops_per_step": flops_step, "l2": "inputs larger than L2 (no flush)",
                        "parallelism": f"replicas{world}" if world > 1 else "single GPU",
-                       "shapes": per_shape},
+                       "shapes_ms": {f"{r['n']}x{r['k']}": [r["plan_ms"], r["solve_ms"]] for r in per_shape}},
             "roofline": {"bound": "alu", "kernel": "it_inv_solve_kernel",
-                         "achieved": solve_achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                         "frac": solve_achieved / fp64_peak,
-                         "peak_source": "measured DFMA throughput (trsm_fp64_peak) in this run; "
-                                        f"nominal {SMS} SMs x 2 DFMA/clk x 2 flop x {NOMINAL_SM_MHZ:.0f} MHz"
-                                        f" = {SMS * 4 * NOMINAL_SM_MHZ / 1e6:.3f}",
-                         "traffic": traffic,
-                         "traffic_unit": "bytes per launch (mean over the step's three solve launches)",
-                         "traffic_by_shape": traffic_by_shape},
-            "parity_max_rel_err": err,
-            "backward_err": bwd,
-            "mixed_precision": mixed,
-            "residual_roofline": residual,
-            "batched": batched,
-            "serving": serving,
-            "schedules": schedules,
+                         "achieved": round(solve_achieved, 4), "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
+                         "frac": round(solve_achieved / fp64_peak, 4),
+                         "peak_source": f"measured DFMA this run (nominal {sms} SMs: {fp64_nominal:.3f})",
+                         "traffic": traffic},
+            "parity_max_rel_err": _sig(err),
+            "backward_err": _sig(bwd),
             "e2e": e2e,
             "cpu_baseline": cpu,
             "gpu_launches": launches,
             "clocks": clk,
+            "fp32_peak": {"measured": round(fp32_peak, 2), "nominal": round(fp32_nominal, 2), "unit": "TFLOP/s"},
         }
-        print(json.dumps(line), flush=True)
+        if sweep is not None:
+            line["n0_sweep"] = {"cols": ["n0", "plan_ms", "solve_ms", "tflops"], **sweep}
+        if mixed is not None:
+            line["precision"] = compact_precision(mixed)
+        if residual is not None:
+            line["residual_roofline"] = {key: {"ms": v["ms"], "achieved": v["achieved"], "frac": v["frac"],
+                                              "peak": v["peak"]} for key, v in residual.items()}
+        if batched is not None:
+            line["batched"] = [{"dtype": b["dtype"], "ms": b["ms_per_batch"], "tflops": b["tflops_n2k"],
+                                "frac": b["roofline"]["frac"], "peak": b["roofline"]["peak"],
+                                "status": b["status"], "err": _sig(b["spot_check_rel_err"])} for b in batched]
+        if serving is not None:
+            line["serving"] = {"cols": ["offered", "served", "p50_ms", "p99_ms", "fp64_p99_ms", "mixed_p99_ms",
+                                        "ok"],
+                               "rates": [[r["offered_rate"], round(r["solves_per_s"], 1), round(r["p50_ms"], 2),
+                                          round(r["p99_ms"], 2), round(r.get("fp64", {}).get("p99_ms", 0.0), 2),
+                                          round(r.get("mixed", {}).get("p99_ms", 0.0), 2), r["statuses_ok"]]
+                                         for r in serving["rates"]],
+                               "slots": serving["rates"][0]["slots"] if serving["rates"] else None}
+        if schedules is not None:
+            line["schedules_ms"] = {f"{r['n']}x{r['k']}": {key: r[key]["solve_ms"] for key in SCHEDULE_NAMES
+                                                           if key in r} for r in schedules}
+        print(json.dumps(line, separators=(",", ":")), flush=True)
 
 
 def main():
@@ -809,7 +892,6 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--sweep", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-check", action="store_true")
@@ -818,6 +900,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-systems figure")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving figure")
     ap.add_argument("--no-schedules", action="store_true", help="skip the solve-schedule comparison")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the n0 sweep")
+    ap.add_argument("--details", default="", help="also write every study's full records to this JSON file")
     ap.add_argument("--precision", action="store_true", help="print the full c x inner x s-step study")
     ap.add_argument("--case", default="", help="profiling case: sliced:N:K[:PLANES], mixed:N:K:N0[:INNER[:S32]], engine:M:N:K, batch:COUNT:BITS")
     ap.add_argument("--shapes", default="", help="override workload, e.g. 6144:1024:256 (not a bench line)")

@@ -139,8 +139,11 @@ int trsm_solve_ws(trsm_handle_t h, const double* B_dev, int64_t k, int64_t ldb, 
  *   there; each call resets what must start at zero.  Calls whose device work
  *   overlaps (other streams, other host threads) race: serialise them.
  *   The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress, with that device current) and caches it; make it
- *   before any stream capture begins.
+ *   (cudaGetSymbolAddress, with that device current) and caches it together
+ *   with the id of the CUDA context it belongs to; make it before any stream
+ *   capture begins.  After a cudaDeviceReset the next call sees a new
+ *   context and looks the address up again (so it, too, belongs before any
+ *   capture).
  * Asynchronous on `stream`.  Errors: TRSM_EINVAL, TRSM_ENOSCRATCH,
  * TRSM_ECUDA. */
 int trsm_solve_noalloc(trsm_handle_t h, const double* B_dev, int64_t k, int64_t ldb,
@@ -324,6 +327,12 @@ int64_t trsm_launch_count(int reset);
  * `iters` x 8 x 2 flops per thread on every SM and writes TFLOP/s to
  * *tflops.  Synchronous. */
 int trsm_fp64_peak(int iters, double* tflops, void* stream);
+
+/* FP32 counterpart of trsm_fp64_peak (no counterpart in the paper: the
+ * roofline denominator of the FP32 batches): an FFMA-only kernel, eight
+ * independent chains per thread, 32 warps per SM, `iters` x 8 x 2 flops per
+ * thread; writes TFLOP/s to *tflops.  Synchronous. */
+int trsm_fp32_peak(int iters, double* tflops, void* stream);
 
 #ifdef __cplusplus
 }

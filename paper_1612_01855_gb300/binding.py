@@ -82,6 +82,7 @@ SIGNATURES = {
     "trsm_error_string": (ctypes.c_char_p, [_int]),
     "trsm_launch_count": (_i64, [_int]),
     "trsm_fp64_peak": (_int, [_int, ctypes.POINTER(ctypes.c_double), _vp]),
+    "trsm_fp32_peak": (_int, [_int, ctypes.POINTER(ctypes.c_double), _vp]),
     "trsm_tc_gemm_selftest": (_int, [_int, _vp, _vp, _vp, _i64, _i64, _i64, _vp, _vp]),
     "trsm_wait_selftest": (_int, [_int, _i64, _vp]),
     "trsm_residual_sliced": (_int, [_dp, _i64, _i64, _dp, _i64, _i64, _dp, _i64, _dp, _i64, _int, _vp, _vp]),
@@ -385,6 +386,15 @@ def fp64_peak(iters=4096, device=None):
     out = ctypes.c_double()
     s = ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
     _check(load_library().trsm_fp64_peak(int(iters), ctypes.byref(out), s), "trsm_fp64_peak")
+    return out.value
+
+
+def fp32_peak(iters=8192, device=None):
+    """Measured FP32 FFMA throughput of the device, TFLOP/s."""
+    torch = _torch()
+    out = ctypes.c_double()
+    s = ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+    _check(load_library().trsm_fp32_peak(int(iters), ctypes.byref(out), s), "trsm_fp32_peak")
     return out.value
 
 

@@ -74,6 +74,50 @@ __global__ void dfma_peak_kernel(double* out, int iters, double a, double b) {
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// FP32 counterpart: eight independent FFMA chains per thread, 32 warps per
+// SM, so that every FMA lane has an instruction ready each clock.
+__global__ void ffma_peak_kernel(double* out, int iters, float a, float b) {
+  float acc[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) acc[c] = threadIdx.x * 1e-3f + c;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] = fmaf(acc[c], a, b);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) s += acc[c];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+// Times one launch of a peak kernel (after a short warm-up launch) and
+// returns TFLOP/s for `iters` x 8 FMAs per thread.
+template <class Launch>
+int timed_peak(int iters, int blocks, int threads, double* tflops, cudaStream_t s, Launch launch) {
+  double* out = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&out, sizeof(double) * blocks * threads, s);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) {
+    launch(out, 64);  // warm-up
+    cudaEventRecord(e0, s);
+    launch(out, iters);
+    cudaEventRecord(e1, s);
+    trsm::count_launch(2);
+    e = cudaEventSynchronize(e1);
+  }
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (out) cudaFreeAsync(out, s);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) return from_cuda(e);
+  const double flops = 2.0 * 8.0 * (double)iters * blocks * threads;
+  *tflops = flops / ((double)ms * 1e-3) / 1e12;
+  return TRSM_SUCCESS;
+}
+
 }  // namespace
 
 namespace trsm {
@@ -349,30 +393,19 @@ int64_t trsm_launch_count(int reset) {
 int trsm_fp64_peak(int iters, double* tflops, void* stream) {
   if (iters < 1 || !tflops) return TRSM_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  const int sms = trsm::device_sm_count();
-  const int blocks = sms * 2, threads = 256;
-  double* out = nullptr;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&out, sizeof(double) * blocks * threads, s);
-  if (e == cudaSuccess) e = cudaEventCreate(&e0);
-  if (e == cudaSuccess) e = cudaEventCreate(&e1);
-  float ms = 0.f;
-  if (e == cudaSuccess) {
-    dfma_peak_kernel<<<blocks, threads, 0, s>>>(out, 64, 1.0000001, 1e-9);  // warm-up
-    cudaEventRecord(e0, s);
-    dfma_peak_kernel<<<blocks, threads, 0, s>>>(out, iters, 1.0000001, 1e-9);
-    cudaEventRecord(e1, s);
-    trsm::count_launch(2);
-    e = cudaEventSynchronize(e1);
-  }
-  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-  if (out) cudaFreeAsync(out, s);
-  if (e0) cudaEventDestroy(e0);
-  if (e1) cudaEventDestroy(e1);
-  if (e != cudaSuccess) return from_cuda(e);
-  const double flops = 2.0 * 8.0 * (double)iters * blocks * threads;
-  *tflops = flops / ((double)ms * 1e-3) / 1e12;
-  return TRSM_SUCCESS;
+  const int blocks = trsm::device_sm_count() * 2, threads = 256;
+  return timed_peak(iters, blocks, threads, tflops, s, [&](double* out, int it) {
+    dfma_peak_kernel<<<blocks, threads, 0, s>>>(out, it, 1.0000001, 1e-9);
+  });
+}
+
+int trsm_fp32_peak(int iters, double* tflops, void* stream) {
+  if (iters < 1 || !tflops) return TRSM_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int blocks = trsm::device_sm_count() * 4, threads = 256;
+  return timed_peak(iters, blocks, threads, tflops, s, [&](double* out, int it) {
+    ffma_peak_kernel<<<blocks, threads, 0, s>>>(out, it, 1.0000001f, 1e-9f);
+  });
 }
 
 }  // extern "C"

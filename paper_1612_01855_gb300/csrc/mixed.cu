@@ -24,9 +24,9 @@
 // factor on alpha.
 //
 // The residual is either the digit-sliced tensor-core product of sliced.cu
-// (seven planes: about 2^-40 relative to |L||X|; eight: about 2^-46; or
-// seven until the updates stagnate above tol, then eight) or a plain FP64
-// DFMA product.
+// (relative to |B| + |L||X|: about 2^-43 with seven planes, about 2^-49
+// with eight; or seven until the updates stagnate above tol, then eight) or
+// a plain FP64 DFMA product.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -45,7 +45,7 @@
 namespace trsm {
 
 struct MixedPlan {
-  int inner = 0;            // TRSM_INNER_BF16 or TRSM_INNER_TF32
+  int inner = 0;            // TRSM_INNER_BF16, _TF32, _BF16X3 or _FP16X3
   int64_t n0p = 0;          // n0 rounded up to 8 (TMA row granule)
   void* panels = nullptr;   // low-precision L(T_{i+1}, S_i), i = 0..N-2, row-major [rows][n0p]
   double* diag = nullptr;   // diag(L)

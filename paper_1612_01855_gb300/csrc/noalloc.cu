@@ -23,7 +23,12 @@
 // Set-up: the array's name is only a host-side stand-in in host code; its
 // device address comes from cudaGetSymbolAddress, taken once per device by
 // the first call on that device (with that device current) and cached.  Make
-// that first call before any stream capture begins.
+// that first call before any stream capture begins.  The cache is keyed by
+// the unique id of the CUDA context the address was taken in: after a
+// cudaDeviceReset (or any other teardown of the device's primary context)
+// the next call sees a new context and takes the address again.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -38,20 +43,52 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-std::mutex g_scratch_mutex;
-void* g_scratch_addr[kMaxDevices] = {nullptr};
+struct ScratchAddr {
+  unsigned long long ctx_id = 0;  // id of the context the address belongs to (0: none yet)
+  void* addr = nullptr;
+};
 
-// Device address of the scratch array on the current device (set-up on first
-// use per device).
+std::mutex g_scratch_mutex;
+ScratchAddr g_scratch_addr[kMaxDevices];
+
+// Unique id of the calling thread's current context (0 if none is current or
+// the driver entry points are unavailable).
+unsigned long long current_context_id() {
+  static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+  static PFN_cuCtxGetId_v12000 get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(p);
+  });
+  if (!get_current || !get_id) return 0;
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return 0;
+  if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// Device address of the scratch array on the current device: taken at the
+// first use per device and context, cached afterwards.
 cudaError_t scratch_address(int dev, void** out) {
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (g_scratch_addr[dev] == nullptr) {
+  ScratchAddr& c = g_scratch_addr[dev];
+  const unsigned long long id = current_context_id();
+  if (c.addr == nullptr || id == 0 || id != c.ctx_id) {
     void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // makes the device's context current
     if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = p;
+    c.addr = p;
+    c.ctx_id = current_context_id();
   }
-  *out = g_scratch_addr[dev];
+  *out = c.addr;
   return cudaSuccess;
 }
 

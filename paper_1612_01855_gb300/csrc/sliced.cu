@@ -33,9 +33,9 @@
 // exponents and push the off-diagonal entries into the low digits).  Each
 // P-digit expansion is exact to 2^(e-6P-1), dropped pairs (s + u >= P) are
 // below 2^(eL+eX-6P+1) per product, so entries much smaller than their
-// (row, chunk) maximum carry fewer significant bits; on the workloads here
-// the residual is accurate to about 2^-40 (P = 7) or 2^-46 (P = 8) relative
-// to |L| |X|.
+// (row, chunk) maximum carry fewer significant bits.  Measured against an
+// exactly rounded residual on the workloads here, the error is about 2^-43
+// (P = 7) or 2^-49 (P = 8) relative to |B| + |L| |X|.
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -4,27 +4,39 @@ Each L is planned once (`trsm_plan`: its inverted diagonal blocks stay in
 HBM), so a request — a right-hand side B for one of the resident L — only
 pays for the blocked solve (Algorithm It-Inv-TRSM, Section 6.2).  The loop:
 
-* requests wait in arrival order;
-* whenever one of `streams` launch slots is free, requests are admitted from
-  the head of the queue while their memory (B, X and the batch's share of
-  the workspace) fits in the HBM budget next to the resident plans, and the
-  admitted requests run as ONE persistent batched launch (`trsm_batch_*`
-  with resident plans, laid out in an arena from torch's caching allocator:
-  no device allocation by the library);
+* requests wait in two queues, each in arrival order: FP64 requests, and
+  requests for the refined mixed-precision solve (`mixed=True`; its plan
+  needs `trsm_plan_mixed`);
+* whenever one of `streams` launch slots is free, it takes work: the FP64
+  requests at the head of their queue, admitted while their memory (B, X and
+  the batch's share of the workspace) fits in the HBM budget next to the
+  resident plans, run as ONE persistent batched launch (`trsm_batch_*` with
+  resident plans, laid out in an arena from torch's caching allocator: no
+  device allocation by the library);
+* a mixed-precision solve decides on the host when to stop refining, so it
+  cannot join a persistent batch: it takes a slot alone and runs in a worker
+  thread on the slot's stream (the C call releases the interpreter lock).
+  At most `mixed_slots` slots hold such solves at a time, so the other slots
+  always keep serving FP64 batches;
+* between the two queues a free slot goes to whichever head arrived first,
+  unless that head cannot start (a mixed request while every mixed slot is
+  taken, or a request whose memory does not fit yet): then the other queue's
+  head may pass it.  No request waits behind one of the other kind;
 * batches run on different streams overlap on the device; a request that
   arrives while others are on the GPU is admitted as soon as a slot and
   memory free up;
 * latency = completion seen by the host - arrival.
 
-A request may instead ask for the mixed-precision solve refined to a
-tolerance (`mixed=True`; its plan needs `trsm_plan_mixed`).  That solve
-decides on the host when to stop refining, so it cannot join a persistent
-batch: it takes a launch slot alone and runs in a worker thread on the
-slot's stream (the C call releases the interpreter lock), while the other
-slots keep serving batches.
+Stream order: a request's B may still be in production on the caller's
+stream when it is submitted (an asynchronous copy or kernel).  `submit`
+records an event on the caller's current stream; the slot stream waits on it
+before reading B, and B is marked as used on the slot stream so that the
+caching allocator does not hand its memory out again before the solve ends.
 
-The result of a FP64 request does not depend on which other requests share
-its batch: every tile's updates are applied in a fixed order.
+Results do not depend on the traffic: an FP64 request's X is the same bits
+whichever requests share its batch (every tile's updates are applied in a
+fixed order), and a mixed request's refined solve runs alone with its own
+fixed sequence of kernels.
 """
 import time
 from collections import deque
@@ -87,6 +99,7 @@ class Request:
     tol: float = 1e-12
     status: int = None
     iterations: int = None
+    ready: object = None  # CUDA event recorded at submission on the caller's stream
 
     @property
     def latency(self):
@@ -101,6 +114,7 @@ class _InFlight:
     nbytes: int
     arena: object = field(default=None)
     future: object = None  # a mixed-precision request's worker
+    slot: int = 0
 
 
 def _has_mixed_data(plan):
@@ -108,20 +122,33 @@ def _has_mixed_data(plan):
 
 
 class Server:
-    def __init__(self, plans, budget_bytes, streams=2, max_batch=64, mixed_residual="adaptive"):
+    def __init__(self, plans, budget_bytes, streams=4, max_batch=64, mixed_slots=None,
+                 mixed_residual="adaptive"):
+        if streams < 1:
+            raise ValueError("at least one launch slot")
         self.plans = plans
         resident = sum(self.plan_bytes(p) for p in plans)
         self.adm = Admission(budget_bytes, resident)
         self.mixed_residual = mixed_residual
         self.pool = None
-        self.pending = deque()
+        self.queue_fp64 = deque()
+        self.queue_mixed = deque()
         self.inflight = []
         self.done = []
         self.nstreams = streams
+        # slots that may hold a mixed-precision solve at once: half of them,
+        # at least one; with a single slot the two kinds take turns
+        self.mixed_slots = max(1, streams // 2) if mixed_slots is None else int(mixed_slots)
         self.streams = None  # created at the first dispatch (host-side logic runs without a GPU)
         self.busy = [False] * streams
+        self.mixed_busy = 0
         self.max_batch = max_batch
         self.launches = 0
+
+    @property
+    def pending(self):
+        """Requests not admitted yet, in arrival order."""
+        return sorted(list(self.queue_fp64) + list(self.queue_mixed), key=lambda r: (r.arrival, r.rid))
 
     @staticmethod
     def plan_bytes(plan):
@@ -147,19 +174,23 @@ class Server:
             raise AdmissionError(f"request {req.rid}: mixed precision asked for, but L #{req.lid} has no "
                                  "mixed-precision plan (trsm_plan_mixed)")
         self.adm.check_request(self.request_bytes(plan.n, req.B.shape[1], req.mixed))
-        self.pending.append(req)
+        if getattr(req.B, "is_cuda", False):
+            torch = self._torch()
+            req.ready = torch.cuda.Event()
+            req.ready.record(torch.cuda.current_stream(req.B.device))
+        (self.queue_mixed if req.mixed else self.queue_fp64).append(req)
 
     def cancel(self, rid):
         """Drops a request that has not been admitted yet."""
-        for r in self.pending:
-            if r.rid == rid:
-                r.cancelled = True
-                self.pending.remove(r)
-                return True
+        for q in (self.queue_fp64, self.queue_mixed):
+            for r in q:
+                if r.rid == rid:
+                    r.cancelled = True
+                    q.remove(r)
+                    return True
         return False
 
     def poll(self):
-        now = time.perf_counter()
         still = []
         for f in self.inflight:
             if f.future is not None:
@@ -175,6 +206,7 @@ class Server:
                 self.done.append(r)
                 self.adm.release(f.nbytes)
                 self.busy[f.slot] = False
+                self.mixed_busy -= 1
                 continue
             if f.event.query():
                 now = time.perf_counter()
@@ -196,6 +228,15 @@ class Server:
         import torch
         return torch
 
+    @staticmethod
+    def _order_after_submission(r, stream):
+        """The slot stream waits for B's producer; B stays allocated until
+        the slot stream's work on it is done."""
+        if r.ready is not None:
+            stream.wait_event(r.ready)
+        if getattr(r.B, "is_cuda", False):
+            r.B.record_stream(stream)
+
     def _solve_mixed(self, slot, r):
         """Worker: one refined mixed-precision solve on the slot's stream.
         Returns (status, iterations)."""
@@ -208,46 +249,67 @@ class Server:
             except binding.TrsmError as e:
                 return e.code, None
 
+    def _next_kind(self):
+        """Which queue a free slot serves: "fp64", "mixed" or None (the
+        arrival-order rule of the module docstring)."""
+        mixed_ok = bool(self.queue_mixed) and self.mixed_busy < self.mixed_slots
+        if mixed_ok:
+            r = self.queue_mixed[0]
+            mixed_ok = self.adm.fits(self.request_bytes(self.plans[r.lid].n, r.B.shape[1], True))
+        fp64_ok = False
+        if self.queue_fp64:
+            r = self.queue_fp64[0]
+            fp64_ok = self.adm.fits(self.request_bytes(self.plans[r.lid].n, r.B.shape[1]))
+        if mixed_ok and fp64_ok:
+            return "mixed" if self.queue_mixed[0].arrival < self.queue_fp64[0].arrival else "fp64"
+        return "mixed" if mixed_ok else "fp64" if fp64_ok else None
+
+    def _take_fp64(self):
+        """FP64 requests from the head of their queue that fit together."""
+        take, nbytes = [], 0
+        while self.queue_fp64 and len(take) < self.max_batch:
+            r = self.queue_fp64[0]
+            b = self.request_bytes(self.plans[r.lid].n, r.B.shape[1])
+            if not self.adm.fits(nbytes + b):
+                break
+            take.append(self.queue_fp64.popleft())
+            nbytes += b
+        return take, nbytes
+
     def dispatch(self):
         import torch
         if self.streams is None:
             self.streams = [torch.cuda.Stream() for _ in range(self.nstreams)]
         for slot in range(len(self.streams)):
-            if self.busy[slot] or not self.pending:
+            if self.busy[slot]:
                 continue
-            head = self.pending[0]
-            if head.mixed:
-                b = self.request_bytes(self.plans[head.lid].n, head.B.shape[1], True)
-                if not self.adm.take(b):
-                    continue
-                r = self.pending.popleft()
+            kind = self._next_kind()
+            if kind is None:
+                break
+            stream = self.streams[slot]
+            if kind == "mixed":
+                r = self.queue_mixed.popleft()
+                b = self.request_bytes(self.plans[r.lid].n, r.B.shape[1], True)
+                self.adm.take(b)
                 n, k = r.B.shape
-                with torch.cuda.stream(self.streams[slot]):
+                with torch.cuda.stream(stream):
+                    self._order_after_submission(r, stream)
                     r.X = torch.empty((k, n), dtype=torch.float64, device="cuda").t()
                 r.t_admit = time.perf_counter()
                 if self.pool is None:
-                    self.pool = ThreadPoolExecutor(max_workers=self.nstreams)
-                f = _InFlight(None, None, [r], b, future=self.pool.submit(self._solve_mixed, slot, r))
-                f.slot = slot
+                    self.pool = ThreadPoolExecutor(max_workers=self.mixed_slots)
+                f = _InFlight(None, None, [r], b, future=self.pool.submit(self._solve_mixed, slot, r), slot=slot)
                 self.busy[slot] = True
+                self.mixed_busy += 1
                 self.inflight.append(f)
                 self.launches += 1
                 continue
-            take, nbytes = [], 0
-            while self.pending and len(take) < self.max_batch and not self.pending[0].mixed:
-                r = self.pending[0]
-                b = self.request_bytes(self.plans[r.lid].n, r.B.shape[1])
-                if not self.adm.fits(nbytes + b):
-                    break
-                take.append(self.pending.popleft())
-                nbytes += b
-            if not take:
-                continue
+            take, nbytes = self._take_fp64()
             self.adm.take(nbytes)
-            stream = self.streams[slot]
             with torch.cuda.stream(stream):
                 systems = []
                 for r in take:
+                    self._order_after_submission(r, stream)
                     n, k = r.B.shape
                     r.X = torch.empty((k, n), dtype=torch.float64, device="cuda").t()
                     r.t_admit = time.perf_counter()
@@ -259,14 +321,13 @@ class Server:
                 batch.run()
                 ev = torch.cuda.Event()
                 ev.record(stream)
-            f = _InFlight(batch, ev, take, nbytes, arena)
-            f.slot = slot
+            f = _InFlight(batch, ev, take, nbytes, arena, slot=slot)
             self.busy[slot] = True
             self.inflight.append(f)
             self.launches += 1
 
     def drain(self):
-        while self.pending or self.inflight:
+        while self.queue_fp64 or self.queue_mixed or self.inflight:
             self.poll()
             self.dispatch()
 
@@ -278,7 +339,7 @@ class Server:
         for r in order:
             r.arrival += t0
         i = 0
-        while i < len(order) or self.pending or self.inflight:
+        while i < len(order) or self.queue_fp64 or self.queue_mixed or self.inflight:
             now = time.perf_counter()
             while i < len(order) and order[i].arrival <= now:
                 self.submit(order[i])
@@ -296,12 +357,15 @@ class Server:
         out = {"requests": len(order), "seconds": t1 - t0, "solves_per_s": len(order) / (t1 - t0),
                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
                "mean_ms": float(lat.mean() * 1e3), "tflops_n2k": flops / (t1 - t0) / 1e12,
-               "batches": self.launches, "peak_inflight_gb": self.adm.peak / 1e9,
+               "batches": self.launches, "slots": self.nstreams, "mixed_slots": self.mixed_slots,
+               "peak_inflight_gb": self.adm.peak / 1e9,
                "statuses_ok": all(r.status == 0 for r in order)}
-        mixed = [r for r in order if r.mixed and r.latency is not None]
-        if mixed:
-            ml = np.array([r.latency for r in mixed])
-            out["mixed"] = {"requests": len(mixed), "p50_ms": float(np.percentile(ml, 50) * 1e3),
-                            "p99_ms": float(np.percentile(ml, 99) * 1e3),
-                            "mean_iterations": float(np.mean([r.iterations or 0 for r in mixed]))}
+        for kind, sel in (("fp64", lambda r: not r.mixed), ("mixed", lambda r: r.mixed)):
+            part = [r for r in order if sel(r) and r.latency is not None]
+            if part:
+                pl = np.array([r.latency for r in part])
+                out[kind] = {"requests": len(part), "p50_ms": float(np.percentile(pl, 50) * 1e3),
+                             "p99_ms": float(np.percentile(pl, 99) * 1e3)}
+                if kind == "mixed":
+                    out[kind]["mean_iterations"] = float(np.mean([r.iterations or 0 for r in part]))
         return out

@@ -42,8 +42,8 @@ def test_cpu_oracle_rate_takes_a_bounded_sample():
     parts = sample.split("; ")
     assert parts[0].startswith("n=64: ") and parts[1].startswith("n=96: ")
     for part, (n, k) in zip(parts, shapes):
-        used = int(part.split(": ")[1].split(" of ")[0])
-        assert 1 <= used <= k and part.endswith(f"of {k} columns")
+        used = int(part.split(": ")[1].split("/")[0])
+        assert 1 <= used <= k and part.endswith(f"/{k} cols")
 
 
 def test_replica_throughput_counts_every_rank():
@@ -72,3 +72,21 @@ def test_clock_sampler_reads_throttle_reasons(tmp_path):
     assert out["samples"] == 3 and out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0
     assert out["reasons"] == ["sw_power_cap"]
     assert not os.path.exists(s.path)
+
+
+def test_compact_precision_records():
+    """The bench line's precision block: FP64 figures per c, one row per
+    (c, inner format), and a status that tells a met target, a missed one
+    and a non-finite result apart."""
+    recs = [{"c": 2, "fp64_solve_ms": 880.0, "fp64_fwd_err": 5.2e-16,
+             "mixed": [{"inner": "fp16x3", "ms": 70.1, "iterations": 3, "fwd_err": 7.0e-13, "bwd_err": 5.4e-15,
+                        "speedup_vs_fp64": 12.6, "converged": True},
+                       {"inner": "tf32", "ms": 95.0, "iterations": 5, "fwd_err": 3.4e-9, "bwd_err": 1e-15,
+                        "speedup_vs_fp64": 9.3, "converged": False}]},
+            {"c": 6, "fp64_solve_ms": 881.0, "fp64_fwd_err": None,
+             "mixed": [{"inner": "fp16x3", "ms": 5.0, "iterations": 1, "fwd_err": None, "bwd_err": None,
+                        "speedup_vs_fp64": 176.2, "converged": False}]}]
+    out = bench.compact_precision(recs)
+    assert out["fp64"] == {"2": [880.0, 5.2e-16], "6": [881.0, None]}
+    assert [r[-1] for r in out["rows"]] == ["ok", "miss", "nan"]
+    assert out["rows"][0][:4] == [2, "fp16x3", 70.1, 3] and len(out["cols"]) == len(out["rows"][0])

@@ -171,3 +171,39 @@ def test_mixed_argument_errors(cuda_lib):
     g.trsm_plan_mixed(plan, _dev(L), "bf16")
     with pytest.raises(g.TrsmError):  # in place not allowed
         g.trsm_solve_mixed(plan, Bd, X=Bd)
+
+
+@pytest.mark.parametrize("c", [2, 4])
+def test_full_size_precision_config(cuda_lib, c):
+    """The precision configuration at its full size and in the bench's launch
+    configuration: n = 16384, k = 4096, n0 = 1024, graded diagonal
+    geomspace(1, 10^-c) permuted, split-fp16 updates, FP32 diagonal
+    multiplies, the adaptive residual (seven digit planes, then eight).  The
+    forward error on a seeded sample of columns, against the double-double
+    substitution of the same columns (columns of X are independent), stays
+    within the 1e-10 target; the backward error of those columns is FP64
+    class."""
+    import torch
+    import paper_1612_01855_gb300 as g
+    n, k, n0 = 16384, 4096, 1024
+    L, B = inputs.graded_diagonal(n, k, c, seed=0)
+    cols = np.sort(np.random.default_rng(17).choice(k, size=6, replace=False))
+    hi, lo = oracle.forward_subst_dd(L, B[:, cols])
+    ref = hi + lo
+    assert np.all(np.isfinite(ref))
+    Ld, Bd = _dev(L), _dev(B)
+    del L
+    plan = g.trsm_plan(Ld, n0)
+    g.trsm_plan_mixed(plan, Ld, "fp16x3")
+    X, iters, upd = g.trsm_solve_mixed(plan, Bd, residual="adaptive", max_iter=30, tol=1e-12, s_fp32=True)
+    ci = torch.from_numpy(cols).cuda()
+    got = X[:, ci].cpu().numpy()
+    fwd = _rel(got, ref)
+    Lt = torch.tril(Ld)
+    Xs = X[:, ci]
+    bwd = (Bd[:, ci] - Lt @ Xs).abs().max().item() / (Lt.abs().sum(dim=1).max().item() * Xs.abs().max().item())
+    print(f"precision config c={c}: {iters} sweeps, last update {upd:.2e}, forward error {fwd:.2e}, "
+          f"backward error {bwd:.2e}")
+    assert fwd <= 1e-10
+    assert bwd <= 1e-14
+    plan.destroy()

@@ -76,7 +76,9 @@ def test_server_respects_tight_budget(cuda_lib):
 def test_server_mixes_fp64_and_refined_requests(cuda_lib):
     """Half the requests ask for the mixed-precision solve (split-bf16
     updates, refined on the tensor cores): they run alone on a slot's worker
-    thread next to the FP64 batches; every result matches the oracle."""
+    thread next to the FP64 batches; every result matches the oracle and is
+    the same bits as the request's solve run alone."""
+    import torch
     import paper_1612_01855_gb300 as g
     from paper_1612_01855_gb300.serve import Server
     Ls, plans = _setup(4, seed=7)
@@ -92,4 +94,45 @@ def test_server_mixes_fp64_and_refined_requests(cuda_lib):
     for r, B in zip(reqs, host):
         want = oracle.forward_subst(Ls[r.lid], B)
         assert np.max(np.abs(r.X.cpu().numpy() - want)) <= 1e-12 * np.max(np.abs(want)), (r.rid, r.mixed)
+        # same bits alone and in the mix, for both kinds of request
+        if r.mixed:
+            alone, _, _ = g.trsm_solve_mixed(plans[r.lid], r.B, residual=srv.mixed_residual, tol=r.tol)
+        else:
+            alone = g.trsm_solve(plans[r.lid], r.B)
+            g.trsm_sync_status(plans[r.lid])
+        assert torch.equal(alone, r.X), (r.rid, r.mixed)
     assert all(p.device_bytes() > 8 * p.n * p.n for p in plans)  # L~ plus the mixed data
+
+
+def test_server_waits_for_b_produced_on_the_callers_stream(cuda_lib):
+    """B is still being written by a kernel on the caller's stream when it is
+    submitted (the stream first sleeps, then copies B in): the slot streams
+    must wait for it, for FP64 batches and for mixed solves alike."""
+    import torch
+    import paper_1612_01855_gb300 as g
+    from paper_1612_01855_gb300.serve import Request, Server
+    Ls, plans = _setup(3, seed=11)
+    for L, p in zip(Ls, plans):
+        g.trsm_plan_mixed(p, _dev(L), "fp16x3")
+    srv = Server(plans, budget_bytes=40 * 2**30, streams=4, max_batch=8)
+    producer = torch.cuda.Stream()
+    reqs, host = [], []
+    rng = np.random.default_rng(12)
+    for rid in range(12):
+        lid = rid % len(Ls)
+        n, k = Ls[lid].shape[0], int(rng.integers(1, 40))
+        Bh = inputs.rhs(n, k, seed=500 + rid)
+        src = torch.from_numpy(np.ascontiguousarray(Bh.T)).pin_memory()
+        with torch.cuda.stream(producer):
+            B = torch.full((k, n), float("nan"), dtype=torch.float64, device="cuda").t()
+            torch.cuda._sleep(20_000_000)  # about 10 ms of device time before B is written
+            B.t().copy_(src, non_blocking=True)
+            r = Request(rid, lid, B, 0.0, mixed=rid % 3 == 0)
+            srv.submit(r)  # the event is recorded on `producer`, before B is complete
+        reqs.append(r)
+        host.append(Bh)
+    srv.drain()
+    for r, B in zip(reqs, host):
+        assert r.status == 0, r.rid
+        want = oracle.forward_subst(Ls[r.lid], B)
+        assert np.max(np.abs(r.X.cpu().numpy() - want)) <= 1e-12 * np.max(np.abs(want)), (r.rid, r.mixed)

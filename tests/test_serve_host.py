@@ -66,3 +66,45 @@ def test_autotune_buckets_and_paper_rule():
     assert autotune.paper_rule_n0(16384, 256) == 2048 and autotune.paper_rule_n0(100, 10000) == 100
     table = {0: (32, 0), 1: (64, 32)}
     assert autotune.choose(100, table=table) == (64, 32) and autotune.choose(900, table=table) == (32, 0)
+
+
+def test_queues_have_no_head_of_line_blocking():
+    """A free slot serves the earlier of the two queue heads, unless that head
+    cannot start: an FP64 request passes a mixed one while every mixed slot
+    is taken, and a mixed one passes an FP64 request that does not fit."""
+    plans = [_Plan(64), _Plan(128)]
+    plans[1].inner = "fp16x3"
+    srv = Server(plans, budget_bytes=10**9, streams=4)
+    assert srv.mixed_slots == 2
+    srv.submit(Request(0, 1, _B(128, 8), 0.0, mixed=True))
+    srv.submit(Request(1, 0, _B(64, 8), 1.0))
+    assert [r.rid for r in srv.pending] == [0, 1]
+    assert srv._next_kind() == "mixed"           # earlier head, a mixed slot is free
+    srv.mixed_busy = srv.mixed_slots
+    assert srv._next_kind() == "fp64"            # the mixed head must wait; FP64 passes it
+    srv.mixed_busy = 0
+    take, nbytes = srv._take_fp64()
+    assert [r.rid for r in take] == [1] and nbytes == Server.request_bytes(64, 8)
+    assert srv._next_kind() == "mixed"
+    # an FP64 head that does not fit the budget is passed by a mixed request that does
+    tight = Server(plans, budget_bytes=8 * (64 * 64 + 128 * 128) + Server.request_bytes(64, 2000) + 10,
+                   streams=2)
+    tight.submit(Request(2, 0, _B(64, 2000), 0.0))
+    tight.submit(Request(3, 1, _B(128, 8), 1.0, mixed=True))
+    assert Server.request_bytes(64, 2000) > Server.request_bytes(128, 8, True)
+    tight.adm.take(tight.adm.budget - tight.adm.resident - Server.request_bytes(128, 8, True))
+    assert not tight.adm.fits(Server.request_bytes(64, 2000))
+    assert tight._next_kind() == "mixed"
+    assert tight.cancel(2) and tight.cancel(3) and not tight.pending
+
+
+def test_single_slot_serves_both_kinds():
+    plans = [_Plan(64)]
+    plans[0].inner = "bf16x3"
+    srv = Server(plans, budget_bytes=10**9, streams=1)
+    assert srv.mixed_slots == 1
+    srv.submit(Request(0, 0, _B(64, 2), 0.0))
+    srv.submit(Request(1, 0, _B(64, 2), 0.5, mixed=True))
+    assert srv._next_kind() == "fp64"
+    srv.queue_fp64.clear()
+    assert srv._next_kind() == "mixed"

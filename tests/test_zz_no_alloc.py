@@ -1,8 +1,9 @@
 """trsm_solve_noalloc: the solve for callers that may not allocate device
 memory while solving (an application that owns all GPU memory through its
 own arena, or a latency-critical loop that cannot pay for an allocation).
-It must give the same X as trsm_solve, call after call, from its fixed
-64 MiB scratch array, and refuse problems whose workspace does not fit.
+It must give the same X as trsm_solve and the oracle, call after call and in
+place, from its fixed 64 MiB scratch array, and refuse problems whose
+workspace does not fit.
 
 This file is named to be collected last, so that a failure here cannot hide
 the results of the other GPU tests in a run that stops at the first failure.
@@ -33,18 +34,23 @@ def _rel(a, b):
     return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
 
 
-def test_noalloc_matches_trsm_solve_twice(cuda_lib):
+@pytest.mark.parametrize("n,k,n0", [(1000, 300, 64), (777, 33, 100)])
+def test_noalloc_matches_trsm_solve_twice(cuda_lib, n, k, n0):
+    """Two calls in a row with different B: each equals trsm_solve and the
+    oracle.  (777, 33, 100) leaves a short last block row (77 rows) and a
+    narrow last column tile, so ragged tiles go through the shared scratch."""
     import torch
+    import oracle
     import paper_1612_01855_gb300 as g
     lib = cuda_lib
-    n, k, n0 = 1000, 300, 64
     L = inputs.well_conditioned_L(n, seed=21)
     plan = g.trsm_plan(_dev(L), n0)
     need = ctypes.c_size_t()
     assert lib.trsm_solve_workspace_size(plan.handle, k, ctypes.byref(need)) == 0
     assert need.value <= 64 << 20
     for call, seed in enumerate((31, 32)):  # two calls in a row, different B
-        B = _dev(inputs.rhs(n, k, seed))
+        Bh = inputs.rhs(n, k, seed)
+        B = _dev(Bh)
         X_ref = g.trsm_solve(plan, B)
         X = torch.full((k, n), float("nan"), dtype=torch.float64, device="cuda").t()
         rc = lib.trsm_solve_noalloc(plan.handle, ctypes.c_void_p(B.data_ptr()), k, B.stride(1),
@@ -52,7 +58,29 @@ def test_noalloc_matches_trsm_solve_twice(cuda_lib):
         assert rc == 0, lib.trsm_error_string(rc)
         g.trsm_sync_status(plan)
         assert torch.isfinite(X).all().item(), call
-        assert _rel(X.cpu().numpy(), X_ref.cpu().numpy()) < TOL, call
+        got = X.cpu().numpy()
+        assert _rel(got, X_ref.cpu().numpy()) < TOL, call
+        assert _rel(got, oracle.forward_subst(L, Bh)) < TOL, call
+
+
+def test_noalloc_in_place(cuda_lib):
+    """X_dev == B_dev (same leading dimension) is allowed: the solve
+    overwrites B with X."""
+    import torch
+    import oracle
+    import paper_1612_01855_gb300 as g
+    lib = cuda_lib
+    n, k, n0 = 777, 33, 100
+    L = inputs.well_conditioned_L(n, seed=23)
+    plan = g.trsm_plan(_dev(L), n0)
+    Bh = inputs.rhs(n, k, 33)
+    B = _dev(Bh)
+    rc = lib.trsm_solve_noalloc(plan.handle, ctypes.c_void_p(B.data_ptr()), k, B.stride(1),
+                                ctypes.c_void_p(B.data_ptr()), B.stride(1), _stream())
+    assert rc == 0, lib.trsm_error_string(rc)
+    g.trsm_sync_status(plan)
+    assert torch.isfinite(B).all().item()
+    assert _rel(B.cpu().numpy(), oracle.forward_subst(L, Bh)) < TOL
 
 
 def test_noalloc_rejects_oversized_workspace(cuda_lib):
