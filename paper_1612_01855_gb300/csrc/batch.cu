@@ -262,165 +262,263 @@ struct SysUnit {
   int cw;   // chunk width: 8, 16 or 32
 };
 
+constexpr int kSysMaxCW = 32;  // widest column chunk of a unit
+// W_l is formed after the product's last K chunk and read before the next
+// block row stages its first one, so it shares memory with the staging
+// buffers (30 KB per CTA).
 struct SysSmem {
   float inv[64][68];  // inv[col][row]: L~_ll, zeros above the diagonal (rows 16-byte aligned)
-  float w[64][36];    // w[row][col]: W_l for the chunk's columns
   union {
+    float w[64][kSysMaxCW + 4];  // w[row][col]: W_l for the chunk's columns
     struct {
-      float a[kSysKC][68];  // a[kk][row] = L(s0 + row, t0 + kk)
-      float b[kSysKC][36];  // b[kk][col] = X(t0 + kk, c0 + col)
+      float a[kSysKC][68];             // a[kk][row] = L(s0 + row, t0 + kk)
+      float b[kSysKC][kSysMaxCW + 4];  // b[kk][col] = X(t0 + kk, c0 + col)
     } g;
-    struct {
-      float ls[2][32][33];  // leaf-inversion scratch
-      float t[32][33];      // combine: t[c][q] = L21(q, c), then T
-    } v;
-  } u;
+  };
 };
 
-// The inversion launch needs only the inverse and the leaf scratch: 30 KB
-// instead of 40, so seven CTAs fit per SM instead of five (two of a CTA's
-// four warps wait at the barrier during the leaf substitutions).
+// The inversion launch: the block being inverted in place and the T factor
+// of the RecTriInv combine (about 26 KB: eight CTAs per SM).
 struct InvSmem {
-  float inv[64][68];
-  union {
-    struct {
-      float ls[2][32][33];
-      float t[32][33];
-    } v;
-  } u;
+  float inv[64][68];  // inv[col][row]
+  float t[32][33];    // t[node * h + c][r] = T(r, c) of the node being combined
 };
 
-// L~_ll for the diagonal block at s0 (order m <= 64) into sm.inv.
-template <class Smem>
-__device__ void sys_invert(const BatchSys<float>& a, int64_t s0, int m, Smem& sm) {
-  const int tid = threadIdx.x, warp = tid >> 5;
-  for (int e = tid; e < 64 * 68; e += kSysThreads) (&sm.inv[0][0])[e] = 0.f;
-  __syncthreads();
-  const float* Lb = a.L + s0 * a.ldl + s0;
-  const int h = m > 32 ? 32 : m, r2 = m - h;
-  if (warp == 0) leaf_invert_warp<float>(Lb, a.ldl, h, &sm.inv[0][0], 68, sm.u.v.ls[0], a.status, s0);
-  if (warp == 1 && r2 > 0)
-    leaf_invert_warp<float>(Lb + 32 * a.ldl + 32, a.ldl, r2, &sm.inv[32][32], 68, sm.u.v.ls[1], a.status, s0 + 32);
-  if (r2 == 0) {
-    __syncthreads();
-    return;
-  }
-  {
-    float lv[8];
+// One level of the RecTriInv combine over `nodes` nodes of order 2H at once
+// (the first product, T = -(L22^-1 L21), into sm.t; then L21^-1 = T L11^-1
+// in place).  Thread tid holds outputs e = tid + 128 j: rows over the lanes
+// (so the column-major block is read without bank conflicts), and all its
+// outputs advance together through the sum, so that their multiply-adds are
+// independent.  Both sums run over the full H terms: the triangular
+// factors' upper parts are zeros.
+template <int H>
+__device__ __forceinline__ void combine_level(InvSmem& sm, int nodes) {
+  constexpr int J = (32 * H + kSysThreads - 1) / kSysThreads;  // outputs per thread: 64 / (2H) nodes of H x H
+  const int tid = threadIdx.x;
+  const int outs = nodes * H * H, rows = nodes * H;
+  int rr[J], cc[J], bb[J];
+  bool on[J];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int e = tid + kSysThreads * j, c = e >> 5, q = e & 31;
-      lv[j] = (q < r2) ? Lb[static_cast<int64_t>(c) * a.ldl + 32 + q] : 0.f;
-    }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int e = tid + kSysThreads * j;
-      sm.u.v.t[e >> 5][e & 31] = lv[j];
-    }
+  for (int j = 0; j < J; ++j) {
+    const int e = tid + kSysThreads * j;
+    on[j] = e < outs;
+    const int r = e % rows, q = r / H;
+    rr[j] = r % H;
+    cc[j] = e / rows;
+    bb[j] = 2 * H * q;
   }
-  __syncthreads();
-  // T = -(L22^-1 L21), r2 x 32 (the paper's order: this product first)
-  float tv[8];
+  float acc[J];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const int e = tid + kSysThreads * j, r = e >> 5, c = e & 31;
-    float acc = 0.f;
-    if (r < r2)
-      for (int q = 0; q <= r; ++q) acc = fmaf(sm.inv[32 + q][32 + r], sm.u.v.t[c][q], acc);
-    tv[j] = -acc;
-  }
+  for (int j = 0; j < J; ++j) acc[j] = 0.f;
+#pragma unroll 4
+  for (int pp = 0; pp < H; ++pp)
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+      if (on[j])
+        acc[j] = fmaf(sm.inv[bb[j] + H + pp][bb[j] + H + rr[j]], sm.inv[bb[j] + cc[j]][bb[j] + H + pp], acc[j]);
+#pragma unroll
+  for (int j = 0; j < J; ++j)
+    if (on[j]) sm.t[(bb[j] / (2 * H)) * H + cc[j]][rr[j]] = -acc[j];
   __syncthreads();
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const int e = tid + kSysThreads * j, r = e >> 5, c = e & 31;
-    sm.u.v.t[r][c] = tv[j];  // now t[r][c] = T(r, c)
-  }
-  __syncthreads();
-  // L21^-1 = T L11^-1
+  for (int j = 0; j < J; ++j) acc[j] = 0.f;
+#pragma unroll 4
+  for (int pp = 0; pp < H; ++pp)
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const int e = tid + kSysThreads * j, r = e >> 5, c = e & 31;
-    if (r < r2) {
-      float acc = 0.f;
-      for (int q = c; q < 32; ++q) acc = fmaf(sm.u.v.t[r][q], sm.inv[c][q], acc);
-      sm.inv[c][32 + r] = acc;
-    }
-  }
+    for (int j = 0; j < J; ++j)
+      if (on[j]) acc[j] = fmaf(sm.t[(bb[j] / (2 * H)) * H + pp][rr[j]], sm.inv[bb[j] + cc[j]][bb[j] + pp], acc[j]);
+#pragma unroll
+  for (int j = 0; j < J; ++j)
+    if (on[j]) sm.inv[bb[j] + cc[j]][bb[j] + H + rr[j]] = acc[j];
   __syncthreads();
 }
 
+// L~_ll for the diagonal block at s0 (order m <= 64) into sm.inv, by
+// Algorithm RecTriInv (Section 5.1) with every warp busy at every level:
+// the block, padded to mp = 8, 16, 32 or 64 rows with an identity, is cut
+// into 8 x 8 leaves, inverted by column substitution (one thread per leaf
+// column), then combined level by level, h = 8, 16, 32: every node of a
+// level at once, T = -(L22^-1 L21) first and L21^-1 = T L11^-1 second (the
+// paper's order).  Lanes run over the rows of a product, so that the
+// column-major block is read without bank conflicts; the triangular factor
+// of the first product is read over its full width (its upper part is zero).
+__device__ void sys_invert(const BatchSys<float>& a, int64_t s0, int m, InvSmem& sm) {
+  const int tid = threadIdx.x;
+  const int mp = m <= 8 ? 8 : m <= 16 ? 16 : m <= 32 ? 32 : 64;
+  const float* Lb = a.L + s0 * a.ldl + s0;
+  // the lower triangle of the block, the identity past m, zeros elsewhere;
+  // every load issued before the first store (one memory round trip)
+  {
+    float v[32];
+#pragma unroll
+    for (int it = 0; it < 32; ++it) {
+      const int e = tid + kSysThreads * it, c = e >> 6, r = e & 63;
+      v[it] = (r < m && c < m && r >= c) ? Lb[static_cast<int64_t>(c) * a.ldl + r] : (r == c && r >= m ? 1.f : 0.f);
+    }
+#pragma unroll
+    for (int it = 0; it < 32; ++it) {
+      const int e = tid + kSysThreads * it;
+      sm.inv[e >> 6][e & 63] = v[it];
+    }
+  }
+  __syncthreads();
+  // leaves: thread (b, c) forms column c of the inverse of leaf b
+  float y[8];
+  const int nleaf = mp >> 3;
+  const int lb = tid >> 3, lc = tid & 7, o = 8 * lb;
+  if (lb < nleaf) {
+    const float piv = sm.inv[o + lc][o + lc];
+    if (o + lc < m && (piv == 0.f || !isfinite(piv)))
+      atomicMax(a.status, INT_MAX - static_cast<int>(s0 + o + lc));  // status: INT_MAX - first singular row
+#pragma unroll
+    for (int r = 0; r < 8; ++r) y[r] = (r == lc) ? 1.f : 0.f;
+#pragma unroll
+    for (int l = 0; l < 8; ++l) {
+      y[l] = y[l] / sm.inv[o + l][o + l];
+#pragma unroll
+      for (int r = l + 1; r < 8; ++r) y[r] = fmaf(-sm.inv[o + l][o + r], y[l], y[r]);
+    }
+  }
+  __syncthreads();
+  if (lb < nleaf) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) sm.inv[o + lc][o + r] = y[r];
+  }
+  __syncthreads();
+  if (mp >= 16) combine_level<8>(sm, mp / 16);
+  if (mp >= 32) combine_level<16>(sm, mp / 32);
+  if (mp >= 64) combine_level<32>(sm, 1);
+}
+
+// CPT consecutive floats of a shared-memory row in one vector load (the
+// rows of the staged operands are 16-byte aligned and CPT divides 4): one
+// wavefront per warp instead of CPT.
+template <int CPT>
+__device__ __forceinline__ void load_row(const float* p, float (&v)[CPT]) {
+  if constexpr (CPT == 4) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+    v[3] = q.w;
+  } else if constexpr (CPT == 2) {
+    const float2 q = *reinterpret_cast<const float2*>(p);
+    v[0] = q.x;
+    v[1] = q.y;
+  } else {
+    v[0] = *p;
+  }
+}
+
+// The fields of a system that a unit reads, kept in shared memory for the
+// whole unit: read once from the system table instead of at every use.
+struct UnitSys {
+  const float* L;
+  const float* Linv;
+  const float* B;
+  float* X;
+  int64_t ldl, ldinv, inv_bstride, ldb, ldx, n, k, n0;
+  int N;
+};
+
+// TM (4 or 8) consecutive floats of a 16-byte aligned shared-memory row.
+template <int TM>
+__device__ __forceinline__ void load_rows(const float* p, float (&v)[TM]) {
+#pragma unroll
+  for (int h = 0; h < TM; h += 4) {
+    const float4 q = *reinterpret_cast<const float4*>(p + h);
+    v[h] = q.x;
+    v[h + 1] = q.y;
+    v[h + 2] = q.z;
+    v[h + 3] = q.w;
+  }
+}
+
 // One unit: columns [c0, c0 + nc) of one system.  Thread (ty, tx) owns rows
-// 4 ty .. 4 ty + 3 and columns CPT tx .. CPT tx + CPT - 1 of every block row.
+// TM ty .. TM ty + TM - 1 and columns CPT tx .. CPT tx + CPT - 1 of every
+// block row (TM = 4, CPT = CW / 8).
+// The staging loads of the product use per-thread pointers that advance by a
+// fixed stride, with their bounds decided once per block row: every K chunk
+// of 32 lies below s0, a multiple of n0 (32 or 64), so only the row and the
+// column bounds remain.
 template <int CW>
-__device__ void sys_unit(const BatchSys<float>& a, int c0, SysSmem& sm) {
+__device__ void sys_unit(const UnitSys& a, int c0, SysSmem& sm) {
   constexpr int CPT = CW / 8;
+  constexpr int TX = CW / CPT;                   // threads along the columns (8)
+  constexpr int TM = 64 * TX / kSysThreads;      // rows per thread (4)
   constexpr int NB = kSysKC * CW / kSysThreads;  // staged X values per thread and chunk
-  const int tid = threadIdx.x, ty = tid >> 3, tx = tid & 7;
+  const int tid = threadIdx.x, ty = tid / TX, tx = tid % TX;
   const int nc = static_cast<int>(imin64(CW, a.k - c0));
+  // staging roles: A value it is L(s0 + arow, t0 + akk + 2 it), B value it
+  // is X(t0 + bkk, c0 + bcol + 4 it) (CW = 32: 4 it spans the 32 columns)
+  const int arow = tid & 63, akk = tid >> 6;
+  const int bkk = tid & 31, bcol = tid >> 5;
+  constexpr int kBColStep = kSysThreads / 32;
+  const int64_t astep = 2 * a.ldl, bstep = kBColStep * a.ldx;
+  bool bok[NB];
+#pragma unroll
+  for (int it = 0; it < NB; ++it) bok[it] = bcol + kBColStep * it < nc;
+  const float* const pb0 = a.X + static_cast<int64_t>(c0 + bcol) * a.ldx + bkk;
   for (int l = 0; l < a.N; ++l) {
     const int64_t s0 = static_cast<int64_t>(l) * a.n0;
     const int m = static_cast<int>(imin64(a.n0, a.n - s0));
     {
       // L~_ll from the workspace, every load in flight before the stores
-      const float* Li = a.Linv + static_cast<int64_t>(l) * a.inv_bstride;
+      const float* Li = a.Linv + static_cast<int64_t>(l) * a.inv_bstride + static_cast<int64_t>(akk) * a.ldinv + arow;
+      const bool rok = arow < m;
       float iv[32];
 #pragma unroll
       for (int it = 0; it < 32; ++it) {
-        const int e = tid + kSysThreads * it, c = e >> 6, r = e & 63;
-        iv[it] = (c < m && r < m) ? Li[static_cast<int64_t>(c) * a.ldinv + r] : 0.f;
+        iv[it] = (rok && akk + 2 * it < m) ? *Li : 0.f;
+        Li += 2 * a.ldinv;
       }
 #pragma unroll
-      for (int it = 0; it < 32; ++it) {
-        const int e = tid + kSysThreads * it;
-        sm.inv[e >> 6][e & 63] = iv[it];
-      }
+      for (int it = 0; it < 32; ++it) sm.inv[akk + 2 * it][arow] = iv[it];
       __syncthreads();
     }
-    float acc[4][CPT];
+    float acc[TM][CPT];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < TM; ++i)
 #pragma unroll
       for (int j = 0; j < CPT; ++j) acc[i][j] = 0.f;
     // acc = L(S_l, 0:s0) X(0:s0, chunk), K in chunks of kSysKC, the next
     // chunk's operands loaded into registers while this one is used
+    const bool aok = arow < m;
+    const float* pa = a.L + static_cast<int64_t>(akk) * a.ldl + s0 + arow;
+    const float* pb = pb0;
     float ra[16], rb[NB];
-    auto load = [&](int64_t t0) {
+    auto load = [&]() {
+      const float* q = pa;
 #pragma unroll
       for (int it = 0; it < 16; ++it) {
-        const int e = tid + kSysThreads * it, kk = e >> 6, row = e & 63;
-        const int64_t t = t0 + kk;
-        ra[it] = (row < m && t < s0) ? a.L[t * a.ldl + s0 + row] : 0.f;
+        ra[it] = aok ? *q : 0.f;
+        q += astep;
       }
+      const float* r = pb;
 #pragma unroll
       for (int it = 0; it < NB; ++it) {
-        const int e = tid + kSysThreads * it, col = e >> 5, kk = e & 31;
-        const int64_t t = t0 + kk;
-        rb[it] = (col < nc && t < s0) ? a.X[static_cast<int64_t>(c0 + col) * a.ldx + t] : 0.f;
+        rb[it] = bok[it] ? *r : 0.f;
+        r += bstep;
       }
+      pa += kSysKC * a.ldl;
+      pb += kSysKC;
     };
-    if (s0 > 0) load(0);
+    if (s0 > 0) load();
     for (int64_t t0 = 0; t0 < s0; t0 += kSysKC) {
 #pragma unroll
-      for (int it = 0; it < 16; ++it) {
-        const int e = tid + kSysThreads * it;
-        sm.u.g.a[e >> 6][e & 63] = ra[it];
-      }
+      for (int it = 0; it < 16; ++it) sm.g.a[akk + 2 * it][arow] = ra[it];
 #pragma unroll
-      for (int it = 0; it < NB; ++it) {
-        const int e = tid + kSysThreads * it;
-        sm.u.g.b[e & 31][e >> 5] = rb[it];
-      }
+      for (int it = 0; it < NB; ++it) sm.g.b[bkk][bcol + kBColStep * it] = rb[it];
       __syncthreads();
-      if (t0 + kSysKC < s0) load(t0 + kSysKC);
+      if (t0 + kSysKC < s0) load();
 #pragma unroll 8
       for (int kk = 0; kk < kSysKC; ++kk) {
-        const float4 av = *reinterpret_cast<const float4*>(&sm.u.g.a[kk][ty * 4]);
-        const float a4[4] = {av.x, av.y, av.z, av.w};
+        float a4[TM];
+        load_rows<TM>(&sm.g.a[kk][ty * TM], a4);
         float bv[CPT];
+        load_row<CPT>(&sm.g.b[kk][tx * CPT], bv);
 #pragma unroll
-        for (int j = 0; j < CPT; ++j) bv[j] = sm.u.g.b[kk][tx * CPT + j];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < TM; ++i)
 #pragma unroll
           for (int j = 0; j < CPT; ++j) acc[i][j] = fmaf(a4[i], bv[j], acc[i][j]);
       }
@@ -428,8 +526,8 @@ __device__ void sys_unit(const BatchSys<float>& a, int c0, SysSmem& sm) {
     }
     // W_l = B_l - acc (zeros outside the block and the chunk)
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int row = ty * 4 + i;
+    for (int i = 0; i < TM; ++i) {
+      const int row = ty * TM + i;
 #pragma unroll
       for (int j = 0; j < CPT; ++j) {
         const int col = tx * CPT + j;
@@ -439,26 +537,30 @@ __device__ void sys_unit(const BatchSys<float>& a, int c0, SysSmem& sm) {
       }
     }
     __syncthreads();
-    // X_l = L~_ll W_l
-    float x[4][CPT];
+    // X_l = L~_ll W_l.  L~_ll is lower triangular and warp w holds rows
+    // 16 w .. 16 w + 15, so its sums stop at t = 16 w + 16 (the products
+    // past it are zeros); the trip count is a multiple of 8, the rows and
+    // columns past m being zeros, so that the loop unrolls.
+    float x[TM][CPT];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < TM; ++i)
 #pragma unroll
       for (int j = 0; j < CPT; ++j) x[i][j] = 0.f;
-    for (int t = 0; t < m; ++t) {
-      const float4 iv = *reinterpret_cast<const float4*>(&sm.inv[t][ty * 4]);
-      const float i4[4] = {iv.x, iv.y, iv.z, iv.w};
+    const int tend = min((m + 7) & ~7, ((tid >> 5) + 1) * (32 / TX) * TM);
+#pragma unroll 8
+    for (int t = 0; t < tend; ++t) {
+      float i4[TM];
+      load_rows<TM>(&sm.inv[t][ty * TM], i4);
       float wv[CPT];
+      load_row<CPT>(&sm.w[t][tx * CPT], wv);
 #pragma unroll
-      for (int j = 0; j < CPT; ++j) wv[j] = sm.w[t][tx * CPT + j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < CPT; ++j) x[i][j] = fmaf(i4[i], wv[j], x[i][j]);
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int row = ty * 4 + i;
+    for (int i = 0; i < TM; ++i) {
+      const int row = ty * TM + i;
 #pragma unroll
       for (int j = 0; j < CPT; ++j) {
         const int col = tx * CPT + j;
@@ -487,14 +589,19 @@ __global__ void __launch_bounds__(kSysThreads) inv32_kernel(const BatchSys<float
   }
 }
 
-__global__ void __launch_bounds__(kSysThreads, 4) sys32_kernel(const BatchSys<float>* __restrict__ sys,
+__global__ void __launch_bounds__(kSysThreads, 6) sys32_kernel(const BatchSys<float>* __restrict__ sys,
                                                             const SysUnit* __restrict__ units) {
   __shared__ __align__(16) SysSmem sm;
+  __shared__ UnitSys us;
   const SysUnit u = units[blockIdx.x];
-  const BatchSys<float>& a = sys[u.sys];
-  if (u.cw == 8) sys_unit<8>(a, u.c0, sm);
-  else if (u.cw == 16) sys_unit<16>(a, u.c0, sm);
-  else sys_unit<32>(a, u.c0, sm);
+  if (threadIdx.x == 0) {
+    const BatchSys<float>& a = sys[u.sys];
+    us = UnitSys{a.L, a.Linv, a.B, a.X, a.ldl, a.ldinv, a.inv_bstride, a.ldb, a.ldx, a.n, a.k, a.n0, a.N};
+  }
+  __syncthreads();
+  if (u.cw == 8) sys_unit<8>(us, u.c0, sm);
+  else if (u.cw == 16) sys_unit<16>(us, u.c0, sm);
+  else sys_unit<32>(us, u.c0, sm);
 }
 
 // One (phase, part, system) range of tickets.
@@ -923,6 +1030,8 @@ int build_batch32(const trsm_batch_item* items, int count, trsm_batch_s* b, void
     inv_off[s] = off;
     off = trsm::al256(off + sizeof(float) * a.N * a.n0 * a.n0);
     // chunks of cw columns; by k, 32-wide chunks and one narrower last chunk
+    // (64-wide chunks halve the units but double the longest one, which
+    // sets the launch's tail: measured slower)
     if (it.tile_cols == 0 && a.k > 32) {
       int64_t c0 = 0;
       for (; c0 + 32 <= a.k; c0 += 32) units.push_back(trsm::SysUnit{s, static_cast<int>(c0), 32});
