@@ -109,13 +109,40 @@ int trsm_solve(trsm_handle_t h, const double* B_dev, int64_t k, int64_t ldb, dou
  *                             boundaries, X1 = Rec(L11,B1), B2 -= L21 X1,
  *                             X2 = Rec(L22,B2); the base case X = L^-1 B uses
  *                             the plan's inverted diagonal block.
- * B_dev must not alias X_dev for the last two.  Asynchronous; allocates its
- * workspace stream-ordered.  Errors as trsm_solve. */
+ *   TRSM_SCHED_SLICED         It-Inv-TRSM in its right-looking order with
+ *                             both matrix multiplies, X_i = L~_ii W_i and
+ *                             W(T_{i+1}) -= L(T_{i+1}, S_i) X_i, on the BF16
+ *                             tensor cores: each factor is split into eight
+ *                             6-bit integer digit planes with a power-of-two
+ *                             exponent per row (per row and block column for
+ *                             L), the 36 plane pairs of weight >= 2^-42 are
+ *                             multiplied with exact FP32 sums, and the
+ *                             results are combined and applied in FP64.
+ *                             Each product carries about 2^-49 of |A| |B|
+ *                             (an FP64-class result, not FP64 rounding).
+ *                             Needs trsm_plan_sliced on the plan first
+ *                             (else TRSM_EINVAL); X_dev may equal B_dev
+ *                             with ldx == ldb.
+ * B_dev must not alias X_dev for RIGHT_LOOKING and RECURSIVE.  Asynchronous;
+ * allocates its workspace stream-ordered.  Errors as trsm_solve. */
 #define TRSM_SCHED_DAG 0
 #define TRSM_SCHED_RIGHT_LOOKING 1
 #define TRSM_SCHED_RECURSIVE 2
+#define TRSM_SCHED_SLICED 3
 int trsm_solve_schedule(trsm_handle_t h, const double* B_dev, int64_t k, int64_t ldb, double* X_dev,
                         int64_t ldx, int schedule, void* stream);
+
+/* trsm_plan_sliced — adds the data of TRSM_SCHED_SLICED to a plan (no
+ * counterpart in the paper, which assumes exact arithmetic: this is the
+ * digit splitting of Ozaki, Ogita, Oishi & Rump, 2012, applied to the two
+ * matrix multiplies of It-Inv-TRSM, Section 6.2).  From the plan's L~ it
+ * makes eight bf16 digit planes of L off the diagonal blocks (16 n^2 bytes)
+ * and of the rows of the inverted diagonal blocks (16 n n0 bytes), counted
+ * by trsm_plan_device_bytes and freed by trsm_destroy.  The block order must
+ * be a multiple of 64 and at most 2048, or the plan a single block (n0 >= n)
+ * of order at most 2048 (else TRSM_EINVAL).  A second call is a no-op.
+ * Synchronous.  Errors: TRSM_EINVAL, TRSM_ENOMEM, TRSM_ECUDA. */
+int trsm_plan_sliced(trsm_handle_t h, void* stream);
 
 /* Workspace-explicit form of trsm_solve: the caller passes device memory
  * `ws_dev` of at least trsm_solve_workspace_size(h, k) bytes (256-byte

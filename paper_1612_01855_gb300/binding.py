@@ -57,6 +57,7 @@ SIGNATURES = {
     "trsm_solve_workspace_size": (_int, [_vp, _i64, ctypes.POINTER(ctypes.c_size_t)]),
     "trsm_solve_ws": (_int, [_vp, _dp, _i64, _i64, _dp, _i64, _vp, ctypes.c_size_t, _vp]),
     "trsm_solve_noalloc": (_int, [_vp, _dp, _i64, _i64, _dp, _i64, _vp]),
+    "trsm_plan_sliced": (_int, [_vp, _vp]),
     "trsm_plan_mixed": (_int, [_vp, _dp, _i64, _int, _vp]),
     "trsm_solve_mixed": (_int, [_vp, _dp, _i64, _i64, _dp, _i64, _int, _int, ctypes.c_double,
                                 ctypes.POINTER(_int), ctypes.POINTER(ctypes.c_double), _vp]),
@@ -292,14 +293,26 @@ def trsm_solve_mixed(plan, B, X=None, residual="sliced", max_iter=30, tol=1e-14,
     return X, it.value, upd.value
 
 
-SCHEDULES = {"dag": 0, "right-looking": 1, "recursive": 2}
+SCHEDULES = {"dag": 0, "right-looking": 1, "recursive": 2, "sliced": 3}
+
+
+def trsm_plan_sliced(plan):
+    """Adds the digit planes of the sliced schedule to a plan (synchronous;
+    a no-op when they are there)."""
+    torch = _torch()
+    s = ctypes.c_void_p(torch.cuda.current_stream(plan.device).cuda_stream)
+    _check(load_library().trsm_plan_sliced(plan.handle, s), "trsm_plan_sliced")
 
 
 def trsm_solve_schedule(plan, B, X=None, schedule="dag"):
     """trsm_solve with a chosen schedule: "dag" (default persistent
-    kernel), "right-looking" (the paper's B~ loop with look-ahead) or
-    "recursive" (Rec-TRSM).  Asynchronous."""
+    kernel), "right-looking" (the paper's B~ loop with look-ahead),
+    "recursive" (Rec-TRSM) or "sliced" (both matrix multiplies as
+    FP64-class digit-sliced tensor-core products; its plan data is made on
+    first use).  Asynchronous."""
     torch = _torch()
+    if schedule == "sliced":
+        trsm_plan_sliced(plan)
     B = _dev_matrix(B, "B")
     n, k = B.shape
     if X is None:

@@ -332,13 +332,15 @@ void trsm_destroy(trsm_handle_t h) {
   if (h->Lt) cudaFree(h->Lt);
   if (h->status) cudaFree(h->status);
   trsm::mixed_release(h);
+  trsm::sliced_release(h);
   if (cur != h->device) cudaSetDevice(cur);
   delete h;
 }
 
 size_t trsm_plan_device_bytes(trsm_handle_t h) {
   if (!h) return 0;
-  return sizeof(double) * (size_t)h->ldt * (size_t)h->n + sizeof(int) + trsm::mixed_bytes(h);
+  return sizeof(double) * (size_t)h->ldt * (size_t)h->n + sizeof(int) + trsm::mixed_bytes(h) +
+         trsm::sliced_bytes(h);
 }
 
 int trsm_plan_sizes(trsm_handle_t h, int64_t* n, int64_t* n0, int64_t* nblocks) {

@@ -9,6 +9,7 @@
 
 namespace trsm {
 struct MixedPlan;
+struct SlicedPlan;
 }
 
 // The plan behind trsm_handle_t.
@@ -17,7 +18,8 @@ struct trsm_plan_s {
   double* Lt = nullptr;   // L~: n x n, leading dimension ldt
   int* status = nullptr;  // sticky device status of solves
   int device = 0;
-  trsm::MixedPlan* mixed = nullptr;  // low-precision data (trsm_plan_mixed), or null
+  trsm::MixedPlan* mixed = nullptr;    // low-precision data (trsm_plan_mixed), or null
+  trsm::SlicedPlan* sliced = nullptr;  // digit planes of the sliced schedule (trsm_plan_sliced), or null
 };
 
 namespace trsm {
@@ -26,6 +28,13 @@ namespace trsm {
 // Device bytes of the plan's mixed-precision data (0 without it).
 size_t mixed_bytes(const trsm_plan_s* h);
 void mixed_release(trsm_plan_s* h);
+// The same for the digit planes of the sliced schedule.
+size_t sliced_bytes(const trsm_plan_s* h);
+void sliced_release(trsm_plan_s* h);
+// X = L^-1 B by the sliced schedule (sched_sliced.cu): B is copied first, so
+// X may alias B (same leading dimension).
+int solve_sliced(trsm_plan_s* h, const double* B, int64_t k, int64_t ldb, double* X, int64_t ldx,
+                 cudaStream_t s);
 
 // A diagonal block to invert in place: top-left element at A + off, order m;
 // row0 is its first row in the caller's numbering (for singular reports).

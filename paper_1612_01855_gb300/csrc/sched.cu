@@ -14,6 +14,9 @@
 // Recursive, as Algorithm Rec-TRSM (Section 4): X1 = Rec(L11, B1);
 // B2 -= L21 X1; X2 = Rec(L22, B2), halving on block boundaries; at a single
 // diagonal block the base case X = L^-1 B applies the plan's inverse.
+//
+// The sliced schedule (FP64-class products on the tensor cores) lives in
+// sched_sliced.cu.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -185,6 +188,12 @@ cudaError_t recursive(const trsm_plan_s* h, int64_t b0, int64_t b1, double* W, i
 extern "C" int trsm_solve_schedule(trsm_handle_t h, const double* B_dev, int64_t k, int64_t ldb, double* X_dev,
                                    int64_t ldx, int schedule, void* stream) {
   if (schedule == TRSM_SCHED_DAG) return trsm_solve(h, B_dev, k, ldb, X_dev, ldx, stream);
+  if (schedule == TRSM_SCHED_SLICED) {
+    if (!h || !h->sliced || k < 0) return TRSM_EINVAL;
+    if (k == 0) return TRSM_SUCCESS;
+    if (!B_dev || !X_dev || ldb < h->n || ldx < h->n || (B_dev == X_dev && ldb != ldx)) return TRSM_EINVAL;
+    return trsm::solve_sliced(h, B_dev, k, ldb, X_dev, ldx, static_cast<cudaStream_t>(stream));
+  }
   if (!h || k < 0 || (schedule != TRSM_SCHED_RIGHT_LOOKING && schedule != TRSM_SCHED_RECURSIVE)) return TRSM_EINVAL;
   if (k == 0) return TRSM_SUCCESS;
   if (!B_dev || !X_dev || ldb < h->n || ldx < h->n || B_dev == X_dev) return TRSM_EINVAL;

@@ -89,15 +89,17 @@ __device__ __forceinline__ void digits_of(double a, int e, float (&dig)[kPlanes]
   dig[0] = static_cast<float>(static_cast<int>(v));  // |d_0| <= 64
 }
 
+// nch chunks of kc values per row are sliced (the last one up to K);
+// ex_stride is the operand's exponent row stride.
 __global__ void slice_rows_kernel(const double* __restrict__ src, int64_t ld, int64_t rows, int64_t K,
-                                  int64_t nch, __nv_bfloat16* __restrict__ dst, int64_t kp,
-                                  int64_t plane_elems, int16_t* __restrict__ ex) {
+                                  int64_t nch, int64_t kc, int64_t ex_stride, __nv_bfloat16* __restrict__ dst,
+                                  int64_t kp, int64_t plane_elems, int16_t* __restrict__ ex) {
   const int64_t wid = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (wid >= rows * nch) return;
   const int64_t r = wid / nch, c = wid % nch;
   const double* p = src + r * ld;
-  const int64_t k0 = c * kChunk, k1 = (K < k0 + kChunk) ? K : k0 + kChunk;
+  const int64_t k0 = c * kc, k1 = (K < k0 + kc) ? K : k0 + kc;
   // max |a| over the chunk, compared as the bit patterns of |a| (ordered
   // like the values for non-negative doubles)
   unsigned long long mb = 0;
@@ -116,7 +118,7 @@ __global__ void slice_rows_kernel(const double* __restrict__ src, int64_t ld, in
     const int E = static_cast<int>(mb >> 52);
     e = (E != 0) ? E - 1022 : -1022;
   }
-  if (lane == 0) ex[r * nch + c] = static_cast<int16_t>(e);
+  if (lane == 0) ex[r * ex_stride + c] = static_cast<int16_t>(e);
   // padding columns of the last chunk (up to kp, a multiple of 8) are zeros
   const int64_t kw1 = (c == nch - 1) ? kp : k1;
   __nv_bfloat16* drow = dst + r * kp;
@@ -157,6 +159,57 @@ __global__ void transpose_lower_kernel(const double* __restrict__ L, int64_t ldl
   for (int yy = ty; yy < 32; yy += 8) {
     const int64_t i = bi + yy, j = bj + tx;  // write row i, column j of T (row-major)
     if (i < n && j < n) T[i * n + j] = tile[tx][yy];
+  }
+}
+
+// Row-major copy of L~ off its diagonal blocks: T(i, j) = L~(i, j) for
+// i > j in different blocks of order n0, zero elsewhere (the trailing
+// updates of the sliced schedule read only these entries, and leaving the
+// diagonal blocks out keeps their large entries from setting the row
+// exponents).
+__global__ void transpose_offdiag_kernel(const double* __restrict__ L, int64_t ldl, double* __restrict__ T, int64_t n,
+                                         int64_t n0) {
+  __shared__ double tile[32][33];
+  const int64_t bi = blockIdx.y * 32, bj = blockIdx.x * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int yy = ty; yy < 32; yy += 8) {
+    const int64_t i = bi + tx, j = bj + yy;
+    double v = 0.0;
+    if (i < n && j < n && i > j && i / n0 != j / n0) v = L[j * ldl + i];
+    tile[yy][tx] = v;
+  }
+  __syncthreads();
+  for (int yy = ty; yy < 32; yy += 8) {
+    const int64_t i = bi + yy, j = bj + tx;
+    if (i < n && j < n) T[i * n + j] = tile[tx][yy];
+  }
+}
+
+// Row-major n x n0 copy of the rows of L~'s diagonal blocks below their
+// diagonal: T(r, c) = L~(r, b n0 + c) for c < r - b n0 (b = r / n0), zero
+// elsewhere; diag[r] = L~(r, r).  The diagonal stays out of the digit planes
+// (applied in FP64 by the diagonal multiply): it dominates the rows of the
+// inverse, and digits relative to it would leave the other entries few
+// significant bits.
+__global__ void transpose_diag_blocks_kernel(const double* __restrict__ L, int64_t ldl, double* __restrict__ T,
+                                             double* __restrict__ diag, int64_t n, int64_t n0) {
+  __shared__ double tile[32][33];
+  const int64_t bi = blockIdx.y * 32, bj = blockIdx.x * 32;  // rows r, block columns c
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int yy = ty; yy < 32; yy += 8) {
+    const int64_t r = bi + tx, c = bj + yy;
+    double v = 0.0;
+    if (r < n && c < n0) {
+      const int64_t b0 = r / n0 * n0;
+      if (b0 + c < r) v = L[(b0 + c) * ldl + r];
+      if (b0 + c == r) diag[r] = L[r * ldl + r];
+    }
+    tile[yy][tx] = v;
+  }
+  __syncthreads();
+  for (int yy = ty; yy < 32; yy += 8) {
+    const int64_t r = bi + yy, c = bj + tx;
+    if (r < n && c < n0) T[r * n0 + c] = tile[tx][yy];
   }
 }
 
@@ -201,6 +254,8 @@ struct ResidualEpi {
   int64_t nch;
   int M, N, K;  // R is M x N, L is M x K
   int lower;
+  int kc_steps;            // K steps of 64 per exactly-summed chunk (the operands' kc / 64)
+  int a_k0 = 0, a_row0 = 0;  // TMA coordinates of A's first K element and row (0: the whole L)
   struct State {
     float ph[16], pl[16];
   };
@@ -226,7 +281,7 @@ struct ResidualEpi {
     const int kend = lower ? min(K, (tm + 1) * 128) : K;
     kb0 = 0;
     kb1 = (kend + kStepK - 1) / kStepK;
-    chunk = kChunk / kStepK;
+    chunk = kc_steps;
   }
   __device__ void init(State&) const {}
   __device__ void group(State& st, int, int, int, int, int, int g, const float (&v)[16]) const {
@@ -294,6 +349,101 @@ struct ResidualEpi {
 };
 
 
+// x 2^n for a double, exact: an add to the exponent field when x and the
+// result are normal (integer work: GB300's FP64 pipe is narrow), ldexp out of
+// line otherwise.
+__device__ __noinline__ double scale2d_slow(double x, int n) { return ldexp(x, n); }
+__device__ __forceinline__ double scale2d(double x, int n) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  const int E = static_cast<int>((b >> 52) & 0x7FF);
+  if (E != 0 && E != 0x7FF && E + n >= 1 && E + n <= 0x7FE)
+    return __longlong_as_double(static_cast<long long>(b + (static_cast<unsigned long long>(n) << 52)));
+  if ((b << 1) == 0) return x;  // +-0
+  return scale2d_slow(x, n);
+}
+
+// Epilogue of one product of the sliced schedule (a single chunk along K):
+// the groups of a slab are added in float-float arithmetic as in the
+// residual, then Y(y_row0 + r, c) is set to, or decreased by, (hi + lo)
+// 2^(eA + eB - 12) in FP64.
+template <int BN>
+struct StepEpi {
+  double* Y;
+  int64_t ldy, y_row0;
+  const int16_t* eA;  // A's exponents: eA[(a_row0 + r) * a_nch + a_chunk]
+  int64_t a_nch;
+  int a_chunk;
+  const int16_t* eB;  // B's exponents: eB[c * b_nch] (one chunk)
+  int64_t b_nch;
+  int M, N, K;
+  int lower, subtract;
+  int a_k0, a_row0;
+  // optional FP64 diagonal term (the diagonal multiply): Y(y_row0 + r, c) =
+  // dg[r] D(r, c) + P(r, c), with D(r, c) = Dm[c * ldd + r]
+  const double* dg;
+  const double* Dm;
+  int64_t ldd;
+  struct State {
+    float ph[16], pl[16];
+  };
+  static constexpr int kGroupRows = 16;
+  __device__ void tile(int& tm, int& tn) const {
+    const int R = static_cast<int>(gridDim.x), C = static_cast<int>(gridDim.y);
+    const int lin = tm + R * tn;
+    const int grp = lin / (kGroupRows * C);
+    const int g0 = grp * kGroupRows;
+    const int gsz = min(kGroupRows, R - g0);
+    const int idx = lin - g0 * C;
+    const int r = g0 + idx % gsz;
+    tn = idx / gsz;
+    tm = lower ? R - 1 - r : r;
+  }
+  __device__ void k_range(int tm, int, int& kb0, int& kb1, int& chunk) const {
+    const int kend = lower ? min(K, (tm + 1) * 128) : K;
+    kb0 = 0;
+    kb1 = (kend + kStepK - 1) / kStepK;
+    chunk = kb1 > 0 ? kb1 : 1;
+  }
+  __device__ void init(State&) const {}
+  __device__ void group(State& st, int, int, int, int, int, int g, const float (&v)[16]) const {
+    if (g == 0) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        st.ph[j] = v[j];
+        st.pl[j] = 0.f;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) ff_add(st.ph[j], st.pl[j], v[j], 0.f);
+    }
+  }
+  __device__ void slab_done(State& st, int tm, int tn, int, int row, int sl) const {
+    const int grow = tm * 128 + row;
+    if (grow >= M) return;
+    const int ea = eA[static_cast<int64_t>(a_row0 + grow) * a_nch + a_chunk];
+    const int col0 = tn * BN + sl * 16;
+    const int ncol = min(16, N - col0);
+    double* base = Y + static_cast<int64_t>(col0) * ldy + y_row0 + grow;
+    int eb[16];
+    double old[16];  // Y (update) or D (diagonal term)
+    const double d = dg ? dg[grow] : 0.0;
+    const double* dcol = Dm ? Dm + static_cast<int64_t>(col0) * ldd + grow : nullptr;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      eb[j] = (j < ncol) ? __ldg(eB + static_cast<int64_t>(col0 + j) * b_nch) : 0;
+      old[j] = (j >= ncol) ? 0.0 : subtract ? base[static_cast<int64_t>(j) * ldy] : dcol ? dcol[j * ldd] : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (j >= ncol) continue;
+      const double v =
+          scale2d(static_cast<double>(st.ph[j]) + static_cast<double>(st.pl[j]), ea + eb[j] - 2 * kDigitBits);
+      base[static_cast<int64_t>(j) * ldy] = subtract ? old[j] - v : fma(d, old[j], v);
+    }
+  }
+  __device__ void finish(State&, int, int, int, int, int, int) const {}
+};
+
 // ---------------------------------------------------------------- kernel
 // The residual's own tcgen05 kernel.  All P + P planes of one 64-wide K
 // step take 196-208 KB of shared memory, so a ring over whole K steps has
@@ -357,10 +507,10 @@ __device__ __forceinline__ void for_items(int kb0, int kb1, int chunk, F&& f) {
   }
 }
 
-template <int P>
+template <int P, class Epi>
 __global__ void __launch_bounds__(Stream<P>::kThreads, 1)
-    stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                  const ResidualEpi<Stream<P>::BN> epi, int* err) {
+    stream_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, const Epi epi,
+                  int* err) {
   using S = Stream<P>;
   constexpr int BN = S::BN;
   constexpr int NG = S::NG;
@@ -409,8 +559,8 @@ __global__ void __launch_bounds__(Stream<P>::kThreads, 1)
         const int s0 = S::begin(gi), s1 = S::end(gi);
         tc::mbar_arrive_expect_tx(&full_bar[q], S::bytes(gi));
         const int kx = j * kStepK;
-        for (int sp = s0; sp < s1; ++sp)
-          tc::tma_load_3d(sa + (sp - s0) * S::A_SL, &mapA, &full_bar[q], kx, tm * 128, sp);
+        const int ax = kx + epi.a_k0, ay = tm * 128 + epi.a_row0;
+        for (int sp = s0; sp < s1; ++sp) tc::tma_load_3d(sa + (sp - s0) * S::A_SL, &mapA, &full_bar[q], ax, ay, sp);
         uint8_t* sb = sa + (s1 - s0) * S::A_SL;
         for (int u = 0; u < P - s0; ++u) tc::tma_load_3d(sb + u * S::B_SL, &mapB, &full_bar[q], kx, tn * BN, u);
         return true;
@@ -456,7 +606,7 @@ __global__ void __launch_bounds__(Stream<P>::kThreads, 1)
     constexpr int kSlabs = BN / 16, kShares = S::kEpiWarps / 4;
     constexpr int kPer = (kSlabs + kShares - 1) / kShares;
     const int sl0 = ((warp - 2) / 4) * kPer, sl1 = min(kSlabs, sl0 + kPer);
-    typename ResidualEpi<BN>::State st;
+    typename Epi::State st;
     epi.init(st);
     for (int c = 0; c < nchunks; ++c) {
       if (!tc::mbar_wait(&tfull_bar, c & 1, abort_flag)) break;
@@ -495,21 +645,22 @@ __global__ void __launch_bounds__(Stream<P>::kThreads, 1)
 }  // namespace sliced
 
 // ---------------------------------------------------------------- host
-size_t sliced_operand_bytes(int64_t rows, int64_t K) {
+size_t sliced_operand_bytes(int64_t rows, int64_t K, int64_t kc) {
   const int64_t kp = (K + 7) / 8 * 8;
-  const int64_t nch = (K + kChunk - 1) / kChunk;
+  const int64_t nch = (K + kc - 1) / kc;
   size_t b = sizeof(__nv_bfloat16) * static_cast<size_t>(kPlanes) * rows * kp;
   b = (b + 255) / 256 * 256;
   b += sizeof(int16_t) * static_cast<size_t>(rows) * nch;
   return (b + 255) / 256 * 256;
 }
 
-SlicedOperand sliced_operand_view(void* base, int64_t rows, int64_t K) {
+SlicedOperand sliced_operand_view(void* base, int64_t rows, int64_t K, int64_t kc) {
   SlicedOperand o;
   o.rows = rows;
   o.K = K;
   o.kp = (K + 7) / 8 * 8;
-  o.nch = (K + kChunk - 1) / kChunk;
+  o.kc = kc;
+  o.nch = (K + kc - 1) / kc;
   o.digits = static_cast<__nv_bfloat16*>(base);
   size_t b = sizeof(__nv_bfloat16) * static_cast<size_t>(kPlanes) * rows * o.kp;
   b = (b + 255) / 256 * 256;
@@ -517,14 +668,27 @@ SlicedOperand sliced_operand_view(void* base, int64_t rows, int64_t K) {
   return o;
 }
 
-cudaError_t slice_rows(const double* src, int64_t ld, const SlicedOperand& o, cudaStream_t s) {
-  const int64_t warps = o.rows * o.nch;
+namespace {
+cudaError_t launch_slice(const double* src, int64_t ld, int64_t K, int64_t nch, const SlicedOperand& o,
+                         cudaStream_t s) {
+  const int64_t warps = o.rows * nch;
   const int64_t threads = warps * 32;
+  if (threads == 0) return cudaSuccess;
   const unsigned blocks = static_cast<unsigned>((threads + 255) / 256);
-  sliced::slice_rows_kernel<<<blocks, 256, 0, s>>>(src, ld, o.rows, o.K, o.nch, o.digits, o.kp,
+  sliced::slice_rows_kernel<<<blocks, 256, 0, s>>>(src, ld, o.rows, K, nch, o.kc, o.nch, o.digits, o.kp,
                                                    o.rows * o.kp, o.ex);
   count_launch();
   return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t slice_rows(const double* src, int64_t ld, const SlicedOperand& o, cudaStream_t s) {
+  return launch_slice(src, ld, o.K, o.nch, o, s);
+}
+
+cudaError_t slice_rows_prefix(const double* src, int64_t ld, int64_t K, const SlicedOperand& o, cudaStream_t s) {
+  if (K < 1 || K > o.K || o.nch != 1) return cudaErrorInvalidValue;
+  return launch_slice(src, ld, K, 1, o, s);
 }
 
 cudaError_t slice_lower_rows(const double* L, int64_t ldl, int64_t n, const SlicedOperand& o,
@@ -535,6 +699,75 @@ cudaError_t slice_lower_rows(const double* L, int64_t ldl, int64_t n, const Slic
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return slice_rows(tmp_rowmajor, n, o, s);
+}
+
+cudaError_t slice_offdiag_block_rows(const double* Lt, int64_t ldt, int64_t n, int64_t n0, const SlicedOperand& off,
+                                     double* tmp_rowmajor, cudaStream_t s) {
+  if (off.rows != n || off.K != n || off.kc != n0) return cudaErrorInvalidValue;
+  dim3 grid(static_cast<unsigned>((n + 31) / 32), static_cast<unsigned>((n + 31) / 32));
+  sliced::transpose_offdiag_kernel<<<grid, dim3(32, 8), 0, s>>>(Lt, ldt, tmp_rowmajor, n, n0);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return slice_rows(tmp_rowmajor, n, off, s);
+}
+
+cudaError_t slice_inverse_block_rows(const double* Lt, int64_t ldt, int64_t n, int64_t n0, const SlicedOperand& inv,
+                                     double* diag, double* tmp_rowmajor, cudaStream_t s) {
+  if (inv.rows != n || inv.K != n0 || inv.nch != 1) return cudaErrorInvalidValue;
+  dim3 grid(static_cast<unsigned>((n0 + 31) / 32), static_cast<unsigned>((n + 31) / 32));
+  sliced::transpose_diag_blocks_kernel<<<grid, dim3(32, 8), 0, s>>>(Lt, ldt, tmp_rowmajor, diag, n, n0);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return slice_rows(tmp_rowmajor, n0, inv, s);
+}
+
+cudaError_t sliced_step(const SlicedOperand& A, int64_t a_row0, int64_t a_k0, const SlicedOperand& Bop, int64_t M,
+                        int64_t K, double* Y, int64_t ldy, int64_t y_row0, bool lower, bool subtract, const double* dg,
+                        const double* D, int64_t ldd, int* err, cudaStream_t s) {
+  constexpr int P = 8;
+  using St = sliced::Stream<P>;
+  constexpr int BN = sliced::Shape<P>::BN;
+  const int64_t N = Bop.rows;
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  // one chunk: K within A's chunk at a_k0 and within B's only chunk; the
+  // TMA x coordinate of A must be a multiple of 8 (16 bytes of bf16)
+  if (K < 1 || K > A.kc || a_k0 % A.kc != 0 || a_k0 + K > A.K || Bop.nch != 1 || K > Bop.K ||
+      a_row0 < 0 || a_row0 + M > A.rows || (a_k0 & 7) != 0 || (subtract && (dg || D)) || (!dg != !D))
+    return cudaErrorInvalidValue;
+  CUtensorMap ma, mb;
+  if (!tc::make_kmajor_map(&ma, A.digits, false, A.kp, A.rows, A.kp, kPlanes, A.rows * A.kp, 128, 1, 128))
+    return cudaErrorInvalidValue;
+  if (!tc::make_kmajor_map(&mb, Bop.digits, false, Bop.kp, Bop.rows, Bop.kp, kPlanes, Bop.rows * Bop.kp, BN, 1, 128))
+    return cudaErrorInvalidValue;
+  sliced::StepEpi<BN> epi;
+  epi.Y = Y;
+  epi.ldy = ldy;
+  epi.y_row0 = y_row0;
+  epi.eA = A.ex;
+  epi.a_nch = A.nch;
+  epi.a_chunk = static_cast<int>(a_k0 / A.kc);
+  epi.eB = Bop.ex;
+  epi.b_nch = Bop.nch;
+  epi.M = static_cast<int>(M);
+  epi.N = static_cast<int>(N);
+  epi.K = static_cast<int>(K);
+  epi.lower = lower ? 1 : 0;
+  epi.subtract = subtract ? 1 : 0;
+  epi.a_k0 = static_cast<int>(a_k0);
+  epi.a_row0 = static_cast<int>(a_row0);
+  epi.dg = dg;
+  epi.Dm = D;
+  epi.ldd = ldd;
+  auto kern = sliced::stream_kernel<P, sliced::StepEpi<BN>>;
+  cudaError_t e =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(St::SMEM_BYTES));
+  if (e != cudaSuccess) return e;
+  dim3 grid(static_cast<unsigned>((M + 127) / 128), static_cast<unsigned>((N + BN - 1) / BN));
+  kern<<<grid, St::kThreads, St::SMEM_BYTES, s>>>(ma, mb, epi, err);
+  count_launch();
+  return cudaGetLastError();
 }
 
 size_t sliced_partial_bytes(int64_t n, int64_t k) { return sizeof(float2) * static_cast<size_t>(n) * k; }
@@ -581,7 +814,8 @@ cudaError_t launch_residual(const SlicedOperand& Ls, const SlicedOperand& Xs, co
   epi.N = static_cast<int>(Xs.rows);
   epi.K = static_cast<int>(Ls.K);
   epi.lower = a.lower ? 1 : 0;
-  auto kern = sliced::stream_kernel<P>;
+  epi.kc_steps = static_cast<int>(Ls.kc / sliced::kStepK);
+  auto kern = sliced::stream_kernel<P, sliced::ResidualEpi<BN>>;
   cudaError_t e =
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(St::SMEM_BYTES));
   if (e != cudaSuccess) return e;
@@ -596,7 +830,7 @@ cudaError_t launch_residual(const SlicedOperand& Ls, const SlicedOperand& Xs, co
 cudaError_t sliced_residual(const SlicedOperand& Ls, const double* L, int64_t ldl, const SlicedOperand& Xs,
                             const double* X, int64_t ldx, const double* B, int64_t ldb, double* R,
                             int64_t ldr, void* partial, bool lower, int planes, int* err, cudaStream_t s) {
-  if (planes != 7 && planes != 8) return cudaErrorInvalidValue;
+  if ((planes != 7 && planes != 8) || Ls.kc != Xs.kc || Ls.kc % sliced::kStepK != 0) return cudaErrorInvalidValue;
   const ResidualArgs a{B, ldb, L, ldl, X, ldx, R, ldr, partial, lower};
   return planes == 8 ? launch_residual<8>(Ls, Xs, a, err, s) : launch_residual<7>(Ls, Xs, a, err, s);
 }

@@ -81,8 +81,9 @@ def test_every_entry_point_checks_its_arguments_on_the_host():
     E = binding.TRSM_EINVAL
     p16 = ctypes.c_void_p(16)
     # solves on a null plan, under every schedule and workspace form
-    for sched in (0, 1, 2, 5):
+    for sched in (0, 1, 2, 3, 5):
         assert lib.trsm_solve_schedule(None, p16, 1, 8, p16, 8, sched, None) == E
+    assert lib.trsm_plan_sliced(None, None) == E
     assert lib.trsm_solve_ws(None, p16, 1, 8, p16, 8, p16, 1 << 20, None) == E
     assert lib.trsm_solve_noalloc(None, p16, 1, 8, p16, 8, None) == E
     assert lib.trsm_plan_mixed(None, p16, 8, binding.TRSM_INNER_TF32, None) == E
