@@ -34,7 +34,13 @@ SHAPES = [(16384, 256), (8192, 8192), (2048, 131072)]
 # package); the paper's a-priori rule for p = 1 is n0 ~ min(sqrt(n k), n).
 DEFAULT_N0 = {(16384, 256): 256, (8192, 8192): 512, (2048, 131072): 2048}
 SWEEP_N0 = [64, 128, 256, 512, 1024, None]  # None = n (full inversion)
-SCHEDULE_NAMES = ("dag", "right-looking", "recursive")
+SCHEDULE_NAMES = ("dag", "right-looking", "recursive", "sliced")
+# Block sizes of the sliced schedule (FP64-class products on the tensor
+# cores): longer blocks mean longer, more efficient tensor-core products
+# (measured, ms: 16384x256 9.7 / 7.2 / 5.8 at n0 = 256 / 512 / 1024;
+# 8192x8192 26.0 / 22.0 / 20.0 at 512 / 1024 / 2048; 2048x131072 32.4 /
+# 29.7 / 30.3 at 512 / 1024 / 2048)
+SLICED_N0 = {(16384, 256): 1024, (8192, 8192): 2048, (2048, 131072): 1024}
 # Block size of the mixed-precision figure (n = 16384, k = 4096).  Larger
 # blocks suit the mixed path: fewer, longer tensor-core updates, and the
 # diagonal multiplies run in FP32 (measured: 163 / 137 / 131 / 135 ms at
@@ -209,7 +215,7 @@ def cpu_oracle_rate(data, shapes, budget_s, max_cols=None):
             cols = min(cols * 2, k)
         flops += float(n) * n * c_used
         secs += t_used
-        desc.append(f"n={n}: {c_used}/{k} cols")
+        desc.append(f"{n}:{c_used}/{k}")
     return flops / secs / 1e12, "; ".join(desc), cores
 
 
@@ -306,7 +312,7 @@ def compact_precision(recs):
         for m in rec["mixed"]:
             st = "ok" if m["converged"] else ("nan" if m["fwd_err"] is None else "miss")
             rows.append([rec["c"], m["inner"], m["ms"], m["iterations"], _sig(m["fwd_err"]), _sig(m["bwd_err"]),
-                         m["speedup_vs_fp64"], st])
+                         None if st == "nan" else m["speedup_vs_fp64"], st])
     return {"fp64": fp64, "cols": ["c", "inner", "ms", "sweeps", "fwd", "bwd", "x_fp64", "status"], "rows": rows}
 
 
@@ -347,14 +353,19 @@ def n0_sweep_study(g, torch, dev_in, outs, shapes, sweep=None):
 
 def residual_roofline(g, torch, n=16384, k=4096, reps=3):
     """The sliced FP64-class residual (the mixed path's dominant kernel) at
-    n = 16384, k = 4096: bf16 MMA flops (P(P+1)/2 plane pairs x 2 x n^2/2 x k)
-    per call / CUDA-event time, against the bf16 tensor peak.  The call
-    slices L and X too, so the fraction is a lower bound for the kernel."""
+    n = 16384, k = 4096, as each refinement sweep runs it: L's digit planes
+    come from the plan (trsm_plan_mixed), X is sliced inside the timed call,
+    then the stream kernel forms R = B - L X.  bf16 MMA flops (P(P+1)/2
+    plane pairs x 2 x n^2/2 x k) per call / CUDA-event time, against the bf16
+    tensor peak; the slicing of X (about 1 % of the call) counts as time."""
     import ctypes
     lib = g.load_library()
     L = torch.tril(torch.rand(n, n, dtype=torch.float64, device="cuda") * 2 - 1) / n
     L.diagonal().copy_(2 + torch.rand(n, dtype=torch.float64, device="cuda"))
     L = L.t().contiguous().t()
+    plan = g.trsm_plan(L, MIXED_N0)
+    g.trsm_plan_mixed(plan, L, "fp16x3")
+    del L
     X = (torch.rand(k, n, dtype=torch.float64, device="cuda") * 2 - 1).t()
     B = (torch.rand(k, n, dtype=torch.float64, device="cuda") * 2 - 1).t()
     R = torch.empty(k, n, dtype=torch.float64, device="cuda").t()
@@ -364,9 +375,9 @@ def residual_roofline(g, torch, n=16384, k=4096, reps=3):
     out = {}
     for planes in (7, 8):
         def call():
-            return lib.trsm_residual_sliced(ctypes.c_void_p(L.data_ptr()), n, n, ctypes.c_void_p(X.data_ptr()), k, n,
-                                            ctypes.c_void_p(B.data_ptr()), n, ctypes.c_void_p(R.data_ptr()), n,
-                                            planes, ctypes.c_void_p(err.data_ptr()), s)
+            return lib.trsm_residual_plan(plan.handle, ctypes.c_void_p(X.data_ptr()), k, n,
+                                          ctypes.c_void_p(B.data_ptr()), n, ctypes.c_void_p(R.data_ptr()), n,
+                                          planes, ctypes.c_void_p(err.data_ptr()), s)
         assert call() == 0
         torch.cuda.synchronize()
         ts = []
@@ -380,11 +391,12 @@ def residual_roofline(g, torch, n=16384, k=4096, reps=3):
         ms = statistics.median(ts)
         flops = planes * (planes + 1) / 2 * float(n) * n * k
         achieved = flops / (ms * 1e-3) / 1e12
-        out[f"planes{planes}"] = {"bound": "tensor", "kernel": "sliced stream_kernel (slicing of L and X included)",
+        out[f"planes{planes}"] = {"bound": "tensor", "kernel": "sliced stream_kernel (with the slicing of X)",
                                   "ms": round(ms, 3), "achieved": round(achieved, 1), "peak": burst,
                                   "unit": "TFLOP/s", "frac": round(achieved / burst, 4), "peak_source": src,
                                   "err_flag": int(err.item())}
-    del L, X, B, R
+    plan.destroy()
+    del X, B, R
     return out
 
 
@@ -472,7 +484,7 @@ def schedules_study(g, torch, dev_in, outs, shapes, n0s, reps=3, stream=None, fp
     for (Ld, Bd), X, (n, k), n0 in zip(dev_in, outs, shapes, n0s):
         p = g.trsm_plan(Ld, n0)
         rec = {"n": n, "k": k, "n0": n0}
-        for sched in ("dag", "right-looking", "recursive"):
+        for sched in SCHEDULE_NAMES:
             g.trsm_solve_schedule(p, Bd, X=X, schedule=sched)
             torch.cuda.synchronize()
             ts = []
@@ -488,11 +500,68 @@ def schedules_study(g, torch, dev_in, outs, shapes, n0s, reps=3, stream=None, fp
             rec[sched] = {"solve_ms": round(ms, 3), "tflops": round(tf, 4)}
             if fp64_peak:
                 rec[sched]["frac_of_measured_dfma"] = round(tf / fp64_peak, 4)
-        rec["autotuned"] = min(("dag", "right-looking", "recursive"), key=lambda x: rec[x]["solve_ms"])
+        rec["autotuned"] = min(SCHEDULE_NAMES, key=lambda x: rec[x]["solve_ms"])
         g.trsm_sync_status(p)
         p.destroy()
         out.append(rec)
     return out
+
+
+def sliced_mma_flops(n, k, nb):
+    """BF16 tensor-core flops of one sliced solve: 36 digit-plane pairs for
+    every product; the updates W(T_{i+1}) -= L(T_{i+1}, S_i) X_i take
+    2 (n - (i+1) nb) nb k each, the diagonal multiplies 2 m_i^2 k / 2 (the
+    strictly lower part of each inverted block)."""
+    N = -(-n // nb)
+    upd = sum(2.0 * (n - (i + 1) * nb) * nb * k for i in range(N - 1))
+    diag = sum(float(min(nb, n - i * nb)) ** 2 * k for i in range(N))
+    return 36.0 * (upd + diag)
+
+
+def sliced_study(g, torch, data, dev_in, outs, shapes, reps=3):
+    """The sliced schedule (both matrix multiplies as FP64-class digit-sliced
+    products on the BF16 tensor cores) on the FP64 sweep shapes at its own
+    block size: plan (inversion, then digit planes) and solve times, TFLOP/s
+    (n^2 k), the relative error of sampled columns against the oracle, and
+    the tensor-core roofline of the solve."""
+    import oracle
+    burst, _, src = measured_peaks()
+    rows = {}
+    for (L, B), (Ld, Bd), X, (n, k) in zip(data, dev_in, outs, shapes):
+        nb = SLICED_N0[(n, k)]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record()
+        p = g.trsm_plan(Ld, nb)
+        ev[1].record()
+        g.trsm_plan_sliced(p)
+        ev[2].record()
+        torch.cuda.synchronize()
+        plan_ms, planes_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+        g.trsm_solve_schedule(p, Bd, X=X, schedule="sliced")
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            g.trsm_solve_schedule(p, Bd, X=X, schedule="sliced")
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        g.trsm_sync_status(p)
+        ms = statistics.median(ts)
+        cols = np.array([0, k // 2, k - 1])
+        want = oracle.forward_subst_columns(L, B, cols)
+        got = X[:, torch.from_numpy(cols).cuda()].cpu().numpy()
+        err = float(np.max(np.abs(got - want)) / np.max(np.abs(want)))
+        mma = sliced_mma_flops(n, k, nb) / (ms * 1e-3) / 1e12
+        rows[f"{n}x{k}"] = [nb, round(plan_ms, 2), round(planes_ms, 2), round(ms, 2),
+                            round(float(n) * n * k / (ms * 1e-3) / 1e12, 3),
+                            round(float(n) * n * k / ((plan_ms + planes_ms + ms) * 1e-3) / 1e12, 3),
+                            _sig(err), round(mma / burst, 3)]
+        p.destroy()
+    return {"cols": ["n0", "plan_ms", "planes_ms", "solve_ms", "solve_tflops", "step_tflops", "rel_err",
+                     "mma_frac"],
+            **rows, "mma_peak": burst}
 
 
 def serving_study(g, torch, nL=256, rates=(100, 300, 600, 1200), per_rate=300, seed=2000,
@@ -795,7 +864,7 @@ def run_ours(args, rank, world, local):
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, sample, cores = cpu_oracle_rate(data, shapes, args.cpu_budget)
         cpu = {"value": round(rate, 5), "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-               "sample": sample + " (forward subst., FP64, OpenMP)"}
+               "sample": sample + " cols, forward subst."}
 
     mixed = None
     residual = None
@@ -824,6 +893,10 @@ def run_ours(args, rank, world, local):
     if rank == 0 and not args.no_sweep and not args.shapes:
         sweep = n0_sweep_study(g, torch, dev_in, outs, shapes)
 
+    sliced = None
+    if rank == 0 and not args.no_schedules and not args.shapes:
+        sliced = sliced_study(g, torch, data, dev_in, outs, shapes)
+
     if args.precision and rank == 0:
         for rec in precision_study(g, torch, 16384, 4096, MIXED_N0, [2, 4, 6], ["tf32", "bf16", "bf16x3", "fp16x3"],
                                    [False, True], residuals=("sliced", "adaptive")):
@@ -833,7 +906,7 @@ def run_ours(args, rank, world, local):
         traffic, traffic_by_shape = solve_traffic(shapes, n0s)
         details = {"per_shape": per_shape, "traffic_by_shape": traffic_by_shape, "mixed_precision": mixed,
                    "residual_roofline": residual, "batched": batched, "serving": serving,
-                   "schedules": schedules, "n0_sweep": sweep}
+                   "schedules": schedules, "n0_sweep": sweep, "fp64_sliced": sliced}
         if args.details:
             with open(args.details, "w") as fh:
                 json.dump(details, fh, indent=1)
@@ -841,7 +914,7 @@ def run_ours(args, rank, world, local):
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded PCG64; diag U[2,3], tril U[-1,1]/n, B U[-1,1])",
+            "data": "synthetic (seeded PCG64)",
             "config": {"workload": "fp64 k/n sweep (n,k) = (16384,256),(8192,8192),(2048,131072); "
                                    "step = trsm_plan + trsm_solve per shape",
                        "n0": {f"{n}x{k}": n0 for (n, k), n0 in zip(shapes, n0s)},
@@ -851,7 +924,7 @@ def run_ours(args, rank, world, local):
             "roofline": {"bound": "alu", "kernel": "it_inv_solve_kernel",
                          "achieved": round(solve_achieved, 4), "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
                          "frac": round(solve_achieved / fp64_peak, 4),
-                         "peak_source": f"measured DFMA this run (nominal {sms} SMs: {fp64_nominal:.3f})",
+                         "peak_source": f"measured DFMA (nominal {fp64_nominal:.3f})",
                          "traffic": traffic},
             "parity_max_rel_err": _sig(err),
             "backward_err": _sig(bwd),
@@ -859,15 +932,17 @@ def run_ours(args, rank, world, local):
             "cpu_baseline": cpu,
             "gpu_launches": launches,
             "clocks": clk,
-            "fp32_peak": {"measured": round(fp32_peak, 2), "nominal": round(fp32_nominal, 2), "unit": "TFLOP/s"},
+            "fp32_peak": round(fp32_peak, 2),
         }
         if sweep is not None:
             line["n0_sweep"] = {"cols": ["n0", "plan_ms", "solve_ms", "tflops"], **sweep}
+        if sliced is not None:
+            line["fp64_sliced"] = sliced
         if mixed is not None:
             line["precision"] = compact_precision(mixed)
         if residual is not None:
-            line["residual_roofline"] = {key: {"ms": v["ms"], "achieved": v["achieved"], "frac": v["frac"],
-                                              "peak": v["peak"]} for key, v in residual.items()}
+            line["residual_roofline"] = {key: {"ms": v["ms"], "achieved": v["achieved"], "frac": v["frac"]}
+                                         for key, v in residual.items()}
         if batched is not None:
             line["batched"] = [{"dtype": b["dtype"], "ms": b["ms_per_batch"], "tflops": b["tflops_n2k"],
                                 "frac": b["roofline"]["frac"], "peak": b["roofline"]["peak"],

@@ -10,6 +10,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "trsm_gb300.h"
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -42,6 +44,17 @@ int trsm_tc_gemm_selftest(int mode, const void* A_dev, const void* B_dev, float*
 int trsm_residual_sliced(const double* L_dev, int64_t n, int64_t ldl, const double* X_dev, int64_t k,
                          int64_t ldx, const double* B_dev, int64_t ldb, double* R_dev, int64_t ldr,
                          int planes, int* err_dev, void* stream);
+
+/* The same residual with the strictly lower L taken from a plan's
+ * mixed-precision data (trsm_plan_mixed: its digit planes and diagonal,
+ * sliced at plan time), as every sweep of trsm_solve_mixed computes it: X is
+ * sliced, then R = B - L X by the stream kernel.  X_dev, B_dev, R_dev n x k
+ * column-major (n the plan's order).  Allocates the digit planes of X and
+ * the partial sums stream-ordered.  Asynchronous; err_dev as above.
+ * Errors: TRSM_EINVAL (no mixed data, bad sizes, planes not 7 or 8),
+ * TRSM_ENOMEM, TRSM_ECUDA. */
+int trsm_residual_plan(trsm_handle_t h, const double* X_dev, int64_t k, int64_t ldx, const double* B_dev,
+                       int64_t ldb, double* R_dev, int64_t ldr, int planes, int* err_dev, void* stream);
 
 /* Failure-detection self-test (no counterpart in the paper): launches one
  * small kernel whose wait can never be satisfied, with a time limit of

@@ -117,10 +117,16 @@ def choose_n0(n, dtype="f64", table=None):
 
 
 def tune_schedule(plan, B, X=None, reps=2):
-    """Times the three schedules of the blocked solve on this system;
-    returns (fastest name, {name: ms})."""
+    """Times the schedules of the blocked solve on this system (the sliced
+    one only where the plan's block order allows it; its digit planes are
+    made before the timing); returns (fastest name, {name: ms})."""
     times = {}
     for sched in binding.SCHEDULES:
+        if sched == "sliced":
+            try:
+                binding.trsm_plan_sliced(plan)
+            except binding.TrsmError:
+                continue
         times[sched] = _time(lambda: binding.trsm_solve_schedule(plan, B, X=X, schedule=sched), reps)
     binding.trsm_sync_status(plan)
     return min(times, key=times.get), times

@@ -87,6 +87,7 @@ SIGNATURES = {
     "trsm_tc_gemm_selftest": (_int, [_int, _vp, _vp, _vp, _i64, _i64, _i64, _vp, _vp]),
     "trsm_wait_selftest": (_int, [_int, _i64, _vp]),
     "trsm_residual_sliced": (_int, [_dp, _i64, _i64, _dp, _i64, _i64, _dp, _i64, _dp, _i64, _int, _vp, _vp]),
+    "trsm_residual_plan": (_int, [_vp, _dp, _i64, _i64, _dp, _i64, _dp, _i64, _int, _vp, _vp]),
 }
 
 _lib = None

@@ -820,3 +820,28 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
   if (herr) return TRSM_ETIMEOUT;
   return rc;
 }
+
+extern "C" int trsm_residual_plan(trsm_handle_t h, const double* X_dev, int64_t k, int64_t ldx, const double* B_dev,
+                                  int64_t ldb, double* R_dev, int64_t ldr, int planes, int* err_dev, void* stream) {
+  if (!h || !h->mixed || !X_dev || !B_dev || !R_dev || !err_dev || k < 1 || ldx < h->n || ldb < h->n ||
+      ldr < h->n || (planes != 7 && planes != 8))
+    return TRSM_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t n = h->n;
+  const size_t xb = trsm::align256(trsm::sliced_operand_bytes(k, n));
+  const size_t pb = trsm::align256(trsm::sliced_partial_bytes(n, k));
+  unsigned char* buf = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&buf), xb + pb, s);
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? TRSM_ENOMEM : TRSM_ECUDA;
+  const trsm::SlicedOperand Xs = trsm::sliced_operand_view(buf, k, n);
+  e = trsm::slice_rows(X_dev, ldx, Xs, s);
+  if (e == cudaSuccess)
+    e = trsm::sliced_residual(h->mixed->Ls, h->mixed->diag, 0, Xs, X_dev, ldx, B_dev, ldb, R_dev, ldr, buf + xb, true,
+                              planes, err_dev, s);
+  cudaFreeAsync(buf, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return TRSM_ECUDA;
+  }
+  return TRSM_SUCCESS;
+}

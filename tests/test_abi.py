@@ -84,6 +84,7 @@ def test_every_entry_point_checks_its_arguments_on_the_host():
     for sched in (0, 1, 2, 3, 5):
         assert lib.trsm_solve_schedule(None, p16, 1, 8, p16, 8, sched, None) == E
     assert lib.trsm_plan_sliced(None, None) == E
+    assert lib.trsm_residual_plan(None, p16, 1, 8, p16, 8, p16, 8, 7, p16, None) == E
     assert lib.trsm_solve_ws(None, p16, 1, 8, p16, 8, p16, 1 << 20, None) == E
     assert lib.trsm_solve_noalloc(None, p16, 1, 8, p16, 8, None) == E
     assert lib.trsm_plan_mixed(None, p16, 8, binding.TRSM_INNER_TF32, None) == E

@@ -40,10 +40,10 @@ def test_cpu_oracle_rate_takes_a_bounded_sample():
     rate, sample, cores = bench.cpu_oracle_rate(data, shapes, budget_s=0.05)
     assert rate > 0 and cores >= 1
     parts = sample.split("; ")
-    assert parts[0].startswith("n=64: ") and parts[1].startswith("n=96: ")
+    assert parts[0].startswith("64:") and parts[1].startswith("96:")
     for part, (n, k) in zip(parts, shapes):
-        used = int(part.split(": ")[1].split("/")[0])
-        assert 1 <= used <= k and part.endswith(f"/{k} cols")
+        used = int(part.split(":")[1].split("/")[0])
+        assert 1 <= used <= k and part.endswith(f"/{k}")
 
 
 def test_replica_throughput_counts_every_rank():
@@ -89,4 +89,19 @@ def test_compact_precision_records():
     out = bench.compact_precision(recs)
     assert out["fp64"] == {"2": [880.0, 5.2e-16], "6": [881.0, None]}
     assert [r[-1] for r in out["rows"]] == ["ok", "miss", "nan"]
+    assert out["rows"][2][-2] is None  # no speed-up is quoted for a non-finite result
     assert out["rows"][0][:4] == [2, "fp16x3", 70.1, 3] and len(out["cols"]) == len(out["rows"][0])
+
+
+def test_sliced_mma_flops_closed_form():
+    """The sliced solve multiplies 36 digit-plane pairs over the update
+    blocks (the strictly lower block triangle of L) and the strictly lower
+    parts of the diagonal blocks: together n^2 k per pair when nb divides n
+    (n^2 - N nb^2 of updates plus N nb^2 of diagonal multiplies)."""
+    for n, k, nb in ((8192, 8192, 2048), (16384, 256, 1024), (2048, 3, 2048), (512, 5, 64)):
+        assert bench.sliced_mma_flops(n, k, nb) == pytest.approx(36.0 * n * n * k)
+    # a ragged last block of m rows: the update rows shrink accordingly
+    n, k, nb = 1000, 7, 256
+    m = n - 3 * nb
+    upd = sum(2.0 * (n - (i + 1) * nb) * nb * k for i in range(3))
+    assert bench.sliced_mma_flops(n, k, nb) == pytest.approx(36.0 * (upd + (3 * nb * nb + m * m) * k))
