@@ -220,7 +220,7 @@ def cpu_oracle_rate(data, shapes, budget_s, max_cols=None):
 
 
 def precision_study(g, torch, n, k, n0, cs, inners, s_modes, dd_cols=4, stream=None, quick=False,
-                    residuals=("sliced",)):
+                    residuals=("sliced",), combos=None, with_sliced=False):
     """Mixed-precision refinement on the graded-diagonal workload (diagonal
     geomspace(1, 10^-c), permuted): time, iterations, forward error against
     the double-double oracle and backward error ||B - L X|| / (||L|| ||X||)
@@ -268,32 +268,59 @@ def precision_study(g, torch, n, k, n0, cs, inners, s_modes, dd_cols=4, stream=N
         rec = {"c": c, "n": n, "k": k, "n0": n0, "fp64_solve_ms": round(t64, 2),
                "fp64_fwd_err": ferr(X64), "fp64_bwd_err": berr(X64), "dd_reference_finite": ref_ok,
                "sampled_columns": [int(v) for v in cols], "mixed": []}
-        for inner in inners:
-            g.trsm_plan_mixed(plan, Ld, inner)
-            for s32, res in ((a, b) for a in s_modes for b in residuals):
-                def solve(X=None):
-                    try:
-                        X, it, upd = g.trsm_solve_mixed(plan, Bd, X=X, residual=res, max_iter=30, tol=1e-12,
-                                                        raise_on_noconv=False, s_fp32=s32)
-                        return X, it, upd, 0
-                    except binding.TrsmError as e:  # e.g. a non-finite working copy
-                        return X, None, None, e.code
-                X, it, upd, rc = solve()
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                X, it, upd, rc = solve(X)
-                torch.cuda.synchronize()
-                tm = (time.perf_counter() - t0) * 1e3
-                fe = ferr(X) if X is not None else None
-                converged = bool(fe is not None and fe <= 1e-10)
-                status = "ok" if converged else ("non-finite" if fe is None else "target missed")
-                rec["mixed"].append({"inner": inner, "s_step": "fp32" if s32 else "fp64",
-                                     "residual": res, "ms": round(tm, 2),
-                                     "tflops_equiv": round(float(n) * n * k / (tm * 1e-3) / 1e12, 3),
-                                     "iterations": it, "last_update": upd, "fwd_err": fe,
-                                     "bwd_err": berr(X) if X is not None else None,
-                                     "converged": converged, "status": status, "rc": rc,
-                                     "speedup_vs_fp64": round(t64 / tm, 3)})
+        # (inner format, diagonal-multiply mode, residual) triples: a given
+        # list, or every inner x s_mode x residual
+        runs = combos or [(i, sm, r) for i in inners for sm in s_modes for r in residuals]
+        cur = None
+        for inner, smode, res in runs:
+            if inner != cur:
+                g.trsm_plan_mixed(plan, Ld, inner)
+                cur = inner
+            s32 = smode in (True, "fp32")
+            stc = smode == "tc"
+            def solve(X=None):
+                try:
+                    X, it, upd = g.trsm_solve_mixed(plan, Bd, X=X, residual=res, max_iter=30, tol=1e-12,
+                                                    raise_on_noconv=False, s_fp32=s32, s_tc=stc)
+                    return X, it, upd, 0
+                except binding.TrsmError as e:  # e.g. a non-finite working copy
+                    return X, None, None, e.code
+            X, it, upd, rc = solve()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            X, it, upd, rc = solve(X)
+            torch.cuda.synchronize()
+            tm = (time.perf_counter() - t0) * 1e3
+            fe = ferr(X) if X is not None else None
+            converged = bool(fe is not None and fe <= 1e-10)
+            status = "ok" if converged else ("non-finite" if fe is None else "target missed")
+            rec["mixed"].append({"inner": inner, "s_step": "tc" if stc else "fp32" if s32 else "fp64",
+                                 "residual": res, "ms": round(tm, 2),
+                                 "tflops_equiv": round(float(n) * n * k / (tm * 1e-3) / 1e12, 3),
+                                 "iterations": it, "last_update": upd, "fwd_err": fe,
+                                 "bwd_err": berr(X) if X is not None else None,
+                                 "converged": converged, "status": status, "rc": rc,
+                                 "speedup_vs_fp64": round(t64 / tm, 3)})
+        if with_sliced:
+            # the sliced schedule: FP64-class products, one pass, no refinement
+            g.trsm_plan_sliced(plan)
+            X = g.trsm_solve_schedule(plan, Bd, schedule="sliced")
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            X = g.trsm_solve_schedule(plan, Bd, X=X, schedule="sliced")
+            e1.record()
+            torch.cuda.synchronize()
+            g.trsm_sync_status(plan)
+            tm = e0.elapsed_time(e1)
+            fe = ferr(X)
+            rec["mixed"].append({"inner": "sliced", "s_step": "sliced", "residual": None, "ms": round(tm, 2),
+                                 "tflops_equiv": round(float(n) * n * k / (tm * 1e-3) / 1e12, 3),
+                                 "iterations": 1, "last_update": None, "fwd_err": fe, "bwd_err": berr(X),
+                                 "converged": bool(fe is not None and fe <= 1e-10),
+                                 "status": "ok" if fe is not None and fe <= 1e-10 else (
+                                     "non-finite" if fe is None else "target missed"), "rc": 0,
+                                 "speedup_vs_fp64": round(t64 / tm, 3)})
         plan.destroy()
         del Ld, Bd, X64
         out.append(rec)
@@ -311,9 +338,10 @@ def compact_precision(recs):
     for rec in recs:
         for m in rec["mixed"]:
             st = "ok" if m["converged"] else ("nan" if m["fwd_err"] is None else "miss")
-            rows.append([rec["c"], m["inner"], m["ms"], m["iterations"], _sig(m["fwd_err"]), _sig(m["bwd_err"]),
-                         None if st == "nan" else m["speedup_vs_fp64"], st])
-    return {"fp64": fp64, "cols": ["c", "inner", "ms", "sweeps", "fwd", "bwd", "x_fp64", "status"], "rows": rows}
+            rows.append([rec["c"], m["inner"], m["s_step"], m["ms"], m["iterations"], _sig(m["fwd_err"]),
+                         _sig(m["bwd_err"]), None if st == "nan" else m["speedup_vs_fp64"], st])
+    return {"fp64": fp64, "cols": ["c", "inner", "s", "ms", "sweeps", "fwd", "bwd", "x_fp64", "status"],
+            "rows": rows}
 
 
 def _sig(v, digits=3):
@@ -871,11 +899,13 @@ def run_ours(args, rank, world, local):
     if rank == 0 and not args.no_mixed and not args.shapes:
         residual = residual_roofline(g, torch)
     if rank == 0 and not args.no_mixed and not args.shapes:
-        # config 2 at c = 2, 4, 6: split fp16 and tf32 updates, FP32
-        # diagonal multiplies, the adaptive residual, at the mixed path's
-        # block size
-        mixed = precision_study(g, torch, 16384, 4096, MIXED_N0, [2, 4, 6], ["fp16x3", "tf32"], [True],
-                                residuals=("adaptive",))
+        # config 2 at c = 2, 4, 6 at the mixed path's block size: refined
+        # solves (split-fp16 updates with FP32 diagonal multiplies, tf32
+        # updates with tensor-core ones; the adaptive residual), and the
+        # sliced schedule's direct FP64-class solve
+        mixed = precision_study(g, torch, 16384, 4096, MIXED_N0, [2, 4, 6], None, None,
+                                combos=[("fp16x3", "fp32", "adaptive"), ("tf32", "tc", "adaptive")],
+                                with_sliced=True)
 
     batched = None
     if rank == 0 and not args.no_batched and not args.shapes:

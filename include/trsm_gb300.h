@@ -62,6 +62,11 @@ extern "C" {
 /* Flag or-ed into `residual`: apply the FP64 inverses of the diagonal blocks
  * in FP32 arithmetic inside the inner solve (default: FP64 arithmetic). */
 #define TRSM_SOLVE_S_FP32 0x100
+/* Flag or-ed into `residual` (not with TRSM_SOLVE_S_FP32): apply them on the
+ * tensor cores: the inverse and W_i are each cut into three tf32 planes and
+ * the six plane products of weight 2^-22 and above are summed in FP32
+ * (FP32-class, about 2^-24 per product). */
+#define TRSM_SOLVE_S_TC 0x200
 
 /* Opaque plan: the paper's L~ (Algorithm Diagonal-Inverter, Section 6.1) —
  * a device copy of L whose n0 x n0 diagonal blocks are replaced by their
@@ -184,7 +189,8 @@ int trsm_solve_noalloc(trsm_handle_t h, const double* B_dev, int64_t k, int64_t 
  *     TRSM_INNER_FP16X3), for the tensor-core updates;
  *   - the original diagonal blocks and diagonal of L in FP64;
  *   - FP32 copies of the plan's inverted diagonal blocks L~_ii (n x n0
- *     floats), for the FP32 diagonal-block multiply;
+ *     floats), for the FP32 diagonal-block multiply, and three tf32 planes
+ *     of them (3 n x n0 floats), for the tensor-core one;
  *   - eight 6-bit integer digit planes of the strictly lower L, for the
  *     FP64-class residual.
  *   L_dev : the same matrix the plan was made from (n x n, ldl >= n).
@@ -202,7 +208,8 @@ int trsm_plan_mixed(trsm_handle_t h, const double* L_dev, int64_t ldl, int inner
  * inner precision with FP32 accumulation (W is the FP32 copy of R).
  *   residual : TRSM_RESIDUAL_SLICED, _SLICED8, _ADAPTIVE or _FP64 (the
  *              latter needs n0 a multiple of 32 when there is more than one
- *              block), optionally or-ed with TRSM_SOLVE_S_FP32.  The
+ *              block), optionally or-ed with TRSM_SOLVE_S_FP32 or
+ *              TRSM_SOLVE_S_TC.  The
  *              residual's accuracy sets the attainable error: about
  *              cond * 2^-43 (SLICED), cond * 2^-49 (SLICED8), cond * 2^-53
  *              (FP64), with cond the componentwise condition of the system

@@ -34,6 +34,7 @@ TRSM_RESIDUAL_FP64 = 1
 TRSM_RESIDUAL_SLICED8 = 2
 TRSM_RESIDUAL_ADAPTIVE = 3
 TRSM_SOLVE_S_FP32 = 0x100
+TRSM_SOLVE_S_TC = 0x200
 
 TRSM_F64 = 0
 TRSM_F32 = 1
@@ -269,9 +270,10 @@ def trsm_plan_mixed(plan, L, inner="tf32"):
 
 
 def trsm_solve_mixed(plan, B, X=None, residual="sliced", max_iter=30, tol=1e-14, raise_on_noconv=True,
-                     s_fp32=False):
-    """Iterative refinement around the low-precision solve.  Returns
-    (X, iterations, last max|D|/max|X|)."""
+                     s_fp32=False, s_tc=False):
+    """Iterative refinement around the low-precision solve (s_fp32: the
+    diagonal multiplies in FP32; s_tc: on the tensor cores as split-tf32
+    products).  Returns (X, iterations, last max|D|/max|X|)."""
     torch = _torch()
     B = _dev_matrix(B, "B")
     n, k = B.shape
@@ -285,6 +287,8 @@ def trsm_solve_mixed(plan, B, X=None, residual="sliced", max_iter=30, tol=1e-14,
             "adaptive": TRSM_RESIDUAL_ADAPTIVE}[residual]
     if s_fp32:
         code |= TRSM_SOLVE_S_FP32
+    if s_tc:
+        code |= TRSM_SOLVE_S_TC
     rc = load_library().trsm_solve_mixed(plan.handle, ctypes.c_void_p(B.data_ptr()), k, _ld(B),
                                          ctypes.c_void_p(X.data_ptr()), _ld(X), code, int(max_iter),
                                          float(tol), ctypes.byref(it), ctypes.byref(upd), _stream(B))

@@ -54,6 +54,8 @@ struct MixedPlan {
   SlicedOperand Ls;
   int* panel_exp = nullptr; // split fp16: panel i is stored times 2^panel_exp[i]
   float* dinv32 = nullptr;  // FP32 copies of the inverted diagonal blocks L~_ii, N x n0 x n0 (ld n0)
+  float* dinv_tc = nullptr; // tf32 hi / mid / lo planes of the inverted blocks, K-major: block b at
+                            // b * 3 n0 n0p, plane stride n0 n0p, row stride n0p (tensor-core multiply)
   size_t bytes = 0;         // device bytes held by the fields above
 };
 
@@ -68,6 +70,7 @@ void mixed_release(trsm_plan_s* h) {
   if (mp->lsl) cudaFree(mp->lsl);
   if (mp->panel_exp) cudaFree(mp->panel_exp);
   if (mp->dinv32) cudaFree(mp->dinv32);
+  if (mp->dinv_tc) cudaFree(mp->dinv_tc);
   delete mp;
   h->mixed = nullptr;
 }
@@ -254,6 +257,67 @@ __global__ void pack_panels_kernel(const double* __restrict__ L, int64_t ldl, in
     const double v = (c < n0) ? L[(i * n0 + c) * ldl + (i + 1) * n0 + r] : 0.0;
     LowP<kMode>::put(P + e, total, v);
   }
+}
+
+__device__ __forceinline__ float to_tf32(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return __uint_as_float(r);
+}
+
+// tf32 planes of the inverted diagonal blocks for the tensor-core diagonal
+// multiply: row r of block b holds L~_bb(r, t) for t < n0p (zeros past the
+// block and above its diagonal), hi = tf32(v), mid = tf32(v - hi), lo =
+// tf32(v - hi - mid) with v the FP64 entry (plan time).
+__global__ void pack_inv_tf32_kernel(const double* __restrict__ Lt, int64_t ldt, int64_t n, int64_t n0, int64_t n0p,
+                                     float* __restrict__ out) {
+  const int64_t b = blockIdx.y, s0 = b * n0;
+  const int64_t m = imin64(n0, n - s0);
+  const int64_t total = n0 * n0p;
+  float* o = out + b * 3 * total;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = e / n0p, t = e % n0p;
+    double v = (r < m && t <= r) ? Lt[(s0 + t) * ldt + s0 + r] : 0.0;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float p = to_tf32(static_cast<float>(v));
+      o[q * total + e] = p;
+      v -= static_cast<double>(p);
+    }
+  }
+}
+
+// W_i (FP32, rows s0 .. s0 + m of W) into three tf32 planes, K-major: row j
+// of a plane holds column j of W_i (zeros from m to n0p); hi = tf32(w),
+// mid = tf32(w - hi), lo = w - hi - mid (every difference exact in FP32, and
+// the three planes hold all 24 bits of w).  Rows on threadIdx.x.
+__global__ void pack_w_tf32_kernel(const float* __restrict__ W, int64_t ldw, int64_t s0, int m, int64_t k,
+                                   int64_t n0p, float* __restrict__ Wt) {
+  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t >= n0p) return;
+  const int64_t plane = k * n0p;
+  for (int64_t j = blockIdx.y; j < k; j += gridDim.y) {
+    float w = (t < m) ? W[j * ldw + s0 + t] : 0.f;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float p = to_tf32(w);
+      Wt[q * plane + j * n0p + t] = p;
+      w -= p;
+    }
+  }
+}
+
+// D_i (FP64) into the low-precision B operand of the update (bf16, tf32 or
+// split bf16; split fp16 takes pack_dt_f16_kernel): the tensor-core
+// diagonal multiply writes D alone.
+template <int kMode>
+__global__ void pack_dt_kernel(const double* __restrict__ D, int64_t ldd, int64_t s0, int m, int64_t k, int64_t n0p,
+                               typename LowP<kMode>::T* __restrict__ Dt) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= m) return;
+  for (int64_t col = blockIdx.y; col < k; col += gridDim.y)
+    LowP<kMode>::put(Dt + col * n0p + row, k * n0p, static_cast<float>(D[col * ldd + s0 + row]));
 }
 
 // FP32 copies of the inverted diagonal blocks of L~ (the FP32 diagonal
@@ -628,6 +692,16 @@ extern "C" int trsm_plan_mixed(trsm_handle_t h, const double* L_dev, int64_t ldl
     trsm::count_launch();
     e = cudaGetLastError();
   }
+  const size_t tc_bytes = sizeof(float) * 3 * static_cast<size_t>(N) * n0 * mp->n0p;
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&mp->dinv_tc), tc_bytes);
+  if (e == cudaSuccess) {
+    mp->bytes += tc_bytes;
+    const unsigned gx = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((n0 * mp->n0p + 255) / 256, 1024)));
+    trsm::pack_inv_tf32_kernel<<<dim3(gx, static_cast<unsigned>(N)), 256, 0, s>>>(h->Lt, h->ldt, n, n0, mp->n0p,
+                                                                                   mp->dinv_tc);
+    trsm::count_launch();
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) {
     mp->Ls = trsm::sliced_operand_view(mp->lsl, n, n);
     e = trsm::slice_lower_rows(L_dev, ldl, n, mp->Ls, tmp, s);
@@ -649,7 +723,9 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
   if (last_update) *last_update = 0.0;
   if (!h || !h->mixed || k < 0 || max_iter < 1 || !(tol >= 0.0)) return TRSM_EINVAL;
   const bool s32 = (residual & TRSM_SOLVE_S_FP32) != 0;
-  residual &= ~TRSM_SOLVE_S_FP32;
+  const bool stc = (residual & TRSM_SOLVE_S_TC) != 0;
+  residual &= ~(TRSM_SOLVE_S_FP32 | TRSM_SOLVE_S_TC);
+  if (s32 && stc) return TRSM_EINVAL;
   if (residual != TRSM_RESIDUAL_SLICED && residual != TRSM_RESIDUAL_FP64 && residual != TRSM_RESIDUAL_SLICED8 &&
       residual != TRSM_RESIDUAL_ADAPTIVE)
     return TRSM_EINVAL;
@@ -683,6 +759,8 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
   off = trsm::align256(off + sizeof(unsigned long long) * N);
   const size_t oGscale = off;
   off = trsm::align256(off + sizeof(float) * N);
+  const size_t oWt = off;  // tf32 planes of W_i (tensor-core diagonal multiply)
+  if (stc) off = trsm::align256(off + sizeof(float) * 3 * static_cast<size_t>(k) * n0p);
   unsigned char* ws = nullptr;
   cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), off, s);
   if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? TRSM_ENOMEM : TRSM_ECUDA;
@@ -695,6 +773,7 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
   int* err = reinterpret_cast<int*>(ws + oNorm + 2 * sizeof(unsigned long long));
   unsigned long long* dmax = reinterpret_cast<unsigned long long*>(ws + oDmax);
   float* gscale = reinterpret_cast<float*>(ws + oGscale);
+  float* Wt = reinterpret_cast<float*>(ws + oWt);
 
   int rc = TRSM_SUCCESS;
   e = cudaMemsetAsync(err, 0, sizeof(int), s);
@@ -719,14 +798,42 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
       dim3 g(static_cast<unsigned>((R + 1) / 2), static_cast<unsigned>((k + trsm::TILE - 1) / trsm::TILE));
       unsigned long long* dmax_i = dmax + i;
       const float* Lf = mp->dinv32 + s0 * n0;  // block i of the FP32 copies
-      switch (mode) {
-        case 1: trsm::launch_s_step<1>(s32, h->Lt, h->ldt, Lf, n0, W, ld, D, Dt, n0p, s0, m, k, dmax_i, s); break;
-        case 2: trsm::launch_s_step<2>(s32, h->Lt, h->ldt, Lf, n0, W, ld, D, Dt, n0p, s0, m, k, dmax_i, s); break;
-        case 3: trsm::launch_s_step<3>(s32, h->Lt, h->ldt, Lf, n0, W, ld, D, Dt, n0p, s0, m, k, dmax_i, s); break;
-        default: trsm::launch_s_step<0>(s32, h->Lt, h->ldt, Lf, n0, W, ld, D, Dt, n0p, s0, m, k, dmax_i, s); break;
+      if (stc) {
+        // D_i = L~_ii W_i on the tensor cores (split tf32), D_i in FP64 and
+        // max |D_i| from the epilogue; then D_i into the update's operand
+        const dim3 gw(static_cast<unsigned>((n0p + 255) / 256),
+                      static_cast<unsigned>(std::min<int64_t>(k, std::max<int64_t>(1, 4864 / ((n0p + 255) / 256)))));
+        trsm::pack_w_tf32_kernel<<<gw, 256, 0, s>>>(W, ld, s0, m, k, n0p, Wt);
+        trsm::count_launch();
+        e = cudaGetLastError();
+        if (e == cudaSuccess)
+          e = trsm::tc::gemm_split_tf32_tri(mp->dinv_tc + i * 3 * n0 * n0p, n0p, n0 * n0p, Wt, n0p, k * n0p, D + s0, ld,
+                                            m, k, m, dmax_i, err, s);
+        if (e == cudaSuccess && mode != 3 && i < N - 1) {
+          const dim3 gp(static_cast<unsigned>((m + 255) / 256),
+                        static_cast<unsigned>(std::min<int64_t>(k, std::max<int64_t>(1, 2432 / ((m + 255) / 256)))));
+          switch (mode) {
+            case 1: trsm::pack_dt_kernel<1><<<gp, 256, 0, s>>>(D, ld, s0, m, k, n0p, static_cast<float*>(Dt)); break;
+            case 2:
+              trsm::pack_dt_kernel<2><<<gp, 256, 0, s>>>(D, ld, s0, m, k, n0p, static_cast<__nv_bfloat16*>(Dt));
+              break;
+            default:
+              trsm::pack_dt_kernel<0><<<gp, 256, 0, s>>>(D, ld, s0, m, k, n0p, static_cast<__nv_bfloat16*>(Dt));
+              break;
+          }
+          trsm::count_launch();
+          e = cudaGetLastError();
+        }
+      } else {
+        switch (mode) {
+          case 1: trsm::launch_s_step<1>(s32, h->Lt, h->ldt, Lf, n0, W, ld, D, Dt, n0p, s0, m, k, dmax_i, s); break;
+          case 2: trsm::launch_s_step<2>(s32, h->Lt, h->ldt, Lf, n0, W, ld, D, Dt, n0p, s0, m, k, dmax_i, s); break;
+          case 3: trsm::launch_s_step<3>(s32, h->Lt, h->ldt, Lf, n0, W, ld, D, Dt, n0p, s0, m, k, dmax_i, s); break;
+          default: trsm::launch_s_step<0>(s32, h->Lt, h->ldt, Lf, n0, W, ld, D, Dt, n0p, s0, m, k, dmax_i, s); break;
+        }
+        trsm::count_launch();
+        e = cudaGetLastError();
       }
-      trsm::count_launch();
-      e = cudaGetLastError();
       if (e == cudaSuccess && i < N - 1) {
         const int64_t rows = n - (i + 1) * n0;
         const unsigned char* P =

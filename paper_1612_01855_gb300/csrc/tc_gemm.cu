@@ -103,6 +103,62 @@ struct StoreF32Epi {
   __device__ void finish(State&, int, int, int, int) const {}
 };
 
+// D (FP64, column-major, ldd) = A B^T with a single FP32 group (the
+// diagonal multiply of the mixed solve), and max |D| folded into *dmax as
+// the ordered bit pattern of a non-negative double (a NaN as the largest
+// pattern).  lower: A is lower triangular, row tile q's sums stop at
+// K = 128 (q + 1), the longest rows first.  Lanes hold consecutive rows, so
+// the stores of a warp are one 256-byte run per column.
+template <int BN, int KB>
+struct StoreF64MaxEpi {
+  double* D;
+  int64_t ldd;
+  int M, N, K;
+  int lower;
+  unsigned long long* dmax;
+  struct State {};
+  // Launch order -> tile: the row tiles from the last (longest sums) to the
+  // first, each over all its column tiles.
+  __device__ void tile(int& tm, int& tn) const {
+    if (!lower) return;
+    const int R = static_cast<int>(gridDim.x), C = static_cast<int>(gridDim.y);
+    const int lin = tm + R * tn;
+    tm = R - 1 - lin / C;
+    tn = lin % C;
+  }
+  __device__ void k_range(int tm, int, int& kb0, int& kb1, int& chunk) const {
+    const int kend = lower ? min(K, (tm + 1) * 128) : K;
+    kb0 = 0;
+    kb1 = (kend + KB - 1) / KB;
+    chunk = kb1 > 0 ? kb1 : 1;
+  }
+  __device__ void init(State&) const {}
+  __device__ void group(State&, int tm, int tn, int, int row, int sl, int, const float (&v)[16]) const {
+    const int r = tm * 128 + row;
+    const int c0 = tn * BN + sl * 16;
+    const int ncol = (r < M) ? min(16, N - c0) : 0;
+    double* base = D + static_cast<int64_t>(c0) * ldd + r;
+    unsigned long long mb = 0;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (j >= ncol) continue;
+      base[static_cast<int64_t>(j) * ldd] = static_cast<double>(v[j]);
+      const float a = fabsf(v[j]);
+      const unsigned long long b = (a != a) ? 0x7FF8000000000000ull
+                                            : static_cast<unsigned long long>(__double_as_longlong(static_cast<double>(a)));
+      mb = b > mb ? b : mb;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long b = __shfl_xor_sync(0xffffffffu, mb, o);
+      mb = b > mb ? b : mb;
+    }
+    if ((threadIdx.x & 31) == 0 && mb) atomicMax(dmax, mb);
+  }
+  __device__ void slab_done(State&, int, int, int, int, int) const {}
+  __device__ void finish(State&, int, int, int, int) const {}
+};
+
 template <bool kTf32, int BN, int STAGES>
 cudaError_t plain_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t M,
                        int64_t N, int64_t K, int64_t ldc, float alpha, float beta, int* err,
@@ -156,6 +212,36 @@ cudaError_t split_gemm(const void* A, int64_t lda, int64_t a_plane, const void* 
 }
 
 }  // namespace
+
+// Three tf32 planes per factor (hi, mid, lo: 11 + 11 + 11 bits), the six
+// products of weight 2^-22 and above: A B^T to about 2^-24, as in FP32.
+struct Split3Pairs {
+  static constexpr int N = 6;
+  __device__ static constexpr int a(int p) { return p == 0 || p == 1 || p == 3 ? 0 : p == 2 || p == 4 ? 1 : 2; }
+  __device__ static constexpr int b(int p) { return p == 0 || p == 2 || p == 5 ? 0 : p == 1 || p == 4 ? 1 : 2; }
+  __device__ static constexpr int g(int) { return 0; }
+};
+
+cudaError_t gemm_split_tf32_tri(const float* A, int64_t lda, int64_t a_plane, const float* B, int64_t ldb,
+                                int64_t b_plane, double* D, int64_t ldd, int64_t M, int64_t N, int64_t K,
+                                unsigned long long* dmax, int* err, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+  constexpr int BN = 128, STAGES = 2;
+  using Cfg = TileCfg<true, BN, 3, 3, 1, STAGES>;
+  using Epi = StoreF64MaxEpi<BN, Cfg::KB>;
+  CUtensorMap ma, mb;
+  if (!make_kmajor_map(&ma, A, true, K, M, lda, 3, a_plane, 128, 3, 128)) return cudaErrorInvalidValue;
+  if (!make_kmajor_map(&mb, B, true, K, N, ldb, 3, b_plane, BN, 3, 128)) return cudaErrorInvalidValue;
+  Epi epi{D, ldd, static_cast<int>(M), static_cast<int>(N), static_cast<int>(K), 1, dmax};
+  auto kern = tc_tile_kernel<Cfg, Split3Pairs, Epi>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(Cfg::SMEM_BYTES));
+  if (e != cudaSuccess) return e;
+  dim3 grid(static_cast<unsigned>((M + 127) / 128), static_cast<unsigned>((N + BN - 1) / BN));
+  kern<<<grid, 192, Cfg::SMEM_BYTES, s>>>(ma, mb, epi, err);
+  count_launch();
+  return cudaGetLastError();
+}
 
 cudaError_t gemm_split_bf16(const void* A, int64_t lda, int64_t a_plane, const void* B, int64_t ldb,
                             int64_t b_plane, float* C, int64_t ldc, int64_t M, int64_t N, int64_t K, float alpha,

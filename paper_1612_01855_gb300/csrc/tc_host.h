@@ -41,5 +41,17 @@ cudaError_t gemm_split_f16(const void* A, int64_t lda, int64_t a_plane, const vo
                            int64_t b_plane, float* C, int64_t ldc, int64_t M, int64_t N, int64_t K, float alpha,
                            const float* scale, float beta, int* err, cudaStream_t s);
 
+// D (FP64, column-major, ldd) = A B^T for the diagonal multiply of the
+// mixed solve: A (M x K, lower triangular) and B (N x K) are each three tf32
+// planes stored as fp32 (hi = tf32(v), mid = tf32(v - hi), lo = tf32(v - hi
+// - mid); K-major, row strides lda / ldb, planes a_plane / b_plane elements
+// apart), multiplied as the six plane pairs of weight 2^-22 and above with
+// FP32 accumulation (FP32-class, about 2^-24 per product); row tile q's sums
+// stop at K = 128 (q + 1).  max |D| is folded into *dmax (ordered bit
+// pattern of a non-negative double).  128 x 128 tiles, 2-stage TMA ring.
+cudaError_t gemm_split_tf32_tri(const float* A, int64_t lda, int64_t a_plane, const float* B, int64_t ldb,
+                                int64_t b_plane, double* D, int64_t ldd, int64_t M, int64_t N, int64_t K,
+                                unsigned long long* dmax, int* err, cudaStream_t s);
+
 }  // namespace tc
 }  // namespace trsm

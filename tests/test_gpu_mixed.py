@@ -19,46 +19,52 @@ def _rel(a, b):
 
 
 @pytest.mark.parametrize("inner", ["tf32", "bf16", "bf16x3", "fp16x3"])
-@pytest.mark.parametrize("residual,s32", [("sliced", False), ("fp64", False), ("sliced", True)])
+@pytest.mark.parametrize("residual,smode", [("sliced", "fp64"), ("fp64", "fp64"), ("sliced", "fp32"),
+                                            ("sliced", "tc")])
 @pytest.mark.parametrize("n,k,n0", [(1024, 64, 128), (1000, 37, 64), (300, 5, 300)])
-def test_mixed_well_conditioned(cuda_lib, inner, residual, s32, n, k, n0):
+def test_mixed_well_conditioned(cuda_lib, inner, residual, smode, n, k, n0):
+    """smode: the diagonal multiplies in FP64, in FP32, or on the tensor
+    cores (split tf32)."""
     import paper_1612_01855_gb300 as g
     L, B = inputs.well_conditioned(n, k, seed=n + k)
     Ld = _dev(L)
     plan = g.trsm_plan(Ld, n0)
     g.trsm_plan_mixed(plan, Ld, inner)
     X, iters, upd = g.trsm_solve_mixed(plan, _dev(B), residual=residual, max_iter=40, tol=1e-15,
-                                       raise_on_noconv=False, s_fp32=s32)
+                                       raise_on_noconv=False, s_fp32=smode == "fp32", s_tc=smode == "tc")
     got = X.cpu().numpy()
     want = oracle.forward_subst(L, B)
     err = _rel(got, want)
-    print(f"mixed {inner}/{residual} n={n} k={k} n0={n0}: {iters} iterations, last update {upd:.2e}, rel err {err:.2e}")
+    print(f"mixed {inner}/{residual}/{smode} n={n} k={k} n0={n0}: {iters} iterations, last update {upd:.2e}, "
+          f"rel err {err:.2e}")
     # the refinement's limit is the residual's accuracy: ~2^-40 of |L||X| (sliced), ~n eps (fp64)
     assert err < (5e-12 if residual == "sliced" else 1e-13)
     assert iters <= {"tf32": 12, "bf16": 25, "bf16x3": 6, "fp16x3": 6}[inner]
 
 
 @pytest.mark.parametrize("inner", ["tf32", "bf16x3", "fp16x3"])
+@pytest.mark.parametrize("smode", ["fp32", "tc"])
 @pytest.mark.parametrize("n,k,n0", [(1500, 70, 600), (2048, 33, 1024), (1100, 130, 512)])
-def test_mixed_wide_blocks_fp32_diagonal_multiply(cuda_lib, inner, n, k, n0):
+def test_mixed_wide_blocks_fp32_diagonal_multiply(cuda_lib, inner, smode, n, k, n0):
     """Blocks of 512 rows and more take the 64 x 64 register-blocked FP32
-    diagonal multiply (ragged last blocks the 32 x 32 tile)."""
+    diagonal multiply (ragged last blocks the 32 x 32 tile), or the
+    tensor-core one (several row tiles per block, ragged last blocks)."""
     import paper_1612_01855_gb300 as g
     L, B = inputs.well_conditioned(n, k, seed=n + 3 * k)
     Ld = _dev(L)
     plan = g.trsm_plan(Ld, n0)
     g.trsm_plan_mixed(plan, Ld, inner)
     X, iters, upd = g.trsm_solve_mixed(plan, _dev(B), residual="sliced", max_iter=40, tol=1e-15,
-                                       raise_on_noconv=False, s_fp32=True)
+                                       raise_on_noconv=False, s_fp32=smode == "fp32", s_tc=smode == "tc")
     err = _rel(X.cpu().numpy(), oracle.forward_subst(L, B))
-    print(f"mixed {inner}/s32 n={n} k={k} n0={n0}: {iters} iterations, rel err {err:.2e}")
+    print(f"mixed {inner}/{smode} n={n} k={k} n0={n0}: {iters} iterations, rel err {err:.2e}")
     assert err < 5e-12
     assert iters <= 12
 
 
 @pytest.mark.parametrize("inner", ["tf32", "bf16x3", "fp16x3"])
-@pytest.mark.parametrize("s32", [False, True])
-def test_mixed_power_of_two_scaling_is_exact(cuda_lib, inner, s32):
+@pytest.mark.parametrize("smode", ["fp64", "fp32", "tc"])
+def test_mixed_power_of_two_scaling_is_exact(cuda_lib, inner, smode):
     """Every scale in the refined solve (chunk exponents of the sliced
     residual, the fp16 panel and D_i scales, the FP32 inner solve) is a power
     of two, so solving with 2^s B gives 2^s X bit for bit while nothing leaves
@@ -72,7 +78,7 @@ def test_mixed_power_of_two_scaling_is_exact(cuda_lib, inner, s32):
     runs = {}
     for sc in (0, -60, 60):
         X, iters, upd = g.trsm_solve_mixed(plan, _dev(np.ldexp(B, sc)), residual="sliced", max_iter=40, tol=1e-13,
-                                           raise_on_noconv=False, s_fp32=s32)
+                                           raise_on_noconv=False, s_fp32=smode == "fp32", s_tc=smode == "tc")
         runs[sc] = (X.cpu().numpy(), iters)
     for sc in (-60, 60):
         assert runs[sc][1] == runs[0][1]
@@ -174,11 +180,13 @@ def test_mixed_argument_errors(cuda_lib):
 
 
 @pytest.mark.parametrize("c", [2, 4])
-def test_full_size_precision_config(cuda_lib, c):
+@pytest.mark.parametrize("smode", ["fp32", "tc"])
+def test_full_size_precision_config(cuda_lib, c, smode):
     """The precision configuration at its full size and in the bench's launch
     configuration: n = 16384, k = 4096, n0 = 1024, graded diagonal
     geomspace(1, 10^-c) permuted, split-fp16 updates, FP32 diagonal
-    multiplies, the adaptive residual (seven digit planes, then eight).  The
+    multiplies (FP32, or split tf32 on the tensor cores), the adaptive
+    residual (seven digit planes, then eight).  The
     forward error on a seeded sample of columns, against the double-double
     substitution of the same columns (columns of X are independent), stays
     within the 1e-10 target; the backward error of those columns is FP64
@@ -195,14 +203,15 @@ def test_full_size_precision_config(cuda_lib, c):
     del L
     plan = g.trsm_plan(Ld, n0)
     g.trsm_plan_mixed(plan, Ld, "fp16x3")
-    X, iters, upd = g.trsm_solve_mixed(plan, Bd, residual="adaptive", max_iter=30, tol=1e-12, s_fp32=True)
+    X, iters, upd = g.trsm_solve_mixed(plan, Bd, residual="adaptive", max_iter=30, tol=1e-12,
+                                       s_fp32=smode == "fp32", s_tc=smode == "tc")
     ci = torch.from_numpy(cols).cuda()
     got = X[:, ci].cpu().numpy()
     fwd = _rel(got, ref)
     Lt = torch.tril(Ld)
     Xs = X[:, ci]
     bwd = (Bd[:, ci] - Lt @ Xs).abs().max().item() / (Lt.abs().sum(dim=1).max().item() * Xs.abs().max().item())
-    print(f"precision config c={c}: {iters} sweeps, last update {upd:.2e}, forward error {fwd:.2e}, "
+    print(f"precision config c={c} {smode}: {iters} sweeps, last update {upd:.2e}, forward error {fwd:.2e}, "
           f"backward error {bwd:.2e}")
     assert fwd <= 1e-10
     assert bwd <= 1e-14
