@@ -159,12 +159,33 @@ __global__ void __launch_bounds__(NTHREADS) combine_second_kernel(double* __rest
   }
 }
 
+// Lt = the lower triangle of L.  VEC: both matrices' columns start on 16-byte
+// boundaries (aligned bases, even leading dimensions), and each thread moves
+// a pair of rows with one 16-byte load and store; the pair that straddles
+// the diagonal loads its lower element alone, and pairs above the diagonal
+// are written as zeros without reading L.
+template <bool VEC>
 __global__ void copy_lower_kernel(const double* __restrict__ L, int64_t ldl, double* __restrict__ Lt,
                                   int64_t ldt, int64_t n) {
   for (int64_t j = blockIdx.y; j < n; j += gridDim.y) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-      Lt[j * ldt + i] = (i >= j) ? L[j * ldl + i] : 0.0;
+    const double* src = L + j * ldl;
+    double* dst = Lt + j * ldt;
+    if constexpr (VEC) {
+      for (int64_t i = 2 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x); i < n;
+           i += 2 * (int64_t)gridDim.x * blockDim.x) {
+        if (i + 1 < n) {
+          double2 v = make_double2(0.0, 0.0);
+          if (i >= j) v = *reinterpret_cast<const double2*>(src + i);
+          else if (i + 1 == j) v.y = src[i + 1];
+          *reinterpret_cast<double2*>(dst + i) = v;
+        } else {
+          dst[i] = (i >= j) ? src[i] : 0.0;
+        }
+      }
+    } else {
+      for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+           i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (i >= j) ? src[i] : 0.0;
     }
   }
 }
@@ -185,14 +206,31 @@ __global__ void pack_blocks_kernel(const double* __restrict__ L, int64_t ldl, do
   }
 }
 
+// W = B (n x k).  VEC: 16-byte loads and stores of row pairs, as above.
+template <bool VEC>
 __global__ void copy_panel_kernel(const double* __restrict__ B, int64_t ldb, double* __restrict__ W,
                                   int64_t ldw, int64_t n, int64_t k) {
   for (int64_t j = blockIdx.y; j < k; j += gridDim.y) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-      W[j * ldw + i] = B[j * ldb + i];
+    const double* src = B + j * ldb;
+    double* dst = W + j * ldw;
+    if constexpr (VEC) {
+      for (int64_t i = 2 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x); i < n;
+           i += 2 * (int64_t)gridDim.x * blockDim.x) {
+        if (i + 1 < n) *reinterpret_cast<double2*>(dst + i) = *reinterpret_cast<const double2*>(src + i);
+        else dst[i] = src[i];
+      }
+    } else {
+      for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+           i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
     }
   }
+}
+
+// Columns of both matrices start on 16-byte boundaries.
+inline bool pairs_aligned(const void* a, int64_t lda, const void* b, int64_t ldb) {
+  return ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15) == 0 && (lda % 2) == 0 &&
+         (ldb % 2) == 0;
 }
 
 // Host-side recursion tree.  A node of order m > LEAF splits at
@@ -306,7 +344,10 @@ static dim3 grid2d(int64_t rows, int64_t cols) {
 
 cudaError_t copy_lower(const double* L, int64_t ldl, double* Lt, int64_t ldt, int64_t n,
                        cudaStream_t s) {
-  copy_lower_kernel<<<grid2d(n, n), 256, 0, s>>>(L, ldl, Lt, ldt, n);
+  if (pairs_aligned(L, ldl, Lt, ldt))
+    copy_lower_kernel<true><<<grid2d((n + 1) / 2, n), 256, 0, s>>>(L, ldl, Lt, ldt, n);
+  else
+    copy_lower_kernel<false><<<grid2d(n, n), 256, 0, s>>>(L, ldl, Lt, ldt, n);
   count_launch();
   return cudaGetLastError();
 }
@@ -340,7 +381,10 @@ cudaError_t zero_upper_blocks(double* Lt, int64_t ldt, int64_t n, int64_t n0, cu
 
 cudaError_t copy_panel(const double* B, int64_t ldb, double* W, int64_t ldw, int64_t n, int64_t k,
                        cudaStream_t s) {
-  copy_panel_kernel<<<grid2d(n, k), 256, 0, s>>>(B, ldb, W, ldw, n, k);
+  if (pairs_aligned(B, ldb, W, ldw))
+    copy_panel_kernel<true><<<grid2d((n + 1) / 2, k), 256, 0, s>>>(B, ldb, W, ldw, n, k);
+  else
+    copy_panel_kernel<false><<<grid2d(n, k), 256, 0, s>>>(B, ldb, W, ldw, n, k);
   count_launch();
   return cudaGetLastError();
 }
