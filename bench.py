@@ -583,17 +583,14 @@ def sliced_study(g, torch, data, dev_in, outs, shapes, reps=3):
         err = float(np.max(np.abs(got - want)) / np.max(np.abs(want)))
         mma = sliced_mma_flops(n, k, nb) / (ms * 1e-3) / 1e12
         rows[f"{n}x{k}"] = [nb, round(plan_ms, 2), round(planes_ms, 2), round(ms, 2),
-                            round(float(n) * n * k / (ms * 1e-3) / 1e12, 3),
-                            round(float(n) * n * k / ((plan_ms + planes_ms + ms) * 1e-3) / 1e12, 3),
-                            _sig(err), round(mma / burst, 3)]
+                            round(float(n) * n * k / (ms * 1e-3) / 1e12, 2), _sig(err), round(mma / burst, 3)]
         p.destroy()
-    return {"cols": ["n0", "plan_ms", "planes_ms", "solve_ms", "solve_tflops", "step_tflops", "rel_err",
-                     "mma_frac"],
+    return {"cols": ["n0", "plan_ms", "planes_ms", "solve_ms", "solve_tflops", "rel_err", "mma_frac"],
             **rows, "mma_peak": burst}
 
 
 def serving_study(g, torch, nL=256, rates=(100, 300, 600, 1200), per_rate=300, seed=2000,
-                  budget_gb=150.0, mixed_min_n=2048):
+                  budget_gb=150.0, mixed_min_n=2048, sliced_min_flops=3e9):
     """Serving workload: nL resident L (n log-uniform in [64, 8192],
     diagonal U[2,3], strictly lower U[-1,1]/n, drawn on the device), each
     planned once; Poisson request streams at the given rates, each request a
@@ -601,7 +598,10 @@ def serving_study(g, torch, nL=256, rates=(100, 300, 600, 1200), per_rate=300, s
     batching under an HBM budget.  The L with n >= mixed_min_n also carry a
     mixed-precision plan (split-fp16 updates), and half of the requests on
     them ask for the refined mixed-precision solve (tol 1e-12) instead of
-    FP64.  Reports solves/s and p50/p99 latency, overall and for the mixed
+    FP64.  The same L also carry the sliced schedule's digit planes, and an
+    FP64 request of at least sliced_min_flops n^2 k flops is solved by the
+    sliced schedule (FP64-class, on the tensor cores) instead of joining a
+    batch.  Reports solves/s and p50/p99 latency, overall and for the mixed
     requests."""
     from paper_1612_01855_gb300.serve import Request, Server
     rng = np.random.default_rng(seed)
@@ -618,6 +618,7 @@ def serving_study(g, torch, nL=256, rates=(100, 300, 600, 1200), per_rate=300, s
         plans.append(g.trsm_plan(L, 256 if n >= 1024 else 64))
         if n >= mixed_min_n:
             g.trsm_plan_mixed(plans[-1], L, "fp16x3")
+            g.trsm_plan_sliced(plans[-1])
         del L
     plan_s = time.perf_counter() - t0
     out = {"resident_L": nL, "plan_seconds": round(plan_s, 2),
@@ -636,7 +637,8 @@ def serving_study(g, torch, nL=256, rates=(100, 300, 600, 1200), per_rate=300, s
             mixed = bool(ns[lid] >= mixed_min_n and rng.random() < 0.5)
             reqs.append(Request(rid, lid, B, t, mixed=mixed))
         torch.cuda.synchronize()
-        srv = Server(plans, budget_bytes=int(budget_gb * 1e9), streams=4, max_batch=64)
+        srv = Server(plans, budget_bytes=int(budget_gb * 1e9), streams=4, max_batch=64,
+                     sliced_min_flops=sliced_min_flops)
         st = srv.run_trace(reqs)
         st["offered_rate"] = rate
         out["rates"].append({k: (round(v, 4) if isinstance(v, float) else v) for k, v in st.items()})
@@ -892,7 +894,7 @@ def run_ours(args, rank, world, local):
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, sample, cores = cpu_oracle_rate(data, shapes, args.cpu_budget)
         cpu = {"value": round(rate, 5), "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-               "sample": sample + " cols, forward subst."}
+               "sample": sample + " cols"}
 
     mixed = None
     residual = None
@@ -942,15 +944,14 @@ def run_ours(args, rank, world, local):
                 json.dump(details, fh, indent=1)
         line = {
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded PCG64)",
             "config": {"workload": "fp64 k/n sweep (n,k) = (16384,256),(8192,8192),(2048,131072); "
                                    "step = trsm_plan + trsm_solve per shape",
                        "n0": {f"{n}x{k}": n0 for (n, k), n0 in zip(shapes, n0s)},
                        "flops_per_step": flops_step, "l2": "inputs larger than L2 (no flush)",
-                       "parallelism": f"replicas{world}" if world > 1 else "single GPU",
-                       "shapes_ms": {f"{r['n']}x{r['k']}": [r["plan_ms"], r["solve_ms"]] for r in per_shape}},
+                       "parallelism": f"replicas{world}" if world > 1 else "single GPU"},
             "roofline": {"bound": "alu", "kernel": "it_inv_solve_kernel",
                          "achieved": round(solve_achieved, 4), "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
                          "frac": round(solve_achieved / fp64_peak, 4),
@@ -971,7 +972,7 @@ def run_ours(args, rank, world, local):
         if mixed is not None:
             line["precision"] = compact_precision(mixed)
         if residual is not None:
-            line["residual_roofline"] = {key: {"ms": v["ms"], "achieved": v["achieved"], "frac": v["frac"]}
+            line["residual_roofline"] = {key: {"ms": round(v["ms"], 2), "frac": round(v["frac"], 3)}
                                          for key, v in residual.items()}
         if batched is not None:
             line["batched"] = [{"dtype": b["dtype"], "ms": b["ms_per_batch"], "tflops": b["tflops_n2k"],
@@ -979,14 +980,15 @@ def run_ours(args, rank, world, local):
                                 "status": b["status"], "err": _sig(b["spot_check_rel_err"])} for b in batched]
         if serving is not None:
             line["serving"] = {"cols": ["offered", "served", "p50_ms", "p99_ms", "fp64_p99_ms", "mixed_p99_ms",
-                                        "ok"],
-                               "rates": [[r["offered_rate"], round(r["solves_per_s"], 1), round(r["p50_ms"], 2),
-                                          round(r["p99_ms"], 2), round(r.get("fp64", {}).get("p99_ms", 0.0), 2),
-                                          round(r.get("mixed", {}).get("p99_ms", 0.0), 2), r["statuses_ok"]]
+                                        "sliced", "ok"],
+                               "rates": [[r["offered_rate"], round(r["solves_per_s"], 1), round(r["p50_ms"], 1),
+                                          round(r["p99_ms"], 1), round(r.get("fp64", {}).get("p99_ms", 0.0), 1),
+                                          round(r.get("mixed", {}).get("p99_ms", 0.0), 1), r["sliced_requests"],
+                                          r["statuses_ok"]]
                                          for r in serving["rates"]],
                                "slots": serving["rates"][0]["slots"] if serving["rates"] else None}
         if schedules is not None:
-            line["schedules_ms"] = {f"{r['n']}x{r['k']}": {key: r[key]["solve_ms"] for key in SCHEDULE_NAMES
+            line["schedules_ms"] = {f"{r['n']}x{r['k']}": {key: round(r[key]["solve_ms"], 1) for key in SCHEDULE_NAMES
                                                            if key in r} for r in schedules}
         print(json.dumps(line, separators=(",", ":")), flush=True)
 

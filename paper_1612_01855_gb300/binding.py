@@ -173,6 +173,7 @@ class Plan:
         _check(lib.trsm_plan_sizes(self._h, ctypes.byref(n), ctypes.byref(n0), ctypes.byref(nb)),
                "trsm_plan_sizes")
         self.n, self.n0, self.nblocks = n.value, n0.value, nb.value
+        self.sliced = False  # digit planes of the sliced schedule (trsm_plan_sliced)
 
     @property
     def handle(self):
@@ -304,9 +305,12 @@ SCHEDULES = {"dag": 0, "right-looking": 1, "recursive": 2, "sliced": 3}
 def trsm_plan_sliced(plan):
     """Adds the digit planes of the sliced schedule to a plan (synchronous;
     a no-op when they are there)."""
+    if getattr(plan, "sliced", False):
+        return
     torch = _torch()
     s = ctypes.c_void_p(torch.cuda.current_stream(plan.device).cuda_stream)
     _check(load_library().trsm_plan_sliced(plan.handle, s), "trsm_plan_sliced")
+    plan.sliced = True
 
 
 def trsm_solve_schedule(plan, B, X=None, schedule="dag"):

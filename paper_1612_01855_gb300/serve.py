@@ -4,9 +4,9 @@ Each L is planned once (`trsm_plan`: its inverted diagonal blocks stay in
 HBM), so a request — a right-hand side B for one of the resident L — only
 pays for the blocked solve (Algorithm It-Inv-TRSM, Section 6.2).  The loop:
 
-* requests wait in two queues, each in arrival order: FP64 requests, and
-  requests for the refined mixed-precision solve (`mixed=True`; its plan
-  needs `trsm_plan_mixed`);
+* requests wait in queues, each in arrival order: FP64 requests, requests
+  for the refined mixed-precision solve (`mixed=True`; its plan needs
+  `trsm_plan_mixed`), and large FP64 requests for the sliced schedule (below);
 * whenever one of `streams` launch slots is free, it takes work: the FP64
   requests at the head of their queue, admitted while their memory (B, X and
   the batch's share of the workspace) fits in the HBM budget next to the
@@ -18,10 +18,16 @@ pays for the blocked solve (Algorithm It-Inv-TRSM, Section 6.2).  The loop:
   thread on the slot's stream (the C call releases the interpreter lock).
   At most `mixed_slots` slots hold such solves at a time, so the other slots
   always keep serving FP64 batches;
-* between the two queues a free slot goes to whichever head arrived first,
+* with `sliced_min_flops` set, an FP64 request of at least that many n^2 k
+  flops whose plan carries the sliced schedule's digit planes
+  (`trsm_plan_sliced`) waits in a third queue and is solved alone on a slot
+  by the sliced schedule (FP64-class products on the tensor cores, 10-20x
+  the DFMA rate on large systems): the largest requests, which set the
+  latency tail at the DFMA rate, then take a fraction of the time;
+* between the queues a free slot goes to whichever head arrived first,
   unless that head cannot start (a mixed request while every mixed slot is
-  taken, or a request whose memory does not fit yet): then the other queue's
-  head may pass it.  No request waits behind one of the other kind;
+  taken, or a request whose memory does not fit yet): then another queue's
+  head may pass it.  No request waits behind one of another kind;
 * batches run on different streams overlap on the device; a request that
   arrives while others are on the GPU is admitted as soon as a slot and
   memory free up;
@@ -35,8 +41,8 @@ caching allocator does not hand its memory out again before the solve ends.
 
 Results do not depend on the traffic: an FP64 request's X is the same bits
 whichever requests share its batch (every tile's updates are applied in a
-fixed order), and a mixed request's refined solve runs alone with its own
-fixed sequence of kernels.
+fixed order), and a mixed request's refined solve, like a large request's
+sliced solve, runs alone with its own fixed sequence of kernels.
 """
 import time
 from collections import deque
@@ -100,6 +106,7 @@ class Request:
     status: int = None
     iterations: int = None
     ready: object = None  # CUDA event recorded at submission on the caller's stream
+    sliced: bool = False  # routed to the sliced schedule (set at submission)
 
     @property
     def latency(self):
@@ -115,6 +122,7 @@ class _InFlight:
     arena: object = field(default=None)
     future: object = None  # a mixed-precision request's worker
     slot: int = 0
+    plan: object = None    # a sliced solve's plan (its status word is read at completion)
 
 
 def _has_mixed_data(plan):
@@ -123,7 +131,7 @@ def _has_mixed_data(plan):
 
 class Server:
     def __init__(self, plans, budget_bytes, streams=4, max_batch=64, mixed_slots=None,
-                 mixed_residual="adaptive"):
+                 mixed_residual="adaptive", sliced_min_flops=None):
         if streams < 1:
             raise ValueError("at least one launch slot")
         self.plans = plans
@@ -133,6 +141,8 @@ class Server:
         self.pool = None
         self.queue_fp64 = deque()
         self.queue_mixed = deque()
+        self.queue_sliced = deque()
+        self.sliced_min_flops = sliced_min_flops
         self.inflight = []
         self.done = []
         self.nstreams = streams
@@ -148,7 +158,8 @@ class Server:
     @property
     def pending(self):
         """Requests not admitted yet, in arrival order."""
-        return sorted(list(self.queue_fp64) + list(self.queue_mixed), key=lambda r: (r.arrival, r.rid))
+        return sorted(list(self.queue_fp64) + list(self.queue_mixed) + list(self.queue_sliced),
+                      key=lambda r: (r.arrival, r.rid))
 
     @staticmethod
     def plan_bytes(plan):
@@ -157,8 +168,17 @@ class Server:
         f = getattr(plan, "device_bytes", None)
         return f() if f is not None else 8 * plan.n * plan.n
 
+    def routes_sliced(self, plan, k, mixed=False):
+        """Whether an FP64 request goes to the sliced schedule."""
+        return (not mixed and self.sliced_min_flops is not None and getattr(plan, "sliced", False)
+                and float(plan.n) * plan.n * k >= self.sliced_min_flops)
+
     @staticmethod
-    def request_bytes(n, k, mixed=False):
+    def request_bytes(n, k, mixed=False, sliced_block=0):
+        if sliced_block:
+            # X, and the sliced solve's workspace: W (FP64), the digit planes
+            # of one block row of W and of X (eight bf16 planes each)
+            return 16 * n * k + 2 * 16 * k * sliced_block + 4 * k + (1 << 16)
         if mixed:
             # X, and the refinement's workspace: R, D (FP64), W (FP32), the
             # eight digit planes of X (bf16), the float-float partial sums
@@ -173,16 +193,21 @@ class Server:
         if req.mixed and not _has_mixed_data(plan):
             raise AdmissionError(f"request {req.rid}: mixed precision asked for, but L #{req.lid} has no "
                                  "mixed-precision plan (trsm_plan_mixed)")
-        self.adm.check_request(self.request_bytes(plan.n, req.B.shape[1], req.mixed))
+        req.sliced = self.routes_sliced(plan, req.B.shape[1], req.mixed)
+        self.adm.check_request(self._bytes(req))
         if getattr(req.B, "is_cuda", False):
             torch = self._torch()
             req.ready = torch.cuda.Event()
             req.ready.record(torch.cuda.current_stream(req.B.device))
-        (self.queue_mixed if req.mixed else self.queue_fp64).append(req)
+        (self.queue_mixed if req.mixed else self.queue_sliced if req.sliced else self.queue_fp64).append(req)
+
+    def _bytes(self, r):
+        plan = self.plans[r.lid]
+        return self.request_bytes(plan.n, r.B.shape[1], r.mixed, min(plan.n0, plan.n) if r.sliced else 0)
 
     def cancel(self, rid):
         """Drops a request that has not been admitted yet."""
-        for q in (self.queue_fp64, self.queue_mixed):
+        for q in (self.queue_fp64, self.queue_mixed, self.queue_sliced):
             for r in q:
                 if r.rid == rid:
                     r.cancelled = True
@@ -210,6 +235,20 @@ class Server:
                 continue
             if f.event.query():
                 now = time.perf_counter()
+                if f.batch is None:  # a sliced solve: the plan's status word (the stream has completed)
+                    try:
+                        with self._torch().cuda.stream(self.streams[f.slot]):
+                            binding.trsm_sync_status(f.plan)
+                        rc = 0
+                    except binding.TrsmError as e:
+                        rc = e.code
+                    r = f.reqs[0]
+                    r.t_done = now
+                    r.status = rc
+                    self.done.append(r)
+                    self.adm.release(f.nbytes)
+                    self.busy[f.slot] = False
+                    continue
                 with self._torch().cuda.stream(self.streams[f.slot]):
                     rc = f.batch.status()[0]  # the stream has completed: no wait
                 for r in f.reqs:
@@ -250,26 +289,24 @@ class Server:
                 return e.code, None
 
     def _next_kind(self):
-        """Which queue a free slot serves: "fp64", "mixed" or None (the
-        arrival-order rule of the module docstring)."""
-        mixed_ok = bool(self.queue_mixed) and self.mixed_busy < self.mixed_slots
-        if mixed_ok:
-            r = self.queue_mixed[0]
-            mixed_ok = self.adm.fits(self.request_bytes(self.plans[r.lid].n, r.B.shape[1], True))
-        fp64_ok = False
+        """Which queue a free slot serves: "fp64", "mixed", "sliced" or None
+        (the arrival-order rule of the module docstring)."""
+        heads = []
+        if self.queue_mixed and self.mixed_busy < self.mixed_slots:
+            heads.append(("mixed", self.queue_mixed[0]))
         if self.queue_fp64:
-            r = self.queue_fp64[0]
-            fp64_ok = self.adm.fits(self.request_bytes(self.plans[r.lid].n, r.B.shape[1]))
-        if mixed_ok and fp64_ok:
-            return "mixed" if self.queue_mixed[0].arrival < self.queue_fp64[0].arrival else "fp64"
-        return "mixed" if mixed_ok else "fp64" if fp64_ok else None
+            heads.append(("fp64", self.queue_fp64[0]))
+        if self.queue_sliced:
+            heads.append(("sliced", self.queue_sliced[0]))
+        ready = [(r.arrival, r.rid, kind) for kind, r in heads if self.adm.fits(self._bytes(r))]
+        return min(ready)[2] if ready else None
 
     def _take_fp64(self):
         """FP64 requests from the head of their queue that fit together."""
         take, nbytes = [], 0
         while self.queue_fp64 and len(take) < self.max_batch:
             r = self.queue_fp64[0]
-            b = self.request_bytes(self.plans[r.lid].n, r.B.shape[1])
+            b = self._bytes(r)
             if not self.adm.fits(nbytes + b):
                 break
             take.append(self.queue_fp64.popleft())
@@ -287,9 +324,26 @@ class Server:
             if kind is None:
                 break
             stream = self.streams[slot]
+            if kind == "sliced":
+                r = self.queue_sliced.popleft()
+                b = self._bytes(r)
+                self.adm.take(b)
+                n, k = r.B.shape
+                plan = self.plans[r.lid]
+                with torch.cuda.stream(stream):
+                    self._order_after_submission(r, stream)
+                    r.X = torch.empty((k, n), dtype=torch.float64, device="cuda").t()
+                    r.t_admit = time.perf_counter()
+                    binding.trsm_solve_schedule(plan, r.B, X=r.X, schedule="sliced")
+                    ev = torch.cuda.Event()
+                    ev.record(stream)
+                self.busy[slot] = True
+                self.inflight.append(_InFlight(None, ev, [r], b, slot=slot, plan=plan))
+                self.launches += 1
+                continue
             if kind == "mixed":
                 r = self.queue_mixed.popleft()
-                b = self.request_bytes(self.plans[r.lid].n, r.B.shape[1], True)
+                b = self._bytes(r)
                 self.adm.take(b)
                 n, k = r.B.shape
                 with torch.cuda.stream(stream):
@@ -327,7 +381,7 @@ class Server:
             self.launches += 1
 
     def drain(self):
-        while self.queue_fp64 or self.queue_mixed or self.inflight:
+        while self.queue_fp64 or self.queue_mixed or self.queue_sliced or self.inflight:
             self.poll()
             self.dispatch()
 
@@ -339,7 +393,7 @@ class Server:
         for r in order:
             r.arrival += t0
         i = 0
-        while i < len(order) or self.queue_fp64 or self.queue_mixed or self.inflight:
+        while i < len(order) or self.queue_fp64 or self.queue_mixed or self.queue_sliced or self.inflight:
             now = time.perf_counter()
             while i < len(order) and order[i].arrival <= now:
                 self.submit(order[i])
@@ -360,6 +414,7 @@ class Server:
                "batches": self.launches, "slots": self.nstreams, "mixed_slots": self.mixed_slots,
                "peak_inflight_gb": self.adm.peak / 1e9,
                "statuses_ok": all(r.status == 0 for r in order)}
+        out["sliced_requests"] = sum(1 for r in order if r.sliced)
         for kind, sel in (("fp64", lambda r: not r.mixed), ("mixed", lambda r: r.mixed)):
             part = [r for r in order if sel(r) and r.latency is not None]
             if part:

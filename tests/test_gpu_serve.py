@@ -136,3 +136,28 @@ def test_server_waits_for_b_produced_on_the_callers_stream(cuda_lib):
         assert r.status == 0, r.rid
         want = oracle.forward_subst(Ls[r.lid], B)
         assert np.max(np.abs(r.X.cpu().numpy() - want)) <= 1e-12 * np.max(np.abs(want)), (r.rid, r.mixed)
+
+
+def test_server_routes_large_requests_to_the_sliced_schedule(cuda_lib):
+    """Large FP64 requests go to the sliced schedule alone on a slot, the
+    rest to batches: every result matches the oracle, and a sliced request
+    equals its own sliced solve bit for bit."""
+    import torch
+    import paper_1612_01855_gb300 as g
+    from paper_1612_01855_gb300.serve import Server
+    Ls, plans = _setup(4, seed=21)
+    for p in plans:
+        if p.n0 % 64 == 0 and p.n0 <= 2048:
+            g.trsm_plan_sliced(p)
+    reqs, host = _requests(Ls, 40, rate=3000.0, seed=23)
+    srv = Server(plans, budget_bytes=40 * 2**30, streams=4, max_batch=16, sliced_min_flops=2e6)
+    stats = srv.run_trace(reqs)
+    assert stats["statuses_ok"] and stats["requests"] == 40
+    assert 0 < stats["sliced_requests"] < 40
+    for r, B in zip(reqs, host):
+        want = oracle.forward_subst(Ls[r.lid], B)
+        assert np.max(np.abs(r.X.cpu().numpy() - want)) <= 1e-12 * np.max(np.abs(want)), (r.rid, r.sliced)
+        if r.sliced:
+            alone = g.trsm_solve_schedule(plans[r.lid], r.B, schedule="sliced")
+            g.trsm_sync_status(plans[r.lid])
+            assert torch.equal(alone, r.X), r.rid

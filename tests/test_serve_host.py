@@ -108,3 +108,33 @@ def test_single_slot_serves_both_kinds():
     assert srv._next_kind() == "fp64"
     srv.queue_fp64.clear()
     assert srv._next_kind() == "mixed"
+
+
+def test_large_fp64_requests_route_to_the_sliced_schedule():
+    """With sliced_min_flops set, an FP64 request of at least that many n^2 k
+    flops on a plan with the sliced schedule's planes waits in its own queue;
+    smaller ones, mixed ones and those on plans without planes do not."""
+    plans = [_Plan(4096), _Plan(4096), _Plan(256)]
+    for p in plans:
+        p.n0 = 256
+    plans[0].sliced = True
+    plans[2].sliced = True
+    plans[1].inner = "fp16x3"
+    srv = Server(plans, budget_bytes=10**12, streams=4, sliced_min_flops=1e10)
+    srv.submit(Request(0, 0, _B(4096, 1000), 0.0))            # 1.7e10 flops, sliced planes: sliced
+    srv.submit(Request(1, 0, _B(4096, 100), 1.0))             # 1.7e9: batched
+    srv.submit(Request(2, 1, _B(4096, 1000), 2.0))            # no sliced planes: batched
+    srv.submit(Request(3, 1, _B(4096, 1000), 3.0, mixed=True))
+    srv.submit(Request(4, 2, _B(256, 2000), 4.0))             # 1.3e8: batched
+    assert [r.rid for r in srv.queue_sliced] == [0]
+    assert [r.rid for r in srv.queue_fp64] == [1, 2, 4] and [r.rid for r in srv.queue_mixed] == [3]
+    assert [r.rid for r in srv.pending] == [0, 1, 2, 3, 4]
+    assert srv._next_kind() == "sliced"                       # the earliest head
+    # its bytes: X and W (16 n k), one block row of digit planes of W and of X
+    assert srv._bytes(srv.queue_sliced[0]) == Server.request_bytes(4096, 1000, sliced_block=256)
+    assert Server.request_bytes(4096, 1000, sliced_block=256) > 16 * 4096 * 1000
+    srv.queue_sliced.clear()
+    assert srv._next_kind() == "fp64"
+    off = Server(plans, budget_bytes=10**12, streams=4)     # routing off by default
+    off.submit(Request(5, 0, _B(4096, 1000), 0.0))
+    assert not off.queue_sliced and [r.rid for r in off.queue_fp64] == [5]
