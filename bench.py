@@ -663,8 +663,10 @@ def run_case(args):
                      digit planes, twice;
     mixed:N:K:N0[:I[:S]]  one mixed-precision refined solve (graded diagonal,
                      c = 2); inner I = 0 tf32, 1 bf16, 2 split bf16, 3 split
-                     fp16; S = 1 for
-                     the FP32 diagonal-block multiply;
+                     fp16; S = 1 for the FP32 diagonal-block multiply, 2 for
+                     the tensor-core one;
+    sched:N:K:N0     the sliced schedule of the FP64 solve (well-conditioned
+                     L), its digit planes made first, then two solves;
     engine:M:N:K     the bf16 tensor-core GEMM self-test, twice;
     batch:COUNT:BITS one batched launch of COUNT systems of the batching
                      workload in FP64 (BITS = 64) or FP32 (32), twice."""
@@ -702,7 +704,19 @@ def run_case(args):
             plan = g.trsm_plan(L, dims[2])
             g.trsm_plan_mixed(plan, L, inner)
             g.trsm_solve_mixed(plan, B, max_iter=30, tol=1e-12, raise_on_noconv=False,
-                               s_fp32=len(dims) > 4 and dims[4] == 1)
+                               s_fp32=len(dims) > 4 and dims[4] == 1, s_tc=len(dims) > 4 and dims[4] == 2)
+    elif kind == "sched":
+        n, k, n0 = dims
+        L = torch.tril(torch.rand(n, n, dtype=torch.float64, device="cuda") * 2 - 1) / n
+        L.diagonal().copy_(2 + torch.rand(n, dtype=torch.float64, device="cuda"))
+        L = L.t().contiguous().t()
+        B = (torch.rand(k, n, dtype=torch.float64, device="cuda") * 2 - 1).t()
+        plan = g.trsm_plan(L, n0)
+        g.trsm_plan_sliced(plan)
+        X = torch.empty(k, n, dtype=torch.float64, device="cuda").t()
+        for _ in range(2):
+            g.trsm_solve_schedule(plan, B, X=X, schedule="sliced")
+        g.trsm_sync_status(plan)
     elif kind == "engine":
         M, N, K = dims
         A = torch.randn(M, K, device="cuda").to(torch.bfloat16)
@@ -1010,7 +1024,8 @@ def main():
     ap.add_argument("--no-sweep", action="store_true", help="skip the n0 sweep")
     ap.add_argument("--details", default="", help="also write every study's full records to this JSON file")
     ap.add_argument("--precision", action="store_true", help="print the full c x inner x s-step study")
-    ap.add_argument("--case", default="", help="profiling case: sliced:N:K[:PLANES], mixed:N:K:N0[:INNER[:S32]], engine:M:N:K, batch:COUNT:BITS")
+    ap.add_argument("--case", default="", help="profiling case: sliced:N:K[:PLANES], mixed:N:K:N0[:INNER[:S]], "
+                                               "sched:N:K:N0, engine:M:N:K, batch:COUNT:BITS")
     ap.add_argument("--shapes", default="", help="override workload, e.g. 6144:1024:256 (not a bench line)")
     args = ap.parse_args()
     rank, world, local = dist_env()
