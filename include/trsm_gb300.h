@@ -59,6 +59,12 @@ extern "C" {
 #define TRSM_RESIDUAL_FP64 1     /* FP64 fused multiply-add                                */
 #define TRSM_RESIDUAL_SLICED8 2  /* as SLICED with 8 digit planes: ~2^-49 instead of ~2^-43 */
 #define TRSM_RESIDUAL_ADAPTIVE 3 /* SLICED until the updates stagnate above tol, then SLICED8 */
+/* As ADAPTIVE, but an early residual takes 5 or 6 digit planes (15 or 21
+ * plane products instead of 28; about 2^-31 and 2^-37 of |B| + |L||X|)
+ * while the iterate's error, estimated from the last update and its
+ * contraction, is far above what they resolve; 7 planes after that, 8 once
+ * the updates stagnate. */
+#define TRSM_RESIDUAL_PROGRESSIVE 4
 /* Flag or-ed into `residual`: apply the FP64 inverses of the diagonal blocks
  * in FP32 arithmetic inside the inner solve (default: FP64 arithmetic). */
 #define TRSM_SOLVE_S_FP32 0x100
@@ -206,7 +212,7 @@ int trsm_plan_mixed(trsm_handle_t h, const double* L_dev, int64_t ldl, int inner
  * D_i = L~_ii W_i with the FP64 inverse (FP64 arithmetic), then the trailing
  * update W(T_{i+1}) -= L(T_{i+1}, S_i) D_i as one tcgen05 GEMM in the plan's
  * inner precision with FP32 accumulation (W is the FP32 copy of R).
- *   residual : TRSM_RESIDUAL_SLICED, _SLICED8, _ADAPTIVE or _FP64 (the
+ *   residual : TRSM_RESIDUAL_SLICED, _SLICED8, _ADAPTIVE, _PROGRESSIVE or _FP64 (the
  *              latter needs n0 a multiple of 32 when there is more than one
  *              block), optionally or-ed with TRSM_SOLVE_S_FP32 or
  *              TRSM_SOLVE_S_TC.  The

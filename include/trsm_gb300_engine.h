@@ -31,13 +31,14 @@ int trsm_tc_gemm_selftest(int mode, const void* A_dev, const void* B_dev, float*
                           int64_t N, int64_t K, int* err_dev, void* stream);
 
 /* FP64-class residual R = B - tril(L) X on the BF16 tensor cores: the
- * strictly lower L and X are split into `planes` (7 or 8) 6-bit integer
+ * strictly lower L and X are split into `planes` (5 to 8) 6-bit integer
  * digit planes per (row, 2048-wide chunk of K) with a power-of-two exponent
  * each; the digit-pair products with s + u <= planes - 1 are accumulated in
  * FP32 per chunk (exactly for s + u <= 3) and combined in float-float
  * arithmetic (error-free splitting after Ozaki, Ogita, Oishi & Rump 2012);
  * the diagonal of L is applied in FP64.  Relative error about 2^-43
- * (7 planes) or 2^-49 (8 planes) of (|B| + |L| |X|).
+ * (7 planes) or 2^-49 (8 planes) of (|B| + |L| |X|), 6 bits less per
+ * plane fewer (about 2^-31 with 5 planes).
  *   L_dev n x n column-major (lower triangle read), X_dev, B_dev, R_dev
  *   n x k column-major.  Allocates its slice buffers stream-ordered.
  *   Asynchronous; err_dev as for the self-test; -1 for bad arguments. */
@@ -51,7 +52,7 @@ int trsm_residual_sliced(const double* L_dev, int64_t n, int64_t ldl, const doub
  * sliced, then R = B - L X by the stream kernel.  X_dev, B_dev, R_dev n x k
  * column-major (n the plan's order).  Allocates the digit planes of X and
  * the partial sums stream-ordered.  Asynchronous; err_dev as above.
- * Errors: TRSM_EINVAL (no mixed data, bad sizes, planes not 7 or 8),
+ * Errors: TRSM_EINVAL (no mixed data, bad sizes, planes not in 5 .. 8),
  * TRSM_ENOMEM, TRSM_ECUDA. */
 int trsm_residual_plan(trsm_handle_t h, const double* X_dev, int64_t k, int64_t ldx, const double* B_dev,
                        int64_t ldb, double* R_dev, int64_t ldr, int planes, int* err_dev, void* stream);

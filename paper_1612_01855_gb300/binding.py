@@ -33,6 +33,7 @@ TRSM_RESIDUAL_SLICED = 0
 TRSM_RESIDUAL_FP64 = 1
 TRSM_RESIDUAL_SLICED8 = 2
 TRSM_RESIDUAL_ADAPTIVE = 3
+TRSM_RESIDUAL_PROGRESSIVE = 4
 TRSM_SOLVE_S_FP32 = 0x100
 TRSM_SOLVE_S_TC = 0x200
 
@@ -285,7 +286,7 @@ def trsm_solve_mixed(plan, B, X=None, residual="sliced", max_iter=30, tol=1e-14,
     it = ctypes.c_int()
     upd = ctypes.c_double()
     code = {"sliced": TRSM_RESIDUAL_SLICED, "fp64": TRSM_RESIDUAL_FP64, "sliced8": TRSM_RESIDUAL_SLICED8,
-            "adaptive": TRSM_RESIDUAL_ADAPTIVE}[residual]
+            "adaptive": TRSM_RESIDUAL_ADAPTIVE, "progressive": TRSM_RESIDUAL_PROGRESSIVE}[residual]
     if s_fp32:
         code |= TRSM_SOLVE_S_FP32
     if s_tc:

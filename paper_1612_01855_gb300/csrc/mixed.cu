@@ -727,7 +727,7 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
   residual &= ~(TRSM_SOLVE_S_FP32 | TRSM_SOLVE_S_TC);
   if (s32 && stc) return TRSM_EINVAL;
   if (residual != TRSM_RESIDUAL_SLICED && residual != TRSM_RESIDUAL_FP64 && residual != TRSM_RESIDUAL_SLICED8 &&
-      residual != TRSM_RESIDUAL_ADAPTIVE)
+      residual != TRSM_RESIDUAL_ADAPTIVE && residual != TRSM_RESIDUAL_PROGRESSIVE)
     return TRSM_EINVAL;
   if (k == 0) return TRSM_SUCCESS;
   if (!B_dev || !X_dev || ldb < h->n || ldx < h->n || B_dev == X_dev) return TRSM_EINVAL;
@@ -782,8 +782,12 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
   if (e == cudaSuccess) e = trsm::copy_panel(B_dev, ldb, R, ld, n, k, s);
   double best = HUGE_VAL, prev = HUGE_VAL;
   // digit planes of the sliced residual: the adaptive mode starts with seven
-  // and moves to eight when the updates stagnate above tol
+  // and moves to eight when the updates stagnate above tol; the progressive
+  // mode chooses five, six or seven from the iterate's estimated error (then
+  // eight on stagnation)
+  const bool progressive = residual == TRSM_RESIDUAL_PROGRESSIVE;
   int planes = residual == TRSM_RESIDUAL_SLICED8 ? 8 : 7;
+  int floor_planes = 5;  // the progressive mode never goes back below this
   int it = 0;
   for (it = 1; it <= max_iter && e == cudaSuccess; ++it) {
     // ---- D = inner_solve(R) ----
@@ -885,16 +889,33 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
     // floor) and further sweeps cannot improve X.  Accept the iterate when
     // that floor is small, otherwise report non-convergence.
     if (it >= 2 && ratio > 0.5 * prev) {
-      if (residual == TRSM_RESIDUAL_ADAPTIVE && planes == 7) {
-        planes = 8;  // lower the residual's floor and keep refining
+      if ((residual == TRSM_RESIDUAL_ADAPTIVE || progressive) && planes < 8) {
+        // lower the residual's floor and keep refining
+        planes = progressive && planes < 7 ? 7 : 8;
+        floor_planes = planes;
         prev = HUGE_VAL;
       } else {
         if (ratio > 1e-10) rc = TRSM_ENOCONV;
         break;
       }
     } else {
+      if (progressive && it >= 2) {
+        // The next residual only has to be accurate against the error of
+        // the iterate, estimated as this update times its contraction
+        // (ratio / prev); a P-plane residual carries about 2^-(6P - 5) of
+        // |B| + |L||X|, and the factor 1e5 covers the condition number
+        // that multiplies it in the correction.
+        const double est = ratio * (ratio / prev);
+        const int want = est >= 4.7e-10 * 1e5 ? 5 : est >= 7.3e-12 * 1e5 ? 6 : 7;
+        planes = std::max(floor_planes, want);
+      }
       prev = ratio;
     }
+    // After the first sweep no contraction is known yet: the iterate's error
+    // is about that of the inner solve, so the first residual's planes
+    // follow the inner format (about 2^-11, 2^-8, 2^-16 and 2^-22 per
+    // product for tf32, bf16, split bf16 and split fp16).
+    if (progressive && it == 1) planes = mode == 3 ? 7 : mode == 2 ? 6 : 5;
     best = std::min(best, ratio);
     if (it == max_iter) {
       rc = TRSM_ENOCONV;
@@ -931,7 +952,7 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
 extern "C" int trsm_residual_plan(trsm_handle_t h, const double* X_dev, int64_t k, int64_t ldx, const double* B_dev,
                                   int64_t ldb, double* R_dev, int64_t ldr, int planes, int* err_dev, void* stream) {
   if (!h || !h->mixed || !X_dev || !B_dev || !R_dev || !err_dev || k < 1 || ldx < h->n || ldb < h->n ||
-      ldr < h->n || (planes != 7 && planes != 8))
+      ldr < h->n || planes < 5 || planes > 8)
     return TRSM_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int64_t n = h->n;

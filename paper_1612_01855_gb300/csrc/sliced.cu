@@ -25,6 +25,10 @@
 //              roundings, the fast variant;
 //       P = 8: d = 0..4 alone, d >= 5 together (2^-30 of the total), 80
 //              columns per tile: below 2^-47;
+//       P = 5, 6 (the early residuals of a refinement, when the iterate's
+//              error is far above FP64 accuracy): five groups of 96 columns
+//              as for P = 7; about 2^-31 and 2^-37 of |B| + |L| |X|, with
+//              15 and 21 plane pairs instead of 28;
 //   * after each chunk the epilogue adds the six groups in float-float
 //     arithmetic (about 48 bits), scales by 2^(eL + eX - 12) and
 //     accumulates (in a float-float partial buffer when a tile has more than
@@ -52,10 +56,12 @@ namespace sliced {
 // Tile shape per plane count: BN columns of the residual per CTA, NG FP32
 // accumulator groups of BN TMEM columns each (480 of the 512 columns).
 // K advances in steps of 64 bf16 (one 128-byte swizzled row).
+// P = 5, 6 or 7: five groups of 96 columns (every d alone for P = 5; d = 4
+// and 5 together for P = 6, d >= 4 for P = 7); P = 8: six groups of 80.
 template <int P>
 struct Shape {
-  static constexpr int BN = P == 7 ? 96 : 80;
-  static constexpr int NG = P == 7 ? 5 : 6;  // the last group holds every d >= NG - 1
+  static constexpr int BN = P <= 7 ? 96 : 80;
+  static constexpr int NG = P <= 7 ? 5 : 6;  // the last group holds every d >= NG - 1
 };
 constexpr int kStepK = 64;
 static_assert(kChunk % kStepK == 0, "chunk must be a whole number of K steps");
@@ -469,7 +475,7 @@ struct Stream {
   static constexpr uint32_t A_SL = 128u * 128u;
   static constexpr uint32_t B_SL = static_cast<uint32_t>(BN) * 128u;
   __host__ __device__ static constexpr int begin(int gi) {
-    return P == 7 ? (gi == 0 ? 0 : gi == 1 ? 1 : 3) : (gi == 0 ? 0 : gi == 1 ? 2 : 4);
+    return P <= 7 ? (gi == 0 ? 0 : gi == 1 ? 1 : 3) : (gi == 0 ? 0 : gi == 1 ? 2 : 4);
   }
   __host__ __device__ static constexpr int end(int gi) { return gi + 1 < kGroups ? begin(gi + 1) : P; }
   __host__ __device__ static constexpr uint32_t bytes(int gi) {
@@ -830,9 +836,14 @@ cudaError_t launch_residual(const SlicedOperand& Ls, const SlicedOperand& Xs, co
 cudaError_t sliced_residual(const SlicedOperand& Ls, const double* L, int64_t ldl, const SlicedOperand& Xs,
                             const double* X, int64_t ldx, const double* B, int64_t ldb, double* R,
                             int64_t ldr, void* partial, bool lower, int planes, int* err, cudaStream_t s) {
-  if ((planes != 7 && planes != 8) || Ls.kc != Xs.kc || Ls.kc % sliced::kStepK != 0) return cudaErrorInvalidValue;
+  if (planes < 5 || planes > 8 || Ls.kc != Xs.kc || Ls.kc % sliced::kStepK != 0) return cudaErrorInvalidValue;
   const ResidualArgs a{B, ldb, L, ldl, X, ldx, R, ldr, partial, lower};
-  return planes == 8 ? launch_residual<8>(Ls, Xs, a, err, s) : launch_residual<7>(Ls, Xs, a, err, s);
+  switch (planes) {
+    case 5: return launch_residual<5>(Ls, Xs, a, err, s);
+    case 6: return launch_residual<6>(Ls, Xs, a, err, s);
+    case 7: return launch_residual<7>(Ls, Xs, a, err, s);
+    default: return launch_residual<8>(Ls, Xs, a, err, s);
+  }
 }
 
 }  // namespace trsm
@@ -841,7 +852,7 @@ extern "C" int trsm_residual_sliced(const double* L_dev, int64_t n, int64_t ldl,
                                     int64_t k, int64_t ldx, const double* B_dev, int64_t ldb,
                                     double* R_dev, int64_t ldr, int planes, int* err_dev, void* stream) {
   if (!L_dev || !X_dev || !B_dev || !R_dev || !err_dev || n < 1 || k < 1 || ldl < n || ldx < n ||
-      ldb < n || ldr < n || (planes != 7 && planes != 8))
+      ldb < n || ldr < n || planes < 5 || planes > 8)
     return -1;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t lb = trsm::sliced_operand_bytes(n, n);

@@ -112,7 +112,8 @@ def test_every_entry_point_checks_its_arguments_on_the_host():
     # engine building blocks
     assert lib.trsm_tc_gemm_selftest(4, p16, p16, p16, 128, 128, 64, p16, None) == -1   # no mode 4
     assert lib.trsm_tc_gemm_selftest(0, p16, p16, p16, 128, 128, 60, p16, None) == -1   # K not a multiple of 8
-    assert lib.trsm_residual_sliced(p16, 8, 8, p16, 1, 8, p16, 8, p16, 8, 6, p16, None) == -1  # 7 or 8 planes
+    for planes in (4, 9):  # 5 to 8 planes
+        assert lib.trsm_residual_sliced(p16, 8, 8, p16, 1, 8, p16, 8, p16, 8, planes, p16, None) == -1
     assert lib.trsm_residual_sliced(None, 8, 8, p16, 1, 8, p16, 8, p16, 8, 7, p16, None) == -1
     assert lib.trsm_wait_selftest(2, 1000, None) == E
     assert lib.trsm_wait_selftest(0, 0, None) == E
