@@ -265,7 +265,10 @@ struct SysUnit {
 constexpr int kSysMaxCW = 32;  // widest column chunk of a unit
 // W_l is formed after the product's last K chunk and read before the next
 // block row stages its first one, so it shares memory with the staging
-// buffers (30 KB per CTA).
+// buffers (30 KB per CTA).  (Measured slower, 4096 systems: the product's
+// operands staged by cp.async into two buffers instead of through
+// registers, 1.60 -> 2.05 ms at five CTAs per SM; L~_ll alone copied by
+// cp.async behind the product, 1.74 ms.)
 struct SysSmem {
   float inv[64][68];  // inv[col][row]: L~_ll, zeros above the diagonal (rows 16-byte aligned)
   union {
