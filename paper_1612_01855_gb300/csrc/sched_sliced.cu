@@ -76,32 +76,83 @@ int solve_sliced(trsm_plan_s* h, const double* B, int64_t k, int64_t ldb, double
   const size_t wbytes = al256(sizeof(double) * static_cast<size_t>(ld) * static_cast<size_t>(k));
   const size_t pbytes = sliced_operand_bytes(k, nb, nb);
   unsigned char* ws = nullptr;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), wbytes + 2 * pbytes + 256, s);
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), wbytes + 3 * pbytes + 256, s);
   if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? TRSM_ENOMEM : TRSM_ECUDA;
   double* W = reinterpret_cast<double*>(ws);
   const SlicedOperand Wp = sliced_operand_view(ws + wbytes, k, nb, nb);
-  const SlicedOperand Xp = sliced_operand_view(ws + wbytes + pbytes, k, nb, nb);
-  int* err = reinterpret_cast<int*>(ws + wbytes + 2 * pbytes);
-  e = cudaMemsetAsync(err, 0, sizeof(int), s);
+  // two buffers for the planes of X(S_i): the far update of block row i
+  // reads one while block row i + 1 fills the other
+  const SlicedOperand Xp[2] = {sliced_operand_view(ws + wbytes + pbytes, k, nb, nb),
+                               sliced_operand_view(ws + wbytes + 2 * pbytes, k, nb, nb)};
+  int* err = reinterpret_cast<int*>(ws + wbytes + 3 * pbytes);
+  // Look-ahead: the chain of block rows (planes of W(S_i), the diagonal
+  // multiply, planes of X(S_i), the update of the next block row S_{i+1})
+  // runs on a high-priority stream; the rest of each trailing update,
+  // T_{i+2}, runs on a low-priority side stream and overlaps the chain's
+  // next steps, which on narrow right-hand sides have few tiles.  Rows
+  // S_{i+1} receive the far update of block row i - 1 before the near
+  // update of block row i (same stream order as the plain loop, so the
+  // results are bitwise those of the plain right-looking order).
+  cudaStream_t chain = nullptr, side = nullptr;
+  cudaEvent_t ev_x = nullptr, ev_far = nullptr, ev_join = nullptr;
+  int lo = 0, hi = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&chain, cudaStreamNonBlocking, hi);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, lo);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_x, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_far, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), s);
   if (e == cudaSuccess) e = copy_panel(B, ldb, W, ld, n, k, s);
+  // both streams start after the set-up on the caller's stream
+  if (e == cudaSuccess) e = cudaEventRecord(ev_join, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(chain, ev_join, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(side, ev_join, 0);
+  bool far_pending = false;
   for (int64_t i = 0; i < N && e == cudaSuccess; ++i) {
     const int64_t s0 = i * nb, m = std::min(nb, n - s0);
     // X(S_i) = L~_ii W(S_i): the columns of W(S_i) are the B operand's rows
-    e = slice_rows_prefix(W + s0, ld, m, Wp, s);
+    e = slice_rows_prefix(W + s0, ld, m, Wp, chain);
     if (e == cudaSuccess)
-      e = sliced_step(sp->inv, s0, 0, Wp, m, m, X, ldx, s0, true, false, sp->diag + s0, W + s0, ld, err, s);
+      e = sliced_step(sp->inv, s0, 0, Wp, m, m, X, ldx, s0, true, false, sp->diag + s0, W + s0, ld, err, chain);
     if (e != cudaSuccess || i == N - 1) break;
-    // W(T_{i+1}) -= L(T_{i+1}, S_i) X(S_i)
-    e = slice_rows_prefix(X + s0, ldx, m, Xp, s);
+    // planes of X(S_i) (their buffer was last read by block row i - 2's
+    // updates, which the chain has waited for)
+    const SlicedOperand& xp = Xp[i & 1];
+    e = slice_rows_prefix(X + s0, ldx, m, xp, chain);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_x, chain);
+    // W(S_{i+1}) -= L(S_{i+1}, S_i) X(S_i), after block row i - 1's far update
+    const int64_t s1 = s0 + nb, m1 = std::min(nb, n - s1);
+    if (e == cudaSuccess && far_pending) e = cudaStreamWaitEvent(chain, ev_far, 0);
     if (e == cudaSuccess)
-      e = sliced_step(sp->off, s0 + nb, s0, Xp, n - s0 - nb, m, W, ld, s0 + nb, false, true, nullptr, nullptr, 0, err,
-                      s);
+      e = sliced_step(sp->off, s1, s0, xp, m1, m, W, ld, s1, false, true, nullptr, nullptr, 0, err, chain);
+    // W(T_{i+2}) -= L(T_{i+2}, S_i) X(S_i) on the side stream
+    const int64_t s2 = s1 + m1;
+    if (e == cudaSuccess && s2 < n) {
+      e = cudaStreamWaitEvent(side, ev_x, 0);
+      if (e == cudaSuccess)
+        e = sliced_step(sp->off, s2, s0, xp, n - s2, m, W, ld, s2, false, true, nullptr, nullptr, 0, err, side);
+      if (e == cudaSuccess) e = cudaEventRecord(ev_far, side);
+      far_pending = true;
+    } else {
+      far_pending = false;
+    }
   }
+  // join: the caller's stream continues after both streams' work
+  if (e == cudaSuccess) e = cudaEventRecord(ev_join, side);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_join, 0);
+  if (e == cudaSuccess) e = cudaEventRecord(ev_join, chain);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_join, 0);
   if (e == cudaSuccess) {
     fold_error_kernel<<<1, 1, 0, s>>>(err, plan_status_word(h));
     count_launch();
     e = cudaGetLastError();
   }
+  if (ev_x) cudaEventDestroy(ev_x);
+  if (ev_far) cudaEventDestroy(ev_far);
+  if (ev_join) cudaEventDestroy(ev_join);
+  if (chain) cudaStreamDestroy(chain);  // deferred by the runtime until their work completes
+  if (side) cudaStreamDestroy(side);
   cudaFreeAsync(ws, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
