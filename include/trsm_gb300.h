@@ -132,8 +132,8 @@ int trsm_solve(trsm_handle_t h, const double* B_dev, int64_t k, int64_t ldb, dou
  *                             Each product carries about 2^-49 of |A| |B|
  *                             (an FP64-class result, not FP64 rounding).
  *                             Needs trsm_plan_sliced on the plan first
- *                             (else TRSM_EINVAL); X_dev may equal B_dev
- *                             with ldx == ldb.
+ *                             (else TRSM_EINVAL) and k <= 5242800; X_dev
+ *                             may equal B_dev with ldx == ldb.
  * B_dev must not alias X_dev for RIGHT_LOOKING and RECURSIVE.  Asynchronous;
  * allocates its workspace stream-ordered.  Errors as trsm_solve. */
 #define TRSM_SCHED_DAG 0

@@ -189,7 +189,9 @@ extern "C" int trsm_solve_schedule(trsm_handle_t h, const double* B_dev, int64_t
                                    int64_t ldx, int schedule, void* stream) {
   if (schedule == TRSM_SCHED_DAG) return trsm_solve(h, B_dev, k, ldb, X_dev, ldx, stream);
   if (schedule == TRSM_SCHED_SLICED) {
-    if (!h || !h->sliced || k < 0) return TRSM_EINVAL;
+    // the tensor-core products tile the k columns 80 at a time, at most
+    // 65535 column tiles per launch
+    if (!h || !h->sliced || k < 0 || k > 65535LL * 80) return TRSM_EINVAL;
     if (k == 0) return TRSM_SUCCESS;
     if (!B_dev || !X_dev || ldb < h->n || ldx < h->n || (B_dev == X_dev && ldb != ldx)) return TRSM_EINVAL;
     return trsm::solve_sliced(h, B_dev, k, ldb, X_dev, ldx, static_cast<cudaStream_t>(stream));

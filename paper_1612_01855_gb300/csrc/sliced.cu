@@ -737,6 +737,7 @@ cudaError_t sliced_step(const SlicedOperand& A, int64_t a_row0, int64_t a_k0, co
   constexpr int BN = sliced::Shape<P>::BN;
   const int64_t N = Bop.rows;
   if (M <= 0 || N <= 0) return cudaSuccess;
+  if ((N + BN - 1) / BN > 65535) return cudaErrorInvalidValue;
   // one chunk: K within A's chunk at a_k0 and within B's only chunk; the
   // TMA x coordinate of A must be a multiple of 8 (16 bytes of bf16)
   if (K < 1 || K > A.kc || a_k0 % A.kc != 0 || a_k0 + K > A.K || Bop.nch != 1 || K > Bop.K ||
