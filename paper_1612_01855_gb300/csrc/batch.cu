@@ -74,47 +74,81 @@ __device__ bool wait_geq_b(const int* p, int target, int* err) {
   return wait_geq_bounded(p, target, err, 1, kWaitNs, kWaitIters, 512) > 0;
 }
 
-// Out of line: unrolled over the 32 columns it is most of the kernel's
-// code, and it runs only in the inversion phase.
+// Inverse of the leading m x m (m <= 32) lower triangle of A (leading
+// dimension lda) into out (leading dimension ldo, the m x m part only), by
+// RecTriInv with the whole CTA: the block, padded with an identity to 32
+// rows, is cut into four 8 x 8 leaves inverted by column substitution (one
+// thread per leaf column), then combined at h = 8 (two nodes) and h = 16,
+// T = -(L22^-1 L21) first and T L11^-1 second.  ls (32 x 33) holds the
+// block, tb (16 x 17) the T factor.  A zero or non-finite pivot folds
+// INT_MAX - row into *status.  Every thread of the CTA must call it (it
+// synchronises).  Out of line: it runs only in the inversion phase.
 template <class T>
-__device__ __noinline__ void leaf_invert_warp(const T* __restrict__ A, int64_t lda, int m, T* __restrict__ out,
-                                 int64_t ldo, T (*ls)[33], int* status, int64_t row0) {
-  const int lane = threadIdx.x & 31;
-  // all 32 loads in flight before the first store (one round trip, not 32)
-  T v[32];
+__device__ __noinline__ void leaf_invert_block(const T* __restrict__ A, int64_t lda, int m, T* __restrict__ out,
+                                               int64_t ldo, T (*ls)[33], T (*tb)[17], int* status, int64_t row0) {
+  const int tid = threadIdx.x;
+  // the lower triangle, the identity past m, zeros elsewhere; every load in
+  // flight before the first store
+  {
+    T v[8];
 #pragma unroll
-  for (int c = 0; c < 32; ++c) v[c] = (lane < m && c < m && lane >= c) ? A[static_cast<int64_t>(c) * lda + lane] : T(0);
+    for (int it = 0; it < 8; ++it) {
+      const int e = tid + NTHREADS * it, c = e >> 5, r = e & 31;
+      v[it] = (r < m && c < m && r >= c) ? A[static_cast<int64_t>(c) * lda + r] : (r == c && r >= m ? T(1) : T(0));
+    }
 #pragma unroll
-  for (int c = 0; c < 32; ++c) ls[lane][c] = v[c];
-  __syncwarp();
-  if (lane < m) {
-    const T dl = ls[lane][lane];
-    // status 0 = fine; otherwise INT_MAX - (smallest singular row)
-    if (dl == T(0) || !isfinite(static_cast<double>(dl))) atomicMax(status, INT_MAX - static_cast<int>(row0 + lane));
-  }
-  // the pivots' reciprocals, all at once, into the padding column: the
-  // substitution below then multiplies instead of dividing at each of its
-  // 32 dependent steps
-  ls[lane][32] = (lane < m) ? T(1) / ls[lane][lane] : T(0);
-  __syncwarp();
-  T y[32];
-#pragma unroll
-  for (int r = 0; r < 32; ++r) y[r] = (r == lane) ? T(1) : T(0);
-#pragma unroll
-  for (int l = 0; l < 32; ++l) {
-    if (l < m) {
-      y[l] = y[l] * ls[l][32];
-#pragma unroll
-      for (int r = l + 1; r < 32; ++r) y[r] = fma(-ls[r][l], y[l], y[r]);
+    for (int it = 0; it < 8; ++it) {
+      const int e = tid + NTHREADS * it;
+      ls[e >> 5][e & 31] = v[it];  // ls[col][row]
     }
   }
-  __syncwarp();
+  __syncthreads();
+  // leaves: thread (b, c) of the first warp forms column c of leaf b's inverse
+  T y[8];
+  const int lb = tid >> 3, lc = tid & 7, o = 8 * lb;
+  if (tid < 32) {
+    const T piv = ls[o + lc][o + lc];
+    if (o + lc < m && (piv == T(0) || !isfinite(static_cast<double>(piv))))
+      atomicMax(status, INT_MAX - static_cast<int>(row0 + o + lc));
 #pragma unroll
-  for (int r = 0; r < 32; ++r) ls[r][lane] = y[r];
-  __syncwarp();
-  // the m x m leaf only: the output block may be narrower than 32 (n < 32)
-  if (lane < m)
-    for (int c = 0; c < m; ++c) out[static_cast<int64_t>(c) * ldo + lane] = ls[lane][c];
+    for (int r = 0; r < 8; ++r) y[r] = (r == lc) ? T(1) : T(0);
+#pragma unroll
+    for (int l = 0; l < 8; ++l) {
+      y[l] = y[l] / ls[o + l][o + l];
+#pragma unroll
+      for (int r = l + 1; r < 8; ++r) y[r] = fma(-ls[o + l][o + r], y[l], y[r]);
+    }
+  }
+  __syncthreads();
+  if (tid < 32) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) ls[o + lc][o + r] = y[r];
+  }
+  __syncthreads();
+  // combine level h: nodes of order 2h at base b = 2 h q; lanes over rows
+#pragma unroll
+  for (int h = 8; h <= 16; h *= 2) {
+    const int nodes = 32 / (2 * h), rows = nodes * h, outs = rows * h;
+    for (int e = tid; e < outs; e += NTHREADS) {
+      const int rr = e % rows, c = e / rows, q = rr / h, r = rr % h, b = 2 * h * q;
+      T acc = T(0);
+      for (int p = 0; p < h; ++p) acc = fma(ls[b + h + p][b + h + r], ls[b + c][b + h + p], acc);
+      tb[q * h + c][r] = -acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < outs; e += NTHREADS) {
+      const int rr = e % rows, c = e / rows, q = rr / h, r = rr % h, b = 2 * h * q;
+      T acc = T(0);
+      for (int p = c; p < h; ++p) acc = fma(tb[q * h + p][r], ls[b + c][b + p], acc);
+      ls[b + c][b + h + r] = acc;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < m * m; e += NTHREADS) {
+    const int c = e / m, r = e % m;
+    out[static_cast<int64_t>(c) * ldo + r] = ls[c][r];
+  }
+  __syncthreads();  // ls may be refilled right after
 }
 
 // acc += A(rows [0,m), K [kbeg,kend)) * B(K [kbeg,kend), cols [0,nc)) for a
@@ -670,12 +704,12 @@ __global__ void __launch_bounds__(NTHREADS, 8) batch_kernel(const BatchSys<T>* _
       const int m = static_cast<int>(imin64(a.n0, a.n - s0));
       T* inv = const_cast<T*>(a.Linv) + b * a.inv_bstride;
       const T* Lb = a.L + s0 * a.ldl + s0;
-      const int warp = tid >> 5;
       const int h = (m > 32) ? 32 : m, r2 = m - h;
-      if (warp == 0) leaf_invert_warp<T>(Lb, a.ldl, h, inv, a.ldinv, ls[0], a.status, s0);
-      if (warp == 1 && r2 > 0)
-        leaf_invert_warp<T>(Lb + 32 * a.ldl + 32, a.ldl, r2, inv + 32 * a.ldinv + 32, a.ldinv, ls[1], a.status,
-                            s0 + 32);
+      T(*tb)[17] = reinterpret_cast<T(*)[17]>(&ls[1][0][0]);
+      leaf_invert_block<T>(Lb, a.ldl, h, inv, a.ldinv, ls[0], tb, a.status, s0);
+      if (r2 > 0)
+        leaf_invert_block<T>(Lb + 32 * a.ldl + 32, a.ldl, r2, inv + 32 * a.ldinv + 32, a.ldinv, ls[0], tb, a.status,
+                             s0 + 32);
       __threadfence_block();
       __syncthreads();
       if (r2 > 0) {
