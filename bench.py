@@ -40,7 +40,7 @@ SCHEDULE_NAMES = ("dag", "right-looking", "recursive", "sliced")
 # (measured, ms: 16384x256 9.7 / 7.2 / 5.8 at n0 = 256 / 512 / 1024;
 # 8192x8192 26.0 / 22.0 / 20.0 at 512 / 1024 / 2048; 2048x131072 32.4 /
 # 29.7 / 30.3 at 512 / 1024 / 2048)
-SLICED_N0 = {(16384, 256): 1024, (8192, 8192): 2048, (2048, 131072): 1024}
+SLICED_N0 = {(16384, 256): 1024, (8192, 8192): 2048, (2048, 131072): 2048}
 # Block size of the mixed-precision figure (n = 16384, k = 4096).  Larger
 # blocks suit the mixed path: fewer, longer tensor-core updates, and the
 # diagonal multiplies run in FP32 (measured: 163 / 137 / 131 / 135 ms at

@@ -344,6 +344,23 @@ const double* trsm_plan_lt(trsm_handle_t h, int64_t* ldt);
  * that admit work against an HBM budget. */
 size_t trsm_plan_device_bytes(trsm_handle_t h);
 
+/* Workspace memory.  The per-call scratch of every solve, plan and batch
+ * run (working copy of B, digit planes, counters) comes from a
+ * stream-ordered memory pool the library owns, one per device.  Memory a
+ * call frees stays reserved in the pool for the next call (the device's
+ * default pool would unmap it at each synchronisation and the next call
+ * would map it again, about 1 ms per GB), and is not handed to another
+ * stream before its free has completed there.  No counterpart in the paper.
+ *   trsm_workspace_trim: returns the current device's idle pool memory to
+ *     the system until at most keep_bytes stay reserved (memory of calls
+ *     still in flight stays).  TRSM_SUCCESS, also when the pool was never
+ *     used; TRSM_ECUDA without a usable device.  An allocation the pool
+ *     cannot satisfy trims the pool itself and retries once.
+ *   trsm_workspace_reserved_bytes: bytes the current device's pool holds
+ *     mapped (in use or idle); 0 without a device or before the first call. */
+int trsm_workspace_trim(size_t keep_bytes);
+size_t trsm_workspace_reserved_bytes(void);
+
 /* Waits for `stream` and returns the device status of the last solve
  * enqueued with this plan: TRSM_SUCCESS or TRSM_ETIMEOUT. */
 int trsm_sync_status(trsm_handle_t h, void* stream);

@@ -78,6 +78,8 @@ SIGNATURES = {
     "trsm_destroy": (None, [_vp]),
     "trsm_plan_sizes": (_int, [_vp, _pi64, _pi64, _pi64]),
     "trsm_plan_device_bytes": (ctypes.c_size_t, [_vp]),
+    "trsm_workspace_trim": (_int, [ctypes.c_size_t]),
+    "trsm_workspace_reserved_bytes": (ctypes.c_size_t, []),
     "trsm_plan_lt": (_vp, [_vp, _pi64]),
     "trsm_sync_status": (_int, [_vp, _vp]),
     "trsm_singular_index": (_i64, []),
@@ -419,6 +421,17 @@ def fp32_peak(iters=8192, device=None):
     s = ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
     _check(load_library().trsm_fp32_peak(int(iters), ctypes.byref(out), s), "trsm_fp32_peak")
     return out.value
+
+
+def workspace_trim(keep_bytes=0):
+    """Returns the library's idle workspace memory on the current device to
+    the system, keeping at most `keep_bytes` reserved."""
+    _check(load_library().trsm_workspace_trim(int(keep_bytes)), "trsm_workspace_trim")
+
+
+def workspace_reserved_bytes():
+    """Bytes the library's workspace pool holds on the current device."""
+    return int(load_library().trsm_workspace_reserved_bytes())
 
 
 def launch_count(reset=False):

@@ -43,14 +43,14 @@ std::vector<trsm::DiagBlock> diag_blocks(int64_t n, int64_t n0, int64_t ld, bool
 int invert_and_check(double* A, int64_t ld, const std::vector<trsm::DiagBlock>& blocks,
                      cudaStream_t s) {
   unsigned long long* sing = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&sing, sizeof(unsigned long long), s);
+  cudaError_t e = trsm::ws_alloc((void**)&sing, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return from_cuda(e);
   unsigned long long h_sing = ULLONG_MAX;
   e = cudaMemsetAsync(sing, 0xFF, sizeof(unsigned long long), s);
   if (e == cudaSuccess) e = trsm::invert_diag_blocks(A, ld, blocks, sing, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&h_sing, sing, sizeof(h_sing), cudaMemcpyDeviceToHost, s);
-  cudaFreeAsync(sing, s);
+  trsm::ws_free(sing, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return from_cuda(e);
   if (h_sing != ULLONG_MAX) {
@@ -96,7 +96,7 @@ template <class Launch>
 int timed_peak(int iters, int blocks, int threads, double* tflops, cudaStream_t s, Launch launch) {
   double* out = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&out, sizeof(double) * blocks * threads, s);
+  cudaError_t e = trsm::ws_alloc((void**)&out, sizeof(double) * blocks * threads, s);
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   float ms = 0.f;
@@ -109,7 +109,7 @@ int timed_peak(int iters, int blocks, int threads, double* tflops, cudaStream_t 
     e = cudaEventSynchronize(e1);
   }
   if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-  if (out) cudaFreeAsync(out, s);
+  if (out) trsm::ws_free(out, s);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   if (e != cudaSuccess) return from_cuda(e);
@@ -205,10 +205,10 @@ int trsm_solve(trsm_handle_t h, const double* B_dev, int64_t k, int64_t ldb, dou
   cudaStream_t s = (cudaStream_t)stream;
   const size_t need = trsm::solve_workspace_bytes(h->n, h->n0, k);
   void* ws = nullptr;
-  cudaError_t e = cudaMallocAsync(&ws, need, s);
+  cudaError_t e = trsm::ws_alloc(&ws, need, s);
   if (e != cudaSuccess) return from_cuda(e);
   e = trsm::solve_enqueue(h->Lt, h->ldt, h->n, h->n0, B_dev, k, ldb, X_dev, ldx, ws, h->status, s);
-  cudaError_t e2 = cudaFreeAsync(ws, s);
+  cudaError_t e2 = trsm::ws_free(ws, s);
   return from_cuda(e != cudaSuccess ? e : e2);
 }
 
@@ -247,11 +247,11 @@ int trsm_host(const double* L_host, int64_t n, int64_t ldl, int64_t n0, const do
   // L~ lives only for this call: stream-ordered allocation (the pool keeps
   // the memory between calls instead of a synchronous cudaMalloc/cudaFree)
   double* Lt = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&Lt, sizeof(double) * (size_t)ld * (size_t)n, s);
+  cudaError_t e = trsm::ws_alloc((void**)&Lt, sizeof(double) * (size_t)ld * (size_t)n, s);
   h->Lt = Lt;
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(int), s);
-  if (e == cudaSuccess && k > 0) e = cudaMallocAsync((void**)&dB, sizeof(double) * (size_t)ld * (size_t)k, s);
+  if (e == cudaSuccess && k > 0) e = trsm::ws_alloc((void**)&dB, sizeof(double) * (size_t)ld * (size_t)k, s);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cin, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cout, cudaStreamNonBlocking);
   for (int64_t c = 0; c * kc < k && e == cudaSuccess; ++c) {
@@ -299,8 +299,8 @@ int trsm_host(const double* L_host, int64_t n, int64_t ldl, int64_t n0, const do
     if (e2 == cudaSuccess) e2 = e3;
   }
   if (rc == TRSM_SUCCESS) rc = trsm_sync_status(h, stream);
-  if (dB) cudaFreeAsync(dB, s);
-  if (Lt) cudaFreeAsync(Lt, s);
+  if (dB) trsm::ws_free(dB, s);
+  if (Lt) trsm::ws_free(Lt, s);
   h->Lt = nullptr;
   cudaError_t e4 = cudaStreamSynchronize(s);
   if (rc == TRSM_SUCCESS) rc = from_cuda(e2 != cudaSuccess ? e2 : e4);

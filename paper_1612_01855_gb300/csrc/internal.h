@@ -79,6 +79,25 @@ cudaError_t solve_enqueue(const double* Lt, int64_t ldt, int64_t n, int64_t n0, 
 int* plan_status_word(trsm_handle_t h);
 int plan_device(trsm_handle_t h);
 
+// Stream-ordered device allocations of the library's workspaces.  They come
+// from a library-owned memory pool of the current device that keeps freed
+// memory for reuse: the device's default pool returns freed memory to the
+// system at every synchronisation, and a large workspace then pays its
+// mapping again at each call (about 1 ms per GB).  trsm_workspace_trim
+// returns the pool's idle memory (pool.cu).
+cudaError_t ws_alloc(void** p, size_t bytes, cudaStream_t s);
+cudaError_t ws_free(void* p, cudaStream_t s);
+template <class T>
+cudaError_t ws_alloc(T** p, size_t bytes, cudaStream_t s) {
+  return ws_alloc(reinterpret_cast<void**>(p), bytes, s);
+}
+
+// Unique id of the calling thread's current CUDA context (0 if none is
+// current or the driver entry points are unavailable): caches of device
+// addresses and pools are keyed by it, so that they are remade after a
+// cudaDeviceReset.
+unsigned long long current_context_id();
+
 // Launch accounting (every kernel launch of the library goes through here).
 void count_launch(int64_t n = 1);
 

@@ -650,13 +650,13 @@ extern "C" int trsm_plan_mixed(trsm_handle_t h, const double* L_dev, int64_t ldl
   if (e == cudaSuccess) e = cudaMalloc(&mp->lsl, lbytes);
   mp->bytes = esz * panel_elems + sizeof(double) * n + sizeof(double) * static_cast<size_t>(N * n0 * n0) + lbytes;
   double* tmp = nullptr;
-  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&tmp), sizeof(double) * n * n, s);
+  if (e == cudaSuccess) e = trsm::ws_alloc(reinterpret_cast<void**>(&tmp), sizeof(double) * n * n, s);
   if (e == cudaSuccess && panel_elems > 0) {
     dim3 grid(static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((n * mp->n0p + 255) / 256, 1024))),
               static_cast<unsigned>(N - 1));
     if (mode == 3) {
       unsigned long long* pmax = nullptr;
-      e = cudaMallocAsync(reinterpret_cast<void**>(&pmax), sizeof(unsigned long long) * N, s);
+      e = trsm::ws_alloc(reinterpret_cast<void**>(&pmax), sizeof(unsigned long long) * N, s);
       if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&mp->panel_exp), sizeof(int) * N);
       if (e == cudaSuccess) e = cudaMemsetAsync(pmax, 0, sizeof(unsigned long long) * N, s);
       if (e == cudaSuccess) {
@@ -665,7 +665,7 @@ extern "C" int trsm_plan_mixed(trsm_handle_t h, const double* L_dev, int64_t ldl
                                                           static_cast<__half*>(mp->panels), mp->panel_exp);
         trsm::count_launch(2);
       }
-      if (pmax) cudaFreeAsync(pmax, s);
+      if (pmax) trsm::ws_free(pmax, s);
       mp->bytes += sizeof(int) * N;
     } else if (mode == 1)
       trsm::pack_panels_kernel<1><<<grid, 256, 0, s>>>(L_dev, ldl, n, n0, mp->n0p, static_cast<float*>(mp->panels));
@@ -706,7 +706,7 @@ extern "C" int trsm_plan_mixed(trsm_handle_t h, const double* L_dev, int64_t ldl
     mp->Ls = trsm::sliced_operand_view(mp->lsl, n, n);
     e = trsm::slice_lower_rows(L_dev, ldl, n, mp->Ls, tmp, s);
   }
-  if (tmp) cudaFreeAsync(tmp, s);
+  if (tmp) trsm::ws_free(tmp, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -762,7 +762,7 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
   const size_t oWt = off;  // tf32 planes of W_i (tensor-core diagonal multiply)
   if (stc) off = trsm::align256(off + sizeof(float) * 3 * static_cast<size_t>(k) * n0p);
   unsigned char* ws = nullptr;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), off, s);
+  cudaError_t e = trsm::ws_alloc(reinterpret_cast<void**>(&ws), off, s);
   if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? TRSM_ENOMEM : TRSM_ECUDA;
   double* R = reinterpret_cast<double*>(ws + oR);
   double* D = reinterpret_cast<double*>(ws + oD);
@@ -938,7 +938,7 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
   }
   int herr = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
-  cudaFreeAsync(ws, s);
+  trsm::ws_free(ws, s);
   cudaError_t e2 = cudaStreamSynchronize(s);
   if (e == cudaSuccess) e = e2;
   if (e != cudaSuccess) {
@@ -959,14 +959,14 @@ extern "C" int trsm_residual_plan(trsm_handle_t h, const double* X_dev, int64_t 
   const size_t xb = trsm::align256(trsm::sliced_operand_bytes(k, n));
   const size_t pb = trsm::align256(trsm::sliced_partial_bytes(n, k));
   unsigned char* buf = nullptr;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&buf), xb + pb, s);
+  cudaError_t e = trsm::ws_alloc(reinterpret_cast<void**>(&buf), xb + pb, s);
   if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? TRSM_ENOMEM : TRSM_ECUDA;
   const trsm::SlicedOperand Xs = trsm::sliced_operand_view(buf, k, n);
   e = trsm::slice_rows(X_dev, ldx, Xs, s);
   if (e == cudaSuccess)
     e = trsm::sliced_residual(h->mixed->Ls, h->mixed->diag, 0, Xs, X_dev, ldx, B_dev, ldb, R_dev, ldr, buf + xb, true,
                               planes, err_dev, s);
-  cudaFreeAsync(buf, s);
+  trsm::ws_free(buf, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return TRSM_ECUDA;

@@ -27,8 +27,6 @@
 // the unique id of the CUDA context the address was taken in: after a
 // cudaDeviceReset (or any other teardown of the device's primary context)
 // the next call sees a new context and takes the address again.
-#include <cuda.h>
-#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -51,42 +49,18 @@ struct ScratchAddr {
 std::mutex g_scratch_mutex;
 ScratchAddr g_scratch_addr[kMaxDevices];
 
-// Unique id of the calling thread's current context (0 if none is current or
-// the driver entry points are unavailable).
-unsigned long long current_context_id() {
-  static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
-  static PFN_cuCtxGetId_v12000 get_id = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      get_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
-    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(p);
-  });
-  if (!get_current || !get_id) return 0;
-  CUcontext ctx = nullptr;
-  unsigned long long id = 0;
-  if (get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return 0;
-  if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
-  return id;
-}
-
 // Device address of the scratch array on the current device: taken at the
 // first use per device and context, cached afterwards.
 cudaError_t scratch_address(int dev, void** out) {
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
   ScratchAddr& c = g_scratch_addr[dev];
-  const unsigned long long id = current_context_id();
+  const unsigned long long id = trsm::current_context_id();
   if (c.addr == nullptr || id == 0 || id != c.ctx_id) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // makes the device's context current
     if (e != cudaSuccess) return e;
     c.addr = p;
-    c.ctx_id = current_context_id();
+    c.ctx_id = trsm::current_context_id();
   }
   *out = c.addr;
   return cudaSuccess;

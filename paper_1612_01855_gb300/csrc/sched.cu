@@ -203,7 +203,7 @@ extern "C" int trsm_solve_schedule(trsm_handle_t h, const double* B_dev, int64_t
   const int64_t ld = (h->n + 3) / 4 * 4;
   const size_t panel = sizeof(double) * static_cast<size_t>(ld) * static_cast<size_t>(k);
   double* ws = nullptr;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), schedule == TRSM_SCHED_RIGHT_LOOKING ? 2 * panel : panel, s);
+  cudaError_t e = trsm::ws_alloc(reinterpret_cast<void**>(&ws), schedule == TRSM_SCHED_RIGHT_LOOKING ? 2 * panel : panel, s);
   if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? TRSM_ENOMEM : TRSM_ECUDA;
   double* W = ws;
   e = trsm::copy_panel(B_dev, ldb, W, ld, h->n, k, s);
@@ -224,7 +224,7 @@ extern "C" int trsm_solve_schedule(trsm_handle_t h, const double* B_dev, int64_t
   } else if (e == cudaSuccess) {
     e = trsm::recursive(h, 0, h->N, W, ld, X_dev, ldx, k, s);
   }
-  cudaFreeAsync(ws, s);
+  trsm::ws_free(ws, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? TRSM_ENOMEM : TRSM_ECUDA;

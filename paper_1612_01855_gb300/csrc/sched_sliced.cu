@@ -75,16 +75,20 @@ int solve_sliced(trsm_plan_s* h, const double* B, int64_t k, int64_t ldb, double
   const int64_t ld = (n + 3) / 4 * 4;
   const size_t wbytes = al256(sizeof(double) * static_cast<size_t>(ld) * static_cast<size_t>(k));
   const size_t pbytes = sliced_operand_bytes(k, nb, nb);
+  // With two block rows or fewer there is no far update (see below), and
+  // one block row has no update at all.
+  const bool lookahead = N > 2;
+  const int nxp = lookahead ? 2 : (N > 1 ? 1 : 0);
   unsigned char* ws = nullptr;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), wbytes + 3 * pbytes + 256, s);
+  cudaError_t e = trsm::ws_alloc(reinterpret_cast<void**>(&ws), wbytes + (1 + nxp) * pbytes + 256, s);
   if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? TRSM_ENOMEM : TRSM_ECUDA;
   double* W = reinterpret_cast<double*>(ws);
   const SlicedOperand Wp = sliced_operand_view(ws + wbytes, k, nb, nb);
-  // two buffers for the planes of X(S_i): the far update of block row i
-  // reads one while block row i + 1 fills the other
-  const SlicedOperand Xp[2] = {sliced_operand_view(ws + wbytes + pbytes, k, nb, nb),
-                               sliced_operand_view(ws + wbytes + 2 * pbytes, k, nb, nb)};
-  int* err = reinterpret_cast<int*>(ws + wbytes + 3 * pbytes);
+  // planes of X(S_i), in two buffers under look-ahead: the far update of
+  // block row i reads one while block row i + 1 fills the other
+  SlicedOperand Xp[2];
+  for (int b = 0; b < nxp; ++b) Xp[b] = sliced_operand_view(ws + wbytes + (1 + b) * pbytes, k, nb, nb);
+  int* err = reinterpret_cast<int*>(ws + wbytes + (1 + nxp) * pbytes);
   // Look-ahead: the chain of block rows (planes of W(S_i), the diagonal
   // multiply, planes of X(S_i), the update of the next block row S_{i+1})
   // runs on a high-priority stream; the rest of each trailing update,
@@ -93,12 +97,16 @@ int solve_sliced(trsm_plan_s* h, const double* B, int64_t k, int64_t ldb, double
   // S_{i+1} receive the far update of block row i - 1 before the near
   // update of block row i (same stream order as the plain loop, so the
   // results are bitwise those of the plain right-looking order).
-  cudaStream_t chain = nullptr, side = nullptr;
+  // With two block rows or fewer there is no far update: everything stays
+  // on the caller's stream.
+  cudaStream_t chain = s, side = s;
   cudaEvent_t ev_x = nullptr, ev_far = nullptr, ev_join = nullptr;
   int lo = 0, hi = 0;
-  if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
-  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&chain, cudaStreamNonBlocking, hi);
-  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, lo);
+  if (lookahead) {
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&chain, cudaStreamNonBlocking, hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, lo);
+  }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_x, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_far, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming);
@@ -118,7 +126,7 @@ int solve_sliced(trsm_plan_s* h, const double* B, int64_t k, int64_t ldb, double
     if (e != cudaSuccess || i == N - 1) break;
     // planes of X(S_i) (their buffer was last read by block row i - 2's
     // updates, which the chain has waited for)
-    const SlicedOperand& xp = Xp[i & 1];
+    const SlicedOperand& xp = Xp[lookahead ? (i & 1) : 0];
     e = slice_rows_prefix(X + s0, ldx, m, xp, chain);
     if (e == cudaSuccess) e = cudaEventRecord(ev_x, chain);
     // W(S_{i+1}) -= L(S_{i+1}, S_i) X(S_i), after block row i - 1's far update
@@ -151,9 +159,11 @@ int solve_sliced(trsm_plan_s* h, const double* B, int64_t k, int64_t ldb, double
   if (ev_x) cudaEventDestroy(ev_x);
   if (ev_far) cudaEventDestroy(ev_far);
   if (ev_join) cudaEventDestroy(ev_join);
-  if (chain) cudaStreamDestroy(chain);  // deferred by the runtime until their work completes
-  if (side) cudaStreamDestroy(side);
-  cudaFreeAsync(ws, s);
+  if (lookahead) {
+    if (chain) cudaStreamDestroy(chain);  // deferred by the runtime until their work completes
+    if (side) cudaStreamDestroy(side);
+  }
+  trsm::ws_free(ws, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? TRSM_ENOMEM : TRSM_ECUDA;
@@ -177,7 +187,7 @@ extern "C" int trsm_plan_sliced(trsm_handle_t h, void* stream) {
   const size_t db = sizeof(double) * static_cast<size_t>(n);
   cudaError_t e = cudaMalloc(&sp->buf, ob + ib + db);
   double* tmp = nullptr;
-  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&tmp), sizeof(double) * n * std::max(n, nb), s);
+  if (e == cudaSuccess) e = trsm::ws_alloc(reinterpret_cast<void**>(&tmp), sizeof(double) * n * std::max(n, nb), s);
   if (e == cudaSuccess && N > 1) {
     sp->off = trsm::sliced_operand_view(sp->buf, n, n, nb);
     e = trsm::slice_offdiag_block_rows(h->Lt, h->ldt, n, nb, sp->off, tmp, s);
@@ -187,7 +197,7 @@ extern "C" int trsm_plan_sliced(trsm_handle_t h, void* stream) {
     sp->diag = reinterpret_cast<double*>(static_cast<unsigned char*>(sp->buf) + ob + ib);
     e = trsm::slice_inverse_block_rows(h->Lt, h->ldt, n, nb, sp->inv, sp->diag, tmp, s);
   }
-  if (tmp) cudaFreeAsync(tmp, s);
+  if (tmp) trsm::ws_free(tmp, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     cudaGetLastError();

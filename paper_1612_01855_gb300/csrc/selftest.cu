@@ -54,7 +54,7 @@ extern "C" int trsm_wait_selftest(int kind, int64_t limit_us, void* stream) {
   if ((kind != 0 && kind != 1) || limit_us < 1 || limit_us > 2000000) return TRSM_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int* buf = nullptr;  // [0]: the counter nobody raises, [1]: the error word
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&buf), 2 * sizeof(int), s);
+  cudaError_t e = trsm::ws_alloc(reinterpret_cast<void**>(&buf), 2 * sizeof(int), s);
   if (e != cudaSuccess) return TRSM_ENOMEM;
   e = cudaMemsetAsync(buf, 0, 2 * sizeof(int), s);
   const long long limit_ns = static_cast<long long>(limit_us) * 1000;
@@ -68,7 +68,7 @@ extern "C" int trsm_wait_selftest(int kind, int64_t limit_us, void* stream) {
   }
   int h_err = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, buf + 1, sizeof(int), cudaMemcpyDeviceToHost, s);
-  cudaFreeAsync(buf, s);
+  trsm::ws_free(buf, s);
   cudaError_t e2 = cudaStreamSynchronize(s);
   if (e == cudaSuccess) e = e2;
   if (e != cudaSuccess) {

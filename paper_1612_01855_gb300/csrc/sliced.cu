@@ -861,7 +861,7 @@ extern "C" int trsm_residual_sliced(const double* L_dev, int64_t n, int64_t ldl,
   const size_t tb = sizeof(double) * static_cast<size_t>(n) * n;
   const size_t pb = (trsm::sliced_partial_bytes(n, k) + 255) / 256 * 256;
   unsigned char* buf = nullptr;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&buf), lb + xb + tb + pb, s);
+  cudaError_t e = trsm::ws_alloc(reinterpret_cast<void**>(&buf), lb + xb + tb + pb, s);
   if (e != cudaSuccess) return -3;
   trsm::SlicedOperand Ls = trsm::sliced_operand_view(buf, n, n);
   trsm::SlicedOperand Xs = trsm::sliced_operand_view(buf + lb, k, n);
@@ -870,7 +870,7 @@ extern "C" int trsm_residual_sliced(const double* L_dev, int64_t n, int64_t ldl,
   if (e == cudaSuccess)
     e = trsm::sliced_residual(Ls, L_dev, ldl, Xs, X_dev, ldx, B_dev, ldb, R_dev, ldr, buf + lb + xb + tb,
                               true, planes, err_dev, s);
-  cudaFreeAsync(buf, s);
+  trsm::ws_free(buf, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return -4;

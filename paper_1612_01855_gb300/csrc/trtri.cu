@@ -298,12 +298,12 @@ cudaError_t invert_diag_blocks(double* A, int64_t ld, const std::vector<DiagBloc
   }
   void* desc = nullptr;
   double* T = nullptr;
-  cudaError_t e = cudaMallocAsync(&desc, host.size(), s);
+  cudaError_t e = trsm::ws_alloc(&desc, host.size(), s);
   if (e != cudaSuccess) return e;
   if (scratch_elems > 0) {
-    e = cudaMallocAsync((void**)&T, sizeof(double) * (size_t)scratch_elems, s);
+    e = trsm::ws_alloc((void**)&T, sizeof(double) * (size_t)scratch_elems, s);
     if (e != cudaSuccess) {
-      cudaFreeAsync(desc, s);
+      trsm::ws_free(desc, s);
       return e;
     }
   }
@@ -331,8 +331,8 @@ cudaError_t invert_diag_blocks(double* A, int64_t ld, const std::vector<DiagBloc
       d_nodes += nn;
     }
   }
-  if (T) cudaFreeAsync(T, s);
-  cudaFreeAsync(desc, s);
+  if (T) trsm::ws_free(T, s);
+  trsm::ws_free(desc, s);
   return e;
 }
 

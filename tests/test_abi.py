@@ -119,6 +119,18 @@ def test_every_entry_point_checks_its_arguments_on_the_host():
     assert lib.trsm_wait_selftest(0, 0, None) == E
 
 
+def test_workspace_pool_queries_without_gpu():
+    """The pool queries need no device work: without a GPU the trim reports
+    the missing device and nothing is reserved."""
+    import torch
+    from paper_1612_01855_gb300 import binding
+    lib = binding.load_library()
+    if torch.cuda.is_available():
+        pytest.skip("host-only check")
+    assert lib.trsm_workspace_reserved_bytes() == 0
+    assert lib.trsm_workspace_trim(0) == binding.TRSM_ECUDA
+
+
 def _imports(path):
     src = open(path).read()
     return re.findall(r"^\s*(?:from|import)\s+([\w\.]+)", src, flags=re.M)
