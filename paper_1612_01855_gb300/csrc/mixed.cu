@@ -343,12 +343,26 @@ __global__ void extract_diag_kernel(const double* __restrict__ L, int64_t ldl, i
   }
 }
 
+// The element-wise passes over n x k column-major panels (R to FP32, X +=
+// D) take two rows per thread, as one 16-byte load of an FP64 pair, when
+// every leading dimension is even and every base 16-byte aligned (kVec);
+// the columns are spread over grid.y, several per CTA (grid_pairs).
+template <bool kVec>
 __global__ void to_float_kernel(const double* __restrict__ R, int64_t ldr, float* __restrict__ W,
                                 int64_t ldw, int64_t n, int64_t k) {
-  for (int64_t j = blockIdx.y; j < k; j += gridDim.y)
-    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+  const int64_t i = 2 * (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x);
+  if (i >= n) return;
+  const bool pair = i + 1 < n;
+#pragma unroll 4
+  for (int64_t j = blockIdx.y; j < k; j += gridDim.y) {
+    if (kVec && pair) {
+      const double2 v = *reinterpret_cast<const double2*>(R + j * ldr + i);
+      *reinterpret_cast<float2*>(W + j * ldw + i) = make_float2(static_cast<float>(v.x), static_cast<float>(v.y));
+    } else {
       W[j * ldw + i] = static_cast<float>(R[j * ldr + i]);
+      if (pair) W[j * ldw + i + 1] = static_cast<float>(R[j * ldr + i + 1]);
+    }
+  }
 }
 
 // D_i = L~_ii W_i (FP64 DFMA), written to D (FP64) and, transposed and
@@ -411,90 +425,46 @@ __global__ void __launch_bounds__(NTHREADS) s_step_kernel(const TA* __restrict__
 }
 
 // The same step in FP32 arithmetic (TRSM_SOLVE_S_FP32), register-blocked
-// for the FFMA pipes: a 64 x 64 output tile per CTA of 256 threads, 4 x 4
-// outputs per thread, K staged through shared memory in chunks of 32 and
-// read back as float4 (16 FMAs per 8 loads; the generic 32 x 32 tile
-// makes 8 per 6).
-constexpr int kS32Tile = 64;
+// for the FFMA pipes: a 128 x 32 output tile per CTA of 128 threads, 8 x 4
+// outputs per thread (rows 4 rg + i and 64 + 4 rg + i, columns 4 cg + c),
+// K staged through shared memory in chunks of 32 and read back as float4:
+// per step along K a warp reads three 128-byte rows of shared memory for
+// 32 FMAs a thread, which keeps the shared-memory pipe below the FMA pipes.
+//   - The next chunk's global loads are issued into registers before the
+//     current chunk's FMAs (two shared-memory buffers, one barrier per
+//     chunk); with 16-byte aligned operands (kVec) they are float4 loads.
+//   - One tile per CTA, the row tiles with the longest K ranges (L~_ii is
+//     lower triangular) first: the CTAs that start later are the short
+//     ones, and they fill in behind the long ones on every SM.
+//   - The output tile goes out through shared memory, so that each warp
+//     stores 32 consecutive rows of one column.
+// Every output is the FMA chain over t = 0, 1, ... in order, the values of
+// the 32 x 32 tile of s_step_kernel in FP32.
+// 16-byte asynchronous copy global -> shared, bypassing L1; `valid` false
+// writes zeros (src-size 0: nothing is read from gsrc).
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, bool valid) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(sdst));
+  const int sz = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gsrc), "r"(sz) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+constexpr int kS32Rows = 128;
+constexpr int kS32Cols = 32;
 constexpr int kS32Chunk = 32;
-constexpr int kS32Threads = 256;
+constexpr int kS32Threads = 128;
 struct S32Smem {
-  float a[kS32Chunk][kS32Tile + 4];  // a[kk][row]: rows 16-byte aligned for float4 reads
-  float b[kS32Chunk][kS32Tile + 4];  // b[kk][col]
+  union {
+    struct {
+      float a[2][kS32Chunk][kS32Rows + 4];  // a[buf][kk][row]: rows 16-byte aligned for float4 reads
+      float b[2][kS32Chunk][kS32Cols + 4];  // b[buf][kk][col]
+    } in;
+    float out[kS32Cols][kS32Rows + 1];  // out[col][row]
+  };
 };
 
-template <int kMode>
-__device__ __forceinline__ void s32_tile(const float* __restrict__ La, int64_t lda, const float* __restrict__ W,
-                                         int64_t ldw, double* __restrict__ D, int64_t ldd,
-                                         typename LowP<kMode>::T* __restrict__ Dt, int64_t n0p, int64_t s0, int m,
-                                         int64_t k, int r, int j, S32Smem& sm, unsigned long long* dmax) {
-  const int tid = threadIdx.x;
-  const int ty = tid >> 4, tx = tid & 15;
-  const int mr = min(kS32Tile, m - r * kS32Tile);
-  const int nc = static_cast<int>(imin64(kS32Tile, k - static_cast<int64_t>(j) * kS32Tile));
-  const int kend = min((r + 1) * kS32Tile, m);  // L~_ii is lower triangular
-  const float* A = La + static_cast<int64_t>(r) * kS32Tile;  // A(row, t) = A[t lda + row]
-  const float* B = W + static_cast<int64_t>(j) * kS32Tile * ldw + s0;         // B(t, col) = B[col ldw + t]
-  float acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) acc[i][c] = 0.f;
-  for (int k0 = 0; k0 < kend; k0 += kS32Chunk) {
-#pragma unroll
-    for (int it = 0; it < (kS32Tile * kS32Chunk) / kS32Threads; ++it) {
-      const int row = tid & 63, kk = (tid >> 6) + 4 * it, t = k0 + kk;
-      sm.a[kk][row] = (row < mr && t < kend) ? A[static_cast<int64_t>(t) * lda + row] : 0.f;
-    }
-#pragma unroll
-    for (int it = 0; it < (kS32Tile * kS32Chunk) / kS32Threads; ++it) {
-      const int kk = tid & 31, col = (tid >> 5) + 8 * it, t = k0 + kk;
-      sm.b[kk][col] = (col < nc && t < kend) ? B[static_cast<int64_t>(col) * ldw + t] : 0.f;
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int kk = 0; kk < kS32Chunk; ++kk) {
-      const float4 av = *reinterpret_cast<const float4*>(&sm.a[kk][ty * 4]);
-      const float4 bv = *reinterpret_cast<const float4*>(&sm.b[kk][tx * 4]);
-      const float a4[4] = {av.x, av.y, av.z, av.w}, b4[4] = {bv.x, bv.y, bv.z, bv.w};
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[i][c] = fmaf(a4[i], b4[c], acc[i][c]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int rr = ty * 4 + i;
-    if (rr >= mr) continue;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int cc = tx * 4 + c;
-      if (cc >= nc) continue;
-      const int64_t col = static_cast<int64_t>(j) * kS32Tile + cc;
-      const int64_t row = static_cast<int64_t>(r) * kS32Tile + rr;
-      D[col * ldd + s0 + row] = static_cast<double>(acc[i][c]);
-      LowP<kMode>::put(Dt + col * n0p + row, k * n0p, acc[i][c]);
-    }
-  }
-  if constexpr (kMode == 3) {
-    // in the accumulator's own type (FP32 here keeps the FP64 pipe free);
-    // like fmax, a NaN never replaces the running maximum
-    using A = typename std::remove_reference<decltype(acc[0][0])>::type;
-    A mx = A(0);
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const A a = acc[i][c] < A(0) ? -acc[i][c] : acc[i][c];
-        mx = a > mx ? a : mx;
-      }
-    fold_max(static_cast<double>(mx), dmax);
-  }
-}
-
-template <int kMode>
+template <int kMode, bool kVec>
 __global__ void __launch_bounds__(kS32Threads) s_step32_kernel(const float* __restrict__ La, int64_t lda,
                                                                const float* __restrict__ W, int64_t ldw,
                                                                double* __restrict__ D, int64_t ldd,
@@ -502,17 +472,162 @@ __global__ void __launch_bounds__(kS32Threads) s_step32_kernel(const float* __re
                                                                int64_t n0p, int64_t s0, int m, int64_t k,
                                                                unsigned long long* dmax) {
   __shared__ __align__(16) S32Smem sm;
-  const int R = (m + kS32Tile - 1) / kS32Tile;
-  const int p = blockIdx.x, j = blockIdx.y;
-  s32_tile<kMode>(La, lda, W, ldw, D, ldd, Dt, n0p, s0, m, k, p, j, sm, dmax);
-  if (R - 1 - p != p) s32_tile<kMode>(La, lda, W, ldw, D, ldd, Dt, n0p, s0, m, k, R - 1 - p, j, sm, dmax);
+  const int R = (m + kS32Rows - 1) / kS32Rows;
+  const int J = static_cast<int>((k + kS32Cols - 1) / kS32Cols);
+  const int r = R - 1 - static_cast<int>(blockIdx.x / J);
+  const int j = static_cast<int>(blockIdx.x % J);
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int cg = lane & 7, rg = ((tid >> 5) << 2) | (lane >> 3);
+  const int mr = min(kS32Rows, m - r * kS32Rows);
+  const int nc = static_cast<int>(imin64(kS32Cols, k - static_cast<int64_t>(j) * kS32Cols));
+  const int kend = min((r + 1) * kS32Rows, m);  // L~_ii is lower triangular
+  const float* A = La + static_cast<int64_t>(r) * kS32Rows;               // A(row, t) = A[t lda + row]
+  const float* B = W + static_cast<int64_t>(j) * kS32Cols * ldw + s0;     // B(t, col) = B[col ldw + t]
+  // per thread and chunk: 32 elements of A and 8 of B.  With kVec, A goes
+  // straight to shared memory by cp.async (16 bytes, 4 rows; a warp per t)
+  // and B through registers (float4 of 4 t, a lane per column, stored
+  // transposed); mr and kend are multiples of 4 there.  Otherwise both go
+  // through registers element by element.
+  float4 ra[kVec ? 1 : 8], rb[2];
+  auto copy_a = [&](int k0, int buf) {
+#pragma unroll
+    for (int it = 0; it < 8; ++it) {
+      const int e = tid + kS32Threads * it, r4 = (e & 31) * 4, kk = e >> 5, t = k0 + kk;
+      const bool ok = r4 < mr && t < kend;
+      cp_async16(&sm.in.a[buf][kk][r4], ok ? A + static_cast<int64_t>(t) * lda + r4 : La, ok);
+    }
+    cp_async_commit();
+  };
+  auto load = [&](int k0) {
+    if constexpr (kVec) {
+#pragma unroll
+      for (int it = 0; it < 2; ++it) {
+        const int e = tid + kS32Threads * it, col = e & 31, t4 = k0 + (e >> 5) * 4;
+        rb[it] = (col < nc && t4 < kend) ? *reinterpret_cast<const float4*>(B + static_cast<int64_t>(col) * ldw + t4)
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    } else {
+      float* fa = reinterpret_cast<float*>(ra);
+      float* fb = reinterpret_cast<float*>(rb);
+#pragma unroll
+      for (int it = 0; it < 32; ++it) {
+        const int e = tid + kS32Threads * it, row = e & 127, t = k0 + (e >> 7);
+        fa[it] = (row < mr && t < kend) ? A[static_cast<int64_t>(t) * lda + row] : 0.f;
+      }
+#pragma unroll
+      for (int it = 0; it < 8; ++it) {
+        const int e = tid + kS32Threads * it, t = k0 + (e & 31), col = e >> 5;
+        fb[it] = (col < nc && t < kend) ? B[static_cast<int64_t>(col) * ldw + t] : 0.f;
+      }
+    }
+  };
+  auto store = [&](int buf) {
+    if constexpr (kVec) {
+#pragma unroll
+      for (int it = 0; it < 2; ++it) {
+        const int e = tid + kS32Threads * it, col = e & 31, kk = (e >> 5) * 4;
+        sm.in.b[buf][kk][col] = rb[it].x;
+        sm.in.b[buf][kk + 1][col] = rb[it].y;
+        sm.in.b[buf][kk + 2][col] = rb[it].z;
+        sm.in.b[buf][kk + 3][col] = rb[it].w;
+      }
+    } else {
+      const float* fa = reinterpret_cast<const float*>(ra);
+      const float* fb = reinterpret_cast<const float*>(rb);
+#pragma unroll
+      for (int it = 0; it < 32; ++it) {
+        const int e = tid + kS32Threads * it;
+        sm.in.a[buf][e >> 7][e & 127] = fa[it];
+      }
+#pragma unroll
+      for (int it = 0; it < 8; ++it) {
+        const int e = tid + kS32Threads * it;
+        sm.in.b[buf][e & 31][e >> 5] = fb[it];
+      }
+    }
+  };
+  float acc[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[i][c] = 0.f;
+  if constexpr (kVec) copy_a(0, 0);
+  load(0);
+  store(0);
+  if constexpr (kVec) cp_async_wait_all();
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < kend; k0 += kS32Chunk) {
+    const bool more = k0 + kS32Chunk < kend;
+    if (more) {
+      if constexpr (kVec) copy_a(k0 + kS32Chunk, buf ^ 1);
+      load(k0 + kS32Chunk);
+    }
+#pragma unroll 8
+    for (int kk = 0; kk < kS32Chunk; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&sm.in.a[buf][kk][rg * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&sm.in.a[buf][kk][64 + rg * 4]);
+      const float4 bv = *reinterpret_cast<const float4*>(&sm.in.b[buf][kk][cg * 4]);
+      const float a8[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float b4[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[i][c] = fmaf(a8[i], b4[c], acc[i][c]);
+    }
+    // the other buffer was last read before the previous barrier
+    if (more) {
+      store(buf ^ 1);
+      if constexpr (kVec) cp_async_wait_all();
+    }
+    __syncthreads();
+    buf ^= 1;
+  }
+  // every thread has passed the last barrier and no copy is in flight: the
+  // input buffers are free
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) sm.out[cg * 4 + c][(i >> 2) * 64 + rg * 4 + (i & 3)] = acc[i][c];
+  __syncthreads();
+  for (int e = tid; e < kS32Rows * kS32Cols; e += kS32Threads) {
+    const int cc = e >> 7, rr = e & 127;
+    if (cc >= nc || rr >= mr) continue;
+    const float v = sm.out[cc][rr];
+    const int64_t col = static_cast<int64_t>(j) * kS32Cols + cc;
+    const int64_t row = static_cast<int64_t>(r) * kS32Rows + rr;
+    D[col * ldd + s0 + row] = static_cast<double>(v);
+    LowP<kMode>::put(Dt + col * n0p + row, k * n0p, v);
+  }
+  if constexpr (kMode == 3) {
+    // in FP32 (keeps the FP64 pipe free); like fmax, a NaN never replaces
+    // the running maximum (the padding outside the tile holds zeros)
+    float mx = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float a = acc[i][c] < 0.f ? -acc[i][c] : acc[i][c];
+        mx = a > mx ? a : mx;
+      }
+    fold_max(static_cast<double>(mx), dmax);
+  }
 }
 
-// Launches the diagonal-block multiply of one block row in the given
-// inner precision: FP64 (DFMA) or FP32 arithmetic; blocks of 512 rows and
-// more take the register-blocked FP32 tile, which gives smaller blocks too
-// few CTAs (measured: n0 = 256 slower, 1024 faster).  Lt: L~ (FP64, ld
-// ldt); Lf: the FP32 copy of this block row's L~_ii (ld ldf).
+inline bool lda_ok(int64_t ld) { return ld % 4 == 0; }
+
+// The FP32 tile kernel holds 42 KB of shared memory per CTA: with the whole
+// unified L1 as shared memory, five CTAs fit on an SM.
+template <int kMode, bool kVec>
+void launch_s32(dim3 g, const float* Lf, int64_t ldf, const float* W, int64_t ld, double* D,
+                typename LowP<kMode>::T* dt, int64_t n0p, int64_t s0, int m, int64_t k, unsigned long long* dmax,
+                cudaStream_t s) {
+  if (cudaFuncSetAttribute(s_step32_kernel<kMode, kVec>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+    cudaGetLastError();  // a preference only
+  s_step32_kernel<kMode, kVec><<<g, kS32Threads, 0, s>>>(Lf, ldf, W, ld, D, ld, dt, n0p, s0, m, k, dmax);
+}
+
 template <int kMode>
 void launch_s_step(bool s32, const double* Lt, int64_t ldt, const float* Lf, int64_t ldf, const float* W,
                    int64_t ld, double* D, void* Dt, int64_t n0p, int64_t s0, int m, int64_t k,
@@ -521,38 +636,90 @@ void launch_s_step(bool s32, const double* Lt, int64_t ldt, const float* Lf, int
   T* dt = static_cast<T*>(Dt);
   const int R = (m + TILE - 1) / TILE;
   const dim3 g(static_cast<unsigned>((R + 1) / 2), static_cast<unsigned>((k + TILE - 1) / TILE));
-  const int R32 = (m + kS32Tile - 1) / kS32Tile;
-  const dim3 g32(static_cast<unsigned>((R32 + 1) / 2), static_cast<unsigned>((k + kS32Tile - 1) / kS32Tile));
+  const int64_t tiles32 = static_cast<int64_t>((m + kS32Rows - 1) / kS32Rows) * ((k + kS32Cols - 1) / kS32Cols);
+  const dim3 g32(static_cast<unsigned>(tiles32));
+  // float4 loads need 16-byte aligned rows of A and columns of W and whole
+  // groups of four at the tile edges
+  const bool vec = lda_ok(ldf) && lda_ok(ld) && s0 % 4 == 0 && m % 4 == 0 &&
+                   reinterpret_cast<uintptr_t>(Lf) % 16 == 0 && reinterpret_cast<uintptr_t>(W) % 16 == 0;
   if (!s32)
     s_step_kernel<kMode, double, double><<<g, NTHREADS, 0, s>>>(Lt + s0 * ldt + s0, ldt, W, ld, D, ld, dt, n0p, s0,
                                                                m, k, dmax);
   else if (m < 512)
     s_step_kernel<kMode, float, float><<<g, NTHREADS, 0, s>>>(Lf, ldf, W, ld, D, ld, dt, n0p, s0, m, k, dmax);
+  else if (vec)
+    launch_s32<kMode, true>(g32, Lf, ldf, W, ld, D, dt, n0p, s0, m, k, dmax, s);
   else
-    s_step32_kernel<kMode><<<g32, kS32Threads, 0, s>>>(Lf, ldf, W, ld, D, ld, dt, n0p, s0, m, k, dmax);
+    launch_s32<kMode, false>(g32, Lf, ldf, W, ld, D, dt, n0p, s0, m, k, dmax, s);
 }
 
-// X += D; folds max|D| and max|X| into norms[0..1] as ordered bit patterns
+// X += D (X = D in the first sweep: kFirst, X not read); folds max|D| and
+// max|X| into norms[0..1] as ordered bit patterns
 // (|v| compared as an unsigned integer: monotone for non-negative doubles,
 // and every NaN pattern lies above inf, so a NaN, once seen, stays the
 // maximum; it is stored as ~0).  Integer maxima keep the FP64 pipe for the
 // additions alone.
+template <bool kVec, bool kFirst>
 __global__ void correct_kernel(double* __restrict__ X, int64_t ldx, const double* __restrict__ D,
                                int64_t ldd, int64_t n, int64_t k,
                                unsigned long long* __restrict__ norms) {
   constexpr unsigned long long kAbs = ~(1ull << 63);
   unsigned long long dm = 0, xm = 0;
-  for (int64_t j = blockIdx.y; j < k; j += gridDim.y)
-    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-      const double d = D[j * ldd + i];
-      const double x = X[j * ldx + i] + d;
-      X[j * ldx + i] = x;
-      const unsigned long long bd = static_cast<unsigned long long>(__double_as_longlong(d)) & kAbs;
-      const unsigned long long bx = static_cast<unsigned long long>(__double_as_longlong(x)) & kAbs;
-      dm = bd > dm ? bd : dm;
-      xm = bx > xm ? bx : xm;
+  auto one = [&](int64_t j, int64_t i) {
+    const double d = D[j * ldd + i];
+    const double x = kFirst ? d : X[j * ldx + i] + d;
+    X[j * ldx + i] = x;
+    const unsigned long long bd = static_cast<unsigned long long>(__double_as_longlong(d)) & kAbs;
+    const unsigned long long bx = static_cast<unsigned long long>(__double_as_longlong(x)) & kAbs;
+    dm = bd > dm ? bd : dm;
+    xm = bx > xm ? bx : xm;
+  };
+  const int64_t i = 2 * (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x);
+  if (i < n) {
+    const bool pair = i + 1 < n;
+    if (kVec && pair) {
+      // four columns' loads issued before their stores (the stores to X
+      // would otherwise order every later load of X behind them)
+      constexpr int U = 4;
+      for (int64_t j0 = blockIdx.y; j0 < k; j0 += U * static_cast<int64_t>(gridDim.y)) {
+        double2 d[U], x[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int64_t j = j0 + u * static_cast<int64_t>(gridDim.y);
+          if (j < k) {
+            d[u] = *reinterpret_cast<const double2*>(D + j * ldd + i);
+            if (!kFirst) x[u] = *reinterpret_cast<const double2*>(X + j * ldx + i);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int64_t j = j0 + u * static_cast<int64_t>(gridDim.y);
+          if (j >= k) continue;
+          if (kFirst) {
+            x[u] = d[u];
+          } else {
+            x[u].x += d[u].x;
+            x[u].y += d[u].y;
+          }
+          *reinterpret_cast<double2*>(X + j * ldx + i) = x[u];
+          const unsigned long long b[4] = {
+              static_cast<unsigned long long>(__double_as_longlong(d[u].x)) & kAbs,
+              static_cast<unsigned long long>(__double_as_longlong(d[u].y)) & kAbs,
+              static_cast<unsigned long long>(__double_as_longlong(x[u].x)) & kAbs,
+              static_cast<unsigned long long>(__double_as_longlong(x[u].y)) & kAbs};
+          dm = b[0] > dm ? b[0] : dm;
+          dm = b[1] > dm ? b[1] : dm;
+          xm = b[2] > xm ? b[2] : xm;
+          xm = b[3] > xm ? b[3] : xm;
+        }
+      }
+    } else {
+      for (int64_t j = blockIdx.y; j < k; j += gridDim.y) {
+        one(j, i);
+        if (pair) one(j, i + 1);
+      }
     }
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const unsigned long long od = __shfl_xor_sync(0xffffffffu, dm, o);
@@ -568,9 +735,9 @@ __global__ void correct_kernel(double* __restrict__ X, int64_t ldx, const double
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int i = 1; i < static_cast<int>(blockDim.x >> 5); ++i) {
-      dm = sd[i] > dm ? sd[i] : dm;
-      xm = sx[i] > xm ? sx[i] : xm;
+    for (int q = 1; q < static_cast<int>(blockDim.x >> 5); ++q) {
+      dm = sd[q] > dm ? sd[q] : dm;
+      xm = sx[q] > xm ? sx[q] : xm;
     }
     constexpr unsigned long long kInf = 0x7FF0000000000000ull;
     atomicMax(norms, dm > kInf ? ~0ull : dm);
@@ -614,10 +781,14 @@ __global__ void __launch_bounds__(NTHREADS) residual_fp64_kernel(
 inline int64_t align4(int64_t x) { return (x + 3) / 4 * 4; }
 inline size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
-dim3 grid_nk(int64_t n, int64_t k) {
-  return dim3(static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 64))),
-              static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(k, 65535))));
+// Grid of the two-rows-per-thread passes (CTAs of 256 threads): the rows
+// of a column across grid.x, about 32 CTAs per SM in all.
+dim3 grid_pairs(int64_t n, int64_t k) {
+  const int64_t gx = std::max<int64_t>(1, (n + 511) / 512);
+  const int64_t gy = std::max<int64_t>(1, std::min<int64_t>({k, int64_t(65535), std::max<int64_t>(1, 32 * 152 / gx)}));
+  return dim3(static_cast<unsigned>(gx), static_cast<unsigned>(gy));
 }
+inline bool pairs_ok(const void* p, int64_t ld) { return ld % 2 == 0 && reinterpret_cast<uintptr_t>(p) % 16 == 0; }
 
 }  // namespace
 
@@ -778,8 +949,8 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
   int rc = TRSM_SUCCESS;
   e = cudaMemsetAsync(err, 0, sizeof(int), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(Dt, 0, esz * n0p * k, s);  // padding columns stay zero
-  if (e == cudaSuccess) e = cudaMemset2DAsync(X_dev, sizeof(double) * ldx, 0, sizeof(double) * n, k, s);
-  if (e == cudaSuccess) e = trsm::copy_panel(B_dev, ldb, R, ld, n, k, s);
+  // The first sweep solves with B itself (its W is made from B_dev) and
+  // sets X = D without reading X.
   double best = HUGE_VAL, prev = HUGE_VAL;
   // digit planes of the sliced residual: the adaptive mode starts with seven
   // and moves to eight when the updates stagnate above tol; the progressive
@@ -793,7 +964,12 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
     // ---- D = inner_solve(R) ----
     e = cudaMemsetAsync(dmax, 0, sizeof(unsigned long long) * N, s);
     if (e != cudaSuccess) break;
-    trsm::to_float_kernel<<<trsm::grid_nk(n, k), 256, 0, s>>>(R, ld, W, ld, n, k);
+    const double* src = it == 1 ? B_dev : R;
+    const int64_t lds = it == 1 ? ldb : ld;
+    if (trsm::pairs_ok(src, lds) && trsm::pairs_ok(W, ld))
+      trsm::to_float_kernel<true><<<trsm::grid_pairs(n, k), 256, 0, s>>>(src, lds, W, ld, n, k);
+    else
+      trsm::to_float_kernel<false><<<trsm::grid_pairs(n, k), 256, 0, s>>>(src, lds, W, ld, n, k);
     trsm::count_launch();
     for (int64_t i = 0; i < N && e == cudaSuccess; ++i) {
       const int64_t s0 = i * n0;
@@ -863,9 +1039,14 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
     // ---- X += D ----
     if (e == cudaSuccess) e = cudaMemsetAsync(norms, 0, 2 * sizeof(unsigned long long), s);
     if (e == cudaSuccess) {
-      dim3 gc(static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 64))),
-              static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(k, 256))));
-      trsm::correct_kernel<<<gc, 256, 0, s>>>(X_dev, ldx, D, ld, n, k, norms);
+      const bool vec = trsm::pairs_ok(X_dev, ldx) && trsm::pairs_ok(D, ld);
+      const dim3 gc = trsm::grid_pairs(n, k);
+      if (it == 1)
+        vec ? trsm::correct_kernel<true, true><<<gc, 256, 0, s>>>(X_dev, ldx, D, ld, n, k, norms)
+            : trsm::correct_kernel<false, true><<<gc, 256, 0, s>>>(X_dev, ldx, D, ld, n, k, norms);
+      else
+        vec ? trsm::correct_kernel<true, false><<<gc, 256, 0, s>>>(X_dev, ldx, D, ld, n, k, norms)
+            : trsm::correct_kernel<false, false><<<gc, 256, 0, s>>>(X_dev, ldx, D, ld, n, k, norms);
       trsm::count_launch();
       e = cudaGetLastError();
     }
