@@ -994,11 +994,12 @@ def run_ours(args, rank, world, local):
                                 "status": b["status"], "err": _sig(b["spot_check_rel_err"])} for b in batched]
         if serving is not None:
             line["serving"] = {"cols": ["offered", "served", "p50_ms", "p99_ms", "fp64_p99_ms", "mixed_p99_ms",
-                                        "sliced", "ok"],
+                                        "wait_p50_ms", "wait_p99_ms", "sliced", "ok"],
                                "rates": [[r["offered_rate"], round(r["solves_per_s"], 1), round(r["p50_ms"], 1),
                                           round(r["p99_ms"], 1), round(r.get("fp64", {}).get("p99_ms", 0.0), 1),
-                                          round(r.get("mixed", {}).get("p99_ms", 0.0), 1), r["sliced_requests"],
-                                          r["statuses_ok"]]
+                                          round(r.get("mixed", {}).get("p99_ms", 0.0), 1),
+                                          round(r.get("wait_p50_ms", 0.0), 2), round(r.get("wait_p99_ms", 0.0), 1),
+                                          r["sliced_requests"], r["statuses_ok"]]
                                          for r in serving["rates"]],
                                "slots": serving["rates"][0]["slots"] if serving["rates"] else None}
         if schedules is not None:

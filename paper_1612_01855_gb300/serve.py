@@ -414,6 +414,12 @@ class Server:
                "batches": self.launches, "slots": self.nstreams, "mixed_slots": self.mixed_slots,
                "peak_inflight_gb": self.adm.peak / 1e9,
                "statuses_ok": all(r.status == 0 for r in order)}
+        # queueing delay (arrival to dispatch): head-of-line blocking shows
+        # here, apart from the spread of the requests' own solve times
+        wait = np.array([r.t_admit - r.arrival for r in order if r.t_admit is not None])
+        if wait.size:
+            out["wait_p50_ms"] = float(np.percentile(wait, 50) * 1e3)
+            out["wait_p99_ms"] = float(np.percentile(wait, 99) * 1e3)
         out["sliced_requests"] = sum(1 for r in order if r.sliced)
         for kind, sel in (("fp64", lambda r: not r.mixed), ("mixed", lambda r: r.mixed)):
             part = [r for r in order if sel(r) and r.latency is not None]
@@ -421,6 +427,9 @@ class Server:
                 pl = np.array([r.latency for r in part])
                 out[kind] = {"requests": len(part), "p50_ms": float(np.percentile(pl, 50) * 1e3),
                              "p99_ms": float(np.percentile(pl, 99) * 1e3)}
+                pw = np.array([r.t_admit - r.arrival for r in part if r.t_admit is not None])
+                if pw.size:
+                    out[kind]["wait_p99_ms"] = float(np.percentile(pw, 99) * 1e3)
                 if kind == "mixed":
                     out[kind]["mean_iterations"] = float(np.mean([r.iterations or 0 for r in part]))
         return out
