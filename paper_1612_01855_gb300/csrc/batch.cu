@@ -152,29 +152,38 @@ __device__ __noinline__ void leaf_invert_block(const T* __restrict__ A, int64_t 
 }
 
 // acc += A(rows [0,m), K [kbeg,kend)) * B(K [kbeg,kend), cols [0,nc)) for a
-// TILE x CW output tile (CW = 8, 16 or 32) on 128 threads: thread (ty, tx)
-// = (tid / (CW/2), tid % (CW/2)) owns rows ty*(CW/8) .. and columns 2 tx,
-// 2 tx + 1; CW = 32 is the layout of the generic tile.  Narrow tiles let
-// systems with few right-hand sides skip most of the padded columns.
+// TILE x CW output tile (CW = 4, 8, 12, 16, 24 or 32) on 128 threads:
+// thread (ty, tx) = (tid / TX, tid % TX) owns TMR rows from ty*TMR and CPT
+// columns from CPT tx, CPT = 3 for CW = 12 and 24, 1 for CW = 4, else 2;
+// every warp holds 8 consecutive rows, and CW = 32 is the layout of the
+// generic tile.  Narrow tiles let systems with few right-hand sides skip
+// most of the padded columns.
 template <int CW>
 struct NarrowMap {
-  static constexpr int TX = CW / 2;
-  static constexpr int TMR = CW / 8;  // rows per thread
+  static constexpr int CPT = CW % 3 == 0 ? 3 : CW == 4 ? 1 : 2;  // columns per thread
+  static constexpr int TX = CW / CPT;                               // threads along the columns
+  static constexpr int TMR = TILE * CW / NTHREADS / CPT;            // rows per thread
+  static_assert(TX * CPT == CW && (NTHREADS / TX) * TMR == TILE && (32 / TX) * TMR == 8, "tile layout");
   __device__ static int row(int i) { return (threadIdx.x / TX) * TMR + i; }
-  __device__ static int col(int j) { return (threadIdx.x % TX) * 2 + j; }
+  __device__ static int col(int j) { return (threadIdx.x % TX) * CPT + j; }
 };
 
 // kTriFrom >= 0: A is lower triangular from K offset kTriFrom on (the
 // diagonal chunk of an S task, A(row, kTriFrom + kk) = 0 for kk > row).
 // Warp w holds rows 8w .. 8w + 7 for every CW, so it stops that chunk after
-// 8w + 8 steps: the products it skips are zeros.
+// 8w + 8 steps: the products it skips are zeros.  For the same reason a
+// warp whose rows all lie at or below m skips the multiply-adds, and every
+// warp stops a chunk at kend (the padding of a short last block row or
+// column; the loads and barriers stay common to all warps).
 template <class TC, bool kAMutable, bool kBMutable, int CW>
 __device__ __forceinline__ void tile_mma_cw(const TC* __restrict__ A, int64_t lda, const TC* __restrict__ B,
                                             int64_t ldb, int m, int nc, int64_t kbeg, int64_t kend,
-                                            TileSmemT<TC>& sm, TC (&acc)[TM][TN], int64_t kTriFrom = -1) {
+                                            TileSmemT<TC>& sm, TC (&acc)[NarrowMap<CW>::TMR][NarrowMap<CW>::CPT],
+                                            int64_t kTriFrom = -1) {
   using Mp = NarrowMap<CW>;
   const int tid = threadIdx.x;
   const int tri_end = 8 * (tid >> 5) + 8;
+  const bool live = 8 * (tid >> 5) < m;  // warp-uniform
   for (int64_t k0 = kbeg; k0 < kend; k0 += KCH) {
 #pragma unroll
     for (int it = 0; it < (KCH * TILE) / NTHREADS; ++it) {
@@ -195,21 +204,30 @@ __device__ __forceinline__ void tile_mma_cw(const TC* __restrict__ A, int64_t ld
       sm.b[kk][c] = v;
     }
     __syncthreads();
-    const int kk_end = (k0 == kTriFrom) ? tri_end : KCH;
+    const int kk_lim = static_cast<int>(imin64(KCH, kend - k0));
+    const int kk_end = !live ? 0 : (k0 == kTriFrom) ? min(tri_end, kk_lim) : kk_lim;
 #pragma unroll 8
     for (int kk = 0; kk < kk_end; ++kk) {
-      TC av[Mp::TMR], bv[2];
+      TC av[Mp::TMR], bv[Mp::CPT];
 #pragma unroll
       for (int i = 0; i < Mp::TMR; ++i) av[i] = sm.a[kk][Mp::row(i)];
 #pragma unroll
-      for (int j = 0; j < 2; ++j) bv[j] = sm.b[kk][Mp::col(j)];
+      for (int j = 0; j < Mp::CPT; ++j) bv[j] = sm.b[kk][Mp::col(j)];
 #pragma unroll
       for (int i = 0; i < Mp::TMR; ++i)
 #pragma unroll
-        for (int j = 0; j < 2; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+        for (int j = 0; j < Mp::CPT; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
     }
     __syncthreads();
   }
+}
+
+template <class T, int CW>
+__device__ __forceinline__ void zero_narrow(T (&acc)[NarrowMap<CW>::TMR][NarrowMap<CW>::CPT]) {
+#pragma unroll
+  for (int i = 0; i < NarrowMap<CW>::TMR; ++i)
+#pragma unroll
+    for (int j = 0; j < NarrowMap<CW>::CPT; ++j) acc[i][j] = T(0);
 }
 
 // X_l[r, j] = L~_ll[r, :] W_l[:, j] (the first block row reads B).
@@ -217,8 +235,8 @@ template <class T, int CW>
 __device__ __forceinline__ void s_body(const BatchSys<T>& a, int l, int r, int j, int64_t s0, int64_t ml,
                                        TileSmemT<T>& sm) {
   using Mp = NarrowMap<CW>;
-  T acc[TM][TN];
-  zero_acc(acc);
+  T acc[Mp::TMR][Mp::CPT];
+  zero_narrow<T, CW>(acc);
   const int m = static_cast<int>(imin64(TILE, ml - static_cast<int64_t>(r) * TILE));
   const int nc = static_cast<int>(imin64(CW, a.k - static_cast<int64_t>(j) * CW));
   const int64_t kend = imin64(static_cast<int64_t>(r + 1) * TILE, ml);
@@ -237,7 +255,7 @@ __device__ __forceinline__ void s_body(const BatchSys<T>& a, int l, int r, int j
     const int rr = Mp::row(i);
     if (rr >= m) continue;
 #pragma unroll
-    for (int jj = 0; jj < 2; ++jj) {
+    for (int jj = 0; jj < Mp::CPT; ++jj) {
       const int cc = Mp::col(jj);
       if (cc >= nc) continue;
       __stcg(a.X + (static_cast<int64_t>(j) * CW + cc) * a.ldx + row0 + rr, acc[i][jj]);
@@ -250,8 +268,8 @@ template <class T, int CW>
 __device__ __forceinline__ void u_body(const BatchSys<T>& a, int l, int i, int r, int j, int64_t s0, int64_t ml,
                                        TileSmemT<T>& sm) {
   using Mp = NarrowMap<CW>;
-  T acc[TM][TN];
-  zero_acc(acc);
+  T acc[Mp::TMR][Mp::CPT];
+  zero_narrow<T, CW>(acc);
   const int64_t si = static_cast<int64_t>(i) * a.n0;
   const int64_t mi = imin64(a.n0, a.n - si);
   const int64_t row0 = si + static_cast<int64_t>(r) * TILE;
@@ -264,7 +282,7 @@ __device__ __forceinline__ void u_body(const BatchSys<T>& a, int l, int i, int r
     const int rr = Mp::row(ii);
     if (rr >= m) continue;
 #pragma unroll
-    for (int jj = 0; jj < 2; ++jj) {
+    for (int jj = 0; jj < Mp::CPT; ++jj) {
       const int cc = Mp::col(jj);
       if (cc >= nc) continue;
       const int64_t col = static_cast<int64_t>(j) * CW + cc;
@@ -762,9 +780,14 @@ __global__ void __launch_bounds__(NTHREADS, 8) batch_kernel(const BatchSys<T>* _
       }
       __syncthreads();
       if (!s_ok) break;
-      if (a.cw == 8) s_body<T, 8>(a, l, r, j, s0, ml, sm);
-      else if (a.cw == 16) s_body<T, 16>(a, l, r, j, s0, ml, sm);
-      else s_body<T, 32>(a, l, r, j, s0, ml, sm);
+      switch (a.cw) {
+        case 4: s_body<T, 4>(a, l, r, j, s0, ml, sm); break;
+        case 8: s_body<T, 8>(a, l, r, j, s0, ml, sm); break;
+        case 12: s_body<T, 12>(a, l, r, j, s0, ml, sm); break;
+        case 16: s_body<T, 16>(a, l, r, j, s0, ml, sm); break;
+        case 24: s_body<T, 24>(a, l, r, j, s0, ml, sm); break;
+        default: s_body<T, 32>(a, l, r, j, s0, ml, sm); break;
+      }
       __threadfence();
       __syncthreads();
       if (tid == 0) atomicAdd(a.xdone + static_cast<int64_t>(l) * a.C + j, 1);
@@ -782,9 +805,14 @@ __global__ void __launch_bounds__(NTHREADS, 8) batch_kernel(const BatchSys<T>* _
       }
       __syncthreads();
       if (!s_ok) break;
-      if (a.cw == 8) u_body<T, 8>(a, l, i, r, j, s0, ml, sm);
-      else if (a.cw == 16) u_body<T, 16>(a, l, i, r, j, s0, ml, sm);
-      else u_body<T, 32>(a, l, i, r, j, s0, ml, sm);
+      switch (a.cw) {
+        case 4: u_body<T, 4>(a, l, i, r, j, s0, ml, sm); break;
+        case 8: u_body<T, 8>(a, l, i, r, j, s0, ml, sm); break;
+        case 12: u_body<T, 12>(a, l, i, r, j, s0, ml, sm); break;
+        case 16: u_body<T, 16>(a, l, i, r, j, s0, ml, sm); break;
+        case 24: u_body<T, 24>(a, l, i, r, j, s0, ml, sm); break;
+        default: u_body<T, 32>(a, l, i, r, j, s0, ml, sm); break;
+      }
       __threadfence();
       __syncthreads();
       if (tid == 0) atomicAdd(a.wdone + q * a.C + j, 1);
@@ -826,7 +854,7 @@ namespace {
 
 // An item whose k is above 32 and not a multiple of it is solved as two
 // parts: its first floor(k / 32) * 32 columns in 32-wide tiles and the rest
-// in one 8-, 16- or 32-wide tile, sharing L and the inverted blocks (only
+// in one 4- to 32-wide tile (fitted_cw), sharing L and the inverted blocks (only
 // the first part inverts them).  A column's arithmetic does not depend on
 // the tile it is in, so the split changes no result; it only drops most of
 // the padded columns of the last tile (on the batching workload the
@@ -839,6 +867,10 @@ struct Part {
   int owner;     // part whose inverted blocks this part reads, or -1
 };
 
+// FP64 tile width fitted to k columns (k <= 32): the narrowest of 4, 8, 12,
+// 16, 24 and 32 that holds them.
+int fitted_cw(int64_t k) { return k <= 4 ? 4 : k <= 8 ? 8 : k <= 12 ? 12 : k <= 16 ? 16 : k <= 24 ? 24 : 32; }
+
 std::vector<Part> split_parts(const trsm_batch_item* items, int count) {
   std::vector<Part> parts;
   for (int s = 0; s < count; ++s) {
@@ -847,9 +879,9 @@ std::vector<Part> split_parts(const trsm_batch_item* items, int count) {
       const int64_t k32 = it.k / 32 * 32, rem = it.k - k32;
       const int own = static_cast<int>(parts.size());
       parts.push_back(Part{s, 0, k32, 32, -1});
-      parts.push_back(Part{s, k32, rem, rem <= 8 ? 8 : rem <= 16 ? 16 : 32, own});
+      parts.push_back(Part{s, k32, rem, fitted_cw(rem), own});
     } else {
-      const int cw = it.tile_cols != 0 ? static_cast<int>(it.tile_cols) : it.k <= 8 ? 8 : it.k <= 16 ? 16 : 32;
+      const int cw = it.tile_cols != 0 ? static_cast<int>(it.tile_cols) : fitted_cw(it.k);
       parts.push_back(Part{s, 0, it.k, cw, -1});
     }
   }
@@ -1165,7 +1197,11 @@ static int validate_items(const trsm_batch_item* items, int count, int dtype) {
     const trsm_batch_item& it = items[s];
     if (it.n < 1 || it.k < 1 || !it.B || !it.X || it.ldb < it.n || it.ldx < it.n || it.B == it.X)
       return TRSM_EINVAL;
-    if (!(it.tile_cols == 0 || it.tile_cols == 8 || it.tile_cols == 16 || it.tile_cols == 32)) return TRSM_EINVAL;
+    // FP64 tiles: 4, 8, 12, 16, 24 or 32 columns; FP32 units: 8, 16 or 32
+    const int64_t tc = it.tile_cols;
+    const bool tc_ok = tc == 0 || tc == 8 || tc == 16 || tc == 32 ||
+                       (dtype == TRSM_F64 && (tc == 4 || tc == 12 || tc == 24));
+    if (!tc_ok) return TRSM_EINVAL;
     if (it.plan) {
       if (dtype != TRSM_F64) return TRSM_EINVAL;
       int64_t pn = 0;

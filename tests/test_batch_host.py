@@ -32,7 +32,10 @@ def test_batch_items_are_validated(host_lib):
     ok = (300, 40, 32, 0)
     assert _size(lib, binding, [ok])[0] == 0
     assert _size(lib, binding, [(300, 40, 48, 0)])[0] == binding.TRSM_EINVAL  # n0 only 32 or 64
-    assert _size(lib, binding, [(300, 40, 32, 12)])[0] == binding.TRSM_EINVAL  # tile width 8, 16, 32
+    assert _size(lib, binding, [(300, 40, 32, 20)])[0] == binding.TRSM_EINVAL  # FP64 widths 4, 8, 12, 16, 24, 32
+    for tile in (4, 12, 24):
+        assert _size(lib, binding, [(300, 40, 32, tile)])[0] == 0
+        assert _size(lib, binding, [(300, 40, 64, tile)], dtype=1)[0] == binding.TRSM_EINVAL  # FP32: 8, 16, 32
     assert _size(lib, binding, [(0, 40, 32, 0)])[0] == binding.TRSM_EINVAL
     assert _size(lib, binding, [(300, 0, 32, 0)])[0] == binding.TRSM_EINVAL
     assert _size(lib, binding, [ok], dtype=2)[0] == binding.TRSM_EINVAL
