@@ -257,9 +257,9 @@ typedef struct trsm_batch_item {
   int64_t ldx;
   int64_t n, k;
   int64_t n0;           /* 32 or 64 when plan == NULL (ignored otherwise)      */
-  int64_t tile_cols;    /* columns per output tile: FP64 4, 8, 12, 16, 24
-                           or 32, FP32 (per CTA) 8, 16 or 32; 0 = fitted to
-                           k (the narrowest width that holds k <= 32, else
+  int64_t tile_cols;    /* columns per output tile: FP64 a multiple of 4
+                           up to 32, FP32 (per CTA) 8, 16 or 32; 0 = fitted
+                           to k (the narrowest width that holds k <= 32, else
                            32-wide tiles and, when 32 does not divide k, one
                            fitted tile for the remainder; results are the
                            same bits either way) */

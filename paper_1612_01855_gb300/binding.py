@@ -442,8 +442,8 @@ class Batch:
     """Many independent systems solved by one persistent launch
     (trsm_batch_*).  `systems` is a list of dicts with keys L (or plan), B,
     X (CUDA tensors, column-major), n0 (32 or 64, plan-less items) and
-    optionally tile_cols (columns per output tile: FP64 4, 8, 12, 16, 24 or
-    32, FP32 8, 16 or 32; default: fitted to k)."""
+    optionally tile_cols (columns per output tile: FP64 a multiple of 4 up
+    to 32, FP32 8, 16 or 32; default: fitted to k)."""
 
     def __init__(self, systems, dtype="f64", arena=None):
         """arena: optional uint8 CUDA tensor to lay the batch out in (no

@@ -152,15 +152,16 @@ __device__ __noinline__ void leaf_invert_block(const T* __restrict__ A, int64_t 
 }
 
 // acc += A(rows [0,m), K [kbeg,kend)) * B(K [kbeg,kend), cols [0,nc)) for a
-// TILE x CW output tile (CW = 4, 8, 12, 16, 24 or 32) on 128 threads:
+// TILE x CW output tile (CW a multiple of 4 up to 32) on 128 threads:
 // thread (ty, tx) = (tid / TX, tid % TX) owns TMR rows from ty*TMR and CPT
-// columns from CPT tx, CPT = 3 for CW = 12 and 24, 1 for CW = 4, else 2;
+// columns from CPT tx, CPT = CW / 4 for CW = 4, 20 and 28, 3 for CW = 12
+// and 24, else 2;
 // every warp holds 8 consecutive rows, and CW = 32 is the layout of the
 // generic tile.  Narrow tiles let systems with few right-hand sides skip
 // most of the padded columns.
 template <int CW>
 struct NarrowMap {
-  static constexpr int CPT = CW % 3 == 0 ? 3 : CW == 4 ? 1 : 2;  // columns per thread
+  static constexpr int CPT = (CW == 4 || CW == 20 || CW == 28) ? CW / 4 : CW % 3 == 0 ? 3 : 2;  // columns per thread
   static constexpr int TX = CW / CPT;                               // threads along the columns
   static constexpr int TMR = TILE * CW / NTHREADS / CPT;            // rows per thread
   static_assert(TX * CPT == CW && (NTHREADS / TX) * TMR == TILE && (32 / TX) * TMR == 8, "tile layout");
@@ -785,7 +786,9 @@ __global__ void __launch_bounds__(NTHREADS, 8) batch_kernel(const BatchSys<T>* _
         case 8: s_body<T, 8>(a, l, r, j, s0, ml, sm); break;
         case 12: s_body<T, 12>(a, l, r, j, s0, ml, sm); break;
         case 16: s_body<T, 16>(a, l, r, j, s0, ml, sm); break;
+        case 20: s_body<T, 20>(a, l, r, j, s0, ml, sm); break;
         case 24: s_body<T, 24>(a, l, r, j, s0, ml, sm); break;
+        case 28: s_body<T, 28>(a, l, r, j, s0, ml, sm); break;
         default: s_body<T, 32>(a, l, r, j, s0, ml, sm); break;
       }
       __threadfence();
@@ -810,7 +813,9 @@ __global__ void __launch_bounds__(NTHREADS, 8) batch_kernel(const BatchSys<T>* _
         case 8: u_body<T, 8>(a, l, i, r, j, s0, ml, sm); break;
         case 12: u_body<T, 12>(a, l, i, r, j, s0, ml, sm); break;
         case 16: u_body<T, 16>(a, l, i, r, j, s0, ml, sm); break;
+        case 20: u_body<T, 20>(a, l, i, r, j, s0, ml, sm); break;
         case 24: u_body<T, 24>(a, l, i, r, j, s0, ml, sm); break;
+        case 28: u_body<T, 28>(a, l, i, r, j, s0, ml, sm); break;
         default: u_body<T, 32>(a, l, i, r, j, s0, ml, sm); break;
       }
       __threadfence();
@@ -867,9 +872,8 @@ struct Part {
   int owner;     // part whose inverted blocks this part reads, or -1
 };
 
-// FP64 tile width fitted to k columns (k <= 32): the narrowest of 4, 8, 12,
-// 16, 24 and 32 that holds them.
-int fitted_cw(int64_t k) { return k <= 4 ? 4 : k <= 8 ? 8 : k <= 12 ? 12 : k <= 16 ? 16 : k <= 24 ? 24 : 32; }
+// FP64 tile width fitted to k columns: the next multiple of 4, at most 32.
+int fitted_cw(int64_t k) { return k >= 32 ? 32 : static_cast<int>((k + 3) / 4 * 4); }
 
 std::vector<Part> split_parts(const trsm_batch_item* items, int count) {
   std::vector<Part> parts;
@@ -1197,10 +1201,10 @@ static int validate_items(const trsm_batch_item* items, int count, int dtype) {
     const trsm_batch_item& it = items[s];
     if (it.n < 1 || it.k < 1 || !it.B || !it.X || it.ldb < it.n || it.ldx < it.n || it.B == it.X)
       return TRSM_EINVAL;
-    // FP64 tiles: 4, 8, 12, 16, 24 or 32 columns; FP32 units: 8, 16 or 32
+    // FP64 tiles: a multiple of 4 up to 32 columns; FP32 units: 8, 16 or 32
     const int64_t tc = it.tile_cols;
     const bool tc_ok = tc == 0 || tc == 8 || tc == 16 || tc == 32 ||
-                       (dtype == TRSM_F64 && (tc == 4 || tc == 12 || tc == 24));
+                       (dtype == TRSM_F64 && tc > 0 && tc <= 32 && tc % 4 == 0);
     if (!tc_ok) return TRSM_EINVAL;
     if (it.plan) {
       if (dtype != TRSM_F64) return TRSM_EINVAL;

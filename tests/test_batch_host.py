@@ -32,8 +32,9 @@ def test_batch_items_are_validated(host_lib):
     ok = (300, 40, 32, 0)
     assert _size(lib, binding, [ok])[0] == 0
     assert _size(lib, binding, [(300, 40, 48, 0)])[0] == binding.TRSM_EINVAL  # n0 only 32 or 64
-    assert _size(lib, binding, [(300, 40, 32, 20)])[0] == binding.TRSM_EINVAL  # FP64 widths 4, 8, 12, 16, 24, 32
-    for tile in (4, 12, 24):
+    for tile in (2, 18, 36):  # FP64 widths: multiples of 4 up to 32
+        assert _size(lib, binding, [(300, 40, 32, tile)])[0] == binding.TRSM_EINVAL
+    for tile in (4, 12, 20, 24, 28):
         assert _size(lib, binding, [(300, 40, 32, tile)])[0] == 0
         assert _size(lib, binding, [(300, 40, 64, tile)], dtype=1)[0] == binding.TRSM_EINVAL  # FP32: 8, 16, 32
     assert _size(lib, binding, [(0, 40, 32, 0)])[0] == binding.TRSM_EINVAL
