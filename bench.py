@@ -40,7 +40,8 @@ SCHEDULE_NAMES = ("dag", "right-looking", "recursive", "sliced")
 # (measured, ms: 16384x256 9.7 / 7.2 / 5.8 at n0 = 256 / 512 / 1024;
 # 8192x8192 26.0 / 22.0 / 20.0 at 512 / 1024 / 2048; 2048x131072 32.4 /
 # 29.7 / 30.3 at 512 / 1024 / 2048)
-SLICED_N0 = {(16384, 256): 1024, (8192, 8192): 2048, (2048, 131072): 2048}
+SLICED_N0 = {(16384, 256): 2048, (8192, 8192): 2048, (2048, 131072): 2048}
+SLICED_PREC_N0 = 2048  # block order of the sliced schedule's precision-configuration row
 # Block size of the mixed-precision figure (n = 16384, k = 4096).  Larger
 # blocks suit the mixed path: fewer, longer tensor-core updates, and the
 # diagonal multiplies run in FP32 (measured: 163 / 137 / 131 / 135 ms at
@@ -302,16 +303,19 @@ def precision_study(g, torch, n, k, n0, cs, inners, s_modes, dd_cols=4, stream=N
                                  "converged": converged, "status": status, "rc": rc,
                                  "speedup_vs_fp64": round(t64 / tm, 3)})
         if with_sliced:
-            # the sliced schedule: FP64-class products, one pass, no refinement
-            g.trsm_plan_sliced(plan)
-            X = g.trsm_solve_schedule(plan, Bd, schedule="sliced")
+            # the sliced schedule: FP64-class products, one pass, no refinement,
+            # on its own plan with 2048-row blocks (measured faster than 1024)
+            splan = g.trsm_plan(Ld, min(SLICED_PREC_N0, n))
+            g.trsm_plan_sliced(splan)
+            X = g.trsm_solve_schedule(splan, Bd, schedule="sliced")
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            X = g.trsm_solve_schedule(plan, Bd, X=X, schedule="sliced")
+            X = g.trsm_solve_schedule(splan, Bd, X=X, schedule="sliced")
             e1.record()
             torch.cuda.synchronize()
-            g.trsm_sync_status(plan)
+            g.trsm_sync_status(splan)
+            splan.destroy()
             tm = e0.elapsed_time(e1)
             fe = ferr(X)
             rec["mixed"].append({"inner": "sliced", "s_step": "sliced", "residual": None, "ms": round(tm, 2),
