@@ -4,6 +4,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "internal.h"
@@ -70,14 +71,16 @@ struct StoreF32Epi {
   // in L2; in plain launch order they spanned every row tile of two or
   // three column tiles and re-read all of A from HBM for each.
   static constexpr int kGroupRows = 16;
-  __device__ void tile(int& tm, int& tn) const {
-    const int R = static_cast<int>(gridDim.x), C = static_cast<int>(gridDim.y);
-    const int lin = tm + R * tn;
+  __device__ void tile_of(int lin, int R, int C, int& tm, int& tn) const {
     const int g0 = lin / (kGroupRows * C) * kGroupRows;
     const int gsz = min(kGroupRows, R - g0);
     const int idx = lin - g0 * C;
     tm = g0 + idx % gsz;
     tn = idx / gsz;
+  }
+  __device__ void tile(int& tm, int& tn) const {
+    const int R = static_cast<int>(gridDim.x), C = static_cast<int>(gridDim.y);
+    tile_of(tm + R * tn, R, C, tm, tn);
   }
   __device__ void k_range(int, int, int& kb0, int& kb1, int& chunk) const {
     kb0 = 0;
@@ -119,12 +122,19 @@ struct StoreF64MaxEpi {
   struct State {};
   // Launch order -> tile: the row tiles from the last (longest sums) to the
   // first, each over all its column tiles.
+  __device__ void tile_of(int lin, int R, int C, int& tm, int& tn) const {
+    if (lower) {
+      tm = R - 1 - lin / C;
+      tn = lin % C;
+    } else {
+      tm = lin % R;
+      tn = lin / R;
+    }
+  }
   __device__ void tile(int& tm, int& tn) const {
     if (!lower) return;
     const int R = static_cast<int>(gridDim.x), C = static_cast<int>(gridDim.y);
-    const int lin = tm + R * tn;
-    tm = R - 1 - lin / C;
-    tn = lin % C;
+    tile_of(tm + R * tn, R, C, tm, tn);
   }
   __device__ void k_range(int tm, int, int& kb0, int& kb1, int& chunk) const {
     const int kend = lower ? min(K, (tm + 1) * 128) : K;
@@ -159,6 +169,29 @@ struct StoreF64MaxEpi {
   __device__ void finish(State&, int, int, int, int) const {}
 };
 
+// Launches the persistent tile kernel over the R x C tiles: as many CTAs as
+// fit on the device at once (shared memory and tensor memory per SM), at
+// most one per tile.
+template <class Cfg, class Pairs, class Epi>
+cudaError_t launch_persistent(const CUtensorMap& ma, const CUtensorMap& mb, const Epi& epi, int64_t R, int64_t C,
+                              int* err, cudaStream_t s) {
+  auto kern = tc_tile_kernel_persistent<Cfg, Pairs, Epi>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(Cfg::SMEM_BYTES));
+  if (e != cudaSuccess) return e;
+  const int64_t tiles = R * C;
+  if (tiles <= 0) return cudaSuccess;
+  if (tiles > INT32_MAX) return cudaErrorInvalidValue;
+  constexpr int kSmemPerSm = 227 * 1024;
+  constexpr int kTmemCols = 2 * Cfg::NG * Cfg::BN <= 128 ? 128 : 2 * Cfg::NG * Cfg::BN <= 256 ? 256 : 512;
+  const int per_sm = std::max(1, std::min(static_cast<int>(kSmemPerSm / Cfg::SMEM_BYTES), 512 / kTmemCols));
+  const int64_t grid = std::min<int64_t>(tiles, static_cast<int64_t>(device_sm_count()) * per_sm);
+  kern<<<static_cast<unsigned>(grid), 192, Cfg::SMEM_BYTES, s>>>(ma, mb, epi, static_cast<int>(R),
+                                                                 static_cast<int>(C), err);
+  count_launch();
+  return cudaGetLastError();
+}
+
 template <bool kTf32, int BN, int STAGES>
 cudaError_t plain_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t M,
                        int64_t N, int64_t K, int64_t ldc, float alpha, float beta, int* err,
@@ -169,14 +202,7 @@ cudaError_t plain_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, f
   if (!make_kmajor_map(&mb, B, kTf32, K, N, ldb, 1, N * ldb, BN, 1, 128)) return cudaErrorInvalidValue;
   StoreF32Epi<BN> epi{C, ldc, static_cast<int>(M), static_cast<int>(N),
                       static_cast<int>((K + Cfg::KB - 1) / Cfg::KB), alpha, beta};
-  auto kern = tc_tile_kernel<Cfg, OnePair, StoreF32Epi<BN>>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(Cfg::SMEM_BYTES));
-  if (e != cudaSuccess) return e;
-  dim3 grid(static_cast<unsigned>((M + 127) / 128), static_cast<unsigned>((N + BN - 1) / BN));
-  kern<<<grid, 192, Cfg::SMEM_BYTES, s>>>(ma, mb, epi, err);
-  count_launch();
-  return cudaGetLastError();
+  return launch_persistent<Cfg, OnePair>(ma, mb, epi, (M + 127) / 128, (N + BN - 1) / BN, err, s);
 }
 
 // Split operands A = Ah + Al, B = Bh + Bl (bf16 planes): A B^T is taken as
@@ -201,14 +227,7 @@ cudaError_t split_gemm(const void* A, int64_t lda, int64_t a_plane, const void* 
   if (!make_kmajor_map(&mb, B, false, K, N, ldb, 2, b_plane, BN, 2, 128)) return cudaErrorInvalidValue;
   StoreF32Epi<BN> epi{C, ldc, static_cast<int>(M), static_cast<int>(N),
                       static_cast<int>((K + Cfg::KB - 1) / Cfg::KB), alpha, beta, scale};
-  auto kern = tc_tile_kernel<Cfg, SplitPairs, StoreF32Epi<BN>>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(Cfg::SMEM_BYTES));
-  if (e != cudaSuccess) return e;
-  dim3 grid(static_cast<unsigned>((M + 127) / 128), static_cast<unsigned>((N + BN - 1) / BN));
-  kern<<<grid, 192, Cfg::SMEM_BYTES, s>>>(ma, mb, epi, err);
-  count_launch();
-  return cudaGetLastError();
+  return launch_persistent<Cfg, SplitPairs>(ma, mb, epi, (M + 127) / 128, (N + BN - 1) / BN, err, s);
 }
 
 }  // namespace
@@ -233,14 +252,7 @@ cudaError_t gemm_split_tf32_tri(const float* A, int64_t lda, int64_t a_plane, co
   if (!make_kmajor_map(&ma, A, true, K, M, lda, 3, a_plane, 128, 3, 128)) return cudaErrorInvalidValue;
   if (!make_kmajor_map(&mb, B, true, K, N, ldb, 3, b_plane, BN, 3, 128)) return cudaErrorInvalidValue;
   Epi epi{D, ldd, static_cast<int>(M), static_cast<int>(N), static_cast<int>(K), 1, dmax};
-  auto kern = tc_tile_kernel<Cfg, Split3Pairs, Epi>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(Cfg::SMEM_BYTES));
-  if (e != cudaSuccess) return e;
-  dim3 grid(static_cast<unsigned>((M + 127) / 128), static_cast<unsigned>((N + BN - 1) / BN));
-  kern<<<grid, 192, Cfg::SMEM_BYTES, s>>>(ma, mb, epi, err);
-  count_launch();
-  return cudaGetLastError();
+  return launch_persistent<Cfg, Split3Pairs>(ma, mb, epi, (M + 127) / 128, (N + BN - 1) / BN, err, s);
 }
 
 cudaError_t gemm_split_bf16(const void* A, int64_t lda, int64_t a_plane, const void* B, int64_t ldb,
