@@ -130,7 +130,7 @@ def _has_mixed_data(plan):
 
 
 class Server:
-    def __init__(self, plans, budget_bytes, streams=4, max_batch=64, mixed_slots=None,
+    def __init__(self, plans, budget_bytes, streams=8, max_batch=64, mixed_slots=None,
                  mixed_residual="adaptive", sliced_min_flops=None):
         if streams < 1:
             raise ValueError("at least one launch slot")
