@@ -40,7 +40,10 @@ def _run(lib, tf32, M, N, K, seed):
 
 @pytest.mark.parametrize("tf32", [0, 1])
 @pytest.mark.parametrize("M,N,K", [(128, 128, 64), (128, 128, 32), (300, 200, 520), (1024, 512, 1024),
-                                   (64, 16, 8), (129, 257, 200), (129, 300, 1032)])
+                                   (64, 16, 8), (129, 257, 200), (129, 300, 1032),
+                                   # several tiles per persistent CTA (two TMEM buffers alternating),
+                                   # ragged edges, short and long K
+                                   (5000, 3000, 1040), (4200, 2100, 96)])
 def test_engine_gemm(cuda_lib, tf32, M, N, K):
     if K % (4 if tf32 else 8):
         pytest.skip("K not a multiple of the TMA row granule")
@@ -52,7 +55,7 @@ def test_engine_gemm(cuda_lib, tf32, M, N, K):
 
 @pytest.mark.parametrize("fmt", ["bf16", "fp16"])
 @pytest.mark.parametrize("M,N,K", [(128, 128, 64), (300, 200, 520), (1024, 512, 1024), (129, 257, 200),
-                                   (256, 64, 256), (129, 300, 1032)])
+                                   (256, 64, 256), (129, 300, 1032), (5000, 3000, 1040), (4200, 2100, 96)])
 def test_engine_split_gemm(cuda_lib, M, N, K, fmt):
     """Split operands (hi + lo planes of bf16 or fp16): C = Ah Bh^T + Ah Bl^T + Al Bh^T."""
     import torch
