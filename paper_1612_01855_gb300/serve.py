@@ -39,6 +39,13 @@ records an event on the caller's current stream; the slot stream waits on it
 before reading B, and B is marked as used on the slot stream so that the
 caching allocator does not hand its memory out again before the solve ends.
 
+Memory outside the budget: the mixed and sliced solves take their scratch
+from the library's workspace pool, which keeps freed memory mapped for the
+next call.  The admission counts each such request's scratch while it runs;
+what the pool holds afterwards (at most the largest scratch the mixed slots
+needed at once) is not counted, so leave that much headroom below the
+device's memory, or call `workspace_trim()` between traces.
+
 Results do not depend on the traffic: an FP64 request's X is the same bits
 whichever requests share its batch (every tile's updates are applied in a
 fixed order), and a mixed request's refined solve, like a large request's
