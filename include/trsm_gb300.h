@@ -73,6 +73,13 @@ extern "C" {
  * the six plane products of weight 2^-22 and above are summed in FP32
  * (FP32-class, about 2^-24 per product). */
 #define TRSM_SOLVE_S_TC 0x200
+/* As TRSM_SOLVE_S_TC with two tf32 planes per factor and the three products
+ * of weight 2^-11 and above (hi hi, hi mid, mid hi: about 2^-21 per product,
+ * the accuracy of the split-fp16 and split-bf16 updates), or with the hi
+ * planes alone (tf32, about 2^-11: the accuracy of the tf32 and bf16
+ * updates).  At most one of the three tensor-core flags. */
+#define TRSM_SOLVE_S_TC2 0x400
+#define TRSM_SOLVE_S_TC1 0x800
 
 /* Opaque plan: the paper's L~ (Algorithm Diagonal-Inverter, Section 6.1) —
  * a device copy of L whose n0 x n0 diagonal blocks are replaced by their
@@ -215,7 +222,7 @@ int trsm_plan_mixed(trsm_handle_t h, const double* L_dev, int64_t ldl, int inner
  *   residual : TRSM_RESIDUAL_SLICED, _SLICED8, _ADAPTIVE, _PROGRESSIVE or _FP64 (the
  *              latter needs n0 a multiple of 32 when there is more than one
  *              block), optionally or-ed with TRSM_SOLVE_S_FP32 or
- *              TRSM_SOLVE_S_TC.  The
+ *              one of TRSM_SOLVE_S_TC, _TC2, _TC1.  The
  *              residual's accuracy sets the attainable error: about
  *              cond * 2^-43 (SLICED), cond * 2^-49 (SLICED8), cond * 2^-53
  *              (FP64), with cond the componentwise condition of the system
@@ -257,8 +264,9 @@ typedef struct trsm_batch_item {
   int64_t ldx;
   int64_t n, k;
   int64_t n0;           /* 32 or 64 when plan == NULL (ignored otherwise)      */
-  int64_t tile_cols;    /* columns per output tile: FP64 a multiple of 4
-                           up to 32, FP32 (per CTA) 8, 16 or 32; 0 = fitted
+  int64_t tile_cols;    /* columns per output tile: FP64 1 to 3 or a
+                           multiple of 4 up to 32, FP32 (per CTA) 8, 16 or
+                           32; 0 = fitted
                            to k (the narrowest width that holds k <= 32, else
                            32-wide tiles and, when 32 does not divide k, one
                            fitted tile for the remainder; results are the

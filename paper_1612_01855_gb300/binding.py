@@ -36,6 +36,8 @@ TRSM_RESIDUAL_ADAPTIVE = 3
 TRSM_RESIDUAL_PROGRESSIVE = 4
 TRSM_SOLVE_S_FP32 = 0x100
 TRSM_SOLVE_S_TC = 0x200
+TRSM_SOLVE_S_TC2 = 0x400
+TRSM_SOLVE_S_TC1 = 0x800
 
 TRSM_F64 = 0
 TRSM_F32 = 1
@@ -274,10 +276,11 @@ def trsm_plan_mixed(plan, L, inner="tf32"):
 
 
 def trsm_solve_mixed(plan, B, X=None, residual="sliced", max_iter=30, tol=1e-14, raise_on_noconv=True,
-                     s_fp32=False, s_tc=False):
+                     s_fp32=False, s_tc=False, s_tc_planes=3):
     """Iterative refinement around the low-precision solve (s_fp32: the
     diagonal multiplies in FP32; s_tc: on the tensor cores as split-tf32
-    products).  Returns (X, iterations, last max|D|/max|X|)."""
+    products of s_tc_planes planes per factor: 3 FP32-class, 2 about
+    2^-21, 1 plain tf32).  Returns (X, iterations, last max|D|/max|X|)."""
     torch = _torch()
     B = _dev_matrix(B, "B")
     n, k = B.shape
@@ -292,7 +295,9 @@ def trsm_solve_mixed(plan, B, X=None, residual="sliced", max_iter=30, tol=1e-14,
     if s_fp32:
         code |= TRSM_SOLVE_S_FP32
     if s_tc:
-        code |= TRSM_SOLVE_S_TC
+        if s_tc_planes not in (1, 2, 3):
+            raise ValueError(f"s_tc_planes must be 1, 2 or 3, not {s_tc_planes}")
+        code |= {3: TRSM_SOLVE_S_TC, 2: TRSM_SOLVE_S_TC2, 1: TRSM_SOLVE_S_TC1}[s_tc_planes]
     rc = load_library().trsm_solve_mixed(plan.handle, ctypes.c_void_p(B.data_ptr()), k, _ld(B),
                                          ctypes.c_void_p(X.data_ptr()), _ld(X), code, int(max_iter),
                                          float(tol), ctypes.byref(it), ctypes.byref(upd), _stream(B))
@@ -442,8 +447,8 @@ class Batch:
     """Many independent systems solved by one persistent launch
     (trsm_batch_*).  `systems` is a list of dicts with keys L (or plan), B,
     X (CUDA tensors, column-major), n0 (32 or 64, plan-less items) and
-    optionally tile_cols (columns per output tile: FP64 a multiple of 4 up
-    to 32, FP32 8, 16 or 32; default: fitted to k)."""
+    optionally tile_cols (columns per output tile: FP64 1 to 3 or a multiple
+    of 4 up to 32, FP32 8, 16 or 32; default: fitted to k)."""
 
     def __init__(self, systems, dtype="f64", arena=None):
         """arena: optional uint8 CUDA tensor to lay the batch out in (no

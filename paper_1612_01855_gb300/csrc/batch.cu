@@ -152,30 +152,38 @@ __device__ __noinline__ void leaf_invert_block(const T* __restrict__ A, int64_t 
 }
 
 // acc += A(rows [0,m), K [kbeg,kend)) * B(K [kbeg,kend), cols [0,nc)) for a
-// TILE x CW output tile (CW a multiple of 4 up to 32) on 128 threads:
-// thread (ty, tx) = (tid / TX, tid % TX) owns TMR rows from ty*TMR and CPT
-// columns from CPT tx, CPT = CW / 4 for CW = 4, 20 and 28, 3 for CW = 12
-// and 24, else 2;
-// every warp holds 8 consecutive rows, and CW = 32 is the layout of the
-// generic tile.  Narrow tiles let systems with few right-hand sides skip
-// most of the padded columns.
+// TILE x CW output tile (CW a multiple of 4 up to 32, or 1 to 3) on 128
+// threads: thread (ty, tx) = (tid / TX, tid % TX) owns TMR rows from ty*TMR
+// and CPT columns from CPT tx, CPT = CW / 4 for CW = 4, 20 and 28, 3 for
+// CW = 12 and 24, else 2; every warp holds RPW = 8 consecutive rows, and
+// CW = 32 is the layout of the generic tile.  Below 4 columns warp 0 alone
+// holds the tile (RPW = 32, a lane per row, all CW columns) and the other
+// warps skip the multiply-adds: a DFMA is issued per warp, so the padded
+// columns of a 4-wide tile would cost as much as real ones.  Narrow tiles
+// let systems with few right-hand sides skip most of the padded columns.
 template <int CW>
 struct NarrowMap {
-  static constexpr int CPT = (CW == 4 || CW == 20 || CW == 28) ? CW / 4 : CW % 3 == 0 ? 3 : 2;  // columns per thread
-  static constexpr int TX = CW / CPT;                               // threads along the columns
-  static constexpr int TMR = TILE * CW / NTHREADS / CPT;            // rows per thread
-  static_assert(TX * CPT == CW && (NTHREADS / TX) * TMR == TILE && (32 / TX) * TMR == 8, "tile layout");
+  static constexpr bool kOneWarp = CW < 4;
+  static constexpr int CPT = kOneWarp ? CW : (CW == 4 || CW == 20 || CW == 28) ? CW / 4 : CW % 3 == 0 ? 3 : 2;
+  static constexpr int TX = CW / CPT;                                   // threads along the columns
+  static constexpr int TMR = kOneWarp ? 1 : TILE * CW / NTHREADS / CPT;  // rows per thread
+  static constexpr int RPW = kOneWarp ? 32 : 8;                         // rows per warp
+  static constexpr int WARPS = TILE / RPW;                              // warps that hold rows
+  static_assert(kOneWarp || (TX * CPT == CW && (NTHREADS / TX) * TMR == TILE && (32 / TX) * TMR == 8),
+                "tile layout");
+  static_assert(!kOneWarp || (TX == 1 && TILE == 32), "one-warp tile layout");
   __device__ static int row(int i) { return (threadIdx.x / TX) * TMR + i; }
   __device__ static int col(int j) { return (threadIdx.x % TX) * CPT + j; }
 };
 
 // kTriFrom >= 0: A is lower triangular from K offset kTriFrom on (the
 // diagonal chunk of an S task, A(row, kTriFrom + kk) = 0 for kk > row).
-// Warp w holds rows 8w .. 8w + 7 for every CW, so it stops that chunk after
-// 8w + 8 steps: the products it skips are zeros.  For the same reason a
-// warp whose rows all lie at or below m skips the multiply-adds, and every
-// warp stops a chunk at kend (the padding of a short last block row or
-// column; the loads and barriers stay common to all warps).
+// Warp w holds rows RPW w .. RPW w + RPW - 1, so it stops that chunk after
+// RPW (w + 1) steps: the products it skips are zeros.  For the same reason
+// a warp whose rows all lie at or below m (or that holds no rows) skips the
+// multiply-adds, and every warp stops a chunk at kend (the padding of a
+// short last block row or column; the loads and barriers stay common to all
+// warps).
 template <class TC, bool kAMutable, bool kBMutable, int CW>
 __device__ __forceinline__ void tile_mma_cw(const TC* __restrict__ A, int64_t lda, const TC* __restrict__ B,
                                             int64_t ldb, int m, int nc, int64_t kbeg, int64_t kend,
@@ -183,8 +191,8 @@ __device__ __forceinline__ void tile_mma_cw(const TC* __restrict__ A, int64_t ld
                                             int64_t kTriFrom = -1) {
   using Mp = NarrowMap<CW>;
   const int tid = threadIdx.x;
-  const int tri_end = 8 * (tid >> 5) + 8;
-  const bool live = 8 * (tid >> 5) < m;  // warp-uniform
+  const int tri_end = Mp::RPW * (tid >> 5) + Mp::RPW;
+  const bool live = (tid >> 5) < Mp::WARPS && Mp::RPW * (tid >> 5) < m;  // warp-uniform
   for (int64_t k0 = kbeg; k0 < kend; k0 += KCH) {
 #pragma unroll
     for (int it = 0; it < (KCH * TILE) / NTHREADS; ++it) {
@@ -196,9 +204,10 @@ __device__ __forceinline__ void tile_mma_cw(const TC* __restrict__ A, int64_t ld
       sm.a[kk][r] = v;
     }
 #pragma unroll
-    for (int it = 0; it < (KCH * CW) / NTHREADS; ++it) {
+    for (int it = 0; it < (KCH * CW + NTHREADS - 1) / NTHREADS; ++it) {
       const int kk = tid & 31;
       const int c = (tid >> 5) + 4 * it;
+      if (CW % 4 != 0 && c >= CW) continue;  // tiles of 1 to 3 columns: warps past the last column
       const int64_t t = k0 + kk;
       TC v = TC(0);
       if (c < nc && t < kend) v = ld_raw<kBMutable>(B + static_cast<int64_t>(c) * ldb + t);
@@ -782,6 +791,9 @@ __global__ void __launch_bounds__(NTHREADS, 8) batch_kernel(const BatchSys<T>* _
       __syncthreads();
       if (!s_ok) break;
       switch (a.cw) {
+        case 1: s_body<T, 1>(a, l, r, j, s0, ml, sm); break;
+        case 2: s_body<T, 2>(a, l, r, j, s0, ml, sm); break;
+        case 3: s_body<T, 3>(a, l, r, j, s0, ml, sm); break;
         case 4: s_body<T, 4>(a, l, r, j, s0, ml, sm); break;
         case 8: s_body<T, 8>(a, l, r, j, s0, ml, sm); break;
         case 12: s_body<T, 12>(a, l, r, j, s0, ml, sm); break;
@@ -809,6 +821,9 @@ __global__ void __launch_bounds__(NTHREADS, 8) batch_kernel(const BatchSys<T>* _
       __syncthreads();
       if (!s_ok) break;
       switch (a.cw) {
+        case 1: u_body<T, 1>(a, l, i, r, j, s0, ml, sm); break;
+        case 2: u_body<T, 2>(a, l, i, r, j, s0, ml, sm); break;
+        case 3: u_body<T, 3>(a, l, i, r, j, s0, ml, sm); break;
         case 4: u_body<T, 4>(a, l, i, r, j, s0, ml, sm); break;
         case 8: u_body<T, 8>(a, l, i, r, j, s0, ml, sm); break;
         case 12: u_body<T, 12>(a, l, i, r, j, s0, ml, sm); break;
@@ -857,13 +872,15 @@ struct trsm_batch_s {
 
 namespace {
 
-// An item whose k is above 32 and not a multiple of it is solved as two
-// parts: its first floor(k / 32) * 32 columns in 32-wide tiles and the rest
-// in one 4- to 32-wide tile (fitted_cw), sharing L and the inverted blocks (only
-// the first part inverts them).  A column's arithmetic does not depend on
-// the tile it is in, so the split changes no result; it only drops most of
-// the padded columns of the last tile (on the batching workload the
-// executed multiply-adds fall by about a tenth).
+// An item with tile_cols = 0 is solved as up to three parts: its first
+// floor(k / 32) * 32 columns in 32-wide tiles, the next multiple of 4 below
+// the rest in one tile of that width, and the last 1 to 3 columns in a
+// one-warp tile, all sharing L and the inverted blocks (only the first part
+// inverts them).  A column's arithmetic does not depend on the tile it is
+// in, so the split changes no result; it only drops the padded columns of
+// the last tiles (on the batching workload the executed multiply-adds fall
+// by about a tenth with the 32-wide split, and by a few percent more with
+// the one-warp remainder).
 struct Part {
   int item;      // the user's item
   int64_t col0;  // first column of the part
@@ -872,22 +889,32 @@ struct Part {
   int owner;     // part whose inverted blocks this part reads, or -1
 };
 
-// FP64 tile width fitted to k columns: the next multiple of 4, at most 32.
-int fitted_cw(int64_t k) { return k >= 32 ? 32 : static_cast<int>((k + 3) / 4 * 4); }
+// FP64 tile width fitted to k columns: k itself below 4, else the next
+// multiple of 4, at most 32.
+int fitted_cw(int64_t k) { return k >= 32 ? 32 : k < 4 ? static_cast<int>(k) : static_cast<int>((k + 3) / 4 * 4); }
 
 std::vector<Part> split_parts(const trsm_batch_item* items, int count) {
   std::vector<Part> parts;
   for (int s = 0; s < count; ++s) {
     const trsm_batch_item& it = items[s];
-    if (it.tile_cols == 0 && it.k > 32 && it.k % 32 != 0) {
-      const int64_t k32 = it.k / 32 * 32, rem = it.k - k32;
-      const int own = static_cast<int>(parts.size());
-      parts.push_back(Part{s, 0, k32, 32, -1});
-      parts.push_back(Part{s, k32, rem, fitted_cw(rem), own});
-    } else {
-      const int cw = it.tile_cols != 0 ? static_cast<int>(it.tile_cols) : fitted_cw(it.k);
-      parts.push_back(Part{s, 0, it.k, cw, -1});
+    if (it.tile_cols != 0) {
+      parts.push_back(Part{s, 0, it.k, static_cast<int>(it.tile_cols), -1});
+      continue;
     }
+    // floor(k / 32) * 32 columns in 32-wide tiles, then the next multiple
+    // of 4 below the rest in one tile, then the last 1 to 3 columns in a
+    // one-warp tile; the first part inverts the blocks for all of them
+    int64_t c0 = 0;
+    int own = -1;
+    auto add = [&](int64_t cols, int cw) {
+      parts.push_back(Part{s, c0, cols, cw, own});
+      if (own < 0) own = static_cast<int>(parts.size()) - 1;
+      c0 += cols;
+    };
+    const int64_t k32 = it.k / 32 * 32, rem = it.k - k32, k4 = rem / 4 * 4;
+    if (k32 > 0) add(k32, 32);
+    if (k4 > 0) add(k4, static_cast<int>(k4));
+    if (rem % 4 != 0) add(rem % 4, static_cast<int>(rem % 4));
   }
   return parts;
 }
@@ -1201,10 +1228,10 @@ static int validate_items(const trsm_batch_item* items, int count, int dtype) {
     const trsm_batch_item& it = items[s];
     if (it.n < 1 || it.k < 1 || !it.B || !it.X || it.ldb < it.n || it.ldx < it.n || it.B == it.X)
       return TRSM_EINVAL;
-    // FP64 tiles: a multiple of 4 up to 32 columns; FP32 units: 8, 16 or 32
+    // FP64 tiles: 1 to 3 or a multiple of 4 up to 32 columns; FP32 units: 8, 16 or 32
     const int64_t tc = it.tile_cols;
     const bool tc_ok = tc == 0 || tc == 8 || tc == 16 || tc == 32 ||
-                       (dtype == TRSM_F64 && tc > 0 && tc <= 32 && tc % 4 == 0);
+                       (dtype == TRSM_F64 && tc > 0 && tc <= 32 && (tc % 4 == 0 || tc < 4));
     if (!tc_ok) return TRSM_EINVAL;
     if (it.plan) {
       if (dtype != TRSM_F64) return TRSM_EINVAL;

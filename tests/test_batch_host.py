@@ -32,9 +32,9 @@ def test_batch_items_are_validated(host_lib):
     ok = (300, 40, 32, 0)
     assert _size(lib, binding, [ok])[0] == 0
     assert _size(lib, binding, [(300, 40, 48, 0)])[0] == binding.TRSM_EINVAL  # n0 only 32 or 64
-    for tile in (2, 18, 36):  # FP64 widths: multiples of 4 up to 32
+    for tile in (5, 18, 36, -1):  # FP64 widths: 1 to 3 and multiples of 4 up to 32
         assert _size(lib, binding, [(300, 40, 32, tile)])[0] == binding.TRSM_EINVAL
-    for tile in (4, 12, 20, 24, 28):
+    for tile in (1, 2, 3, 4, 12, 20, 24, 28):
         assert _size(lib, binding, [(300, 40, 32, tile)])[0] == 0
         assert _size(lib, binding, [(300, 40, 64, tile)], dtype=1)[0] == binding.TRSM_EINVAL  # FP32: 8, 16, 32
     assert _size(lib, binding, [(0, 40, 32, 0)])[0] == binding.TRSM_EINVAL
