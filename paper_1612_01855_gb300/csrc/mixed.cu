@@ -292,6 +292,7 @@ __global__ void pack_inv_tf32_kernel(const double* __restrict__ Lt, int64_t ldt,
 // of a plane holds column j of W_i (zeros from m to n0p); hi = tf32(w),
 // mid = tf32(w - hi), lo = w - hi - mid (every difference exact in FP32, and
 // the three planes hold all 24 bits of w).  Rows on threadIdx.x.
+template <int P>
 __global__ void pack_w_tf32_kernel(const float* __restrict__ W, int64_t ldw, int64_t s0, int m, int64_t k,
                                    int64_t n0p, float* __restrict__ Wt) {
   const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
@@ -300,7 +301,7 @@ __global__ void pack_w_tf32_kernel(const float* __restrict__ W, int64_t ldw, int
   for (int64_t j = blockIdx.y; j < k; j += gridDim.y) {
     float w = (t < m) ? W[j * ldw + s0 + t] : 0.f;
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
+    for (int q = 0; q < P; ++q) {
       const float p = to_tf32(w);
       Wt[q * plane + j * n0p + t] = p;
       w -= p;
@@ -894,8 +895,12 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
   if (last_update) *last_update = 0.0;
   if (!h || !h->mixed || k < 0 || max_iter < 1 || !(tol >= 0.0)) return TRSM_EINVAL;
   const bool s32 = (residual & TRSM_SOLVE_S_FP32) != 0;
-  const bool stc = (residual & TRSM_SOLVE_S_TC) != 0;
-  residual &= ~(TRSM_SOLVE_S_FP32 | TRSM_SOLVE_S_TC);
+  const int tc_flags = residual & (TRSM_SOLVE_S_TC | TRSM_SOLVE_S_TC2 | TRSM_SOLVE_S_TC1);
+  const int tc_planes = tc_flags == TRSM_SOLVE_S_TC ? 3 : tc_flags == TRSM_SOLVE_S_TC2 ? 2
+                        : tc_flags == TRSM_SOLVE_S_TC1 ? 1 : 0;
+  if (tc_flags && !tc_planes) return TRSM_EINVAL;  // more than one of them
+  const bool stc = tc_planes > 0;
+  residual &= ~(TRSM_SOLVE_S_FP32 | TRSM_SOLVE_S_TC | TRSM_SOLVE_S_TC2 | TRSM_SOLVE_S_TC1);
   if (s32 && stc) return TRSM_EINVAL;
   if (residual != TRSM_RESIDUAL_SLICED && residual != TRSM_RESIDUAL_FP64 && residual != TRSM_RESIDUAL_SLICED8 &&
       residual != TRSM_RESIDUAL_ADAPTIVE && residual != TRSM_RESIDUAL_PROGRESSIVE)
@@ -983,12 +988,14 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
         // max |D_i| from the epilogue; then D_i into the update's operand
         const dim3 gw(static_cast<unsigned>((n0p + 255) / 256),
                       static_cast<unsigned>(std::min<int64_t>(k, std::max<int64_t>(1, 4864 / ((n0p + 255) / 256)))));
-        trsm::pack_w_tf32_kernel<<<gw, 256, 0, s>>>(W, ld, s0, m, k, n0p, Wt);
+        if (tc_planes == 3) trsm::pack_w_tf32_kernel<3><<<gw, 256, 0, s>>>(W, ld, s0, m, k, n0p, Wt);
+        else if (tc_planes == 2) trsm::pack_w_tf32_kernel<2><<<gw, 256, 0, s>>>(W, ld, s0, m, k, n0p, Wt);
+        else trsm::pack_w_tf32_kernel<1><<<gw, 256, 0, s>>>(W, ld, s0, m, k, n0p, Wt);
         trsm::count_launch();
         e = cudaGetLastError();
         if (e == cudaSuccess)
           e = trsm::tc::gemm_split_tf32_tri(mp->dinv_tc + i * 3 * n0 * n0p, n0p, n0 * n0p, Wt, n0p, k * n0p, D + s0, ld,
-                                            m, k, m, dmax_i, err, s);
+                                            m, k, m, tc_planes, dmax_i, err, s);
         if (e == cudaSuccess && mode != 3 && i < N - 1) {
           const dim3 gp(static_cast<unsigned>((m + 255) / 256),
                         static_cast<unsigned>(std::min<int64_t>(k, std::max<int64_t>(1, 2432 / ((m + 255) / 256)))));

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <mutex>
 
 #include "internal.h"
@@ -241,18 +242,38 @@ struct Split3Pairs {
   __device__ static constexpr int g(int) { return 0; }
 };
 
-cudaError_t gemm_split_tf32_tri(const float* A, int64_t lda, int64_t a_plane, const float* B, int64_t ldb,
-                                int64_t b_plane, double* D, int64_t ldd, int64_t M, int64_t N, int64_t K,
-                                unsigned long long* dmax, int* err, cudaStream_t s) {
-  if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
-  constexpr int BN = 128, STAGES = 2;
-  using Cfg = TileCfg<true, BN, 3, 3, 1, STAGES>;
+namespace {
+// P tf32 planes of each factor: P = 3 takes the six products above, P = 2
+// the three of weight 2^-11 and above (hi hi, hi mid, mid hi: about 2^-21
+// of the product), P = 1 the hi planes alone (tf32, about 2^-11).  A stage
+// holds P planes of both operands (32 KB each): two stages at P = 3, three
+// at P = 2 and P = 1 (two CTAs per SM at P = 1).
+template <int P>
+cudaError_t split_tf32_tri(const float* A, int64_t lda, int64_t a_plane, const float* B, int64_t ldb,
+                           int64_t b_plane, double* D, int64_t ldd, int64_t M, int64_t N, int64_t K,
+                           unsigned long long* dmax, int* err, cudaStream_t s) {
+  constexpr int BN = 128, STAGES = P == 3 ? 2 : 3;
+  using Cfg = TileCfg<true, BN, P, P, 1, STAGES>;
+  using Pairs = std::conditional_t<P == 3, Split3Pairs, std::conditional_t<P == 2, SplitPairs, OnePair>>;
   using Epi = StoreF64MaxEpi<BN, Cfg::KB>;
   CUtensorMap ma, mb;
-  if (!make_kmajor_map(&ma, A, true, K, M, lda, 3, a_plane, 128, 3, 128)) return cudaErrorInvalidValue;
-  if (!make_kmajor_map(&mb, B, true, K, N, ldb, 3, b_plane, BN, 3, 128)) return cudaErrorInvalidValue;
+  if (!make_kmajor_map(&ma, A, true, K, M, lda, P, a_plane, 128, P, 128)) return cudaErrorInvalidValue;
+  if (!make_kmajor_map(&mb, B, true, K, N, ldb, P, b_plane, BN, P, 128)) return cudaErrorInvalidValue;
   Epi epi{D, ldd, static_cast<int>(M), static_cast<int>(N), static_cast<int>(K), 1, dmax};
-  return launch_persistent<Cfg, Split3Pairs>(ma, mb, epi, (M + 127) / 128, (N + BN - 1) / BN, err, s);
+  return launch_persistent<Cfg, Pairs>(ma, mb, epi, (M + 127) / 128, (N + BN - 1) / BN, err, s);
+}
+}  // namespace
+
+cudaError_t gemm_split_tf32_tri(const float* A, int64_t lda, int64_t a_plane, const float* B, int64_t ldb,
+                                int64_t b_plane, double* D, int64_t ldd, int64_t M, int64_t N, int64_t K,
+                                int planes, unsigned long long* dmax, int* err, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+  switch (planes) {
+    case 1: return split_tf32_tri<1>(A, lda, a_plane, B, ldb, b_plane, D, ldd, M, N, K, dmax, err, s);
+    case 2: return split_tf32_tri<2>(A, lda, a_plane, B, ldb, b_plane, D, ldd, M, N, K, dmax, err, s);
+    case 3: return split_tf32_tri<3>(A, lda, a_plane, B, ldb, b_plane, D, ldd, M, N, K, dmax, err, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t gemm_split_bf16(const void* A, int64_t lda, int64_t a_plane, const void* B, int64_t ldb,

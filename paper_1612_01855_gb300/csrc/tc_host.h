@@ -42,16 +42,18 @@ cudaError_t gemm_split_f16(const void* A, int64_t lda, int64_t a_plane, const vo
                            const float* scale, float beta, int* err, cudaStream_t s);
 
 // D (FP64, column-major, ldd) = A B^T for the diagonal multiply of the
-// mixed solve: A (M x K, lower triangular) and B (N x K) are each three tf32
+// mixed solve: A (M x K, lower triangular) and B (N x K) are each tf32
 // planes stored as fp32 (hi = tf32(v), mid = tf32(v - hi), lo = tf32(v - hi
 // - mid); K-major, row strides lda / ldb, planes a_plane / b_plane elements
-// apart), multiplied as the six plane pairs of weight 2^-22 and above with
-// FP32 accumulation (FP32-class, about 2^-24 per product); row tile q's sums
-// stop at K = 128 (q + 1).  max |D| is folded into *dmax (ordered bit
-// pattern of a non-negative double).  128 x 128 tiles, 2-stage TMA ring.
+// apart), of which the first `planes` (1, 2 or 3) are multiplied with FP32
+// accumulation: with 3 the six plane pairs of weight 2^-22 and above
+// (FP32-class, about 2^-24 per product), with 2 the three of weight 2^-11
+// and above (about 2^-21), with 1 the hi planes alone (tf32, about 2^-11).
+// Row tile q's sums stop at K = 128 (q + 1).  max |D| is folded into *dmax
+// (ordered bit pattern of a non-negative double).  128 x 128 tiles.
 cudaError_t gemm_split_tf32_tri(const float* A, int64_t lda, int64_t a_plane, const float* B, int64_t ldb,
                                 int64_t b_plane, double* D, int64_t ldd, int64_t M, int64_t N, int64_t K,
-                                unsigned long long* dmax, int* err, cudaStream_t s);
+                                int planes, unsigned long long* dmax, int* err, cudaStream_t s);
 
 }  // namespace tc
 }  // namespace trsm

@@ -18,9 +18,41 @@ def _rel(a, b):
     return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
 
 
+def _smode(smode):
+    """Keyword arguments of a diagonal-multiply mode: fp64, fp32, or the
+    tensor cores with 3 (tc), 2 (tc2) or 1 (tc1) tf32 planes per factor."""
+    planes = {"tc": 3, "tc2": 2, "tc1": 1}.get(smode)
+    return dict(s_fp32=smode == "fp32", s_tc=planes is not None, s_tc_planes=planes or 3)
+
+
+def test_mixed_tensor_core_flags_are_exclusive(cuda_lib):
+    """Two of the tensor-core diagonal-multiply flags at once, or one with
+    TRSM_SOLVE_S_FP32, are rejected."""
+    import ctypes
+    import torch
+    import paper_1612_01855_gb300 as g
+    from paper_1612_01855_gb300 import binding as b
+    n, k = 256, 8
+    L, B = inputs.well_conditioned(n, k, seed=5)
+    Ld, Bd = _dev(L), _dev(B)
+    plan = g.trsm_plan(Ld, 64)
+    g.trsm_plan_mixed(plan, Ld, "tf32")
+    X = torch.empty((k, n), dtype=torch.float64, device="cuda").t()
+    lib = b.load_library()
+    it, upd = ctypes.c_int(), ctypes.c_double()
+    for flags in (b.TRSM_SOLVE_S_TC | b.TRSM_SOLVE_S_TC2, b.TRSM_SOLVE_S_TC2 | b.TRSM_SOLVE_S_TC1,
+                  b.TRSM_SOLVE_S_FP32 | b.TRSM_SOLVE_S_TC1):
+        rc = lib.trsm_solve_mixed(plan.handle, ctypes.c_void_p(Bd.data_ptr()), k, n, ctypes.c_void_p(X.data_ptr()),
+                                  n, b.TRSM_RESIDUAL_SLICED | flags, 10, 1e-12, ctypes.byref(it), ctypes.byref(upd),
+                                  None)
+        assert rc == b.TRSM_EINVAL
+    plan.destroy()
+
+
 @pytest.mark.parametrize("inner", ["tf32", "bf16", "bf16x3", "fp16x3"])
 @pytest.mark.parametrize("residual,smode", [("sliced", "fp64"), ("fp64", "fp64"), ("sliced", "fp32"),
-                                            ("sliced", "tc"), ("progressive", "fp32")])
+                                            ("sliced", "tc"), ("sliced", "tc2"), ("sliced", "tc1"),
+                                            ("progressive", "fp32")])
 @pytest.mark.parametrize("n,k,n0", [(1024, 64, 128), (1000, 37, 64), (300, 5, 300)])
 def test_mixed_well_conditioned(cuda_lib, inner, residual, smode, n, k, n0):
     """smode: the diagonal multiplies in FP64, in FP32, or on the tensor
@@ -31,7 +63,7 @@ def test_mixed_well_conditioned(cuda_lib, inner, residual, smode, n, k, n0):
     plan = g.trsm_plan(Ld, n0)
     g.trsm_plan_mixed(plan, Ld, inner)
     X, iters, upd = g.trsm_solve_mixed(plan, _dev(B), residual=residual, max_iter=40, tol=1e-15,
-                                       raise_on_noconv=False, s_fp32=smode == "fp32", s_tc=smode == "tc")
+                                       raise_on_noconv=False, **_smode(smode))
     got = X.cpu().numpy()
     want = oracle.forward_subst(L, B)
     err = _rel(got, want)
@@ -43,7 +75,7 @@ def test_mixed_well_conditioned(cuda_lib, inner, residual, smode, n, k, n0):
 
 
 @pytest.mark.parametrize("inner", ["tf32", "bf16x3", "fp16x3"])
-@pytest.mark.parametrize("smode", ["fp32", "tc"])
+@pytest.mark.parametrize("smode", ["fp32", "tc", "tc2", "tc1"])
 @pytest.mark.parametrize("n,k,n0", [(1500, 70, 600), (2048, 33, 1024), (1100, 130, 512)])
 def test_mixed_wide_blocks_fp32_diagonal_multiply(cuda_lib, inner, smode, n, k, n0):
     """Blocks of 512 rows and more take the 64 x 64 register-blocked FP32
@@ -55,7 +87,7 @@ def test_mixed_wide_blocks_fp32_diagonal_multiply(cuda_lib, inner, smode, n, k, 
     plan = g.trsm_plan(Ld, n0)
     g.trsm_plan_mixed(plan, Ld, inner)
     X, iters, upd = g.trsm_solve_mixed(plan, _dev(B), residual="sliced", max_iter=40, tol=1e-15,
-                                       raise_on_noconv=False, s_fp32=smode == "fp32", s_tc=smode == "tc")
+                                       raise_on_noconv=False, **_smode(smode))
     err = _rel(X.cpu().numpy(), oracle.forward_subst(L, B))
     print(f"mixed {inner}/{smode} n={n} k={k} n0={n0}: {iters} iterations, rel err {err:.2e}")
     assert err < 5e-12
@@ -63,7 +95,7 @@ def test_mixed_wide_blocks_fp32_diagonal_multiply(cuda_lib, inner, smode, n, k, 
 
 
 @pytest.mark.parametrize("inner", ["tf32", "bf16x3", "fp16x3"])
-@pytest.mark.parametrize("smode", ["fp64", "fp32", "tc"])
+@pytest.mark.parametrize("smode", ["fp64", "fp32", "tc", "tc2", "tc1"])
 def test_mixed_power_of_two_scaling_is_exact(cuda_lib, inner, smode):
     """Every scale in the refined solve (chunk exponents of the sliced
     residual, the fp16 panel and D_i scales, the FP32 inner solve) is a power
@@ -78,7 +110,7 @@ def test_mixed_power_of_two_scaling_is_exact(cuda_lib, inner, smode):
     runs = {}
     for sc in (0, -60, 60):
         X, iters, upd = g.trsm_solve_mixed(plan, _dev(np.ldexp(B, sc)), residual="sliced", max_iter=40, tol=1e-13,
-                                           raise_on_noconv=False, s_fp32=smode == "fp32", s_tc=smode == "tc")
+                                           raise_on_noconv=False, **_smode(smode))
         runs[sc] = (X.cpu().numpy(), iters)
     for sc in (-60, 60):
         assert runs[sc][1] == runs[0][1]
@@ -180,7 +212,8 @@ def test_mixed_argument_errors(cuda_lib):
 
 
 @pytest.mark.parametrize("c", [2, 4])
-@pytest.mark.parametrize("smode,residual", [("fp32", "adaptive"), ("tc", "adaptive"), ("fp32", "progressive")])
+@pytest.mark.parametrize("smode,residual", [("fp32", "adaptive"), ("tc", "adaptive"), ("tc2", "adaptive"),
+                                            ("fp32", "progressive")])
 def test_full_size_precision_config(cuda_lib, c, smode, residual):
     """The precision configuration at its full size and in the bench's launch
     configuration: n = 16384, k = 4096, n0 = 1024, graded diagonal
@@ -205,7 +238,7 @@ def test_full_size_precision_config(cuda_lib, c, smode, residual):
     plan = g.trsm_plan(Ld, n0)
     g.trsm_plan_mixed(plan, Ld, "fp16x3")
     X, iters, upd = g.trsm_solve_mixed(plan, Bd, residual=residual, max_iter=30, tol=1e-12,
-                                       s_fp32=smode == "fp32", s_tc=smode == "tc")
+                                       **_smode(smode))
     ci = torch.from_numpy(cols).cuda()
     got = X[:, ci].cpu().numpy()
     fwd = _rel(got, ref)
