@@ -221,13 +221,19 @@ def cpu_oracle_rate(data, shapes, budget_s, max_cols=None):
 
 
 def precision_study(g, torch, n, k, n0, cs, inners, s_modes, dd_cols=4, stream=None, quick=False,
-                    residuals=("sliced",), combos=None, with_sliced=False):
+                    residuals=("sliced",), combos=None, with_sliced=False, tol=1e-11):
     """Mixed-precision refinement on the graded-diagonal workload (diagonal
     geomspace(1, 10^-c), permuted): time, iterations, forward error against
     the double-double oracle and backward error ||B - L X|| / (||L|| ||X||)
     on a seeded sample of columns, beside the FP64 solve of the same system.
-    A solve that stops without reaching the target reports its status
-    (ENOCONV), and a non-finite result or reference reports None errors."""
+    The refinement stops at max|D| <= tol max|X| (1e-11: ten times below the
+    1e-10 target, above the update noise of about 1e-12 that an iterate at
+    this system's FP64 error floor, about 7e-13, still shows) or when the
+    updates stagnate.  s_modes: the diagonal multiply in FP64, FP32
+    ("fp32"), or on the tensor cores with 3, 2 or 1 tf32 planes per factor
+    ("tc", "tc2", "tc1").  A solve that stops without reaching the target
+    reports its status (ENOCONV), and a non-finite result or reference
+    reports None errors."""
     import oracle
     from paper_1612_01855_gb300 import binding, inputs
     out = []
@@ -278,11 +284,13 @@ def precision_study(g, torch, n, k, n0, cs, inners, s_modes, dd_cols=4, stream=N
                 g.trsm_plan_mixed(plan, Ld, inner)
                 cur = inner
             s32 = smode in (True, "fp32")
-            stc = smode == "tc"
+            tc_planes = {"tc": 3, "tc2": 2, "tc1": 1}.get(smode)
+            stc = tc_planes is not None
             def solve(X=None):
                 try:
-                    X, it, upd = g.trsm_solve_mixed(plan, Bd, X=X, residual=res, max_iter=30, tol=1e-12,
-                                                    raise_on_noconv=False, s_fp32=s32, s_tc=stc)
+                    X, it, upd = g.trsm_solve_mixed(plan, Bd, X=X, residual=res, max_iter=30, tol=tol,
+                                                    raise_on_noconv=False, s_fp32=s32, s_tc=stc,
+                                                    s_tc_planes=tc_planes or 3)
                     return X, it, upd, 0
                 except binding.TrsmError as e:  # e.g. a non-finite working copy
                     return X, None, None, e.code
@@ -295,7 +303,7 @@ def precision_study(g, torch, n, k, n0, cs, inners, s_modes, dd_cols=4, stream=N
             fe = ferr(X) if X is not None else None
             converged = bool(fe is not None and fe <= 1e-10)
             status = "ok" if converged else ("non-finite" if fe is None else "target missed")
-            rec["mixed"].append({"inner": inner, "s_step": "tc" if stc else "fp32" if s32 else "fp64",
+            rec["mixed"].append({"inner": inner, "s_step": smode if stc else "fp32" if s32 else "fp64",
                                  "residual": res, "ms": round(tm, 2),
                                  "tflops_equiv": round(float(n) * n * k / (tm * 1e-3) / 1e12, 3),
                                  "iterations": it, "last_update": upd, "fwd_err": fe,
@@ -667,8 +675,8 @@ def run_case(args):
                      digit planes, twice;
     mixed:N:K:N0[:I[:S]]  one mixed-precision refined solve (graded diagonal,
                      c = 2); inner I = 0 tf32, 1 bf16, 2 split bf16, 3 split
-                     fp16; S = 1 for the FP32 diagonal-block multiply, 2 for
-                     the tensor-core one;
+                     fp16; S = 1 for the FP32 diagonal-block multiply, 2, 3
+                     or 4 for the tensor-core one with 3, 2 or 1 tf32 planes;
     sched:N:K:N0     the sliced schedule of the FP64 solve (well-conditioned
                      L), its digit planes made first, then two solves;
     engine:M:N:K     the bf16 tensor-core GEMM self-test, twice;
@@ -707,8 +715,9 @@ def run_case(args):
             inner = ("tf32", "bf16", "bf16x3", "fp16x3")[dims[3]] if len(dims) > 3 else "tf32"
             plan = g.trsm_plan(L, dims[2])
             g.trsm_plan_mixed(plan, L, inner)
-            g.trsm_solve_mixed(plan, B, max_iter=30, tol=1e-12, raise_on_noconv=False,
-                               s_fp32=len(dims) > 4 and dims[4] == 1, s_tc=len(dims) > 4 and dims[4] == 2)
+            sm = dims[4] if len(dims) > 4 else 0
+            g.trsm_solve_mixed(plan, B, max_iter=30, tol=1e-11, raise_on_noconv=False, s_fp32=sm == 1,
+                               s_tc=sm in (2, 3, 4), s_tc_planes={2: 3, 3: 2, 4: 1}.get(sm, 3))
     elif kind == "sched":
         n, k, n0 = dims
         L = torch.tril(torch.rand(n, n, dtype=torch.float64, device="cuda") * 2 - 1) / n
@@ -920,11 +929,13 @@ def run_ours(args, rank, world, local):
         residual = residual_roofline(g, torch)
     if rank == 0 and not args.no_mixed and not args.shapes:
         # config 2 at c = 2, 4, 6 at the mixed path's block size: refined
-        # solves (split-fp16 updates with FP32 diagonal multiplies, tf32
-        # updates with tensor-core ones; the adaptive residual), and the
-        # sliced schedule's direct FP64-class solve
+        # solves (split-fp16 updates with FP32 diagonal multiplies or
+        # tensor-core ones of two tf32 planes, tf32 updates with tensor-core
+        # ones of three; the adaptive residual), and the sliced schedule's
+        # direct FP64-class solve
         mixed = precision_study(g, torch, 16384, 4096, MIXED_N0, [2, 4, 6], None, None,
-                                combos=[("fp16x3", "fp32", "adaptive"), ("tf32", "tc", "adaptive")],
+                                combos=[("fp16x3", "fp32", "adaptive"), ("fp16x3", "tc2", "adaptive"),
+                                        ("tf32", "tc", "adaptive")],
                                 with_sliced=True)
 
     batched = None

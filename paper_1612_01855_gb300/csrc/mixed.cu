@@ -309,6 +309,40 @@ __global__ void pack_w_tf32_kernel(const float* __restrict__ W, int64_t ldw, int
   }
 }
 
+// The same with four rows per thread in 16-byte accesses (ldw, s0 and n0p
+// multiples of 4, W 16-byte aligned) and two columns in flight.
+template <int P>
+__global__ void pack_w_tf32_vec_kernel(const float* __restrict__ W, int64_t ldw, int64_t s0, int m, int64_t k,
+                                       int64_t n0p, float* __restrict__ Wt) {
+  const int64_t t = 4 * (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x);
+  if (t >= n0p) return;
+  const int64_t plane = k * n0p;
+  auto load = [&](int64_t j) {
+    const float* src = W + j * ldw + s0 + t;
+    if (t + 3 < m) return *reinterpret_cast<const float4*>(src);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (t < m) v.x = src[0];
+    if (t + 1 < m) v.y = src[1];
+    if (t + 2 < m) v.z = src[2];
+    return v;
+  };
+  auto store = [&](int64_t j, float4 w) {
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      const float4 p = make_float4(to_tf32(w.x), to_tf32(w.y), to_tf32(w.z), to_tf32(w.w));
+      *reinterpret_cast<float4*>(Wt + q * plane + j * n0p + t) = p;
+      w = make_float4(w.x - p.x, w.y - p.y, w.z - p.z, w.w - p.w);
+    }
+  };
+  for (int64_t j = blockIdx.y; j < k; j += 2 * static_cast<int64_t>(gridDim.y)) {
+    const int64_t j2 = j + gridDim.y;
+    const float4 a = load(j);
+    const float4 b = j2 < k ? load(j2) : make_float4(0.f, 0.f, 0.f, 0.f);
+    store(j, a);
+    if (j2 < k) store(j2, b);
+  }
+}
+
 // D_i (FP64) into the low-precision B operand of the update (bf16, tf32 or
 // split bf16; split fp16 takes pack_dt_f16_kernel): the tensor-core
 // diagonal multiply writes D alone.
@@ -988,7 +1022,13 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
         // max |D_i| from the epilogue; then D_i into the update's operand
         const dim3 gw(static_cast<unsigned>((n0p + 255) / 256),
                       static_cast<unsigned>(std::min<int64_t>(k, std::max<int64_t>(1, 4864 / ((n0p + 255) / 256)))));
-        if (tc_planes == 3) trsm::pack_w_tf32_kernel<3><<<gw, 256, 0, s>>>(W, ld, s0, m, k, n0p, Wt);
+        if (s0 % 4 == 0 && n0p % 4 == 0 && ld % 4 == 0) {
+          const dim3 gv(static_cast<unsigned>((n0p / 4 + 255) / 256),
+                        static_cast<unsigned>(std::min<int64_t>(k, std::max<int64_t>(1, 2432 / ((n0p / 4 + 255) / 256)))));
+          if (tc_planes == 3) trsm::pack_w_tf32_vec_kernel<3><<<gv, 256, 0, s>>>(W, ld, s0, m, k, n0p, Wt);
+          else if (tc_planes == 2) trsm::pack_w_tf32_vec_kernel<2><<<gv, 256, 0, s>>>(W, ld, s0, m, k, n0p, Wt);
+          else trsm::pack_w_tf32_vec_kernel<1><<<gv, 256, 0, s>>>(W, ld, s0, m, k, n0p, Wt);
+        } else if (tc_planes == 3) trsm::pack_w_tf32_kernel<3><<<gw, 256, 0, s>>>(W, ld, s0, m, k, n0p, Wt);
         else if (tc_planes == 2) trsm::pack_w_tf32_kernel<2><<<gw, 256, 0, s>>>(W, ld, s0, m, k, n0p, Wt);
         else trsm::pack_w_tf32_kernel<1><<<gw, 256, 0, s>>>(W, ld, s0, m, k, n0p, Wt);
         trsm::count_launch();

@@ -76,7 +76,7 @@ def test_mixed_well_conditioned(cuda_lib, inner, residual, smode, n, k, n0):
 
 @pytest.mark.parametrize("inner", ["tf32", "bf16x3", "fp16x3"])
 @pytest.mark.parametrize("smode", ["fp32", "tc", "tc2", "tc1"])
-@pytest.mark.parametrize("n,k,n0", [(1500, 70, 600), (2048, 33, 1024), (1100, 130, 512)])
+@pytest.mark.parametrize("n,k,n0", [(1500, 70, 600), (2048, 33, 1024), (1100, 130, 512), (700, 21, 250)])
 def test_mixed_wide_blocks_fp32_diagonal_multiply(cuda_lib, inner, smode, n, k, n0):
     """Blocks of 512 rows and more take the 64 x 64 register-blocked FP32
     diagonal multiply (ragged last blocks the 32 x 32 tile), or the
