@@ -680,8 +680,10 @@ def run_case(args):
     sched:N:K:N0     the sliced schedule of the FP64 solve (well-conditioned
                      L), its digit planes made first, then two solves;
     engine:M:N:K     the bf16 tensor-core GEMM self-test, twice;
-    batch:COUNT:BITS one batched launch of COUNT systems of the batching
-                     workload in FP64 (BITS = 64) or FP32 (32), twice."""
+    batch:COUNT:BITS[:N0] one batched launch of COUNT systems of the
+                     batching workload in FP64 (BITS = 64) or FP32 (32),
+                     twice; n0 = N0 for every system, else 32 below n = 256
+                     and 64 above."""
     import ctypes
     import torch
     import paper_1612_01855_gb300 as g
@@ -741,7 +743,8 @@ def run_case(args):
                                              ctypes.c_void_p(err.data_ptr()), s) == 0
     elif kind == "batch":
         dtype = "f64" if dims[1] == 64 else "f32"
-        systems, _ = batch_systems(torch, dims[0], dtype, 1000, lambda n: 32 if n < 256 else 64)
+        rule = (lambda n: dims[2]) if len(dims) > 2 else (lambda n: 32 if n < 256 else 64)
+        systems, _ = batch_systems(torch, dims[0], dtype, 1000, rule)
         batch = g.Batch(systems, dtype=dtype)
         for _ in range(2):
             batch.run()
@@ -1041,7 +1044,7 @@ def main():
     ap.add_argument("--details", default="", help="also write every study's full records to this JSON file")
     ap.add_argument("--precision", action="store_true", help="print the full c x inner x s-step study")
     ap.add_argument("--case", default="", help="profiling case: sliced:N:K[:PLANES], mixed:N:K:N0[:INNER[:S]], "
-                                               "sched:N:K:N0, engine:M:N:K, batch:COUNT:BITS")
+                                               "sched:N:K:N0, engine:M:N:K, batch:COUNT:BITS[:N0]")
     ap.add_argument("--shapes", default="", help="override workload, e.g. 6144:1024:256 (not a bench line)")
     args = ap.parse_args()
     rank, world, local = dist_env()

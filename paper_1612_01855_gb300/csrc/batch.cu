@@ -332,7 +332,14 @@ constexpr int kSysMaxCW = 32;  // widest column chunk of a unit
 // registers, 1.60 -> 2.05 ms at five CTAs per SM; L~_ll alone copied by
 // cp.async behind the product, 1.74 ms.)
 struct SysSmem {
-  float inv[64][68];  // inv[col][row]: L~_ll, zeros above the diagonal (rows 16-byte aligned)
+  union {
+    float inv[64][68];  // inv[col][row]: L~_ll, zeros above the diagonal (rows 16-byte aligned)
+    struct {            // n0 = 32: the two 32-blocks of a 64-row step, column-major ([col][row])
+      float i11[32][36];  // L~ of the step's first block
+      float i22[32][36];  // L~ of its second block
+      float l21[32][36];  // L(second block rows, first block columns)
+    } p;
+  };
   union {
     float w[64][kSysMaxCW + 4];  // w[row][col]: W_l for the chunk's columns
     struct {
@@ -636,6 +643,233 @@ __device__ void sys_unit(const UnitSys& a, int c0, SysSmem& sm) {
   }
 }
 
+// n0 = 32: the unit walks the system in steps of 64 rows, two diagonal
+// blocks b0 = 2p and b1 = 2p + 1 per step.  W = B - L(S, 0:s0) X(0:s0) is
+// the same 64-row product as above; then, in It-Inv-TRSM's order for the
+// two blocks, X_b0 = L~_b0 W_top, W_bot -= L(b1, b0) X_b0, X_b1 = L~_b1 W_bot
+// (Section 6.2 with n0 = 32, the updates of earlier blocks gathered into
+// one product per step).  Thread (ty, tx) owns rows 2 ty, 2 ty + 1 of a
+// 32-row half and columns CPT tx .. CPT tx + CPT - 1; warp w holds rows
+// 8w .. 8w + 7, so its triangular sums stop at t = 8w + 8.
+template <int CW>
+__device__ __forceinline__ void half_mma(const float (*A)[36], const float* W, int ldw, int tend, int ty, int tx,
+                                         float (&acc)[2][CW / 8]) {
+  constexpr int CPT = CW / 8;
+#pragma unroll 8
+  for (int t = 0; t < tend; ++t) {
+    const float2 a2 = *reinterpret_cast<const float2*>(&A[t][2 * ty]);
+    float wv[CPT];
+    load_row<CPT>(W + t * ldw + tx * CPT, wv);
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) {
+      acc[0][j] = fmaf(a2.x, wv[j], acc[0][j]);
+      acc[1][j] = fmaf(a2.y, wv[j], acc[1][j]);
+    }
+  }
+}
+
+template <int CW>
+__device__ void sys_unit_pair(const UnitSys& a, int c0, SysSmem& sm) {
+  constexpr int CPT = CW / 8;
+  constexpr int TX = CW / CPT;                   // threads along the columns (8)
+  constexpr int TM = 64 * TX / kSysThreads;      // rows per thread of the product (4)
+  constexpr int NB = kSysKC * CW / kSysThreads;  // staged X values per thread and chunk
+  constexpr int LDW = kSysMaxCW + 4;
+  const int tid = threadIdx.x, ty = tid / TX, tx = tid % TX;
+  const int nc = static_cast<int>(imin64(CW, a.k - c0));
+  const int arow = tid & 63, akk = tid >> 6;
+  const int bkk = tid & 31, bcol = tid >> 5;
+  constexpr int kBColStep = kSysThreads / 32;
+  const int64_t astep = 2 * a.ldl, bstep = kBColStep * a.ldx;
+  bool bok[NB];
+#pragma unroll
+  for (int it = 0; it < NB; ++it) bok[it] = bcol + kBColStep * it < nc;
+  const float* const pb0 = a.X + static_cast<int64_t>(c0 + bcol) * a.ldx + bkk;
+  const int steps = static_cast<int>((a.n + 63) / 64);
+  const int warp_end = 8 * (tid >> 5) + 8;  // triangular stop of the 32-row halves
+  for (int p = 0; p < steps; ++p) {
+    const int64_t s0 = static_cast<int64_t>(p) * 64;
+    const int m = static_cast<int>(imin64(64, a.n - s0));
+    const int m0 = min(32, m), m1 = m - m0;
+    {
+      // L~_b0, L~_b1 and L(b1, b0), every load in flight before the stores
+      const int r = tid & 31, c = tid >> 5;  // 4 columns per pass, 8 passes
+      const float* I0 = a.Linv + static_cast<int64_t>(2 * p) * a.inv_bstride;
+      const float* I1 = I0 + a.inv_bstride;
+      const float* L21 = a.L + s0 * a.ldl + s0 + 32;
+      float v0[8], v1[8], v2[8];
+#pragma unroll
+      for (int it = 0; it < 8; ++it) {
+        const int cc = c + 4 * it;
+        v0[it] = (r < m0 && cc < m0) ? I0[cc * 32 + r] : 0.f;
+        v1[it] = (r < m1 && cc < m1) ? I1[cc * 32 + r] : 0.f;
+        v2[it] = (r < m1 && cc < m0) ? L21[static_cast<int64_t>(cc) * a.ldl + r] : 0.f;
+      }
+#pragma unroll
+      for (int it = 0; it < 8; ++it) {
+        const int cc = c + 4 * it;
+        sm.p.i11[cc][r] = v0[it];
+        sm.p.i22[cc][r] = v1[it];
+        sm.p.l21[cc][r] = v2[it];
+      }
+    }
+    float acc[TM][CPT];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < CPT; ++j) acc[i][j] = 0.f;
+    const bool aok = arow < m;
+    const float* pa = a.L + static_cast<int64_t>(akk) * a.ldl + s0 + arow;
+    const float* pb = pb0;
+    float ra[16], rb[NB];
+    auto load = [&]() {
+      const float* q = pa;
+#pragma unroll
+      for (int it = 0; it < 16; ++it) {
+        ra[it] = aok ? *q : 0.f;
+        q += astep;
+      }
+      const float* r = pb;
+#pragma unroll
+      for (int it = 0; it < NB; ++it) {
+        rb[it] = bok[it] ? *r : 0.f;
+        r += bstep;
+      }
+      pa += kSysKC * a.ldl;
+      pb += kSysKC;
+    };
+    if (s0 > 0) load();
+    for (int64_t t0 = 0; t0 < s0; t0 += kSysKC) {
+#pragma unroll
+      for (int it = 0; it < 16; ++it) sm.g.a[akk + 2 * it][arow] = ra[it];
+#pragma unroll
+      for (int it = 0; it < NB; ++it) sm.g.b[bkk][bcol + kBColStep * it] = rb[it];
+      __syncthreads();
+      if (t0 + kSysKC < s0) load();
+#pragma unroll 8
+      for (int kk = 0; kk < kSysKC; ++kk) {
+        float a4[TM];
+        load_rows<TM>(&sm.g.a[kk][ty * TM], a4);
+        float bv[CPT];
+        load_row<CPT>(&sm.g.b[kk][tx * CPT], bv);
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < CPT; ++j) acc[i][j] = fmaf(a4[i], bv[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+    // W = B - acc for the step's 64 rows (zeros outside the step and the chunk)
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      const int row = ty * TM + i;
+#pragma unroll
+      for (int j = 0; j < CPT; ++j) {
+        const int col = tx * CPT + j;
+        sm.w[row][col] = (row < m && col < nc)
+                             ? a.B[static_cast<int64_t>(c0 + col) * a.ldb + s0 + row] - acc[i][j]
+                             : 0.f;
+      }
+    }
+    __syncthreads();
+    const int r0 = 2 * ty;
+    float x[2][CPT];
+    // X_b0 = L~_b0 W_top
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < CPT; ++j) x[i][j] = 0.f;
+    half_mma<CW>(sm.p.i11, &sm.w[0][0], LDW, min((m0 + 7) & ~7, warp_end), ty, tx, x);
+    __syncthreads();  // every read of W_top done before it is overwritten by X_b0
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < CPT; ++j) {
+        const int row = r0 + i, col = tx * CPT + j;
+        sm.w[row][col] = x[i][j];
+        if (row < m0 && col < nc) a.X[static_cast<int64_t>(c0 + col) * a.ldx + s0 + row] = x[i][j];
+      }
+    __syncthreads();
+    if (m1 > 0) {
+      // W_bot -= L(b1, b0) X_b0 (each thread updates only its own W_bot values)
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) x[i][j] = 0.f;
+      half_mma<CW>(sm.p.l21, &sm.w[0][0], LDW, (m0 + 7) & ~7, ty, tx, x);
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) sm.w[32 + r0 + i][tx * CPT + j] -= x[i][j];
+      __syncthreads();
+      // X_b1 = L~_b1 W_bot
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) x[i][j] = 0.f;
+      half_mma<CW>(sm.p.i22, &sm.w[32][0], LDW, min((m1 + 7) & ~7, warp_end), ty, tx, x);
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) {
+          const int row = r0 + i, col = tx * CPT + j;
+          if (row < m1 && col < nc) a.X[static_cast<int64_t>(c0 + col) * a.ldx + s0 + 32 + row] = x[i][j];
+        }
+    }
+    __syncthreads();  // X of the step visible to the block before the next step reads it
+  }
+}
+
+// n0 = 32: one warp per diagonal block, RecTriInv's base case (column
+// substitution, Section 5.1) with a lane per column of the inverse: lane c
+// forms L~(:, c) row by row, x_i = (e_c(i) - sum_{j<i} L(i, j) x_j) / L(i, i),
+// the row of L read from shared memory as one broadcast; the entries above
+// row c come out zero.  Eight blocks per CTA.
+__global__ void __launch_bounds__(256) inv32w_kernel(const BatchSys<float>* __restrict__ sys,
+                                                     const SysUnit* __restrict__ blocks, int nblocks) {
+  __shared__ float Ls[8][32][33];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int bi = blockIdx.x * 8 + w;
+  if (bi >= nblocks) return;  // a warp's own work: no block-wide barrier below
+  const SysUnit u = blocks[bi];
+  const BatchSys<float>& a = sys[u.sys];
+  const int64_t s0 = static_cast<int64_t>(u.c0) * 32;
+  const int m = static_cast<int>(imin64(32, a.n - s0));
+  const float* Lb = a.L + s0 * a.ldl + s0;
+  float(*S)[33] = Ls[w];
+  // S(r, c) = L(s0 + r, s0 + c) on and below the diagonal, the identity past m
+  {
+    float v[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c)
+      v[c] = (lane < m && c < m && lane >= c) ? Lb[static_cast<int64_t>(c) * a.ldl + lane]
+                                              : (lane == c && lane >= m ? 1.f : 0.f);
+#pragma unroll
+    for (int c = 0; c < 32; ++c) S[lane][c] = v[c];
+  }
+  __syncwarp();
+  const float piv = S[lane][lane];
+  if (lane < m && (piv == 0.f || !isfinite(piv)))
+    atomicMax(a.status, INT_MAX - static_cast<int>(s0 + lane));  // status: INT_MAX - first singular row
+  const float rcp = 1.f / piv;
+  float x[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    float acc = (i == lane) ? 1.f : 0.f;
+#pragma unroll
+    for (int j = 0; j < i; ++j) acc = fmaf(-S[i][j], x[j], acc);
+    x[i] = acc * __shfl_sync(0xffffffffu, rcp, i);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int i = 0; i < 32; ++i) S[i][lane] = x[i];
+  __syncwarp();
+  float* Li = const_cast<float*>(a.Linv) + static_cast<int64_t>(u.c0) * a.inv_bstride;
+#pragma unroll 8
+  for (int c = 0; c < 32; ++c)
+    if (c < m && lane < m) Li[c * 32 + lane] = S[lane][c];
+}
+
 // Diagonal block `c0` of system `sys` (the unit's fields reused) into the
 // system's inverse workspace (column-major, ld n0).
 __global__ void __launch_bounds__(kSysThreads) inv32_kernel(const BatchSys<float>* __restrict__ sys,
@@ -664,9 +898,17 @@ __global__ void __launch_bounds__(kSysThreads, 6) sys32_kernel(const BatchSys<fl
     us = UnitSys{a.L, a.Linv, a.B, a.X, a.ldl, a.ldinv, a.inv_bstride, a.ldb, a.ldx, a.n, a.k, a.n0, a.N};
   }
   __syncthreads();
-  if (u.cw == 8) sys_unit<8>(us, u.c0, sm);
-  else if (u.cw == 16) sys_unit<16>(us, u.c0, sm);
-  else sys_unit<32>(us, u.c0, sm);
+  if (us.n0 == 32) {
+    if (u.cw == 8) sys_unit_pair<8>(us, u.c0, sm);
+    else if (u.cw == 16) sys_unit_pair<16>(us, u.c0, sm);
+    else sys_unit_pair<32>(us, u.c0, sm);
+  } else if (u.cw == 8) {
+    sys_unit<8>(us, u.c0, sm);
+  } else if (u.cw == 16) {
+    sys_unit<16>(us, u.c0, sm);
+  } else {
+    sys_unit<32>(us, u.c0, sm);
+  }
 }
 
 // One (phase, part, system) range of tickets.
@@ -854,7 +1096,8 @@ struct trsm_batch_s {
   void* sys_dev = nullptr;   // BatchSys<T>[count], then the phase entries
   void* ent_dev = nullptr;
   int nent = 0;
-  int ninv = 0;              // FP32: diagonal blocks, inverted by a first launch
+  int ninv = 0;              // FP32: diagonal blocks of order 64 (or n0 < 32), inverted by a first launch
+  int ninv32 = 0;            // FP32: diagonal blocks of order 32, one warp each
   void* ws = nullptr;        // W, inverses, scratch, counters, task tables
   size_t ws_bytes = 0;
   bool owns_ws = true;
@@ -1106,7 +1349,7 @@ int build_batch32(const trsm_batch_item* items, int count, trsm_batch_s* b, void
                   cudaStream_t stream, size_t* size_only) {
   using trsm::BatchSys;
   std::vector<BatchSys<float>> sys(count);
-  std::vector<trsm::SysUnit> units, blocks;
+  std::vector<trsm::SysUnit> units, blocks, blocks32;
   size_t off = 0;
   std::vector<size_t> inv_off(count);
   for (int s = 0; s < count; ++s) {
@@ -1140,7 +1383,8 @@ int build_batch32(const trsm_batch_item* items, int count, trsm_batch_s* b, void
     } else {
       for (int c = 0; c < a.C; ++c) units.push_back(trsm::SysUnit{s, c * a.cw, a.cw});
     }
-    for (int l = 0; l < a.N; ++l) blocks.push_back(trsm::SysUnit{s, l, 0});
+    // n0 = 32: warp-per-block inversions (inv32w_kernel); else a CTA per block
+    for (int l = 0; l < a.N; ++l) (a.n0 == 32 ? blocks32 : blocks).push_back(trsm::SysUnit{s, l, 0});
   }
   std::stable_sort(units.begin(), units.end(), [&](const trsm::SysUnit& x, const trsm::SysUnit& y) {
     const BatchSys<float>& p = sys[x.sys];
@@ -1150,7 +1394,7 @@ int build_batch32(const trsm_batch_item* items, int count, trsm_batch_s* b, void
   const size_t table_off = off;
   off = trsm::al256(off + sizeof(BatchSys<float>) * count);
   const size_t unit_off = off;
-  off = trsm::al256(off + sizeof(trsm::SysUnit) * (units.size() + blocks.size()));
+  off = trsm::al256(off + sizeof(trsm::SysUnit) * (units.size() + blocks.size() + blocks32.size()));
   b->counters_off = off;  // statuses and the error word: zeroed by every run
   const size_t status_off = off;
   off = trsm::al256(off + sizeof(int) * count);
@@ -1185,7 +1429,9 @@ int build_batch32(const trsm_batch_item* items, int count, trsm_batch_s* b, void
   b->total = static_cast<int64_t>(units.size());
   b->grid = static_cast<int>(units.size());
   b->ninv = static_cast<int>(blocks.size());
-  units.insert(units.end(), blocks.begin(), blocks.end());  // the block table follows the units
+  b->ninv32 = static_cast<int>(blocks32.size());
+  units.insert(units.end(), blocks.begin(), blocks.end());  // the block tables follow the units
+  units.insert(units.end(), blocks32.begin(), blocks32.end());
   b->host_tables.resize(sizeof(BatchSys<float>) * count + sizeof(trsm::SysUnit) * units.size());
   memcpy(b->host_tables.data(), sys.data(), sizeof(BatchSys<float>) * count);
   memcpy(b->host_tables.data() + sizeof(BatchSys<float>) * count, units.data(), sizeof(trsm::SysUnit) * units.size());
@@ -1210,9 +1456,15 @@ int enqueue(trsm_batch_s* b, cudaStream_t s) {
   else {
     const auto* sys = static_cast<const trsm::BatchSys<float>*>(b->sys_dev);
     const auto* units = static_cast<const trsm::SysUnit*>(b->ent_dev);
-    trsm::inv32_kernel<<<b->ninv, trsm::kSysThreads, 0, s>>>(sys, units + b->nent);
+    if (b->ninv > 0) {
+      trsm::inv32_kernel<<<b->ninv, trsm::kSysThreads, 0, s>>>(sys, units + b->nent);
+      trsm::count_launch();
+    }
+    if (b->ninv32 > 0) {
+      trsm::inv32w_kernel<<<(b->ninv32 + 7) / 8, 256, 0, s>>>(sys, units + b->nent + b->ninv, b->ninv32);
+      trsm::count_launch();
+    }
     trsm::sys32_kernel<<<b->grid, trsm::kSysThreads, 0, s>>>(sys, units);
-    trsm::count_launch();
   }
   trsm::count_launch();
   return cudaGetLastError() == cudaSuccess ? TRSM_SUCCESS : TRSM_ECUDA;
