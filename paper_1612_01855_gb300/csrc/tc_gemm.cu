@@ -122,11 +122,20 @@ struct StoreF64MaxEpi {
   unsigned long long* dmax;
   struct State {};
   // Launch order -> tile: the row tiles from the last (longest sums) to the
-  // first, each over all its column tiles.
+  // first, each over all its column tiles.  In the persistent kernel CTA c
+  // takes the tiles t = c, c + G, c + 2G, ... (G CTAs); lower triangular
+  // tiles are dealt in a snake over those rounds, every odd round in
+  // reverse, so that the CTA that took one of the longest tiles in round 0
+  // takes one of the shortest in round 1 (straight rounds gave one CTA
+  // 12 K-blocks of 128 and another 4 at n0 = 1024; the snake at most 9).
   __device__ void tile_of(int lin, int R, int C, int& tm, int& tn) const {
     if (lower) {
-      tm = R - 1 - lin / C;
-      tn = lin % C;
+      const int G = static_cast<int>(gridDim.x), T = R * C;
+      const int r = lin / G, c = lin - r * G;
+      const int w = min(G, T - r * G);  // CTAs with a tile in round r
+      const int idx = (r & 1) ? r * G + (w - 1 - c) : lin;
+      tm = R - 1 - idx / C;
+      tn = idx % C;
     } else {
       tm = lin % R;
       tn = lin / R;
@@ -135,7 +144,9 @@ struct StoreF64MaxEpi {
   __device__ void tile(int& tm, int& tn) const {
     if (!lower) return;
     const int R = static_cast<int>(gridDim.x), C = static_cast<int>(gridDim.y);
-    tile_of(tm + R * tn, R, C, tm, tn);
+    const int lin = tm + R * tn;
+    tm = R - 1 - lin / C;
+    tn = lin % C;
   }
   __device__ void k_range(int tm, int, int& kb0, int& kb1, int& chunk) const {
     const int kend = lower ? min(K, (tm + 1) * 128) : K;
