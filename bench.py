@@ -469,8 +469,9 @@ def batched_study(g, torch, count=4096, dtypes=("f64", "f32"), reps=5, seed=1000
     """Batching workload: `count` independent systems, n log-uniform in
     [32, 1024], k log-uniform in [1, 256], diagonal U[2,3], strictly lower
     U[-1,1]/n, B U[-1,1] (drawn on the device from a per-system seed), all
-    solved (in-launch inversion + blocked solve) by one persistent launch,
-    replayed as a CUDA graph; n0 per size bucket from the autotuner."""
+    solved in one CUDA graph replay: FP64 by one persistent launch
+    (in-launch inversion + blocked solve), FP32 by an inversion launch and a
+    unit launch; n0 and tile widths per size bucket from the autotuner."""
     from paper_1612_01855_gb300 import autotune
     out = []
     for dtype in dtypes:
@@ -502,7 +503,9 @@ def batched_study(g, torch, count=4096, dtypes=("f64", "f32"), reps=5, seed=1000
             peak, src = fp32_peak, "measured FFMA throughput (trsm_fp32_peak) in this run"
         out.append({"dtype": dtype, "systems": count, "ms_per_batch": round(ms, 3),
                     "tflops_n2k": round(achieved, 3), "status": rc,
-                    "roofline": {"bound": "alu", "kernel": "batch_kernel", "achieved": round(achieved, 4),
+                    "roofline": {"bound": "alu",
+                                 "kernel": "batch_kernel" if dtype == "f64" else "inv32w_kernel + sys32_kernel",
+                                 "achieved": round(achieved, 4),
                                  "peak": round(peak, 4), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
                                  "peak_source": src},
                     "n0_by_bucket": {f"{lo}-{hi - 1}": table[i][0] for i, (lo, hi) in enumerate(autotune.BUCKETS)},
