@@ -1132,9 +1132,6 @@ struct Part {
   int owner;     // part whose inverted blocks this part reads, or -1
 };
 
-// FP64 tile width fitted to k columns: k itself below 4, else the next
-// multiple of 4, at most 32.
-int fitted_cw(int64_t k) { return k >= 32 ? 32 : k < 4 ? static_cast<int>(k) : static_cast<int>((k + 3) / 4 * 4); }
 
 std::vector<Part> split_parts(const trsm_batch_item* items, int count) {
   std::vector<Part> parts;
