@@ -113,11 +113,13 @@ def test_batch_fp32_tiles_mix_and_graph_are_bitwise_stable(cuda_lib):
     assert all(torch.equal(sy["X"], x0) for sy, x0 in zip(systems, ref))
 
 
-def test_batch_fp32_reports_singular_item(cuda_lib):
+@pytest.mark.parametrize("n0", [None, 32, 64])
+def test_batch_fp32_reports_singular_item(cuda_lib, n0):
     """A zero pivot is reported by the first failing item and its row; a
-    later failing item does not hide it."""
+    later failing item does not hide it.  n0 = 32: the warp-per-block
+    inversions; 64: the CTA-per-block RecTriInv; None: both in one batch."""
     import paper_1612_01855_gb300 as g
-    systems = _systems(8, 200, 40, seed=5, dtype=np.float32)
+    systems = _systems(8, 200, 40, seed=5, dtype=np.float32, n0s=(32, 64) if n0 is None else (n0,))
     bad = next(i for i in range(2, 7) if systems[i]["Lh"].shape[0] >= 4)
     r = systems[bad]["Lh"].shape[0] // 2
     systems[bad]["L"][r, r] = 0.0
@@ -126,6 +128,34 @@ def test_batch_fp32_reports_singular_item(cuda_lib):
     b.run()
     rc, item, row = b.status()
     assert rc == -2 and item == bad and row == r
+
+
+def test_batch_fp32_n0_32_two_block_steps(cuda_lib):
+    """n0 = 32: the units walk 64-row steps of two blocks (the second
+    block's update by the first in between); sizes that end a step after
+    one block, in the middle of the second, or on a step boundary, and
+    narrow and wide column chunks, against the oracle and against n0 = 64."""
+    import torch
+    import paper_1612_01855_gb300 as g
+    shapes = [(32, 5), (33, 40), (64, 17), (95, 64), (96, 33), (128, 8), (129, 100), (500, 256), (1000, 31)]
+    got = {}
+    for n0 in (32, 64):
+        systems = []
+        for i, (n, k) in enumerate(shapes):
+            L, B = inputs.well_conditioned(n, k, seed=4200 + i)
+            systems.append({"Lh": L, "Bh": B, "L": _dev(L, np.float32), "B": _dev(B, np.float32),
+                            "X": torch.full((k, n), float("nan"), dtype=torch.float32, device="cuda").t(),
+                            "n0": n0})
+        b = g.Batch(systems, dtype="f32")
+        b.run()
+        assert b.status()[0] == 0
+        got[n0] = [sy["X"].cpu().numpy().astype(np.float64) for sy in systems]
+        for sy, x in zip(systems, got[n0]):
+            want = oracle.forward_subst(sy["Lh"].astype(np.float32).astype(np.float64),
+                                        sy["Bh"].astype(np.float32).astype(np.float64))
+            assert _rel(x, want) < TOL32, (n0, sy["Lh"].shape[0])
+    for a, c in zip(got[32], got[64]):
+        assert _rel(a, c) < 2 * TOL32
 
 
 def test_batch_with_resident_plans_and_graph(cuda_lib):
