@@ -605,7 +605,7 @@ def sliced_study(g, torch, data, dev_in, outs, shapes, reps=3):
 
 
 def serving_study(g, torch, nL=256, rates=(100, 300, 600, 1200), per_rate=300, seed=2000,
-                  budget_gb=150.0, mixed_min_n=2048, sliced_min_flops=3e9, streams=8):
+                  budget_gb=150.0, mixed_min_n=2048, sliced_min_flops=3e8, streams=8):
     """Serving workload: nL resident L (n log-uniform in [64, 8192],
     diagonal U[2,3], strictly lower U[-1,1]/n, drawn on the device), each
     planned once; Poisson request streams at the given rates, each request a
