@@ -605,7 +605,7 @@ def sliced_study(g, torch, data, dev_in, outs, shapes, reps=3):
 
 
 def serving_study(g, torch, nL=256, rates=(100, 300, 600, 1200), per_rate=300, seed=2000,
-                  budget_gb=150.0, mixed_min_n=2048, sliced_min_flops=3e8, streams=8):
+                  budget_gb=150.0, mixed_min_n=2048, sliced_min_flops=3e8, streams=8, mixed_s="tc2"):
     """Serving workload: nL resident L (n log-uniform in [64, 8192],
     diagonal U[2,3], strictly lower U[-1,1]/n, drawn on the device), each
     planned once; Poisson request streams at the given rates, each request a
@@ -653,7 +653,7 @@ def serving_study(g, torch, nL=256, rates=(100, 300, 600, 1200), per_rate=300, s
             reqs.append(Request(rid, lid, B, t, mixed=mixed))
         torch.cuda.synchronize()
         srv = Server(plans, budget_bytes=int(budget_gb * 1e9), streams=streams, max_batch=64,
-                     sliced_min_flops=sliced_min_flops)
+                     sliced_min_flops=sliced_min_flops, mixed_s=mixed_s)
         st = srv.run_trace(reqs)
         st["offered_rate"] = rate
         out["rates"].append({k: (round(v, 4) if isinstance(v, float) else v) for k, v in st.items()})

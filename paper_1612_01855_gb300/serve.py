@@ -17,7 +17,9 @@ pays for the blocked solve (Algorithm It-Inv-TRSM, Section 6.2).  The loop:
   cannot join a persistent batch: it takes a slot alone and runs in a worker
   thread on the slot's stream (the C call releases the interpreter lock).
   At most `mixed_slots` slots hold such solves at a time, so the other slots
-  always keep serving FP64 batches;
+  always keep serving FP64 batches.  `mixed_s` picks its diagonal
+  multiplies: "tc2" (default: two tf32 planes on the tensor cores), "tc",
+  "fp32" or "fp64" (the DFMA pipe, which then dominates the solve);
 * with `sliced_min_flops` set, an FP64 request of at least that many n^2 k
   flops whose plan carries the sliced schedule's digit planes
   (`trsm_plan_sliced`) waits in a third queue and is solved alone on a slot
@@ -137,10 +139,17 @@ def _has_mixed_data(plan):
 
 
 class Server:
+    # keyword arguments of trsm_solve_mixed for each diagonal-multiply mode
+    MIXED_S = {"fp64": {}, "fp32": {"s_fp32": True}, "tc": {"s_tc": True, "s_tc_planes": 3},
+               "tc2": {"s_tc": True, "s_tc_planes": 2}}
+
     def __init__(self, plans, budget_bytes, streams=8, max_batch=64, mixed_slots=None,
-                 mixed_residual="adaptive", sliced_min_flops=None):
+                 mixed_residual="adaptive", sliced_min_flops=None, mixed_s="tc2"):
         if streams < 1:
             raise ValueError("at least one launch slot")
+        if mixed_s not in self.MIXED_S:
+            raise ValueError(f"mixed_s must be one of {sorted(self.MIXED_S)}, not {mixed_s!r}")
+        self.mixed_s = mixed_s
         self.plans = plans
         resident = sum(self.plan_bytes(p) for p in plans)
         self.adm = Admission(budget_bytes, resident)
@@ -283,6 +292,10 @@ class Server:
         if getattr(r.B, "is_cuda", False):
             r.B.record_stream(stream)
 
+    def mixed_kwargs(self):
+        """The diagonal-multiply flags the server's mixed solves use."""
+        return dict(self.MIXED_S[self.mixed_s])
+
     def _solve_mixed(self, slot, r):
         """Worker: one refined mixed-precision solve on the slot's stream.
         Returns (status, iterations)."""
@@ -290,7 +303,7 @@ class Server:
         with torch.cuda.stream(self.streams[slot]):
             try:
                 _, it, _ = binding.trsm_solve_mixed(self.plans[r.lid], r.B, X=r.X, residual=self.mixed_residual,
-                                                    tol=r.tol)
+                                                    tol=r.tol, **self.mixed_kwargs())
                 return 0, it
             except binding.TrsmError as e:
                 return e.code, None

@@ -96,7 +96,8 @@ def test_server_mixes_fp64_and_refined_requests(cuda_lib):
         assert np.max(np.abs(r.X.cpu().numpy() - want)) <= 1e-12 * np.max(np.abs(want)), (r.rid, r.mixed)
         # same bits alone and in the mix, for both kinds of request
         if r.mixed:
-            alone, _, _ = g.trsm_solve_mixed(plans[r.lid], r.B, residual=srv.mixed_residual, tol=r.tol)
+            alone, _, _ = g.trsm_solve_mixed(plans[r.lid], r.B, residual=srv.mixed_residual, tol=r.tol,
+                                             **srv.mixed_kwargs())
         else:
             alone = g.trsm_solve(plans[r.lid], r.B)
             g.trsm_sync_status(plans[r.lid])
