@@ -350,9 +350,9 @@ def compact_precision(recs):
     for rec in recs:
         for m in rec["mixed"]:
             st = "ok" if m["converged"] else ("nan" if m["fwd_err"] is None else "miss")
-            rows.append([rec["c"], m["inner"], m["s_step"], m["ms"], m["iterations"], _sig(m["fwd_err"]),
-                         _sig(m["bwd_err"]), None if st == "nan" else m["speedup_vs_fp64"], st])
-    return {"fp64": fp64, "cols": ["c", "inner", "s", "ms", "sweeps", "fwd", "bwd", "x_fp64", "status"],
+            rows.append([rec["c"], m["inner"], m["s_step"], m["residual"], m["ms"], m["iterations"],
+                         _sig(m["fwd_err"]), _sig(m["bwd_err"]), None if st == "nan" else m["speedup_vs_fp64"], st])
+    return {"fp64": fp64, "cols": ["c", "inner", "s", "residual", "ms", "sweeps", "fwd", "bwd", "x_fp64", "status"],
             "rows": rows}
 
 
@@ -937,11 +937,11 @@ def run_ours(args, rank, world, local):
         # config 2 at c = 2, 4, 6 at the mixed path's block size: refined
         # solves (split-fp16 updates with FP32 diagonal multiplies or
         # tensor-core ones of two tf32 planes, tf32 updates with tensor-core
-        # ones of three; the adaptive residual), and the sliced schedule's
-        # direct FP64-class solve
+        # ones of three; the adaptive residual, and eight planes throughout
+        # for one of them), and the sliced schedule's direct FP64-class solve
         mixed = precision_study(g, torch, 16384, 4096, MIXED_N0, [2, 4, 6], None, None,
                                 combos=[("fp16x3", "fp32", "adaptive"), ("fp16x3", "tc2", "adaptive"),
-                                        ("tf32", "tc", "adaptive")],
+                                        ("fp16x3", "tc2", "sliced8"), ("tf32", "tc", "adaptive")],
                                 with_sliced=True)
 
     batched = None

@@ -58,7 +58,9 @@ extern "C" {
 #define TRSM_RESIDUAL_SLICED 0   /* FP64-class, bf16 tensor cores, 7 integer digit planes */
 #define TRSM_RESIDUAL_FP64 1     /* FP64 fused multiply-add                                */
 #define TRSM_RESIDUAL_SLICED8 2  /* as SLICED with 8 digit planes: ~2^-49 instead of ~2^-43 */
-#define TRSM_RESIDUAL_ADAPTIVE 3 /* SLICED until the updates stagnate above tol, then SLICED8 */
+#define TRSM_RESIDUAL_ADAPTIVE 3 /* SLICED until the updates stagnate above tol or their contraction
+                                    stalls (an update ten times above the last contraction's
+                                    prediction), then SLICED8 */
 /* As ADAPTIVE, but an early residual takes 5 or 6 digit planes (15 or 21
  * plane products instead of 28; about 2^-31 and 2^-37 of |B| + |L||X|)
  * while the iterate's error, estimated from the last update and its

@@ -25,7 +25,8 @@
 //
 // The residual is either the digit-sliced tensor-core product of sliced.cu
 // (relative to |B| + |L||X|: about 2^-43 with seven planes, about 2^-49
-// with eight; or seven until the updates stagnate above tol, then eight) or
+// with eight; or seven until the updates stagnate above tol or their
+// contraction stalls, then eight) or
 // a plain FP64 DFMA product.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -990,9 +991,10 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
   if (e == cudaSuccess) e = cudaMemsetAsync(Dt, 0, esz * n0p * k, s);  // padding columns stay zero
   // The first sweep solves with B itself (its W is made from B_dev) and
   // sets X = D without reading X.
-  double best = HUGE_VAL, prev = HUGE_VAL;
+  double best = HUGE_VAL, prev = HUGE_VAL, prev2 = HUGE_VAL;  // the last two updates
   // digit planes of the sliced residual: the adaptive mode starts with seven
-  // and moves to eight when the updates stagnate above tol; the progressive
+  // and moves to eight when the updates stagnate above tol or their
+  // contraction stalls; the progressive
   // mode chooses five, six or seven from the iterate's estimated error (then
   // eight on stagnation)
   const bool progressive = residual == TRSM_RESIDUAL_PROGRESSIVE;
@@ -1116,11 +1118,25 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
     // refinement has reached the accuracy the residual allows (its error
     // floor) and further sweeps cannot improve X.  Accept the iterate when
     // that floor is small, otherwise report non-convergence.
-    if (it >= 2 && ratio > 0.5 * prev) {
+    // A floor shows one sweep earlier as a stalled contraction: with a
+    // linear contraction the update would be about prev^2 / prev2 (the last
+    // contraction applied once more); ten times that and more means the
+    // residual's error has taken over, so the adaptive modes move to eight
+    // planes at once instead of after a further sweep.
+    const bool stalled = it >= 3 && prev2 < HUGE_VAL && prev < HUGE_VAL && ratio > 10.0 * prev * (prev / prev2);
+    if ((residual == TRSM_RESIDUAL_ADAPTIVE || progressive) && planes < 8 && stalled && !(ratio > 0.5 * prev)) {
+      // the next update corrects the old floor's error: as after a
+      // stagnation, no contraction is judged across the switch
+      planes = 8;
+      floor_planes = planes;
+      prev2 = HUGE_VAL;
+      prev = HUGE_VAL;
+    } else if (it >= 2 && ratio > 0.5 * prev) {
       if ((residual == TRSM_RESIDUAL_ADAPTIVE || progressive) && planes < 8) {
         // lower the residual's floor and keep refining
         planes = progressive && planes < 7 ? 7 : 8;
         floor_planes = planes;
+        prev2 = HUGE_VAL;
         prev = HUGE_VAL;
       } else {
         if (ratio > 1e-10) rc = TRSM_ENOCONV;
@@ -1137,6 +1153,7 @@ extern "C" int trsm_solve_mixed(trsm_handle_t h, const double* B_dev, int64_t k,
         const int want = est >= 4.7e-10 * 1e5 ? 5 : est >= 7.3e-12 * 1e5 ? 6 : 7;
         planes = std::max(floor_planes, want);
       }
+      prev2 = prev;
       prev = ratio;
     }
     // After the first sweep no contraction is known yet: the iterate's error
