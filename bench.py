@@ -612,7 +612,8 @@ def serving_study(g, torch, nL=256, rates=(100, 300, 600, 1200), per_rate=300, s
     B with k log-uniform in [1, 2048] for a random resident L; continuous
     batching under an HBM budget.  The L with n >= mixed_min_n also carry a
     mixed-precision plan (split-fp16 updates), and half of the requests on
-    them ask for the refined mixed-precision solve (tol 1e-12) instead of
+    them ask for the refined mixed-precision solve (tol 1e-12; diagonal
+    multiplies as `mixed_s`: two tf32 planes on the tensor cores) instead of
     FP64.  The same L also carry the sliced schedule's digit planes, and an
     FP64 request of at least sliced_min_flops n^2 k flops is solved by the
     sliced schedule (FP64-class, on the tensor cores) instead of joining a
