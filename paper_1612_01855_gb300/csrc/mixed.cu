@@ -13,8 +13,9 @@
 //
 // inner_solve is the right-looking form of Algorithm It-Inv-TRSM: for every
 // block row i, D_i = L~_ii W_i with the inverse of the diagonal block (in
-// FP64 on the DFMA pipe, or, with TRSM_SOLVE_S_FP32, in FP32 from FP32
-// copies of the inverses kept in the plan), then
+// FP64 on the DFMA pipe; with TRSM_SOLVE_S_FP32 in FP32 from FP32 copies of
+// the inverses kept in the plan; with TRSM_SOLVE_S_TC, _TC2 or _TC1 on the
+// tensor cores from three, two or one tf32 planes per factor), then
 // W(T_{i+1}) -= L(T_{i+1}, S_i) D_i as one
 // tcgen05 GEMM with bf16, tf32, split bf16 or split fp16 (hi + lo planes,
 // three products) operands and FP32 accumulation; W is the FP32 working copy
