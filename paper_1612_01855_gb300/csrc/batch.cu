@@ -304,12 +304,14 @@ __device__ __forceinline__ void u_body(const BatchSys<T>& a, int l, int i, int r
 
 // ---------------------------------------------------------------- FP32
 // FP32 systems run as two launches with no dependency between CTAs inside
-// either.  First every diagonal block of every system is inverted, one CTA
-// per block (RecTriInv with one level, as the INV tasks), into a workspace.
-// Then one CTA per (system, chunk of cw columns) walks its system's block
-// rows in order: it forms W_l = B_l - L(S_l, 0:s0) X(0:s0, chunk) with a
+// either.  First every diagonal block of every system is inverted into a
+// workspace: blocks of order 64 one CTA each (RecTriInv with one level, as
+// the INV tasks), blocks of order 32 one warp each (inv32w_kernel).  Then
+// one CTA per (system, chunk of cw columns) walks its system's block rows
+// in order: it forms W_l = B_l - L(S_l, 0:s0) X(0:s0, chunk) with a
 // register-blocked FP32 product whose operands are staged through shared
-// memory, and writes X_l = L~_ll W_l.  In FP32 the ticketed tasks of the
+// memory, and writes X_l = L~_ll W_l (with n0 = 32, in 64-row steps of two
+// blocks: sys_unit_pair).  In FP32 the ticketed tasks of the
 // kernel above are short next to their dependency waits and global round
 // trips; here a unit is a whole system's chunk, and the units run longest
 // first.  Every output's sums run in a fixed order that depends neither on
