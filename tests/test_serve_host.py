@@ -138,3 +138,20 @@ def test_large_fp64_requests_route_to_the_sliced_schedule():
     off = Server(plans, budget_bytes=10**12, streams=4)     # routing off by default
     off.submit(Request(5, 0, _B(4096, 1000), 0.0))
     assert not off.queue_sliced and [r.rid for r in off.queue_fp64] == [5]
+
+
+def test_mixed_diagonal_multiply_modes():
+    """The mixed requests' diagonal multiply: two tf32 planes on the tensor
+    cores by default, any of the library's modes by name, and the same
+    keyword arguments for the served solve and for a solve alone."""
+    plans = [_Plan(64)]
+    assert Server(plans, budget_bytes=10**9).mixed_kwargs() == {"s_tc": True, "s_tc_planes": 2}
+    assert Server(plans, budget_bytes=10**9, mixed_s="fp32").mixed_kwargs() == {"s_fp32": True}
+    assert Server(plans, budget_bytes=10**9, mixed_s="fp64").mixed_kwargs() == {}
+    assert Server(plans, budget_bytes=10**9, mixed_s="tc").mixed_kwargs() == {"s_tc": True, "s_tc_planes": 3}
+    srv = Server(plans, budget_bytes=10**9)
+    kw = srv.mixed_kwargs()
+    kw["s_tc_planes"] = 1  # a copy: the server's own mode is unchanged
+    assert srv.mixed_kwargs()["s_tc_planes"] == 2
+    with pytest.raises(ValueError):
+        Server(plans, budget_bytes=10**9, mixed_s="tf32")
