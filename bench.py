@@ -936,13 +936,14 @@ def run_ours(args, rank, world, local):
         residual = residual_roofline(g, torch)
     if rank == 0 and not args.no_mixed and not args.shapes:
         # config 2 at c = 2, 4, 6 at the mixed path's block size: refined
-        # solves (split-fp16 updates with FP32 diagonal multiplies or
-        # tensor-core ones of two tf32 planes, tf32 updates with tensor-core
-        # ones of three; the adaptive residual, and eight planes throughout
+        # solves (split-fp16 updates with FP64, FP32 or two-tf32-plane
+        # tensor-core diagonal multiplies, tf32 updates with tensor-core ones
+        # of three planes; the adaptive residual, and eight planes throughout
         # for one of them), and the sliced schedule's direct FP64-class solve
         mixed = precision_study(g, torch, 16384, 4096, MIXED_N0, [2, 4, 6], None, None,
-                                combos=[("fp16x3", "fp32", "adaptive"), ("fp16x3", "tc2", "adaptive"),
-                                        ("fp16x3", "tc2", "sliced8"), ("tf32", "tc", "adaptive")],
+                                combos=[("fp16x3", "fp64", "adaptive"), ("fp16x3", "fp32", "adaptive"),
+                                        ("fp16x3", "tc2", "adaptive"), ("fp16x3", "tc2", "sliced8"),
+                                        ("tf32", "tc", "adaptive")],
                                 with_sliced=True)
 
     batched = None
