@@ -279,16 +279,28 @@ def precision_study(g, torch, n, k, n0, cs, inners, s_modes, dd_cols=4, stream=N
         # list, or every inner x s_mode x residual
         runs = combos or [(i, sm, r) for i in inners for sm in s_modes for r in residuals]
         cur = None
-        for inner, smode, res in runs:
-            if inner != cur:
-                g.trsm_plan_mixed(plan, Ld, inner)
-                cur = inner
+        extra = {}  # a plan at another block size, for combos that name one
+        for run in runs:
+            inner, smode, res = run[:3]
+            rn0 = run[3] if len(run) > 3 else n0
+            if rn0 != n0:
+                if (rn0, inner) not in extra:
+                    for p_ in extra.values():
+                        p_.destroy()
+                    extra = {(rn0, inner): g.trsm_plan(Ld, rn0)}
+                    g.trsm_plan_mixed(extra[(rn0, inner)], Ld, inner)
+                rplan = extra[(rn0, inner)]
+            else:
+                if inner != cur:
+                    g.trsm_plan_mixed(plan, Ld, inner)
+                    cur = inner
+                rplan = plan
             s32 = smode in (True, "fp32")
             tc_planes = {"tc": 3, "tc2": 2, "tc1": 1}.get(smode)
             stc = tc_planes is not None
             def solve(X=None):
                 try:
-                    X, it, upd = g.trsm_solve_mixed(plan, Bd, X=X, residual=res, max_iter=30, tol=tol,
+                    X, it, upd = g.trsm_solve_mixed(rplan, Bd, X=X, residual=res, max_iter=30, tol=tol,
                                                     raise_on_noconv=False, s_fp32=s32, s_tc=stc,
                                                     s_tc_planes=tc_planes or 3)
                     return X, it, upd, 0
@@ -304,12 +316,14 @@ def precision_study(g, torch, n, k, n0, cs, inners, s_modes, dd_cols=4, stream=N
             converged = bool(fe is not None and fe <= 1e-10)
             status = "ok" if converged else ("non-finite" if fe is None else "target missed")
             rec["mixed"].append({"inner": inner, "s_step": smode if stc else "fp32" if s32 else "fp64",
-                                 "residual": res, "ms": round(tm, 2),
+                                 "residual": res, "n0": rn0, "ms": round(tm, 2),
                                  "tflops_equiv": round(float(n) * n * k / (tm * 1e-3) / 1e12, 3),
                                  "iterations": it, "last_update": upd, "fwd_err": fe,
                                  "bwd_err": berr(X) if X is not None else None,
                                  "converged": converged, "status": status, "rc": rc,
                                  "speedup_vs_fp64": round(t64 / tm, 3)})
+        for p_ in extra.values():
+            p_.destroy()
         if with_sliced:
             # the sliced schedule: FP64-class products, one pass, no refinement,
             # on its own plan with 2048-row blocks (measured faster than 1024)
@@ -326,7 +340,8 @@ def precision_study(g, torch, n, k, n0, cs, inners, s_modes, dd_cols=4, stream=N
             splan.destroy()
             tm = e0.elapsed_time(e1)
             fe = ferr(X)
-            rec["mixed"].append({"inner": "sliced", "s_step": "sliced", "residual": None, "ms": round(tm, 2),
+            rec["mixed"].append({"inner": "sliced", "s_step": "sliced", "residual": None,
+                                 "n0": min(SLICED_PREC_N0, n), "ms": round(tm, 2),
                                  "tflops_equiv": round(float(n) * n * k / (tm * 1e-3) / 1e12, 3),
                                  "iterations": 1, "last_update": None, "fwd_err": fe, "bwd_err": berr(X),
                                  "converged": bool(fe is not None and fe <= 1e-10),
@@ -350,9 +365,11 @@ def compact_precision(recs):
     for rec in recs:
         for m in rec["mixed"]:
             st = "ok" if m["converged"] else ("nan" if m["fwd_err"] is None else "miss")
-            rows.append([rec["c"], m["inner"], m["s_step"], m["residual"], m["ms"], m["iterations"],
-                         _sig(m["fwd_err"]), _sig(m["bwd_err"]), None if st == "nan" else m["speedup_vs_fp64"], st])
-    return {"fp64": fp64, "cols": ["c", "inner", "s", "residual", "ms", "sweeps", "fwd", "bwd", "x_fp64", "status"],
+            rows.append([rec["c"], m["inner"], m["s_step"], m["residual"], m.get("n0", rec.get("n0")), m["ms"],
+                         m["iterations"], _sig(m["fwd_err"]), _sig(m["bwd_err"]),
+                         None if st == "nan" else m["speedup_vs_fp64"], st])
+    return {"fp64": fp64,
+            "cols": ["c", "inner", "s", "residual", "n0", "ms", "sweeps", "fwd", "bwd", "x_fp64", "status"],
             "rows": rows}
 
 
@@ -939,9 +956,12 @@ def run_ours(args, rank, world, local):
         # solves (split-fp16 updates with FP64, FP32 or two-tf32-plane
         # tensor-core diagonal multiplies, tf32 updates with tensor-core ones
         # of three planes; the adaptive residual, and eight planes throughout
-        # for one of them), and the sliced schedule's direct FP64-class solve
+        # for one of them), and the sliced schedule's direct FP64-class
+        # solve.  The FP64 multiply runs on its own plan with 256-row blocks
+        # (its DFMA work grows with n0: 120.7 ms at c = 2 against 236.6 at
+        # n0 = 1024)
         mixed = precision_study(g, torch, 16384, 4096, MIXED_N0, [2, 4, 6], None, None,
-                                combos=[("fp16x3", "fp64", "adaptive"), ("fp16x3", "fp32", "adaptive"),
+                                combos=[("fp16x3", "fp64", "adaptive", 256), ("fp16x3", "fp32", "adaptive"),
                                         ("fp16x3", "tc2", "adaptive"), ("fp16x3", "tc2", "sliced8"),
                                         ("tf32", "tc", "adaptive")],
                                 with_sliced=True)

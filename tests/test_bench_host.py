@@ -78,19 +78,20 @@ def test_compact_precision_records():
     """The bench line's precision block: FP64 figures per c, one row per
     (c, inner format, diagonal multiply, residual), and a status that tells a met target, a missed one
     and a non-finite result apart."""
-    recs = [{"c": 2, "fp64_solve_ms": 880.0, "fp64_fwd_err": 5.2e-16,
+    recs = [{"c": 2, "n0": 1024, "fp64_solve_ms": 880.0, "fp64_fwd_err": 5.2e-16,
              "mixed": [{"inner": "fp16x3", "s_step": "fp32", "residual": "adaptive", "ms": 70.1, "iterations": 3,
                         "fwd_err": 7.0e-13, "bwd_err": 5.4e-15, "speedup_vs_fp64": 12.6, "converged": True},
-                       {"inner": "tf32", "s_step": "tc", "residual": "adaptive", "ms": 95.0, "iterations": 5,
+                       {"inner": "tf32", "s_step": "tc", "residual": "adaptive", "n0": 256, "ms": 95.0, "iterations": 5,
                         "fwd_err": 3.4e-9, "bwd_err": 1e-15, "speedup_vs_fp64": 9.3, "converged": False}]},
-            {"c": 6, "fp64_solve_ms": 881.0, "fp64_fwd_err": None,
+            {"c": 6, "n0": 1024, "fp64_solve_ms": 881.0, "fp64_fwd_err": None,
              "mixed": [{"inner": "fp16x3", "s_step": "fp32", "residual": "sliced8", "ms": 5.0, "iterations": 1,
                         "fwd_err": None, "bwd_err": None, "speedup_vs_fp64": 176.2, "converged": False}]}]
     out = bench.compact_precision(recs)
     assert out["fp64"] == {"2": [880.0, 5.2e-16], "6": [881.0, None]}
     assert [r[-1] for r in out["rows"]] == ["ok", "miss", "nan"]
     assert out["rows"][2][-2] is None  # no speed-up is quoted for a non-finite result
-    assert out["rows"][0][:6] == [2, "fp16x3", "fp32", "adaptive", 70.1, 3]
+    assert out["rows"][0][:7] == [2, "fp16x3", "fp32", "adaptive", 1024, 70.1, 3]
+    assert out["rows"][1][4] == 256  # a combo on its own plan
     assert out["rows"][2][3] == "sliced8" and len(out["cols"]) == len(out["rows"][0])
 
 
