@@ -621,7 +621,7 @@ def sliced_study(g, torch, data, dev_in, outs, shapes, reps=3):
             **rows, "mma_peak": burst}
 
 
-def serving_study(g, torch, nL=256, rates=(100, 300, 600, 1200), per_rate=300, seed=2000,
+def serving_study(g, torch, nL=256, rates=(100, 300, 600, 1200, 2400), per_rate=300, seed=2000,
                   budget_gb=150.0, mixed_min_n=2048, sliced_min_flops=3e8, streams=8, mixed_s="tc2"):
     """Serving workload: nL resident L (n log-uniform in [64, 8192],
     diagonal U[2,3], strictly lower U[-1,1]/n, drawn on the device), each
